@@ -1,0 +1,184 @@
+"""Seeded synthetic inputs for VarDCT reconstruction.
+
+The draft measures on no dataset, so every workload here is synthetic. This
+module only draws numbers: it holds none of the reconstruction arithmetic,
+and both the CUDA library's tests/benchmark and the FP64 oracle take their
+inputs from it.
+
+Statistics (per image):
+
+* varblock tiling, per naturally aligned 32x32 cell in raster order:
+  DCT32 p=0.10; a pair of 32x16 (or 16x32) p=0.05; four 32x8 (or 8x32)
+  p=0.05; otherwise four 16x16 cells.  Per 16x16 cell: DCT16 p=0.1875, a
+  pair of 16x8 (or 8x16) p=0.0625, otherwise four 8x8 blocks: DCT8 2/3,
+  DCT4 1/6, DCT2 1/12, Identity 1/12.  Cells that do not fit inside the
+  padded image fall through to the smaller cells.  Expected area: DCT8 40%,
+  DCT16 15%, DCT32 10%, rectangles 15%, DCT4 10%, DCT2 5%, Identity 5%.
+* quantised coefficients: Laplace(0, 64 / (1 + u + v)) rounded to int16, where
+  (u, v) is the position in the varblock's coefficient matrix (the 8x8 matrix
+  for the 8x8-class shapes), the LLF slots included (zero-mean DC);
+* quant field (AcMul): log-uniform in [0.5, 4] per varblock, replicated to
+  all its 8x8 blocks;
+* chroma-from-luma factors kX, kB: uniform in [-0.5, 0.5] per 64x64 tile;
+* sharpness: uniform in {0..7} per 8x8 block.
+
+DctSelect codes (C.5.4 of the draft): 0 DCT8, 1 Identity, 2 DCT2, 3 DCT4,
+4 DCT16, 5 DCT32, 6 16x8 (16 tall), 7 8x16, 8 32x8 (32 tall), 9 8x32,
+10 32x16 (32 tall), 11 16x32, 12 4x8, 13 8x4, 14 AFV; 0xFF marks a block
+covered by a varblock that starts elsewhere.
+"""
+import math
+
+import numpy as np
+
+COVERED = 0xFF
+# (width, height) of each DctSelect code
+SHAPE_WH = {0: (8, 8), 1: (8, 8), 2: (8, 8), 3: (8, 8), 4: (16, 16),
+            5: (32, 32), 6: (8, 16), 7: (16, 8), 8: (8, 32), 9: (32, 8),
+            10: (16, 32), 11: (32, 16), 12: (8, 8), 13: (8, 8), 14: (8, 8)}
+
+
+def _place(vmap, code, bx, by):
+    w, h = SHAPE_WH[code]
+    vmap[by:by + h // 8, bx:bx + w // 8] = COVERED
+    vmap[by, bx] = code
+
+
+def tiling(bw, bh, rng, mix='mixed'):
+    """DctSelect map of bh x bw blocks.  mix: 'mixed' (statistics above),
+    'dct8' (all DCT8), or a single code (every block that code where it fits,
+    DCT8 elsewhere)."""
+    vmap = np.full((bh, bw), COVERED, dtype=np.uint8)
+    if mix == 'dct8':
+        vmap[:] = 0
+        return vmap
+    if isinstance(mix, int):
+        w, h = SHAPE_WH[mix]
+        cw, ch = w // 8, h // 8
+        for by in range(0, bh, ch):
+            for bx in range(0, bw, cw):
+                if by + ch <= bh and bx + cw <= bw:
+                    _place(vmap, mix, bx, by)
+                else:
+                    for yy in range(by, min(by + ch, bh)):
+                        for xx in range(bx, min(bx + cw, bw)):
+                            vmap[yy, xx] = 0
+        return vmap
+
+    def small(bx, by):
+        r = rng.random()
+        code = 0 if r < 2 / 3 else 3 if r < 2 / 3 + 1 / 6 else 2 if r < 11 / 12 else 1
+        vmap[by, bx] = code
+
+    def cell16(bx, by):
+        if bx + 2 <= bw and by + 2 <= bh:
+            r = rng.random()
+            if r < 0.1875:
+                _place(vmap, 4, bx, by)
+                return
+            if r < 0.25:
+                if rng.random() < 0.5:   # two 16-tall, 8-wide
+                    _place(vmap, 6, bx, by)
+                    _place(vmap, 6, bx + 1, by)
+                else:                    # two 8-tall, 16-wide
+                    _place(vmap, 7, bx, by)
+                    _place(vmap, 7, bx, by + 1)
+                return
+        for yy in range(by, min(by + 2, bh)):
+            for xx in range(bx, min(bx + 2, bw)):
+                small(xx, yy)
+
+    for cy in range(0, bh, 4):
+        for cx in range(0, bw, 4):
+            if cx + 4 <= bw and cy + 4 <= bh:
+                r = rng.random()
+                if r < 0.10:
+                    _place(vmap, 5, cx, cy)
+                    continue
+                if r < 0.15:
+                    if rng.random() < 0.5:   # 32 tall, 16 wide
+                        _place(vmap, 10, cx, cy)
+                        _place(vmap, 10, cx + 2, cy)
+                    else:
+                        _place(vmap, 11, cx, cy)
+                        _place(vmap, 11, cx, cy + 2)
+                    continue
+                if r < 0.20:
+                    if rng.random() < 0.5:   # 32 tall, 8 wide
+                        for k in range(4):
+                            _place(vmap, 8, cx + k, cy)
+                    else:
+                        for k in range(4):
+                            _place(vmap, 9, cx, cy + k)
+                    continue
+            for yy in range(cy, min(cy + 4, bh), 2):
+                for xx in range(cx, min(cx + 4, bw), 2):
+                    cell16(xx, yy)
+    return vmap
+
+
+def coefficient_positions(vmap):
+    """Per-sample (u, v) position inside the varblock's coefficient matrix,
+    with the 8x8 matrix of 8x8-class shapes."""
+    bh, bw = vmap.shape
+    ox = np.zeros((bh, bw), dtype=np.int64)
+    oy = np.zeros((bh, bw), dtype=np.int64)
+    tl = np.argwhere(vmap != COVERED)
+    for by, bx in tl:
+        w, h = SHAPE_WH[int(vmap[by, bx])]
+        ox[by:by + h // 8, bx:bx + w // 8] = bx
+        oy[by:by + h // 8, bx:bx + w // 8] = by
+    Hp, Wp = 8 * bh, 8 * bw
+    x0 = np.repeat(np.repeat(ox, 8, 0), 8, 1) * 8
+    y0 = np.repeat(np.repeat(oy, 8, 0), 8, 1) * 8
+    u = np.arange(Wp)[None, :] - x0
+    v = np.arange(Hp)[:, None] - y0
+    return u, v, ox, oy
+
+
+def make_image(xsize, ysize, seed, mix='mixed', acmul=None, cfl=True,
+               coef_scale=64.0, y_dc_offset_q=0):
+    """One synthetic image.  Returns a dict with xsize, ysize, coeffs
+    (int16, 3 x Hp x Wp), vmap (uint8, Hp/8 x Wp/8), acmul (float32, per
+    block), cfl (float32, ceil(Hp/64) x ceil(Wp/64) x 2), sharpness (uint8).
+    ``acmul`` None draws the log-uniform quant field, a number fixes it;
+    ``cfl`` False sets kX = kB = 0; ``y_dc_offset_q`` adds a constant to the
+    quantised DC of the Y channel."""
+    rng = np.random.default_rng(seed)
+    Wp, Hp = 8 * ((xsize + 7) // 8), 8 * ((ysize + 7) // 8)
+    bw, bh = Wp // 8, Hp // 8
+    vmap = tiling(bw, bh, rng, mix)
+    u, v, ox, oy = coefficient_positions(vmap)
+    scale = coef_scale / (1.0 + u + v)
+    lap = rng.laplace(0.0, 1.0, size=(3, Hp, Wp)) * scale[None]
+    coeffs = np.clip(np.rint(lap), -32768, 32767).astype(np.int16)
+    if y_dc_offset_q:
+        tl = np.argwhere(vmap != COVERED)
+        for by, bx in tl:
+            cw, ch = SHAPE_WH[int(vmap[by, bx])]
+            sl = coeffs[1, 8 * by:8 * by + ch // 8, 8 * bx:8 * bx + cw // 8]
+            sl[...] = np.clip(sl.astype(np.int64) + y_dc_offset_q, -32768, 32767)
+    if acmul is None:
+        per_vb = np.exp(rng.uniform(math.log(0.5), math.log(4.0), size=(bh, bw)))
+        am = per_vb[oy, ox].astype(np.float32)
+    else:
+        am = np.full((bh, bw), acmul, dtype=np.float32)
+    th, tw = (Hp + 63) // 64, (Wp + 63) // 64
+    if cfl:
+        cf = rng.uniform(-0.5, 0.5, size=(th, tw, 2)).astype(np.float32)
+    else:
+        cf = np.zeros((th, tw, 2), dtype=np.float32)
+    sharp = rng.integers(0, 8, size=(bh, bw)).astype(np.uint8)
+    return {'xsize': xsize, 'ysize': ysize, 'coeffs': coeffs, 'vmap': vmap,
+            'acmul': am, 'cfl': cf, 'sharpness': sharp}
+
+
+def shape_area_fractions(vmap):
+    """Fraction of the padded area covered by each DctSelect code."""
+    tot = {}
+    for by, bx in np.argwhere(vmap != COVERED):
+        c = int(vmap[by, bx])
+        w, h = SHAPE_WH[c]
+        tot[c] = tot.get(c, 0) + w * h
+    area = 64 * vmap.size
+    return {c: a / area for c, a in sorted(tot.items())}

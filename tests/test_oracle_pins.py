@@ -1,0 +1,378 @@
+"""Pins of the FP64 oracle against what the draft and mathematics fix.
+
+Each test names the passage it relies on. None of them re-derives a value
+with the oracle's own formula: they use closed forms, round trips through
+the draft's forward procedures (I.2.3), invariants the draft states
+(orthonormal AFV basis, weights summing to one, constants preserved), the
+draft's independent I.2.6 downsampling formula, and brute force.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import recon as R
+from oracle import tables as T
+from oracle import transforms as TR
+from paper_1908_03565_gb300 import synth
+
+RNG = np.random.default_rng(1234)
+DCT_SHAPES = [T.SHAPE_WH[c] for c in T.DCT_SHAPES]
+
+
+# --------------------------------------------------------------------------
+# I.2.1 / I.2.2 / Annex R: the inverse DCTs
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("W,H", DCT_SHAPES)
+def test_separable_idct_equals_cosine_sum_bruteforce(W, H):
+    """I.2.2 separable form == the O(N^4) cosine-sum definition (catches
+    transposed operands and swapped axes)."""
+    c = RNG.standard_normal((H, W))
+    np.testing.assert_allclose(TR.idct_2d(c), TR.idct_2d_bruteforce(c),
+                               rtol=0, atol=1e-11)
+
+
+@pytest.mark.parametrize("N", [2, 4, 8, 16, 32])
+def test_numerator_scaled_idct_is_orthonormal(N):
+    """I.2.6.1 defines I(N,u) as the DCT scaling factor used by the C.6.1
+    numerators; with it every 1-D inverse DCT becomes the orthonormal
+    DCT-III basis.  A wrong per-frequency scale S_N (I.2.1, Annex R) breaks
+    this for that frequency."""
+    B = TR.idct_matrix(N) * np.array([T.I(N, u) for u in range(N)])[None, :]
+    np.testing.assert_allclose(B.T @ B, np.eye(N), atol=1e-13)
+    # and the basis is the textbook one
+    ref = np.array([[math.sqrt((1 if u == 0 else 2) / N)
+                     * math.cos((2 * n + 1) * u * math.pi / (2 * N))
+                     for u in range(N)] for n in range(N)])
+    np.testing.assert_allclose(B, ref, atol=1e-13)
+
+
+@pytest.mark.parametrize("W,H", [(16, 16), (32, 32), (8, 16), (16, 8),
+                                 (8, 32), (32, 8), (16, 32), (32, 16)])
+def test_box_mean_matches_draft_downsampling(W, H):
+    """I.2.6.2 (ScaleF, then a small IDCT) yields the 8x downsampled image;
+    it must equal the exact mean of each 8x8 sub-block of the LLF-only
+    reconstruction.  Pins S_N of the large and the small transforms."""
+    cx, cy = W // 8, H // 8
+    llf = RNG.standard_normal((cy, cx))
+    coef = np.zeros((H, W))
+    coef[:cy, :cx] = llf
+    pix = TR.idct_2d(coef)
+    means = pix.reshape(cy, 8, cx, 8).mean(axis=(1, 3))
+    np.testing.assert_allclose(TR.downsample_scalef(coef), means, atol=1e-12)
+    # and llf_from_dc inverts it
+    np.testing.assert_allclose(TR.llf_from_dc(means), llf, atol=1e-11)
+
+
+@pytest.mark.parametrize("W,H", [(16, 16), (32, 32), (8, 16), (32, 16)])
+def test_printed_llf_formula_is_blockcount_times_inverse(W, H):
+    """I.2.7.2 as printed (DCT of the DC block, times ScaleF) differs from
+    the exact inverse of I.2.6.2 by the number of 8x8 sub-blocks; the oracle
+    uses the exact inverse (I.2.7.1 calls the step the inverse of I.2.6)."""
+    cx, cy = W // 8, H // 8
+    dc = RNG.standard_normal((cy, cx))
+    Cm = TR.dct_2d(dc)
+    printed = np.array([[Cm[y, x] * T.ScaleF(cy, H, y) * T.ScaleF(cx, W, x)
+                         for x in range(cx)] for y in range(cy)])
+    np.testing.assert_allclose(printed, cx * cy * TR.llf_from_dc(dc), atol=1e-11)
+
+
+# --------------------------------------------------------------------------
+# I.2.3 / I.2.4: the 8x8-class procedures, through their forward partners
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("S", [2, 4, 8])
+def test_aux_2x2_round_trip(S):
+    b = RNG.standard_normal((8, 8))
+    np.testing.assert_allclose(TR.aux_idct2x2(TR.aux_dct2x2(b, S), S), b, atol=1e-14)
+
+
+@pytest.mark.parametrize("fwd,inv", [
+    (TR.dct_dct2, TR.idct_dct2), (TR.dct_dct4, TR.idct_dct4),
+    (TR.dct_identity, TR.idct_identity), (TR.dct_dct8x4, TR.idct_dct8x4),
+    (TR.dct_dct4x8, TR.idct_dct4x8), (TR.dct_afv, TR.idct_afv)])
+def test_8x8_class_round_trip(fwd, inv):
+    """I.2.3.x forward procedure then I.2.4.x inverse returns the samples.
+    For 4x8 this pins the dcs[y] reading of I.2.4.6."""
+    s = RNG.standard_normal((8, 8))
+    np.testing.assert_allclose(inv(fwd(s)), s, atol=1e-12)
+
+
+def test_identity_round_trip_exact_on_integers():
+    s = RNG.integers(-100, 100, (8, 8)).astype(np.float64) * 16
+    np.testing.assert_array_equal(TR.idct_identity(TR.dct_identity(s)), s)
+
+
+def test_afv_basis_orthonormal():
+    """I.2.2 calls the AFV basis orthonormal; this pins the repair of the
+    two rows printed with 17 entries."""
+    B = T.AFV_BASIS
+    assert B.shape == (16, 16)
+    np.testing.assert_allclose(B @ B.T, np.eye(16), atol=1e-13)
+
+
+@pytest.mark.parametrize("code", sorted(T.SHAPE_WH))
+def test_dc_only_varblock(code):
+    """A varblock with only DC samples (I.2.6/I.2.7 are each other's
+    inverse): every 8x8 sub-block of the result averages to its DC sample,
+    and equal DC samples give a constant varblock."""
+    W, H = T.SHAPE_WH[code]
+    vmap = np.full((H // 8, W // 8), T.COVERED, np.uint8)
+    vmap[0, 0] = code
+    p = R.Params(m_dc=(0.01, 0.002, 0.003))
+    ones = np.ones((H // 8, W // 8), np.float32)
+    nocfl = np.zeros((1, 1, 2), np.float32)
+    coeffs = np.zeros((3, H, W), np.int16)
+    q = RNG.integers(-300, 300, (3, H // 8, W // 8))
+    coeffs[:, :H // 8, :W // 8] = q
+    xyb = R.reconstruct_xyb(coeffs, vmap, ones, nocfl, p)
+    for c in range(3):
+        means = xyb[c].reshape(H // 8, 8, W // 8, 8).mean(axis=(1, 3))
+        np.testing.assert_allclose(means, p.m_dc[c] * q[c], atol=1e-13)
+    coeffs[:, :H // 8, :W // 8] = q[:, :1, :1]
+    xyb = R.reconstruct_xyb(coeffs, vmap, ones, nocfl, p)
+    for c in range(3):
+        np.testing.assert_allclose(xyb[c], p.m_dc[c] * q[c, 0, 0], atol=1e-13)
+
+
+def test_batched_inverse_equals_step_by_step():
+    """The per-shape batched evaluation equals the one-varblock-at-a-time
+    procedures of I.2.4 on a mixed tiling."""
+    im = synth.make_image(96, 64, 7)
+    # make every 8x8-class code appear
+    codes = [12, 13, 14, 1, 2, 3]
+    for i, c in enumerate(codes):
+        im['vmap'][7, i] = c
+    dq = R.dequantize(im['coeffs'], im['vmap'], im['acmul'], im['cfl'], R.Params())
+    np.testing.assert_allclose(R.inverse_transform(dq, im['vmap']),
+                               R.inverse_transform_literal(dq, im['vmap']),
+                               atol=1e-12)
+
+
+# --------------------------------------------------------------------------
+# C.6.1: dequantisation matrices
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("code", sorted(T.SHAPE_WH))
+def test_default_matrices_positive_finite(code):
+    """C.6.1: a non-positive or infinite entry makes the codestream
+    ill-formed, so every default matrix must be positive and finite."""
+    W, H = T.SHAPE_WH[code]
+    for c in range(3):
+        m = T.dequant_matrix(code, c)
+        assert m.shape == (H, W)
+        ac = np.ones((H, W), bool)
+        ac[:H // 8, :W // 8] = False      # LLF slots take no matrix entry
+        assert np.all(np.isfinite(m[ac])) and np.all(m[ac] > 0)
+
+
+@pytest.mark.parametrize("a,b", [(6, 7), (8, 9), (10, 11), (12, 13)])
+def test_transposed_shapes_have_transposed_matrices(a, b):
+    """Both orientations share one default encoding (C.6.1.1), and the
+    weights depend only on (x/X, y/Y); so the matrices are transposes."""
+    for c in range(3):
+        np.testing.assert_allclose(T.dequant_matrix(a, c), T.dequant_matrix(b, c).T,
+                                   rtol=1e-14)
+
+
+def test_dct8_weight_closed_forms():
+    """DCT8 channel X: with eccentricity bands all 0 the eccentricity factor
+    is 1, and the first two distance bands are 5 and 5 * 1/(1-0) = 5, so the
+    weight is 5 wherever the distance lies in the first band interval
+    (distance < sqrt(2)/5)."""
+    num = T.I(8, 1) * T.I(8, 0) / 64.0
+    assert T.dequant_matrix(0, 0)[0, 1] == pytest.approx(num / 5.0, rel=1e-14)
+    assert T.dequant_matrix(0, 0)[1, 1] == pytest.approx(T.I(8, 1) ** 2 / 64.0 / 5.0,
+                                                         rel=1e-14)
+
+
+def test_dct2_identity_matrices_are_reciprocal_parameters():
+    """Modes DCT2 and Identity have numerators 1, so the matrix holds
+    1/parameter at the positions C.6.1 lists."""
+    m = T.dequant_matrix(2, 1)
+    assert m[0, 1] == 1 / 960.0 and m[1, 1] == 1 / 640.0
+    assert m[0, 3] == 1 / 320.0 and m[3, 0] == 1 / 320.0 and m[3, 3] == 1 / 180.0
+    assert m[1, 6] == 1 / 140.0 and m[7, 7] == 1 / 120.0
+    m = T.dequant_matrix(1, 2)
+    assert m[0, 1] == 1 / 23.982311358829531 and m[1, 1] == 1 / 11.201853748207084
+    assert m[5, 5] == 1 / 9.2887405354132238
+
+
+# --------------------------------------------------------------------------
+# F.3 / G: dequantisation and chroma from luma
+# --------------------------------------------------------------------------
+def test_ac_bias_and_cfl():
+    """F.3 bias (|q|<=1 scaled, else q - 0.145/q), AcMul and matrix factors,
+    and G's X += kX Y, B += kB Y on AC coefficients."""
+    vmap = np.zeros((1, 1), np.uint8)
+    coeffs = np.zeros((3, 8, 8), np.int16)
+    coeffs[:, 0, 1] = (1, -7, 3)
+    coeffs[:, 2, 0] = (0, 1, -1)
+    acm = np.full((1, 1), 2.5, np.float32)
+    cfl = np.array([[[0.25, -0.375]]], np.float32)
+    dq = R.dequantize(coeffs, vmap, acm, cfl, R.Params())
+    m = [T.dequant_matrix(0, c) for c in range(3)]
+    y01 = (-7 - 0.145 / -7) * 2.5 * m[1][0, 1]
+    assert dq[1, 0, 1] == pytest.approx(y01, rel=1e-14)
+    assert dq[0, 0, 1] == pytest.approx((1 - T.K_ONE_BIAS[0]) * 2.5 * m[0][0, 1]
+                                        + 0.25 * y01, rel=1e-14)
+    assert dq[2, 0, 1] == pytest.approx((3 - 0.145 / 3) * 2.5 * m[2][0, 1]
+                                        - 0.375 * y01, rel=1e-14)
+    y20 = (1 - T.K_ONE_BIAS[1]) * 2.5 * m[1][2, 0]
+    assert dq[0, 2, 0] == pytest.approx(0.25 * y20, rel=1e-14)
+    assert dq[2, 2, 0] == pytest.approx(-(1 - T.K_ONE_BIAS[2]) * 2.5 * m[2][2, 0]
+                                        - 0.375 * y20, rel=1e-14)
+
+
+def test_cfl_zero_is_identity_and_dc_cfl():
+    im = synth.make_image(64, 64, 3, cfl=False)
+    p0 = R.Params()
+    a = R.dequantize(im['coeffs'], im['vmap'], im['acmul'], im['cfl'], p0)
+    p1 = R.Params(kx_dc=0.5, kb_dc=-0.25)
+    b = R.dequantize(im['coeffs'], im['vmap'], im['acmul'], im['cfl'], p1)
+    np.testing.assert_array_equal(a[1], b[1])
+    # DC CfL enters through the (linear) LLF map: X_b - X_a == 0.5 * Y
+    xa = R.inverse_transform(a, im['vmap'])
+    xb = R.inverse_transform(b, im['vmap'])
+    # only the LLF part differs, and it differs by kX_dc * (LLF-only Y)
+    ll = np.zeros_like(a)
+    for c_, bx, by in R.varblocks(im['vmap']):
+        W, H = T.SHAPE_WH[c_]
+        ll[1, 8 * by:8 * by + H // 8, 8 * bx:8 * bx + W // 8] = \
+            a[1, 8 * by:8 * by + H // 8, 8 * bx:8 * bx + W // 8]
+    yl = R.inverse_transform(ll, im['vmap'])[1]
+    np.testing.assert_allclose(xb[0] - xa[0], 0.5 * yl, atol=1e-12)
+    np.testing.assert_allclose(xb[2] - xa[2], -0.25 * yl, atol=1e-12)
+
+
+# --------------------------------------------------------------------------
+# J.2: edge-preserving filter
+# --------------------------------------------------------------------------
+def test_mul_table_closed_form():
+    """Weight(s, mul) > 0.5 iff floor(64 s mul / 65536) >= -127, i.e.
+    mul >= ceil(-127 * 1024 / s); with the search of J.2.4 starting at
+    -32768 and sad = sigma >> 2, mul_table[sigma] is that bound on the
+    grid, interpolated linearly in between (kSigmaShift = 2)."""
+    t4 = R.mul_table4()
+    for sigma in range(16, 673, 4):
+        s = sigma >> 2
+        bound = max(-32768, -((127 * 1024) // s))   # ceil of a negative
+        assert t4[sigma] == 4 * bound, sigma
+    assert t4[16] == 4 * -32512
+    for sigma in range(16, 672, 4):
+        for i in range(1, 4):
+            assert 4 * t4[sigma + i] == 4 * t4[sigma] + i * (t4[sigma + 4] - t4[sigma])
+    assert np.all(np.diff(t4[16:]) >= 0)
+
+
+def test_weight_properties():
+    """Weight(0, mul) is exactly 1 (sad 27 of J.2.3 is the reference); the
+    weight never increases with sad; it halves when sad * mul / 1024 drops
+    by 128 (one binary32 exponent step)."""
+    for m4 in (-131072, -80000, -4, 0):
+        assert R.weight(0, m4) == 1.0
+    sad = np.arange(0, 600)
+    for m4 in (-131072, -50000, -1000):
+        w = R.weight(sad, m4)
+        assert np.all(np.diff(w) <= 0)
+    # sad 4, mul -32768: high16 = -128 + 16256 -> exactly 0.5
+    assert R.weight(4, -4 * 32768) == 0.5
+    assert R.weight(8, -4 * 32768) == 0.25
+
+
+def test_mirror_rule():
+    """6.5 mirroring: -1 -> 0, size -> size-1, repeated for far coordinates."""
+    assert list(R.mirror(np.array([-1, -2, 5, 6, 7, 12]), 5)) == [0, 1, 4, 3, 2, 2]
+    assert list(R.mirror(np.array([-3, 3, 4]), 2)) == [1, 0, 0]
+
+
+def _constant_inputs(xs, ys, val=(0.01, 0.4, 0.3)):
+    img = np.stack([np.full((ys, xs), v) for v in val])
+    vmap = synth.tiling((xs + 7) // 8, (ys + 7) // 8, np.random.default_rng(0))
+    acm = np.ones(vmap.shape, np.float32)
+    sharp = np.full(vmap.shape, 7, np.uint8)
+    return img, vmap, acm, sharp
+
+
+def test_epf_preserves_constant_and_gaborish_sums_to_one():
+    img, vmap, acm, sharp = _constant_inputs(40, 24)
+    p = R.Params(epf=True, gab=True)
+    np.testing.assert_allclose(R.epf(img, vmap, acm, sharp, p), img, atol=1e-15)
+    np.testing.assert_allclose(R.gaborish(img, p), img, atol=1e-15)
+    delta = np.zeros((3, 9, 9))
+    delta[:, 4, 4] = 1.0
+    g = R.gaborish(delta, p)
+    np.testing.assert_allclose(g.sum(axis=(1, 2)), 1.0, atol=1e-15)
+    w1, w2 = T.GAB_W1[0], T.GAB_W2[0]
+    n = 1 + 4 * w1 + 4 * w2
+    assert g[0, 4, 4] == pytest.approx(1 / n) and g[0, 3, 4] == pytest.approx(w1 / n)
+    assert g[0, 3, 3] == pytest.approx(w2 / n)
+
+
+def test_epf_zero_sad_is_56_tap_mean():
+    """With a guide that is constant (every scaled value clamps to 0) all
+    SADs are 0, all weights 1, and J.2.5 is the plain mean of the 7x8
+    window (mirrored at the borders)."""
+    ys, xs = 20, 24
+    rng = np.random.default_rng(5)
+    img = np.stack([rng.uniform(-0.2, -0.1, (ys, xs)),      # X < -0.03: scaled < 0
+                    rng.uniform(-0.5, -0.01, (ys, xs)),
+                    rng.uniform(-0.5, -0.01, (ys, xs))])
+    vmap = np.zeros(((ys + 7) // 8, (xs + 7) // 8), np.uint8)
+    acm = np.full(vmap.shape, 0.5, np.float32)
+    sharp = np.full(vmap.shape, 7, np.uint8)
+    p = R.Params(epf=True)
+    # ranges are from the unclamped scaled values, so sigma >= 16 here
+    assert R.epf_sigma(img, vmap, acm, sharp, p).min() >= 16
+    out = R.epf(img, vmap, acm, sharp, p)
+    want = np.zeros_like(img)
+    for y in range(ys):
+        for x in range(xs):
+            for cy in range(-3, 4):
+                for cx in range(-3, 5):
+                    want[:, y, x] += img[:, R.mirror(y + cy, ys), R.mirror(x + cx, xs)]
+    np.testing.assert_allclose(out, want / 56.0, atol=1e-14)
+
+
+def test_epf_sigma_rule():
+    """J.2.4: sigma = trunc(min(min(range,70)*12.6*lut, 20/AcMul, 170)),
+    range = max over the varblock of the per-block channel-max range."""
+    ys, xs = 16, 16
+    img = np.zeros((3, ys, xs))
+    img[1, 3, 3] = 0.05       # Y block (0,0): scaled range 0.05*111.965157
+    vmap = np.full((2, 2), T.COVERED, np.uint8)
+    vmap[0, 0] = T.DCT16
+    acm = np.full((2, 2), 1.0, np.float32)
+    sharp = np.array([[7, 3], [0, 7]], np.uint8)
+    p = R.Params(epf=True)
+    s = R.epf_sigma(img, vmap, acm, sharp, p)
+    rng_ = np.float32(np.float32(0.05) * np.float32(111.965157))
+    for (by, bx), sh in np.ndenumerate(sharp):
+        want = min(min(float(rng_), 70.0) * 12.6 * sh / 7.0, 20.0, 170.0)
+        assert s[by, bx] == math.trunc(want)
+    assert s[1, 0] == 0   # sharpness 0: unfiltered
+
+
+# --------------------------------------------------------------------------
+# L.2 colour and the output encodings
+# --------------------------------------------------------------------------
+def test_xyb_round_trip_through_opsin_inverse():
+    """L.2 applies the inverse opsin matrix; inverting that matrix and the
+    cube by hand from linear RGB and going back must return the RGB."""
+    p = R.Params()
+    rgb = np.random.default_rng(2).uniform(0.0, 1.0, (5, 7, 3))
+    M = np.array(p.inv_opsin).reshape(3, 3)
+    div = p.target_nits_div50 * 50 / 250
+    mix = np.einsum('ij,hwj->hwi', np.linalg.inv(M), rgb * 255.0 * div)
+    gam = np.cbrt(mix - np.array(p.opsin_bias))
+    X = (gam[..., 0] - gam[..., 1]) / 2
+    Y = (gam[..., 0] + gam[..., 1]) / 2
+    B = gam[..., 2]
+    back = R.xyb_to_linear01(np.stack([X, Y, B]), p)
+    np.testing.assert_allclose(back, rgb, atol=1e-12)
+
+
+def test_srgb_encoding_values():
+    """IEC 61966-2-1: 0 -> 0, 1 -> 255, 0.5 -> 0.7354 -> 188, linear segment
+    below 0.0031308 (slope 12.92)."""
+    v = R.srgb_u8(np.array([0.0, 1.0, 0.5, 0.002, -1.0, 2.0]))
+    assert list(v) == [0, 255, 188, 7, 0, 255]
+
