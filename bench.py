@@ -1,0 +1,285 @@
+"""Benchmark of VarDCT pixel reconstruction on GB300.
+
+One step = one 4096x4096 image through the whole path (dequantisation, CfL,
+LLF, all inverse transforms, EPF, Gaborish, XYB -> linear RGB f32) with the
+mixed-varblock statistics of the workload description (synthetic inputs;
+the draft has no dataset).  Metric: Mpx/s, whole job over all ranks.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs under torchrun: each rank decodes its own image (weak scaling,
+no collective on the data path); the time is the max over ranks.
+--impl reference times the FP64 CPU oracle on a bounded sample of the same
+workload on the host cores (the only reference this method has).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+XS = YS = 4096
+SEED = 2000
+# algorithmic bytes per pixel (inputs: 3 int16 coefficients + side maps:
+# varblock map 1/64, quant field 4/64, sharpness 1/64, CfL 8/4096; output:
+# 3 float32)
+IN_BPP = 6.0 + 1 / 64 + 4 / 64 + 1 / 64 + 8 / 4096
+OUT_BPP = 12.0
+# algorithmic lane operations per pixel of the filter+colour kernel (EPF with
+# separable 3x4 patch sums on packed guide bytes, J.2.4 weight, J.2.5
+# accumulation, guide, Gaborish, colour); derivation in the design doc
+FILTER_OPS_PER_PX = 56 * 14 + 4 + 17 + 27 + 20
+CPU_SAMPLE = 640          # oracle sample: one 640x640 image, same statistics
+
+
+def env_int(k, d):
+    try:
+        return int(os.environ.get(k, d))
+    except ValueError:
+        return d
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def clocks_start():
+    try:
+        p = subprocess.Popen(
+            ["nvidia-smi", "-i", str(env_int("LOCAL_RANK", 0)),
+             "--query-gpu=clocks.sm,clocks.max.sm,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+             "--format=csv,noheader,nounits", "-lms", "200"],
+            stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+    except OSError:
+        return None
+    return p
+
+
+def clocks_stop(p):
+    if p is None:
+        return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+    p.terminate()
+    try:
+        out, _ = p.communicate(timeout=5)
+    except subprocess.TimeoutExpired:
+        p.kill()
+        out, _ = p.communicate()
+    sm, mx, reasons = [], [], set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for line in out.strip().splitlines():
+        f = [x.strip() for x in line.split(",")]
+        if len(f) < 7:
+            continue
+        try:
+            sm.append(float(f[0]))
+            mx.append(float(f[1]))
+        except ValueError:
+            continue
+        for n, v in zip(names, f[3:7]):
+            if v.lower().startswith("active"):
+                reasons.add(n)
+    return {"sm_mhz": statistics.median(sm) if sm else None,
+            "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+            "samples": len(sm)}
+
+
+def cpu_baseline_run(steps=1):
+    """Times the FP64 oracle on a bounded sample of the workload."""
+    from oracle import recon as R
+    from paper_1908_03565_gb300 import synth
+    img = synth.make_image(CPU_SAMPLE, CPU_SAMPLE, SEED)
+    p = R.Params(epf=True, gab=True)
+    times = []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        R.reconstruct(img, p)
+        times.append(time.perf_counter() - t0)
+    t = statistics.median(times)
+    px = CPU_SAMPLE * CPU_SAMPLE
+    return {"value": px / t / 1e6, "unit": "Mpx/s", "cores": 1, "kind": "oracle",
+            "sample": f"one {CPU_SAMPLE}x{CPU_SAMPLE} image, mixed varblocks, EPF+Gaborish, "
+                      f"FP64 numpy oracle, single process ({px} px in {t:.1f} s)"}
+
+
+def run_reference(args):
+    rank = env_int("RANK", 0)
+    if rank != 0:
+        return 0
+    cb = cpu_baseline_run(steps=max(1, min(args.steps, 3)))
+    line = {"impl": "reference", "metric": "recon Mpx/s at 4096^2", "value": cb["value"],
+            "unit": "Mpx/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": CPU_SAMPLE * CPU_SAMPLE / cb["value"] / 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "4096x4096 mixed varblocks, EPF+Gaborish, f32 linear RGB "
+                                   f"(oracle on a {CPU_SAMPLE}x{CPU_SAMPLE} sample)"},
+            "cpu_baseline": cb,
+            "e2e": {"value": cb["value"], "unit": "Mpx/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    from paper_1908_03565_gb300 import binding, synth
+
+    world = env_int("WORLD_SIZE", 1)
+    rank = env_int("RANK", 0)
+    local = env_int("LOCAL_RANK", 0)
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    peaks, peak_kind = load_peaks()
+    img = synth.make_image(XS, YS, SEED + rank)
+    dimg = binding.to_device(img, torch)
+    out = torch.empty((YS, XS, 3), dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    ctx = binding.Context(device=local, max_slots=2, timing=True, stream=stream.cuda_stream)
+    params = binding.filter_defaults(epf=1, gab=1)
+
+    def step(dev=True, host=None):
+        if dev:
+            return ctx.submit(dimg, params, out, binding.OUT_F32_LINEAR, on_device=True)
+        return ctx.submit(host[0], params, host[1], binding.OUT_F32_LINEAR,
+                          on_device=False, out_on_device=False)
+
+    def run_steps(n, dev=True, host=None):
+        tickets, prev = [], None
+        for _ in range(n):
+            t = step(dev, host)
+            if prev is not None:
+                ctx.poll(prev)
+            tickets.append(t)
+            prev = t
+        if prev is not None:
+            ctx.poll(prev)
+        return tickets
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(v):
+        if dist is None:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    # ---- device-resident timing -----------------------------------------
+    run_steps(max(3, args.warmup))
+    barrier()
+    clk = clocks_start()
+    l0 = ctx.launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    tickets = run_steps(args.steps)
+    e1.record(stream)
+    barrier()
+    clocks = clocks_stop(clk)
+    launches = ctx.launch_count() - l0
+    ms = max_over_ranks(e0.elapsed_time(e1)) / args.steps
+    stage = np.array([ctx.stage_ms(t) for t in tickets])   # validate, recon, filter, copies
+    recon_ms, filter_ms = float(stage[:, 1].mean()), float(stage[:, 2].mean())
+
+    px = XS * YS
+    value = world * px / (ms * 1e-3) / 1e6
+    hbm_peak = peaks["hbm_gbs"]
+    sm_count = torch.cuda.get_device_properties(local).multi_processor_count
+    sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+    alu_peak = sm_count * 128 * sm_mhz * 1e6 / 1e12      # T lane-ops/s
+    dominant = "k_filter" if filter_ms >= recon_ms else "k_recon"
+    achieved_alu = FILTER_OPS_PER_PX * px / (filter_ms * 1e-3) / 1e12
+    recon_gbs = px * (IN_BPP + 12.0 + 4 / 64) / (recon_ms * 1e-3) / 1e9  # reads coefs, writes XYB
+    roof = {"kernel": "k_filter (EPF + Gaborish + colour)", "bound": "alu",
+            "achieved": round(achieved_alu, 3), "peak": round(alu_peak, 3),
+            "unit": "Tops/s", "frac": round(achieved_alu / alu_peak, 4), "traffic": None,
+            "peak_source": f"{sm_count} SMs x 128 lanes x {sm_mhz:.0f} MHz",
+            "ms_per_launch": round(filter_ms, 4)}
+    step_hbm_frac = (px * (IN_BPP + OUT_BPP) / (ms * 1e-3) / 1e9) / hbm_peak
+
+    # ---- end to end through the public API with host buffers -------------
+    e2e = None
+    if rank == 0 or world > 1:
+        himg = dict(img)
+        pinned = {}
+        for k in ("coeffs", "vmap", "acmul", "cfl", "sharpness"):
+            t = torch.from_numpy(np.ascontiguousarray(img[k])).pin_memory()
+            pinned[k] = t
+            himg[k] = t.numpy()
+        hout_t = torch.empty((YS, XS, 3), dtype=torch.float32).pin_memory()
+        hout = hout_t.numpy()
+        run_steps(3, dev=False, host=(himg, hout))
+        barrier()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        n_e2e = max(3, min(args.steps, 10))
+        run_steps(n_e2e, dev=False, host=(himg, hout))
+        f1.record(stream)
+        barrier()
+        ems = max_over_ranks(f0.elapsed_time(f1)) / n_e2e
+        h2d = sum(img[k].nbytes for k in ("coeffs", "vmap", "acmul", "cfl", "sharpness"))
+        e2e = {"value": round(world * px / (ems * 1e-3) / 1e6, 1), "unit": "Mpx/s",
+               "ms_per_step": round(ems, 4), "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(hout.nbytes)}
+
+    if rank == 0:
+        cb = None
+        if world == 1 and not args.no_cpu_baseline:
+            cb = cpu_baseline_run()
+        line = {
+            "metric": "recon Mpx/s at 4096^2", "value": round(value, 1), "unit": "Mpx/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "4096x4096 mixed varblocks (config-1 statistics), "
+                                   "EPF+Gaborish, f32 linear RGB out",
+                       "global_batch": world, "image": f"{XS}x{YS}",
+                       "l2": "inputs larger than L2 (100.7 MB coefficients, 201 MB output)",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": roof,
+            "hbm_roofline_frac_step": round(step_hbm_frac, 4),
+            "stage_ms": {"recon": round(recon_ms, 4), "filter": round(filter_ms, 4),
+                         "recon_gbs": round(recon_gbs, 1)},
+            "peaks": peak_kind,
+            "clocks": clocks, "e2e": e2e, "gpu_launches": int(launches),
+            "cpu_baseline": cb,
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

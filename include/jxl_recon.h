@@ -1,0 +1,212 @@
+/*
+ * jxl_recon.h - C ABI of the GB300 VarDCT pixel-reconstruction library.
+ *
+ * The library turns already entropy-decoded VarDCT data of the JPEG XL
+ * committee draft (ISO/IEC 18181 CD, 2019) into pixels on one GPU:
+ *
+ *   F.2  DC dequantisation            dc = m_DC[c] * q
+ *   F.3  AC dequantisation            bias, * AcMul, * dequant matrix (C.6.1)
+ *   G    chroma from luma             X += kX * Y, B += kB * Y
+ *   I.2.7 LLF from DC, I.2.4 inverse transforms of all 15 varblock shapes
+ *   J.2  edge-preserving filter       (optional, C.10 `epf`)
+ *   J.4  Gaborish                     (optional, C.10 `gab`)
+ *   L.2  XYB -> linear RGB            then f32 / f16 linear or 8-bit sRGB
+ *
+ * Entropy decoding and codestream parsing are the caller's: the inputs are
+ * the decoded fields of C.5.3-C.5.6 and C.8 as plain arrays.
+ *
+ * Conventions for every call:
+ *  - Pointers are plain host or device addresses; sizes are element counts
+ *    unless named *_bytes.  No call takes or returns framework objects.
+ *  - The caller owns every buffer it passes.  Inputs and outputs, host or
+ *    device, must stay valid and unmodified until jxl_recon_poll() for that
+ *    ticket returns something other than JXLR_EAGAIN / JXLR_ETIMEDOUT (host
+ *    buffers are copied asynchronously on the request's stream).
+ *  - A negative jxlr_status is an error; jxl_recon_last_error() then holds
+ *    a message for the calling thread.
+ *  - Thread safety: one context may be driven by one submitting thread and
+ *    one polling thread at the same time.
+ */
+#ifndef JXL_RECON_H_
+#define JXL_RECON_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct jxl_recon_ctx jxl_recon_ctx;
+
+typedef enum {
+  JXLR_OK = 0,
+  JXLR_EAGAIN = 1,         /* poll: the request has not finished yet          */
+  JXLR_EINVAL = -1,        /* ill-formed input: varblock map not a tiling
+                              (C.5.4), non-positive/infinite matrix (C.6.1),
+                              bad sizes, strides or flags                     */
+  JXLR_ENOMEM = -2,        /* the request alone exceeds the HBM cap, or a
+                              device allocation failed                         */
+  JXLR_EBUSY = -3,         /* admission refused for now (no free slot or not
+                              enough free HBM under the cap): retry later     */
+  JXLR_ECUDA = -4,         /* a CUDA runtime call failed                      */
+  JXLR_ETIMEDOUT = -5,     /* poll: the timeout expired (request still runs)  */
+  JXLR_ECANCELLED = -6     /* request dropped by jxl_recon_destroy()          */
+} jxlr_status;
+
+/* Output sample encodings.  All are interleaved [ysize][xsize][3] with the
+ * caller's row stride.  Linear outputs are L.2's RGB divided by 255 (so the
+ * nominal range is [0, 1]; samples outside it are kept).  U8_SRGB applies
+ * the IEC 61966-2-1 transfer curve to clamp(linear, 0, 1) and rounds half
+ * up.  F32_XYB returns the X, Y, B samples unchanged (L.2, colour_space ==
+ * kXYB), after the enabled loop filters. */
+typedef enum {
+  JXLR_OUT_F32_LINEAR = 0,
+  JXLR_OUT_F16_LINEAR = 1,
+  JXLR_OUT_U8_SRGB = 2,
+  JXLR_OUT_F32_XYB = 3
+} jxlr_out_dtype;
+
+typedef enum {
+  JXLR_PREC_FP32 = 0       /* every stage on FP32 CUDA cores */
+} jxlr_precision;
+
+typedef struct {
+  int device;              /* CUDA device ordinal                             */
+  size_t hbm_cap_bytes;    /* device bytes the context may hold for request
+                              scratch and staged inputs; 0 = no cap           */
+  int max_slots;           /* requests in flight at once (>= 1); each slot
+                              owns one CUDA stream and its scratch arena      */
+  int precision;           /* a jxlr_precision                                */
+  int timing;              /* 1: record CUDA events around every kernel so
+                              jxl_recon_stage_ms() can report them            */
+  void* cuda_stream;       /* NULL: one library stream per slot; else a
+                              cudaStream_t of the caller that every slot
+                              enqueues on (requests then run in order)        */
+} jxl_recon_config;
+
+/* Quantised coefficients (C.8), one int16 plane per channel X, Y, B, in the
+ * varblock footprint layout: the coefficient (u, v) of the varblock whose
+ * top-left sample is (x0, y0) is stored at column x0 + u, row y0 + v, u
+ * horizontal frequency.  The LLF slots (u < W/8, v < H/8) of a W x H
+ * varblock hold the quantised DC samples of its 8x8 blocks (x0/8 + u,
+ * y0/8 + v) (F.2, I.2.7).  Planes cover the image padded to multiples of 8:
+ * ceil8(ysize) rows of row_stride_elems >= ceil8(xsize) elements.
+ * on_device: 1 = every input array of this submit (coefficients, maps,
+ * quant field, CfL map, sharpness) is a device pointer; 0 = host pointers. */
+typedef struct {
+  uint32_t xsize, ysize;
+  const int16_t* plane[3];
+  size_t row_stride_elems;
+  int on_device;
+} jxl_recon_coeffs;
+
+/* Chroma from luma (G, C.4.3, C.5.3): k = (kX, kB) pairs per 64x64 tile,
+ * [ceil(Hp/64)][ceil(Wp/64)][2] float, and the DC factors.  The draft's u8
+ * factors map to these by kX = (x - 128) / 256, kB = 0.935669 + (b - 128)/128. */
+typedef struct {
+  const float* k;
+  float kx_dc, kb_dc;
+} jxl_recon_cfl;
+
+/* Loop filter (C.10), DC (C.4.1) and colour (L.2, A.4.5) parameters.
+ * jxl_recon_filter_defaults() fills the draft's defaults with both filters
+ * off.  sharpness: uint8 per 8x8 block [Hp/8][Wp/8] (C.5.6), same memory
+ * space as the other inputs, needed only when epf != 0.  dequant: NULL for
+ * the default matrices of C.6.1.1, or a host array of 10560 floats holding,
+ * for code 0..14 and then channel 0..2, the H x W matrix row-major. */
+typedef struct {
+  int gab;
+  float gab_w1[3], gab_w2[3];
+  int epf;
+  float epf_weight_min;
+  float epf_scale[3];
+  float epf_sharp_lut[8];
+  float epf_range_max, epf_range_mul, epf_quant_mul;
+  uint32_t epf_sigma_max;
+  const uint8_t* sharpness;
+  float m_dc[3];
+  float inv_opsin[9];
+  float opsin_bias[3];
+  uint32_t target_nits_div50;
+  const float* dequant;
+} jxl_recon_filter_params;
+
+/* Caller-owned output buffer of ysize rows, row_stride_bytes apart. */
+typedef struct {
+  void* data;
+  size_t row_stride_bytes;
+  int dtype;               /* a jxlr_out_dtype                                */
+  int on_device;           /* 1: device buffer; 0: host buffer, written by a
+                              copy that completes before poll returns OK      */
+} jxl_recon_output;
+
+/* Fills *p with the defaults of C.10, C.4.1 (m_DC of the synthetic
+ * workloads: (0.02, 0.2, 0.2) / (64 sqrt 2)) and L.2; both filters off. */
+void jxl_recon_filter_defaults(jxl_recon_filter_params* p);
+
+/* Creates a context on config->device: builds the constant tables (C.6.1
+ * matrices, I.2.7 LLF maps, J.2.4 mul_table), one stream per slot.
+ * Returns JXLR_OK and *out, or JXLR_EINVAL / JXLR_ECUDA. */
+jxlr_status jxl_recon_create(const jxl_recon_config* config, jxl_recon_ctx** out);
+
+/* Enqueues the reconstruction of one image and returns at once with a
+ * ticket; the work runs on the slot's stream.  varblock_map: uint8 per 8x8
+ * block [Hp/8][Wp/8], row-major, holding the DctSelect code (C.5.4, 0..14)
+ * at a varblock's top-left block and 0xFF on the other blocks it covers.
+ * quant_field: AcMul (C.5.5) as float per 8x8 block [Hp/8][Wp/8]; the
+ * value at a varblock's top-left block applies to the whole varblock.
+ * Host inputs are validated here (JXLR_EINVAL); device inputs are
+ * validated on the device and reported by jxl_recon_poll().
+ * Returns JXLR_OK, JXLR_EBUSY (no slot or no HBM now), JXLR_ENOMEM,
+ * JXLR_EINVAL or JXLR_ECUDA. */
+jxlr_status jxl_recon_submit(jxl_recon_ctx* ctx, const jxl_recon_coeffs* coeffs,
+                             const uint8_t* varblock_map, const float* quant_field,
+                             const jxl_recon_cfl* cfl_map,
+                             const jxl_recon_filter_params* filter_params,
+                             const jxl_recon_output* out, uint64_t* ticket);
+
+/* Runs only the loop filters and the colour transform (J.2, J.4, L.2) on
+ * XYB samples the caller already has: xyb is a device array of 3 planes
+ * [3][ysize][row_stride_elems] float.  varblock_map and quant_field as in
+ * jxl_recon_submit (device pointers; they define the EPF ranges and
+ * sigma of J.2.4).  Same ticket semantics. */
+jxlr_status jxl_recon_submit_xyb(jxl_recon_ctx* ctx, const float* xyb,
+                                 uint32_t xsize, uint32_t ysize,
+                                 size_t row_stride_elems,
+                                 const uint8_t* varblock_map, const float* quant_field,
+                                 const jxl_recon_filter_params* filter_params,
+                                 const jxl_recon_output* out, uint64_t* ticket);
+
+/* Waits up to timeout_us (0 = just test, < 0 = forever) for a ticket.
+ * JXLR_OK when done (the ticket is then released; *latency_ms, if not
+ * NULL, receives submit-to-completion time), JXLR_EAGAIN / JXLR_ETIMEDOUT
+ * while running, JXLR_EINVAL for a device-side validation failure or an
+ * unknown ticket, JXLR_ECUDA on a CUDA error. */
+jxlr_status jxl_recon_poll(jxl_recon_ctx* ctx, uint64_t ticket, int64_t timeout_us,
+                           double* latency_ms);
+
+/* Device time of each stage of a finished request, in ms, when the
+ * context was created with timing = 1: ms[0] validation, ms[1]
+ * dequantisation + transforms, ms[2] filters + colour, ms[3] host<->device
+ * copies.  Call after jxl_recon_poll() returned JXLR_OK for the ticket;
+ * the values stay until the next completed request of that slot. */
+jxlr_status jxl_recon_stage_ms(jxl_recon_ctx* ctx, uint64_t ticket, float ms[4]);
+
+/* Number of kernels the context has launched so far. */
+uint64_t jxl_recon_launch_count(const jxl_recon_ctx* ctx);
+
+/* Device bytes currently held by the context's slots. */
+size_t jxl_recon_device_bytes(const jxl_recon_ctx* ctx);
+
+/* Waits for all requests, frees everything.  Tickets not yet polled are
+ * dropped (a later poll on them cannot happen: the context is gone). */
+jxlr_status jxl_recon_destroy(jxl_recon_ctx* ctx);
+
+/* Message of the last error on the calling thread ("" if none). */
+const char* jxl_recon_last_error(const jxl_recon_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* JXL_RECON_H_ */

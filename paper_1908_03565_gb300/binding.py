@@ -1,0 +1,265 @@
+"""Thin ctypes binding of libjxlrecon (include/jxl_recon.h).
+
+Only argument marshalling lives here: every step of the reconstruction runs
+in the library's CUDA kernels.  Device buffers come from PyTorch (``torch``
+is used for device memory and nothing else); host buffers are numpy arrays.
+There is no fallback: if the shared library is missing or fails to load,
+``load()`` raises.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libjxlrecon.so")
+
+JXLR_OK, JXLR_EAGAIN, JXLR_EINVAL, JXLR_ENOMEM = 0, 1, -1, -2
+JXLR_EBUSY, JXLR_ECUDA, JXLR_ETIMEDOUT, JXLR_ECANCELLED = -3, -4, -5, -6
+OUT_F32_LINEAR, OUT_F16_LINEAR, OUT_U8_SRGB, OUT_F32_XYB = 0, 1, 2, 3
+OUT_BYTES = {OUT_F32_LINEAR: 12, OUT_F16_LINEAR: 6, OUT_U8_SRGB: 3, OUT_F32_XYB: 12}
+
+EXPORTS = ("jxl_recon_filter_defaults", "jxl_recon_create", "jxl_recon_submit",
+           "jxl_recon_submit_xyb", "jxl_recon_poll", "jxl_recon_stage_ms",
+           "jxl_recon_launch_count", "jxl_recon_device_bytes", "jxl_recon_destroy",
+           "jxl_recon_last_error")
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int), ("hbm_cap_bytes", ctypes.c_size_t),
+                ("max_slots", ctypes.c_int), ("precision", ctypes.c_int),
+                ("timing", ctypes.c_int), ("cuda_stream", ctypes.c_void_p)]
+
+
+class Coeffs(ctypes.Structure):
+    _fields_ = [("xsize", ctypes.c_uint32), ("ysize", ctypes.c_uint32),
+                ("plane", ctypes.c_void_p * 3), ("row_stride_elems", ctypes.c_size_t),
+                ("on_device", ctypes.c_int)]
+
+
+class Cfl(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_void_p), ("kx_dc", ctypes.c_float), ("kb_dc", ctypes.c_float)]
+
+
+class FilterParams(ctypes.Structure):
+    _fields_ = [("gab", ctypes.c_int), ("gab_w1", ctypes.c_float * 3),
+                ("gab_w2", ctypes.c_float * 3), ("epf", ctypes.c_int),
+                ("epf_weight_min", ctypes.c_float), ("epf_scale", ctypes.c_float * 3),
+                ("epf_sharp_lut", ctypes.c_float * 8), ("epf_range_max", ctypes.c_float),
+                ("epf_range_mul", ctypes.c_float), ("epf_quant_mul", ctypes.c_float),
+                ("epf_sigma_max", ctypes.c_uint32), ("sharpness", ctypes.c_void_p),
+                ("m_dc", ctypes.c_float * 3), ("inv_opsin", ctypes.c_float * 9),
+                ("opsin_bias", ctypes.c_float * 3), ("target_nits_div50", ctypes.c_uint32),
+                ("dequant", ctypes.c_void_p)]
+
+
+class Output(ctypes.Structure):
+    _fields_ = [("data", ctypes.c_void_p), ("row_stride_bytes", ctypes.c_size_t),
+                ("dtype", ctypes.c_int), ("on_device", ctypes.c_int)]
+
+
+_lib = None
+
+
+def load(path=LIB_PATH):
+    """Loads the shared library (raises if it is absent)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libjxlrecon.so not built ({path}); run __graft_entry__.build()")
+    lib = ctypes.CDLL(path)
+    P = ctypes.POINTER
+    lib.jxl_recon_filter_defaults.argtypes = [P(FilterParams)]
+    lib.jxl_recon_filter_defaults.restype = None
+    lib.jxl_recon_create.argtypes = [P(Config), P(ctypes.c_void_p)]
+    lib.jxl_recon_create.restype = ctypes.c_int
+    lib.jxl_recon_submit.argtypes = [ctypes.c_void_p, P(Coeffs), ctypes.c_void_p,
+                                     ctypes.c_void_p, P(Cfl), P(FilterParams), P(Output),
+                                     P(ctypes.c_uint64)]
+    lib.jxl_recon_submit.restype = ctypes.c_int
+    lib.jxl_recon_submit_xyb.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint32,
+                                         ctypes.c_uint32, ctypes.c_size_t, ctypes.c_void_p,
+                                         ctypes.c_void_p, P(FilterParams), P(Output),
+                                         P(ctypes.c_uint64)]
+    lib.jxl_recon_submit_xyb.restype = ctypes.c_int
+    lib.jxl_recon_poll.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int64,
+                                   P(ctypes.c_double)]
+    lib.jxl_recon_poll.restype = ctypes.c_int
+    lib.jxl_recon_stage_ms.argtypes = [ctypes.c_void_p, ctypes.c_uint64, P(ctypes.c_float)]
+    lib.jxl_recon_stage_ms.restype = ctypes.c_int
+    lib.jxl_recon_launch_count.argtypes = [ctypes.c_void_p]
+    lib.jxl_recon_launch_count.restype = ctypes.c_uint64
+    lib.jxl_recon_device_bytes.argtypes = [ctypes.c_void_p]
+    lib.jxl_recon_device_bytes.restype = ctypes.c_size_t
+    lib.jxl_recon_destroy.argtypes = [ctypes.c_void_p]
+    lib.jxl_recon_destroy.restype = ctypes.c_int
+    lib.jxl_recon_last_error.argtypes = [ctypes.c_void_p]
+    lib.jxl_recon_last_error.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+class JxlrError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"status {status}: {msg}")
+        self.status = status
+
+
+def filter_defaults(lib=None, **overrides):
+    lib = lib or load()
+    p = FilterParams()
+    lib.jxl_recon_filter_defaults(ctypes.byref(p))
+    for k, v in overrides.items():
+        cur = getattr(p, k)
+        if isinstance(cur, ctypes.Array):
+            for i, x in enumerate(v):
+                cur[i] = x
+        else:
+            setattr(p, k, v)
+    return p
+
+
+def _ptr(a):
+    """Address of a numpy array or torch tensor."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        assert a.flags['C_CONTIGUOUS']
+        return a.ctypes.data
+    return a.data_ptr()
+
+
+class Context:
+    """One jxl_recon_ctx.  Methods mirror the C entry points."""
+
+    def __init__(self, device=0, max_slots=1, hbm_cap_bytes=0, timing=False, stream=None):
+        """stream: optional raw cudaStream_t (int) every request runs on."""
+        self.lib = load()
+        cfg = Config(device, hbm_cap_bytes, max_slots, 0, int(timing), stream)
+        h = ctypes.c_void_p()
+        st = self.lib.jxl_recon_create(ctypes.byref(cfg), ctypes.byref(h))
+        if st != JXLR_OK:
+            raise JxlrError(st, self.last_error())
+        self.h = h
+        self._keep = {}
+
+    def last_error(self):
+        return self.lib.jxl_recon_last_error(None).decode()
+
+    def close(self):
+        if self.h:
+            self.lib.jxl_recon_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, img, params, out, out_dtype, on_device, out_on_device=True,
+               out_stride=None, kx_dc=0.0, kb_dc=0.0):
+        """img: dict with coeffs (3, Hp, Wp) int16, vmap, acmul, cfl, sharpness
+        as numpy arrays (on_device False) or torch CUDA tensors (True)."""
+        xs, ys = img['xsize'], img['ysize']
+        co = img['coeffs']
+        stride = co.shape[2]
+        planes = (ctypes.c_void_p * 3)(*[_ptr(co[c]) for c in range(3)])
+        c = Coeffs(xs, ys, planes, stride, int(on_device))
+        cfl = Cfl(_ptr(img['cfl']), kx_dc, kb_dc)
+        if params.epf:
+            params.sharpness = _ptr(img['sharpness'])
+        if out_stride is None:
+            out_stride = OUT_BYTES[out_dtype] * xs
+        o = Output(_ptr(out), out_stride, out_dtype, int(out_on_device))
+        t = ctypes.c_uint64()
+        st = self.lib.jxl_recon_submit(self.h, ctypes.byref(c), _ptr(img['vmap']),
+                                       _ptr(img['acmul']), ctypes.byref(cfl),
+                                       ctypes.byref(params), ctypes.byref(o), ctypes.byref(t))
+        if st != JXLR_OK:
+            raise JxlrError(st, self.last_error())
+        self._keep[t.value] = (img, params, out, c, cfl, o)
+        return t.value
+
+    def submit_xyb(self, xyb, xs, ys, vmap, acmul, sharpness, params, out, out_dtype,
+                   out_stride=None):
+        """xyb: (3, ys, stride) float32 CUDA tensor; others CUDA tensors."""
+        if params.epf:
+            params.sharpness = _ptr(sharpness)
+        if out_stride is None:
+            out_stride = OUT_BYTES[out_dtype] * xs
+        o = Output(_ptr(out), out_stride, out_dtype, 1)
+        t = ctypes.c_uint64()
+        st = self.lib.jxl_recon_submit_xyb(self.h, _ptr(xyb), xs, ys, xyb.shape[2],
+                                           _ptr(vmap), _ptr(acmul), ctypes.byref(params),
+                                           ctypes.byref(o), ctypes.byref(t))
+        if st != JXLR_OK:
+            raise JxlrError(st, self.last_error())
+        self._keep[t.value] = (xyb, vmap, acmul, sharpness, params, out, o)
+        return t.value
+
+    def poll(self, ticket, timeout_us=-1):
+        """Returns (status, latency_ms); raises on errors other than
+        EAGAIN/ETIMEDOUT."""
+        lat = ctypes.c_double()
+        st = self.lib.jxl_recon_poll(self.h, ticket, timeout_us, ctypes.byref(lat))
+        if st in (JXLR_EAGAIN, JXLR_ETIMEDOUT):
+            return st, None
+        self._keep.pop(ticket, None)
+        if st != JXLR_OK:
+            raise JxlrError(st, self.last_error())
+        return st, lat.value
+
+    def stage_ms(self, ticket):
+        ms = (ctypes.c_float * 4)()
+        st = self.lib.jxl_recon_stage_ms(self.h, ticket, ms)
+        if st != JXLR_OK:
+            raise JxlrError(st, self.last_error())
+        return list(ms)
+
+    def launch_count(self):
+        return self.lib.jxl_recon_launch_count(self.h)
+
+    def device_bytes(self):
+        return self.lib.jxl_recon_device_bytes(self.h)
+
+
+def to_device(img, torch_module, device="cuda"):
+    """Copies a synthetic image's arrays to device tensors (torch memory)."""
+    t = torch_module
+    out = dict(img)
+    for k in ('coeffs', 'vmap', 'acmul', 'cfl', 'sharpness'):
+        out[k] = t.from_numpy(np.ascontiguousarray(img[k])).to(device)
+    return out
+
+
+def out_shape(img, dtype):
+    """(ysize, xsize, 3) output array shape and numpy dtype."""
+    npd = {OUT_F32_LINEAR: np.float32, OUT_F16_LINEAR: np.float16,
+           OUT_U8_SRGB: np.uint8, OUT_F32_XYB: np.float32}[dtype]
+    return (img['ysize'], img['xsize'], 3), npd
+
+
+def decode(ctx, img, params, dtype=OUT_F32_LINEAR, device_io=True):
+    """Synchronous convenience: one image through submit + poll.  Returns a
+    numpy array (ysize, xsize, 3)."""
+    import torch
+    shape, npd = out_shape(img, dtype)
+    if device_io:
+        dimg = to_device(img, torch)
+        tdt = {np.float32: torch.float32, np.float16: torch.float16, np.uint8: torch.uint8}[npd]
+        out = torch.empty(shape, dtype=tdt, device="cuda")
+        t = ctx.submit(dimg, params, out, dtype, on_device=True)
+        ctx.poll(t)
+        return out.cpu().numpy()
+    out = np.empty(shape, dtype=npd)
+    t = ctx.submit(img, params, out, dtype, on_device=False, out_on_device=False)
+    ctx.poll(t)
+    return out

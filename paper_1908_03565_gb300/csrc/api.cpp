@@ -1,0 +1,646 @@
+// C ABI of libjxlrecon: contexts, slots (one stream + scratch arena each),
+// admission under an HBM cap, request tickets.
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/jxl_recon.h"
+#include "internal.h"
+#include "kernels.h"
+
+using namespace jxlr;
+
+namespace {
+
+thread_local std::string g_err;
+
+jxlr_status fail(jxlr_status s, const std::string& msg) {
+  g_err = msg;
+  return s;
+}
+
+jxlr_status cuda_fail(cudaError_t e, const char* what) {
+  return fail(JXLR_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call)                                   \
+  do {                                             \
+    cudaError_t e_ = (call);                       \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+  } while (0)
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+using Clock = std::chrono::steady_clock;
+
+struct Slot {
+  cudaStream_t stream = nullptr;
+  bool own_stream = true;
+  cudaEvent_t done = nullptr;
+  cudaEvent_t ev[5] = {};     // timing marks: start, validated, recon, filter, end
+  char* arena = nullptr;
+  size_t arena_bytes = 0;
+  unsigned* h_status = nullptr;   // pinned: device status copied back here
+  bool busy = false;
+  bool timed = false;
+  bool check_status = false;
+  uint64_t ticket = 0;
+  Clock::time_point t_submit;
+};
+
+struct Timing {
+  float ms[4];
+};
+
+}  // namespace
+
+struct jxl_recon_ctx {
+  int device = 0;
+  size_t cap = 0;
+  bool timing = false;
+  std::vector<Slot> slots;
+  float* d_dequant = nullptr;        // prescaled default matrices
+  std::mutex mu;
+  std::atomic<uint64_t> next_ticket{1};
+  std::atomic<uint64_t> launches{0};
+  size_t bytes = 0;                  // sum of slot arenas
+  std::unordered_map<uint64_t, Timing> timings;
+};
+
+extern "C" {
+
+void jxl_recon_filter_defaults(jxl_recon_filter_params* p) {
+  std::memset(p, 0, sizeof(*p));
+  p->gab = 0;
+  for (int c = 0; c < 3; ++c) {
+    p->gab_w1[c] = 0.115169525f;
+    p->gab_w2[c] = 0.061248592f;
+  }
+  p->epf = 0;
+  p->epf_weight_min = 0.3f;
+  p->epf_scale[0] = 899.676941f;
+  p->epf_scale[1] = 111.965157f;
+  p->epf_scale[2] = 45.275791f;
+  for (int i = 0; i < 8; ++i) p->epf_sharp_lut[i] = static_cast<float>(i / 7.0);
+  p->epf_range_max = 70.0f;
+  p->epf_range_mul = 12.6f;
+  p->epf_quant_mul = 20.0f;
+  p->epf_sigma_max = 170;
+  p->sharpness = nullptr;
+  const double r2 = 64.0 * std::sqrt(2.0);
+  p->m_dc[0] = static_cast<float>(0.02 / r2);
+  p->m_dc[1] = static_cast<float>(0.2 / r2);
+  p->m_dc[2] = static_cast<float>(0.2 / r2);
+  const float m[9] = {2542.56835937500000f, -2326.53173828125000f, 44.17734527587891f,
+                      -698.04852294921875f, 1012.71777343750000f, -76.22974395751953f,
+                      -827.36480712890625f, 709.83502197265625f, 451.38488769531250f};
+  std::memcpy(p->inv_opsin, m, sizeof(m));
+  p->opsin_bias[0] = -0.00100549f;
+  p->opsin_bias[1] = -0.00100549f;
+  p->opsin_bias[2] = -0.00094081f;
+  p->target_nits_div50 = 5;
+  p->dequant = nullptr;
+}
+
+const char* jxl_recon_last_error(const jxl_recon_ctx*) { return g_err.c_str(); }
+
+uint64_t jxl_recon_launch_count(const jxl_recon_ctx* ctx) { return ctx ? ctx->launches.load() : 0; }
+
+size_t jxl_recon_device_bytes(const jxl_recon_ctx* ctx) { return ctx ? ctx->bytes : 0; }
+
+jxlr_status jxl_recon_create(const jxl_recon_config* cfg, jxl_recon_ctx** out) {
+  if (!cfg || !out) return fail(JXLR_EINVAL, "create: null argument");
+  if (cfg->max_slots < 1 || cfg->max_slots > 256) return fail(JXLR_EINVAL, "create: max_slots out of [1, 256]");
+  if (cfg->precision != JXLR_PREC_FP32) return fail(JXLR_EINVAL, "create: unsupported precision");
+  int ndev = 0;
+  CK(cudaGetDeviceCount(&ndev));
+  if (cfg->device < 0 || cfg->device >= ndev) return fail(JXLR_EINVAL, "create: bad device");
+  CK(cudaSetDevice(cfg->device));
+
+  // constant tables (host, double precision -> float)
+  std::vector<float> raw(kDequantFloats), scaled(kDequantFloats);
+  if (!default_dequant(raw.data())) return fail(JXLR_EINVAL, "default dequant matrices ill-formed");
+  prescale_dequant(raw.data(), scaled.data());
+  std::vector<float> llf(kLlfMaps * 256), odd(kOddFloats), afv(256);
+  std::vector<int32_t> mul4(673);
+  llf_maps(llf.data());
+  odd_tables(odd.data());
+  mul_table4(mul4.data());
+  for (int j = 0; j < 16; ++j)
+    for (int i = 0; i < 16; ++i) afv[j * 16 + i] = static_cast<float>(kAfvBasis[j][i]);
+  if (!upload_constants(llf.data(), odd.data(), mul4.data(), afv.data()))
+    return fail(JXLR_ECUDA, "create: constant upload failed");
+
+  auto* ctx = new jxl_recon_ctx();
+  ctx->device = cfg->device;
+  ctx->cap = cfg->hbm_cap_bytes;
+  ctx->timing = cfg->timing != 0;
+  cudaError_t e = cudaMalloc(&ctx->d_dequant, sizeof(float) * kDequantFloats);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(ctx->d_dequant, scaled.data(), sizeof(float) * kDequantFloats,
+                   cudaMemcpyHostToDevice);
+  ctx->slots.resize(cfg->max_slots);
+  for (auto& s : ctx->slots) {
+    if (cfg->cuda_stream) {
+      s.stream = static_cast<cudaStream_t>(cfg->cuda_stream);
+      s.own_stream = false;
+    } else if (e == cudaSuccess) {
+      e = cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking);
+    }
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming);
+    for (auto& ev : s.ev)
+      if (e == cudaSuccess) e = cudaEventCreate(&ev);
+    if (e == cudaSuccess) e = cudaMallocHost(&s.h_status, 4 * sizeof(unsigned));
+  }
+  if (e != cudaSuccess) {
+    jxl_recon_destroy(ctx);
+    return cuda_fail(e, "create");
+  }
+  *out = ctx;
+  return JXLR_OK;
+}
+
+jxlr_status jxl_recon_destroy(jxl_recon_ctx* ctx) {
+  if (!ctx) return JXLR_OK;
+  cudaSetDevice(ctx->device);
+  for (auto& s : ctx->slots) {
+    if (s.stream) cudaStreamSynchronize(s.stream);
+    if (s.arena) cudaFree(s.arena);
+    if (s.h_status) cudaFreeHost(s.h_status);
+    for (auto& ev : s.ev)
+      if (ev) cudaEventDestroy(ev);
+    if (s.done) cudaEventDestroy(s.done);
+    if (s.stream && s.own_stream) cudaStreamDestroy(s.stream);
+  }
+  if (ctx->d_dequant) cudaFree(ctx->d_dequant);
+  delete ctx;
+  return JXLR_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Host-side check of a DctSelect map (C.5.4): every block is covered by
+// exactly one naturally aligned, in-bounds varblock.
+bool host_map_valid(const uint8_t* vmap, int bw, int bh, std::string* why) {
+  std::vector<uint8_t> cov(static_cast<size_t>(bw) * bh, 0);
+  for (int by = 0; by < bh; ++by) {
+    for (int bx = 0; bx < bw; ++bx) {
+      const unsigned code = vmap[by * bw + bx];
+      if (code == kCovered) continue;
+      if (code >= kNumCodes) { *why = "invalid DctSelect code"; return false; }
+      const int w8 = kShapeW[code] / 8, h8 = kShapeH[code] / 8;
+      if (bx % w8 || by % h8) { *why = "varblock not naturally aligned"; return false; }
+      if (bx + w8 > bw || by + h8 > bh) { *why = "varblock out of bounds"; return false; }
+      for (int yy = 0; yy < h8; ++yy)
+        for (int xx = 0; xx < w8; ++xx) {
+          if ((xx | yy) && vmap[(by + yy) * bw + bx + xx] != kCovered) {
+            *why = "varblocks overlap"; return false;
+          }
+          cov[(by + yy) * bw + bx + xx]++;
+        }
+    }
+  }
+  for (auto c : cov)
+    if (c != 1) { *why = "blocks not covered by exactly one varblock"; return false; }
+  return true;
+}
+
+ColorParams color_params(const jxl_recon_filter_params& p) {
+  ColorParams cp;
+  const double div = p.target_nits_div50 * 50.0 / 250.0 * 255.0;
+  for (int i = 0; i < 9; ++i) cp.m[i] = static_cast<float>(p.inv_opsin[i] / div);
+  for (int i = 0; i < 3; ++i) cp.bias[i] = p.opsin_bias[i];
+  return cp;
+}
+
+SigmaParams sigma_params(const jxl_recon_filter_params& p) {
+  SigmaParams sp;
+  const double im3 = std::cbrt(p.target_nits_div50 * 50.0 / 250.0);
+  for (int c = 0; c < 3; ++c) {
+    sp.gmin[c] = static_cast<float>((c == 0 ? -0.03 : 0.0) * im3);
+    sp.gscale[c] = p.epf_scale[c];
+  }
+  sp.range_max = p.epf_range_max;
+  sp.range_mul = p.epf_range_mul;
+  sp.quant_mul = p.epf_quant_mul;
+  sp.sigma_max = static_cast<float>(p.epf_sigma_max);
+  for (int i = 0; i < 8; ++i) sp.lut[i] = p.epf_sharp_lut[i];
+  return sp;
+}
+
+uint32_t weight_min_bits(float wmin) {
+  // smallest binary32 value >= wmin (weights below it are dropped, J.2.5)
+  if (!(wmin > 0)) return 0;
+  uint32_t b;
+  std::memcpy(&b, &wmin, 4);
+  return b;
+}
+
+FilterArgs filter_args(const jxl_recon_filter_params& p) {
+  FilterArgs f;
+  std::memset(&f, 0, sizeof(f));
+  f.epf = p.epf != 0;
+  f.gab = p.gab != 0;
+  for (int c = 0; c < 3; ++c) {
+    const double w1 = p.gab_w1[c], w2 = p.gab_w2[c];
+    const double n = 1.0 + 4.0 * w1 + 4.0 * w2;
+    f.gw[c][0] = static_cast<float>(1.0 / n);
+    f.gw[c][1] = static_cast<float>(w1 / n);
+    f.gw[c][2] = static_cast<float>(w2 / n);
+  }
+  f.wmin_bits = weight_min_bits(p.epf_weight_min);
+  f.sp = sigma_params(p);
+  f.cp = color_params(p);
+  return f;
+}
+
+// Finds a free slot and makes sure its arena holds `need` bytes within the
+// HBM cap.  Called with ctx->mu held.
+jxlr_status acquire_slot(jxl_recon_ctx* ctx, size_t need, Slot** out) {
+  Slot* fit = nullptr;   // smallest idle arena that already holds `need`
+  Slot* any = nullptr;   // else the idle slot with the largest arena
+  for (auto& s : ctx->slots) {
+    if (s.busy) continue;
+    if (s.arena_bytes >= need && (!fit || s.arena_bytes < fit->arena_bytes)) fit = &s;
+    if (!any || s.arena_bytes > any->arena_bytes) any = &s;
+  }
+  Slot* best = fit ? fit : any;
+  if (ctx->cap && need > ctx->cap) return fail(JXLR_ENOMEM, "request exceeds the HBM cap");
+  if (!best) return fail(JXLR_EBUSY, "no free slot");
+  if (best->arena_bytes < need) {
+    const size_t others = ctx->bytes - best->arena_bytes;
+    if (ctx->cap && others + need > ctx->cap) {
+      // free idle arenas before refusing
+      for (auto& s : ctx->slots) {
+        if (!s.busy && &s != best && s.arena) {
+          cudaFree(s.arena);
+          ctx->bytes -= s.arena_bytes;
+          s.arena = nullptr;
+          s.arena_bytes = 0;
+        }
+      }
+      if (ctx->bytes - best->arena_bytes + need > ctx->cap)
+        return fail(JXLR_EBUSY, "not enough HBM under the cap now");
+    }
+    if (best->arena) {
+      cudaFree(best->arena);
+      ctx->bytes -= best->arena_bytes;
+      best->arena = nullptr;
+      best->arena_bytes = 0;
+    }
+    const size_t sz = align_up(need, size_t(1) << 20);
+    cudaError_t e = cudaMalloc(&best->arena, sz);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(JXLR_ENOMEM, std::string("device allocation failed: ") + cudaGetErrorString(e));
+    }
+    best->arena_bytes = sz;
+    ctx->bytes += sz;
+  }
+  *out = best;
+  return JXLR_OK;
+}
+
+struct Carve {
+  char* base;
+  size_t off = 0;
+  explicit Carve(char* b) : base(b) {}
+  template <class T>
+  T* take(size_t count) {
+    off = align_up(off, 256);
+    T* p = reinterpret_cast<T*>(base + off);
+    off += count * sizeof(T);
+    return p;
+  }
+};
+
+void mark(Slot* s, int i) {
+  if (s->timed) cudaEventRecord(s->ev[i], s->stream);
+}
+
+jxlr_status finish_submit(jxl_recon_ctx* ctx, Slot* slot, unsigned* d_status, uint64_t* ticket) {
+  CK(cudaMemcpyAsync(slot->h_status, d_status, 4 * sizeof(unsigned), cudaMemcpyDeviceToHost,
+                     slot->stream));
+  CK(cudaEventRecord(slot->done, slot->stream));
+  CK(cudaGetLastError());
+  slot->busy = true;
+  slot->ticket = ctx->next_ticket++;
+  *ticket = slot->ticket;
+  return JXLR_OK;
+}
+
+}  // namespace
+
+extern "C" jxlr_status jxl_recon_submit(jxl_recon_ctx* ctx, const jxl_recon_coeffs* co,
+                                        const uint8_t* vmap, const float* qf,
+                                        const jxl_recon_cfl* cfl,
+                                        const jxl_recon_filter_params* fp,
+                                        const jxl_recon_output* out, uint64_t* ticket) {
+  if (!ctx || !co || !vmap || !qf || !cfl || !cfl->k || !fp || !out || !ticket)
+    return fail(JXLR_EINVAL, "submit: null argument");
+  const int xs = static_cast<int>(co->xsize), ys = static_cast<int>(co->ysize);
+  if (xs <= 0 || ys <= 0 || xs > 65536 || ys > 65536)
+    return fail(JXLR_EINVAL, "submit: image size out of [1, 65536]");
+  const int wp = (xs + 7) & ~7, hp = (ys + 7) & ~7, bw = wp / 8, bh = hp / 8;
+  const int tw = (wp + 63) / 64, th = (hp + 63) / 64;
+  if (co->row_stride_elems < static_cast<size_t>(wp))
+    return fail(JXLR_EINVAL, "submit: coefficient row stride below the padded width");
+  for (int c = 0; c < 3; ++c)
+    if (!co->plane[c]) return fail(JXLR_EINVAL, "submit: null coefficient plane");
+  if (out->dtype < 0 || out->dtype > 3 || !out->data) return fail(JXLR_EINVAL, "submit: bad output");
+  const size_t px_bytes = out->dtype == 1 ? 6 : out->dtype == 2 ? 3 : 12;
+  if (out->row_stride_bytes < px_bytes * xs) return fail(JXLR_EINVAL, "submit: output stride too small");
+  if (fp->epf && !fp->sharpness) return fail(JXLR_EINVAL, "submit: EPF needs the sharpness map");
+  const bool dev_in = co->on_device != 0;
+  if (dev_in) {
+    if (co->row_stride_elems % 8) return fail(JXLR_EINVAL, "submit: device coefficient rows must be 16-byte multiples");
+    for (int c = 0; c < 3; ++c)
+      if (reinterpret_cast<uintptr_t>(co->plane[c]) & 15)
+        return fail(JXLR_EINVAL, "submit: device coefficient planes must be 16-byte aligned");
+  } else {
+    std::string why;
+    if (!host_map_valid(vmap, bw, bh, &why)) return fail(JXLR_EINVAL, "submit: " + why);
+  }
+  std::vector<float> dq_scaled;
+  if (fp->dequant) {
+    if (!dequant_valid(fp->dequant))
+      return fail(JXLR_EINVAL, "submit: dequant matrix entry non-positive or not finite");
+    dq_scaled.resize(kDequantFloats);
+    prescale_dequant(fp->dequant, dq_scaled.data());
+  }
+  const bool filters = fp->epf || fp->gab;
+
+  // ---- scratch layout ----
+  const size_t cstride = wp;
+  size_t need = 0;
+  auto add = [&](size_t bytes) { need = align_up(need, 256) + bytes; };
+  add(16);                                            // status
+  if (!dev_in) {
+    for (int c = 0; c < 3; ++c) add(sizeof(int16_t) * cstride * hp);
+    add(static_cast<size_t>(bw) * bh);                // map
+    add(sizeof(float) * bw * bh);                     // quant field
+    add(sizeof(float) * tw * th * 2);                 // cfl
+    if (fp->epf) add(static_cast<size_t>(bw) * bh);   // sharpness
+  }
+  if (fp->dequant) add(sizeof(float) * kDequantFloats);
+  if (filters) add(sizeof(float) * 3 * wp * hp);
+  if (fp->epf) add(sizeof(int16_t) * bw * bh);
+  const size_t out_bytes = out->row_stride_bytes * (ys - 1) + px_bytes * xs;
+  if (!out->on_device) add(out_bytes);
+  need = align_up(need, 256);
+
+  std::lock_guard<std::mutex> lock(ctx->mu);
+  CK(cudaSetDevice(ctx->device));
+  Slot* slot = nullptr;
+  jxlr_status st = acquire_slot(ctx, need, &slot);
+  if (st != JXLR_OK) return st;
+  slot->timed = ctx->timing;
+  slot->t_submit = Clock::now();
+  cudaStream_t s = slot->stream;
+  Carve cv(slot->arena);
+  unsigned* d_status = cv.take<unsigned>(4);
+  CK(cudaMemsetAsync(d_status, 0, 16, s));
+  mark(slot, 0);
+
+  ReconArgs ra;
+  std::memset(&ra, 0, sizeof(ra));
+  const uint8_t* d_sharp = fp->sharpness;
+  if (!dev_in) {
+    for (int c = 0; c < 3; ++c) {
+      int16_t* d = cv.take<int16_t>(cstride * hp);
+      CK(cudaMemcpy2DAsync(d, cstride * 2, co->plane[c], co->row_stride_elems * 2, wp * 2, hp,
+                           cudaMemcpyHostToDevice, s));
+      ra.coef[c] = d;
+    }
+    uint8_t* dm = cv.take<uint8_t>(static_cast<size_t>(bw) * bh);
+    CK(cudaMemcpyAsync(dm, vmap, static_cast<size_t>(bw) * bh, cudaMemcpyHostToDevice, s));
+    float* dq = cv.take<float>(static_cast<size_t>(bw) * bh);
+    CK(cudaMemcpyAsync(dq, qf, sizeof(float) * bw * bh, cudaMemcpyHostToDevice, s));
+    float* dc = cv.take<float>(static_cast<size_t>(tw) * th * 2);
+    CK(cudaMemcpyAsync(dc, cfl->k, sizeof(float) * tw * th * 2, cudaMemcpyHostToDevice, s));
+    ra.vmap = dm;
+    ra.acmul = dq;
+    ra.cfl = dc;
+    ra.cstride = cstride;
+    if (fp->epf) {
+      uint8_t* ds = cv.take<uint8_t>(static_cast<size_t>(bw) * bh);
+      CK(cudaMemcpyAsync(ds, fp->sharpness, static_cast<size_t>(bw) * bh, cudaMemcpyHostToDevice, s));
+      d_sharp = ds;
+    }
+  } else {
+    for (int c = 0; c < 3; ++c) ra.coef[c] = co->plane[c];
+    ra.cstride = co->row_stride_elems;
+    ra.vmap = vmap;
+    ra.acmul = qf;
+    ra.cfl = cfl->k;
+  }
+  mark(slot, 1);
+  if (dev_in) {
+    launch_validate(ra.vmap, bw, bh, d_status, s);
+    ctx->launches++;
+  }
+  mark(slot, 2);
+  if (fp->dequant) {
+    float* d = cv.take<float>(kDequantFloats);
+    CK(cudaMemcpyAsync(d, dq_scaled.data(), sizeof(float) * kDequantFloats, cudaMemcpyHostToDevice, s));
+    CK(cudaStreamSynchronize(s));   // dq_scaled is a local buffer
+    ra.dequant = d;
+  } else {
+    ra.dequant = ctx->d_dequant;
+  }
+  ra.sharp = d_sharp;
+  ra.xs = xs; ra.ys = ys; ra.wp = wp; ra.hp = hp; ra.bw = bw; ra.bh = bh; ra.tw = tw;
+  for (int c = 0; c < 3; ++c) {
+    ra.m_dc[c] = fp->m_dc[c];
+    ra.one_minus_bias[c] = static_cast<float>(1.0 - (c == 0 ? 0.05465007330715401
+                                                      : c == 1 ? 0.07005449891748593
+                                                               : 0.049935103337343655));
+  }
+  ra.kx_dc = cfl->kx_dc;
+  ra.kb_dc = cfl->kb_dc;
+  ra.sp = sigma_params(*fp);
+  ra.cp = color_params(*fp);
+
+  OutParams op;
+  char* d_out = nullptr;
+  if (out->on_device) {
+    op.data = out->data;
+  } else {
+    d_out = cv.take<char>(out_bytes);
+    op.data = d_out;
+  }
+  op.stride = out->row_stride_bytes;
+  op.dtype = out->dtype;
+
+  if (filters) {
+    float* xyb = cv.take<float>(static_cast<size_t>(3) * wp * hp);
+    int16_t* sig = fp->epf ? cv.take<int16_t>(static_cast<size_t>(bw) * bh) : nullptr;
+    ra.write_xyb = 1;
+    ra.xyb = xyb;
+    ra.sigma = sig;
+    launch_recon(ra, s);
+    ctx->launches++;
+    mark(slot, 3);
+    FilterArgs fa = filter_args(*fp);
+    fa.xyb = xyb;
+    fa.rstride = wp;
+    fa.pstride = static_cast<size_t>(wp) * hp;
+    fa.xs = xs; fa.ys = ys; fa.bw = bw;
+    fa.sigma = sig;
+    fa.out = op;
+    launch_filter(fa, s);
+    ctx->launches++;
+  } else {
+    ra.write_xyb = 0;
+    ra.out = op;
+    launch_recon(ra, s);
+    ctx->launches++;
+    mark(slot, 3);
+  }
+  mark(slot, 4);
+  if (!out->on_device)
+    CK(cudaMemcpy2DAsync(out->data, out->row_stride_bytes, d_out, out->row_stride_bytes,
+                         px_bytes * xs, ys, cudaMemcpyDeviceToHost, s));
+  slot->check_status = dev_in;
+  return finish_submit(ctx, slot, d_status, ticket);
+}
+
+extern "C" jxlr_status jxl_recon_submit_xyb(jxl_recon_ctx* ctx, const float* xyb, uint32_t xsize,
+                                            uint32_t ysize, size_t row_stride_elems,
+                                            const uint8_t* vmap, const float* qf,
+                                            const jxl_recon_filter_params* fp,
+                                            const jxl_recon_output* out, uint64_t* ticket) {
+  if (!ctx || !xyb || !fp || !out || !ticket) return fail(JXLR_EINVAL, "submit_xyb: null argument");
+  const int xs = static_cast<int>(xsize), ys = static_cast<int>(ysize);
+  if (xs <= 0 || ys <= 0 || xs > 65536 || ys > 65536)
+    return fail(JXLR_EINVAL, "submit_xyb: image size out of [1, 65536]");
+  if (row_stride_elems < static_cast<size_t>(xs)) return fail(JXLR_EINVAL, "submit_xyb: row stride");
+  if (fp->epf && (!vmap || !qf || !fp->sharpness))
+    return fail(JXLR_EINVAL, "submit_xyb: EPF needs the map, quant field and sharpness");
+  if (out->dtype < 0 || out->dtype > 3 || !out->data || !out->on_device)
+    return fail(JXLR_EINVAL, "submit_xyb: output must be a device buffer");
+  const int bw = (xs + 7) / 8, bh = (ys + 7) / 8;
+  size_t need = 256 + (fp->epf ? align_up(sizeof(int16_t) * bw * bh, 256) : 0);
+  std::lock_guard<std::mutex> lock(ctx->mu);
+  CK(cudaSetDevice(ctx->device));
+  Slot* slot = nullptr;
+  jxlr_status st = acquire_slot(ctx, need, &slot);
+  if (st != JXLR_OK) return st;
+  slot->timed = ctx->timing;
+  slot->t_submit = Clock::now();
+  cudaStream_t s = slot->stream;
+  Carve cv(slot->arena);
+  unsigned* d_status = cv.take<unsigned>(4);
+  CK(cudaMemsetAsync(d_status, 0, 16, s));
+  mark(slot, 0);
+  mark(slot, 1);   // no input staging on this path
+  int16_t* sig = nullptr;
+  if (fp->epf) {
+    launch_validate(vmap, bw, bh, d_status, s);
+    ctx->launches++;
+  }
+  mark(slot, 2);
+  if (fp->epf) {
+    sig = cv.take<int16_t>(static_cast<size_t>(bw) * bh);
+    SigmaArgs sa;
+    sa.xyb = xyb;
+    sa.rstride = row_stride_elems;
+    sa.pstride = row_stride_elems * ys;
+    sa.vmap = vmap;
+    sa.acmul = qf;
+    sa.sharp = fp->sharpness;
+    sa.xs = xs; sa.ys = ys; sa.bw = bw; sa.bh = bh;
+    sa.sigma = sig;
+    sa.sp = sigma_params(*fp);
+    launch_sigma(sa, s);
+    ctx->launches++;
+  }
+  mark(slot, 3);
+  FilterArgs fa = filter_args(*fp);
+  fa.xyb = xyb;
+  fa.rstride = row_stride_elems;
+  fa.pstride = row_stride_elems * ys;
+  fa.xs = xs; fa.ys = ys; fa.bw = bw;
+  fa.sigma = sig;
+  fa.out.data = out->data;
+  fa.out.stride = out->row_stride_bytes;
+  fa.out.dtype = out->dtype;
+  launch_filter(fa, s);
+  ctx->launches++;
+  mark(slot, 4);
+  slot->check_status = fp->epf != 0;
+  return finish_submit(ctx, slot, d_status, ticket);
+}
+
+extern "C" jxlr_status jxl_recon_poll(jxl_recon_ctx* ctx, uint64_t ticket, int64_t timeout_us,
+                                      double* latency_ms) {
+  if (!ctx) return fail(JXLR_EINVAL, "poll: null context");
+  Slot* slot = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    for (auto& s : ctx->slots)
+      if (s.busy && s.ticket == ticket) slot = &s;
+  }
+  if (!slot) return fail(JXLR_EINVAL, "poll: unknown or already completed ticket");
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(JXLR_ECUDA, "poll: set device");
+  const auto t0 = Clock::now();
+  cudaError_t q;
+  if (timeout_us < 0) {
+    q = cudaEventSynchronize(slot->done);
+  } else {
+    for (;;) {
+      q = cudaEventQuery(slot->done);
+      if (q != cudaErrorNotReady) break;
+      const auto us = std::chrono::duration_cast<std::chrono::microseconds>(Clock::now() - t0).count();
+      if (us >= timeout_us) return timeout_us == 0 ? JXLR_EAGAIN : JXLR_ETIMEDOUT;
+      std::this_thread::sleep_for(std::chrono::microseconds(20));
+    }
+  }
+  const auto t1 = Clock::now();
+  std::lock_guard<std::mutex> lock(ctx->mu);
+  slot->busy = false;
+  if (q != cudaSuccess) return cuda_fail(q, "poll");
+  if (latency_ms)
+    *latency_ms = std::chrono::duration<double, std::milli>(t1 - slot->t_submit).count();
+  if (slot->timed) {
+    Timing t;
+    float a = 0, b = 0, c = 0, d = 0;
+    cudaEventElapsedTime(&a, slot->ev[0], slot->ev[1]);
+    cudaEventElapsedTime(&b, slot->ev[1], slot->ev[2]);
+    cudaEventElapsedTime(&c, slot->ev[2], slot->ev[3]);
+    cudaEventElapsedTime(&d, slot->ev[3], slot->ev[4]);
+    t.ms[0] = b;   // validation
+    t.ms[1] = c;   // dequantisation + transforms (+ colour when unfiltered)
+    t.ms[2] = d;   // filters + colour
+    t.ms[3] = a;   // input staging copies
+    if (ctx->timings.size() > 4096) ctx->timings.clear();
+    ctx->timings[ticket] = t;
+  }
+  if (slot->check_status && slot->h_status[0] != 0) {
+    char buf[96];
+    std::snprintf(buf, sizeof(buf), "device validation: DctSelect map ill-formed (flags 0x%x)",
+                  slot->h_status[0]);
+    return fail(JXLR_EINVAL, buf);
+  }
+  return JXLR_OK;
+}
+
+extern "C" jxlr_status jxl_recon_stage_ms(jxl_recon_ctx* ctx, uint64_t ticket, float ms[4]) {
+  if (!ctx || !ms) return fail(JXLR_EINVAL, "stage_ms: null argument");
+  std::lock_guard<std::mutex> lock(ctx->mu);
+  auto it = ctx->timings.find(ticket);
+  if (it == ctx->timings.end()) return fail(JXLR_EINVAL, "stage_ms: no timing for this ticket");
+  std::memcpy(ms, it->second.ms, sizeof(float) * 4);
+  return JXLR_OK;
+}

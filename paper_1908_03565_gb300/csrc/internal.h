@@ -1,0 +1,63 @@
+// Internal declarations shared by the translation units of libjxlrecon.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+namespace jxlr {
+
+constexpr int kNumCodes = 15;          // DctSelect codes 0..14 (C.5.4)
+constexpr uint8_t kCovered = 0xFF;     // block covered by a varblock starting elsewhere
+constexpr int kDequantFloats = 10560;  // sum over codes of 3 * W * H
+
+enum Code : int {
+  kDCT8 = 0, kIdentity = 1, kDCT2 = 2, kDCT4 = 3, kDCT16 = 4, kDCT32 = 5,
+  kDCT16x8 = 6, kDCT8x16 = 7, kDCT32x8 = 8, kDCT8x32 = 9, kDCT32x16 = 10,
+  kDCT16x32 = 11, kDCT4x8 = 12, kDCT8x4 = 13, kAFV = 14
+};
+
+// Width and height in samples of each code.  "DCT A x B" names A rows and B
+// columns (C.6.1, I.2.3.5, I.2.3.6).
+extern const int kShapeW[kNumCodes];
+extern const int kShapeH[kNumCodes];
+
+// Float offset of matrix (code, channel) inside a dequant table.
+int dequant_offset(int code, int channel);
+
+// C.6.1 default matrices, val = numerators / weights, [code][c][H][W]
+// row-major in dequant_offset order.  Returns false if an entry outside the
+// LLF slots is non-positive or not finite.
+bool default_dequant(float* out /* kDequantFloats */);
+
+// Multiplies a raw dequant table by the per-frequency scale of the draft's
+// inverse transforms so the kernels can run unscaled cosine sums.
+void prescale_dequant(const float* raw, float* scaled);
+
+// Checks a caller table (C.6.1: non-positive or infinite entries are
+// ill-formed).  LLF slots are not inspected.
+bool dequant_valid(const float* table);
+
+// I.2.7 LLF-from-DC maps for the DCT shapes, already multiplied by the
+// transform scale: llf[j] = sum_i M[j][i] dc[i], j and i row-major over the
+// cy x cx LLF block.  Index by llf_map_index(cx, cy); 16x16 floats each.
+constexpr int kLlfMaps = 8;
+int llf_map_index(int cx, int cy);
+void llf_maps(float* out /* kLlfMaps * 256 */);
+
+// Odd-part matrices of the unscaled N-point inverse DCT for N = 2..32:
+// O_N[n][j] = cos((2n+1)(2j+1) pi / 2N), n, j < N/2, packed N = 32, 16, 8, 4, 2.
+constexpr int kOddFloats = 256 + 64 + 16 + 4 + 1;
+void odd_tables(float* out);
+
+// 4 * mul_table[sigma] of J.2.4 for sigma in [0, 672]; entries below 16 are 0.
+void mul_table4(int32_t* out /* 673 */);
+
+// AFV basis of I.2.2, [coefficient][sample], 16 x 16.
+extern const double kAfvBasis[16][16];
+
+// Device-side constant setup (kernels.cu): copies the tables above into
+// __constant__ memory of the current device.
+bool upload_constants(const float* llf, const float* odd, const int32_t* mul4,
+                      const float* afv);
+
+}  // namespace jxlr

@@ -1,0 +1,886 @@
+// CUDA kernels of VarDCT pixel reconstruction for sm_103a (GB300).
+//
+//   k_validate  C.5.4: the DctSelect map must tile the image with naturally
+//               aligned, in-bounds varblocks.
+//   k_recon     one 32x32 cell per CTA (varblocks are naturally aligned and
+//               at most 32x32, so each lies inside one cell):
+//               F.2/F.3 dequantisation with 128-bit int16 loads, G chroma
+//               from luma, I.2.7 LLF from DC, I.2.4 inverse transforms of
+//               all 15 shapes in shared memory (row pass, column pass), then
+//               either L.2 colour + store, or planar XYB + the J.2.4 sigma
+//               of every 8x8 block.
+//   k_sigma     the J.2.4 sigma pass alone, for XYB supplied by the caller.
+//   k_filter    one output tile per CTA: J.2 edge-preserving filter on the
+//               tile plus a one-sample ring, J.4 Gaborish, L.2 colour, store.
+//
+// The inverse transforms run as unscaled cosine sums
+// x[n] = sum_k c[k] cos((2n+1) k pi / 2N); the per-frequency scale of the
+// draft's transforms is folded into the dequantisation tables and the LLF
+// maps on the host.  The 1-D sums use the even/odd split
+// x[n] = E[n] + O[n], x[N-1-n] = E[n] - O[n] recursively, with the odd-part
+// cosine matrices in constant memory.
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "internal.h"
+#include "kernels.h"
+
+namespace jxlr {
+
+__constant__ float c_llf[kLlfMaps * 256];
+__constant__ float c_odd[kOddFloats];
+__constant__ int32_t c_mul4[673];
+__constant__ float c_afv[256];
+__constant__ int c_shape_w[kNumCodes];
+__constant__ int c_shape_h[kNumCodes];
+__constant__ int c_dq_off[kNumCodes];
+
+bool upload_constants(const float* llf, const float* odd, const int32_t* mul4,
+                      const float* afv) {
+  int offs[kNumCodes];
+  for (int c = 0; c < kNumCodes; ++c) offs[c] = dequant_offset(c, 0);
+  return cudaMemcpyToSymbol(c_llf, llf, sizeof(float) * kLlfMaps * 256) == cudaSuccess &&
+         cudaMemcpyToSymbol(c_odd, odd, sizeof(float) * kOddFloats) == cudaSuccess &&
+         cudaMemcpyToSymbol(c_mul4, mul4, sizeof(int32_t) * 673) == cudaSuccess &&
+         cudaMemcpyToSymbol(c_afv, afv, sizeof(float) * 256) == cudaSuccess &&
+         cudaMemcpyToSymbol(c_shape_w, kShapeW, sizeof(int) * kNumCodes) == cudaSuccess &&
+         cudaMemcpyToSymbol(c_shape_h, kShapeH, sizeof(int) * kNumCodes) == cudaSuccess &&
+         cudaMemcpyToSymbol(c_dq_off, offs, sizeof(int) * kNumCodes) == cudaSuccess;
+}
+
+// ---------------------------------------------------------------------------
+// small helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int llf_map_index_dev(int cx, int cy) {
+  // same order as llf_map_index() on the host
+  if (cx == 2 && cy == 2) return 0;
+  if (cx == 4 && cy == 4) return 1;
+  if (cx == 1 && cy == 2) return 2;
+  if (cx == 2 && cy == 1) return 3;
+  if (cx == 1 && cy == 4) return 4;
+  if (cx == 4 && cy == 1) return 5;
+  if (cx == 2 && cy == 4) return 6;
+  return 7;  // (4, 2)
+}
+
+__device__ __forceinline__ int mirror_coord(int c, int size) {
+  // 6.5: reflect until inside [0, size)
+  while (c < 0 || c >= size) c = c < 0 ? -c - 1 : 2 * size - 1 - c;
+  return c;
+}
+
+template <int N> struct OddOff;
+template <> struct OddOff<32> { static constexpr int v = 0; };
+template <> struct OddOff<16> { static constexpr int v = 256; };
+template <> struct OddOff<8> { static constexpr int v = 320; };
+template <> struct OddOff<4> { static constexpr int v = 336; };
+template <> struct OddOff<2> { static constexpr int v = 340; };
+
+// Unscaled N-point inverse DCT in registers (even/odd recursion).
+template <int N>
+__device__ __forceinline__ void idct1d(float (&x)[N]) {
+  if constexpr (N > 1) {
+    constexpr int H = N / 2;
+    float e[H], o[H];
+#pragma unroll
+    for (int j = 0; j < H; ++j) e[j] = x[2 * j];
+    idct1d<H>(e);
+#pragma unroll
+    for (int n = 0; n < H; ++n) {
+      float s = 0.f;
+#pragma unroll
+      for (int j = 0; j < H; ++j) s = fmaf(x[2 * j + 1], c_odd[OddOff<N>::v + n * H + j], s);
+      o[n] = s;
+    }
+#pragma unroll
+    for (int n = 0; n < H; ++n) {
+      x[n] = e[n] + o[n];
+      x[N - 1 - n] = e[n] - o[n];
+    }
+  }
+}
+
+// src, dst: contiguous in shared memory, 16-byte aligned.
+template <int N>
+__device__ __forceinline__ void row_idct(const float* src, float* dst) {
+  float x[N];
+#pragma unroll
+  for (int i = 0; i < N; i += 4) {
+    float4 v = *reinterpret_cast<const float4*>(src + i);
+    x[i] = v.x; x[i + 1] = v.y; x[i + 2] = v.z; x[i + 3] = v.w;
+  }
+  idct1d<N>(x);
+#pragma unroll
+  for (int i = 0; i < N; i += 4)
+    *reinterpret_cast<float4*>(dst + i) = make_float4(x[i], x[i + 1], x[i + 2], x[i + 3]);
+}
+
+template <int N>
+__device__ __forceinline__ void col_idct(const float* src, float* dst, int stride) {
+  float x[N];
+#pragma unroll
+  for (int i = 0; i < N; ++i) x[i] = src[i * stride];
+  idct1d<N>(x);
+#pragma unroll
+  for (int i = 0; i < N; ++i) dst[i * stride] = x[i];
+}
+
+// Two interleaved 4-point transforms of an 8-vector: even entries -> samples
+// 0..3, odd entries -> samples 4..7 (DCT4 and the 4-point axis of 8x4 / 4x8).
+__device__ __forceinline__ void pair4(const float* src, int sstride, float* dst, int dstride) {
+  float a[4], b[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    a[i] = src[(2 * i) * sstride];
+    b[i] = src[(2 * i + 1) * sstride];
+  }
+  idct1d<4>(a);
+  idct1d<4>(b);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    dst[i * dstride] = a[i];
+    dst[(4 + i) * dstride] = b[i];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// L.2 colour and the output encodings
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void xyb_to_rgb01(const ColorParams& cp, float X, float Y, float B,
+                                             float& r, float& g, float& b) {
+  const float rg = Y + X, gg = Y - X, bg = B;
+  const float mr = rg * rg * rg + cp.bias[0];
+  const float mg = gg * gg * gg + cp.bias[1];
+  const float mb = bg * bg * bg + cp.bias[2];
+  r = fmaf(cp.m[0], mr, fmaf(cp.m[1], mg, cp.m[2] * mb));
+  g = fmaf(cp.m[3], mr, fmaf(cp.m[4], mg, cp.m[5] * mb));
+  b = fmaf(cp.m[6], mr, fmaf(cp.m[7], mg, cp.m[8] * mb));
+}
+
+__device__ __forceinline__ uint32_t srgb8(float v) {
+  float x = fminf(fmaxf(v, 0.f), 1.f);
+  float e = x <= 0.0031308f ? 12.92f * x : fmaf(1.055f, powf(x, 1.f / 2.4f), -0.055f);
+  return static_cast<uint32_t>(floorf(fmaf(e, 255.f, 0.5f)));
+}
+
+// Stores n (1..4) consecutive pixels of one row starting at column px.
+// v[3 * i + c]: channel c of pixel i (XYB or linear RGB01 by dtype).
+__device__ __forceinline__ void store_px4(const OutParams& o, int px, int py, const float* v,
+                                          int n) {
+  char* row = static_cast<char*>(o.data) + static_cast<size_t>(py) * o.stride;
+  if (o.dtype == 0 || o.dtype == 3) {
+    float* p = reinterpret_cast<float*>(row) + 3 * px;
+    if (n == 4 && (reinterpret_cast<uintptr_t>(p) & 15) == 0) {
+      float4* q = reinterpret_cast<float4*>(p);
+      q[0] = make_float4(v[0], v[1], v[2], v[3]);
+      q[1] = make_float4(v[4], v[5], v[6], v[7]);
+      q[2] = make_float4(v[8], v[9], v[10], v[11]);
+    } else {
+      for (int i = 0; i < 3 * n; ++i) p[i] = v[i];
+    }
+  } else if (o.dtype == 1) {
+    __half* p = reinterpret_cast<__half*>(row) + 3 * px;
+    if (n == 4 && (reinterpret_cast<uintptr_t>(p) & 7) == 0) {
+      uint2* q = reinterpret_cast<uint2*>(p);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        __half2 h0 = __floats2half2_rn(v[4 * k], v[4 * k + 1]);
+        __half2 h1 = __floats2half2_rn(v[4 * k + 2], v[4 * k + 3]);
+        q[k] = make_uint2(*reinterpret_cast<uint32_t*>(&h0), *reinterpret_cast<uint32_t*>(&h1));
+      }
+    } else {
+      for (int i = 0; i < 3 * n; ++i) p[i] = __float2half_rn(v[i]);
+    }
+  } else {
+    uint8_t* p = reinterpret_cast<uint8_t*>(row) + 3 * px;
+    if (n == 4 && (reinterpret_cast<uintptr_t>(p) & 3) == 0) {
+      uint32_t* q = reinterpret_cast<uint32_t*>(p);
+#pragma unroll
+      for (int k = 0; k < 3; ++k)
+        q[k] = srgb8(v[4 * k]) | (srgb8(v[4 * k + 1]) << 8) | (srgb8(v[4 * k + 2]) << 16) |
+               (srgb8(v[4 * k + 3]) << 24);
+    } else {
+      for (int i = 0; i < 3 * n; ++i) p[i] = static_cast<uint8_t>(srgb8(v[i]));
+    }
+  }
+}
+
+// Converts (unless XYB output) and stores 4 pixels given as planar XYB.
+__device__ __forceinline__ void emit4(const ColorParams& cp, const OutParams& o, int px, int py,
+                                      int n, const float* X, const float* Y, const float* B) {
+  float v[12];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    if (o.dtype == 3) {
+      v[3 * i] = X[i]; v[3 * i + 1] = Y[i]; v[3 * i + 2] = B[i];
+    } else {
+      xyb_to_rgb01(cp, X[i], Y[i], B[i], v[3 * i], v[3 * i + 1], v[3 * i + 2]);
+    }
+  }
+  store_px4(o, px, py, v, n);
+}
+
+// J.2.2 scaled guide value in binary32, operation by operation.
+__device__ __forceinline__ float guide_scaled(const SigmaParams& sp, int c, float v) {
+  return __fmul_rn(__fsub_rn(v, sp.gmin[c]), sp.gscale[c]);
+}
+
+// ---------------------------------------------------------------------------
+// k_validate
+// ---------------------------------------------------------------------------
+__global__ void k_validate(const uint8_t* __restrict__ vmap, int bw, int bh, unsigned* st) {
+  __shared__ unsigned s_area, s_err;
+  if (threadIdx.x == 0) { s_area = 0; s_err = 0; }
+  __syncthreads();
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  unsigned area = 0, err = 0;
+  if (i < bw * bh) {
+    const int bx = i % bw, by = i / bw;
+    const unsigned code = vmap[i];
+    if (code != kCovered) {
+      if (code >= kNumCodes) {
+        err |= 1;
+      } else {
+        const int w8 = c_shape_w[code] / 8, h8 = c_shape_h[code] / 8;
+        if (bx % w8 || by % h8) {
+          err |= 2;
+        } else if (bx + w8 > bw || by + h8 > bh) {
+          err |= 4;
+        } else {
+          area = w8 * h8;
+          for (int yy = 0; yy < h8; ++yy)
+            for (int xx = 0; xx < w8; ++xx)
+              if ((xx | yy) && vmap[(by + yy) * bw + bx + xx] != kCovered) err |= 8;
+        }
+      }
+    }
+  }
+  if (area) atomicAdd(&s_area, area);
+  if (err) atomicOr(&s_err, err);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (s_area) atomicAdd(&st[1], s_area);
+    if (s_err) atomicOr(&st[0], s_err);
+    __threadfence();
+    const unsigned done = atomicAdd(&st[2], 1u);
+    if (done == gridDim.x - 1) {
+      __threadfence();
+      const unsigned total = atomicAdd(&st[1], 0u);
+      if (total != static_cast<unsigned>(bw * bh)) atomicOr(&st[0], 16u);
+    }
+  }
+}
+
+void launch_validate(const uint8_t* vmap, int bw, int bh, unsigned* status, cudaStream_t s) {
+  const int n = bw * bh;
+  k_validate<<<(n + 255) / 256, 256, 0, s>>>(vmap, bw, bh, status);
+}
+
+// ---------------------------------------------------------------------------
+// k_recon
+// ---------------------------------------------------------------------------
+constexpr int kRS = 36;  // shared row stride in floats: 16-byte rows, no bank
+                         // conflicts for row-per-thread float4 access
+
+struct CellVB {
+  int code, bx, by;      // code and top-left block inside the cell (0..3)
+  float acmul;
+};
+
+struct CellState {
+  CellVB vb[16];
+  int nvb;
+  int owner[16];         // per in-cell block: index into vb, or -1
+  int row_pre[17];       // prefix sums of row-phase items
+  int col_pre[17];       // prefix sums of column-phase items
+  float brange[16];      // per block: max over channels of the scaled range
+};
+
+__device__ __forceinline__ bool separable(int code) {
+  return code != kIdentity && code != kDCT2 && code != kAFV;
+}
+
+__device__ __forceinline__ int row_items(int code) {
+  if (code == kIdentity || code == kDCT2) return 3;   // whole block per channel
+  if (code == kAFV) return 12;                          // 4 quadrants x 3 channels
+  return 3 * c_shape_h[code];
+}
+
+__device__ __forceinline__ int col_items(int code) { return 3 * c_shape_w[code]; }
+
+// Row pass of one item.  S: coefficients, T: output of the pass.
+__device__ void row_item(float (*S)[32][kRS], float (*T)[32][kRS], const CellVB& v, int k) {
+  const int code = v.code;
+  const int x0 = 8 * v.bx, y0 = 8 * v.by;
+  if (code == kDCT2) {
+    // I.2.4.2: AuxIDCT2x2 at S = 2, 4, 8; ping-pong between S and T.
+    const int c = k;
+    float* s = &S[c][y0][x0];
+    float* t = &T[c][y0][x0];
+    for (int y = 0; y < 8; ++y)
+      for (int x = 0; x < 8; ++x) t[y * kRS + x] = s[y * kRS + x];
+    float* src = s;
+    float* dst = t;
+    for (int lv = 2; lv <= 8; lv *= 2) {
+      const int h = lv / 2;
+      for (int y = 0; y < h; ++y) {
+        for (int x = 0; x < h; ++x) {
+          const float c00 = src[y * kRS + x], c01 = src[y * kRS + h + x];
+          const float c10 = src[(y + h) * kRS + x], c11 = src[(y + h) * kRS + h + x];
+          dst[(2 * y) * kRS + 2 * x] = c00 + c01 + c10 + c11;
+          dst[(2 * y) * kRS + 2 * x + 1] = c00 + c01 - c10 - c11;
+          dst[(2 * y + 1) * kRS + 2 * x] = c00 - c01 + c10 - c11;
+          dst[(2 * y + 1) * kRS + 2 * x + 1] = c00 - c01 - c10 + c11;
+        }
+      }
+      float* tmp = src; src = dst; dst = tmp;
+    }
+    // after three levels the result is in T (levels write T, S, T)
+    return;
+  }
+  if (code == kIdentity) {
+    // I.2.4.4
+    const int c = k;
+    const float* s = &S[c][y0][x0];
+    float* t = &T[c][y0][x0];
+    const float c00 = s[0], c01 = s[1], c10 = s[kRS], c11 = s[kRS + 1];
+    const float dcs[2][2] = {{c00 + c01 + c10 + c11, c00 + c01 - c10 - c11},
+                             {c00 - c01 + c10 - c11, c00 - c01 - c10 + c11}};
+    for (int y = 0; y < 2; ++y) {
+      for (int x = 0; x < 2; ++x) {
+        float rs = 0.f;
+        for (int iy = 0; iy < 4; ++iy)
+          for (int ix = 0; ix < 4; ++ix)
+            if (ix | iy) rs += s[(y + 2 * iy) * kRS + x + 2 * ix];
+        const float s11 = dcs[y][x] - rs * (1.f / 16.f);
+        for (int iy = 0; iy < 4; ++iy)
+          for (int ix = 0; ix < 4; ++ix) {
+            float v2;
+            if (ix == 1 && iy == 1) v2 = s11;
+            else if (ix == 0 && iy == 0) v2 = s[(y + 2) * kRS + x + 2] + s11;
+            else v2 = s[(y + 2 * iy) * kRS + x + 2 * ix] + s11;
+            t[(4 * y + iy) * kRS + 4 * x + ix] = v2;
+          }
+      }
+    }
+    return;
+  }
+  if (code == kAFV) {
+    // I.2.4.7: quadrant q = (x, y), channel c
+    const int c = k / 4, q = k % 4, qx = q & 1, qy = q >> 1;
+    const float* s = &S[c][y0][x0];
+    float* t = &T[c][y0][x0];
+    const float a1 = 4.f * s[0], a2 = 4.f * s[1], a3 = 4.f * s[kRS], a4 = 4.f * s[kRS + 1];
+    float dc;
+    if (q == 0) dc = a1 + a2 + a3 + a4;
+    else if (q == 1) dc = a1 + a2 - a3 - a4;
+    else if (q == 2) dc = a1 - a2 + a3 - a4;
+    else dc = a1 - a2 - a3 + a4;
+    float in[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      const int ix = j & 3, iy = j >> 2;
+      in[j] = j == 0 ? dc : s[(qy + 2 * iy) * kRS + qx + 2 * ix];
+    }
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      float acc = 0.f;
+#pragma unroll
+      for (int j = 0; j < 16; ++j) acc = fmaf(in[j], c_afv[j * 16 + i], acc);
+      const int sx = i & 3, sy = i >> 2;                 // sample inside AFV order
+      const int ix = qx ? 3 - sx : sx, iy = qy ? 3 - sy : sy;
+      t[(4 * qy + iy) * kRS + 4 * qx + ix] = acc;
+    }
+    return;
+  }
+  // separable shapes: item = (channel, row)
+  const int H = c_shape_h[code];
+  const int c = k / H, r = k % H;
+  const float* src = &S[c][y0 + r][x0];
+  float* dst = &T[c][y0 + r][x0];
+  switch (code) {
+    case kDCT8: case kDCT16x8: case kDCT32x8: case kDCT4x8: row_idct<8>(src, dst); break;
+    case kDCT16: case kDCT8x16: case kDCT32x16: row_idct<16>(src, dst); break;
+    case kDCT32: case kDCT8x32: case kDCT16x32: row_idct<32>(src, dst); break;
+    case kDCT4: case kDCT8x4: pair4(src, 1, dst, 1); break;
+    default: break;
+  }
+}
+
+// Column pass of one item: T -> S.
+__device__ void col_item(float (*S)[32][kRS], float (*T)[32][kRS], const CellVB& v, int k) {
+  const int code = v.code;
+  const int W = c_shape_w[code];
+  const int c = k / W, col = k % W;
+  const int x0 = 8 * v.bx, y0 = 8 * v.by;
+  const float* src = &T[c][y0][x0 + col];
+  float* dst = &S[c][y0][x0 + col];
+  switch (code) {
+    case kDCT8: case kDCT8x16: case kDCT8x32: case kDCT8x4: col_idct<8>(src, dst, kRS); break;
+    case kDCT16: case kDCT16x8: case kDCT16x32: col_idct<16>(src, dst, kRS); break;
+    case kDCT32: case kDCT32x8: case kDCT32x16: col_idct<32>(src, dst, kRS); break;
+    case kDCT4: case kDCT4x8: pair4(src, kRS, dst, kRS); break;
+    default:  // Identity, DCT2, AFV: the row pass already produced samples
+#pragma unroll
+      for (int i = 0; i < 8; ++i) dst[i * kRS] = src[i * kRS];
+      break;
+  }
+}
+
+// J.2.4 per-block sigma for the 16 blocks of the cell held in S (channel
+// planes, 32 x 32).  Requires cs.owner and cs.vb; 128 threads.
+__device__ void cell_sigma(float (*S)[32][kRS], CellState& cs, const SigmaParams& sp,
+                           int gbx0, int gby0, int xs, int ys, int bw, int bh,
+                           const float* __restrict__ acmul, const uint8_t* __restrict__ sharp,
+                           int16_t* __restrict__ sigma) {
+  const int tid = threadIdx.x;
+  {
+    const int b = tid >> 3, r = tid & 7;        // block b (0..15), row r
+    const int lx0 = 8 * (b & 3), ly = 8 * (b >> 2) + r;
+    const int gy = gby0 * 8 + ly;
+    float rmax = -1.f;
+    bool any = false;
+    float mn[3], mx[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) { mn[c] = 3.0e38f; mx[c] = -3.0e38f; }
+    if (gy < ys) {
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int gx = gbx0 * 8 + lx0 + j;
+        if (gx < xs) {
+          any = true;
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            const float s = guide_scaled(sp, c, S[c][ly][lx0 + j]);
+            mn[c] = fminf(mn[c], s);
+            mx[c] = fmaxf(mx[c], s);
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int off = 1; off < 8; off <<= 1) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        mn[c] = fminf(mn[c], __shfl_xor_sync(0xffffffffu, mn[c], off));
+        mx[c] = fmaxf(mx[c], __shfl_xor_sync(0xffffffffu, mx[c], off));
+      }
+      any = any | (__shfl_xor_sync(0xffffffffu, static_cast<int>(any), off) != 0);
+    }
+    if (any) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) rmax = fmaxf(rmax, __fsub_rn(mx[c], mn[c]));
+    }
+    if (r == 0) cs.brange[b] = any ? rmax : -1.f;
+  }
+  __syncthreads();
+  if (tid < 16) {
+    const int b = tid, gbx = gbx0 + (b & 3), gby = gby0 + (b >> 2);
+    const int o = cs.owner[b];
+    if (o < 0 && gbx < bw && gby < bh) {
+      sigma[gby * bw + gbx] = 0;   // not covered (ill-formed map): unfiltered
+    } else if (o >= 0 && gbx < bw && gby < bh && gbx * 8 < xs && gby * 8 < ys) {
+      const CellVB& v = cs.vb[o];
+      const int w8 = c_shape_w[v.code] / 8, h8 = c_shape_h[v.code] / 8;
+      float rng = 0.f;
+      for (int yy = 0; yy < h8; ++yy)
+        for (int xx = 0; xx < w8; ++xx) rng = fmaxf(rng, cs.brange[(v.by + yy) * 4 + v.bx + xx]);
+      const int bi = gby * bw + gbx;
+      float sg = __fmul_rn(fminf(rng, sp.range_max), sp.range_mul);
+      sg = __fmul_rn(sg, sp.lut[sharp[bi] & 7]);
+      const float quant = __frcp_rn(acmul[bi]);
+      sg = fminf(sg, __fmul_rn(quant, sp.quant_mul));
+      sg = fminf(sg, sp.sigma_max);
+      int si = static_cast<int>(truncf(sg));
+      if (si > 672) si = 672;
+      if (si < 0) si = 0;
+      sigma[bi] = static_cast<int16_t>(si);
+    }
+  }
+}
+
+// Loads the cell's map entries and builds the varblock list (sorted by code
+// so that warps of the transform passes mostly share a shape).
+__device__ void cell_setup(CellState& cs, const uint8_t* __restrict__ vmap,
+                           const float* __restrict__ acmul, int gbx0, int gby0, int bw,
+                           int bh) {
+  __shared__ int s_code[16];
+  __shared__ float s_am[16];
+  const int tid = threadIdx.x;
+  if (tid < 16) {
+    const int gbx = gbx0 + (tid & 3), gby = gby0 + (tid >> 2);
+    int code = kCovered;
+    float am = 1.f;
+    if (gbx < bw && gby < bh) {
+      code = vmap[gby * bw + gbx];
+      am = acmul[gby * bw + gbx];
+    }
+    s_code[tid] = code;
+    s_am[tid] = am;
+    cs.owner[tid] = -1;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    int n = 0;
+    for (int b = 0; b < 16; ++b) {
+      const int code = s_code[b];
+      if (code >= kNumCodes) continue;
+      const int bx = b & 3, by = b >> 2;
+      const int w8 = c_shape_w[code] / 8, h8 = c_shape_h[code] / 8;
+      // ill-formed placements are reported by k_validate; skip them here
+      if (bx % w8 || by % h8 || bx + w8 > 4 || by + h8 > 4) continue;
+      if (gbx0 + bx + w8 > bw || gby0 + by + h8 > bh) continue;
+      CellVB v;
+      v.code = code; v.bx = bx; v.by = by; v.acmul = s_am[b];
+      int i = n++;
+      while (i > 0 && cs.vb[i - 1].code > code) { cs.vb[i] = cs.vb[i - 1]; --i; }
+      cs.vb[i] = v;
+    }
+    cs.nvb = n;
+    cs.row_pre[0] = cs.col_pre[0] = 0;
+    for (int i = 0; i < n; ++i) {
+      const CellVB& v = cs.vb[i];
+      const int w8 = c_shape_w[v.code] / 8, h8 = c_shape_h[v.code] / 8;
+      for (int yy = 0; yy < h8; ++yy)
+        for (int xx = 0; xx < w8; ++xx) cs.owner[(v.by + yy) * 4 + v.bx + xx] = i;
+      cs.row_pre[i + 1] = cs.row_pre[i] + row_items(v.code);
+      cs.col_pre[i + 1] = cs.col_pre[i] + col_items(v.code);
+    }
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(128) k_recon(const ReconArgs a) {
+  __shared__ __align__(16) float S[3][32][kRS];
+  __shared__ __align__(16) float T[3][32][kRS];
+  __shared__ CellState cs;
+  const int tid = threadIdx.x;
+  const int gbx0 = blockIdx.x * 4, gby0 = blockIdx.y * 4;
+  const int px0 = gbx0 * 8, py0 = gby0 * 8;
+
+  cell_setup(cs, a.vmap, a.acmul, gbx0, gby0, a.bw, a.bh);
+
+  // ---- F.2 / F.3 / G: one 8-sample row chunk of all three channels -------
+  {
+    const int y = tid >> 2, k = tid & 3;   // cell row, 8-column chunk
+    const int gy = py0 + y, gx = px0 + 8 * k;
+    const int b = (y >> 3) * 4 + k;
+    const int o = cs.owner[b];
+    float out[3][8];
+    if (o >= 0 && gy < a.hp && gx < a.wp) {
+      const CellVB v = cs.vb[o];
+      const int W = c_shape_w[v.code], H = c_shape_h[v.code];
+      const int u0 = 8 * k - 8 * v.bx, vv = y - 8 * v.by;
+      const int cxl = W >> 3, cyl = H >> 3;
+      const int tile = (gy >> 6) * a.tw + (gx >> 6);
+      const float kx = a.cfl[2 * tile], kb = a.cfl[2 * tile + 1];
+      float q[3][8];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const int4 raw = __ldg(reinterpret_cast<const int4*>(a.coef[c] + gy * a.cstride + gx));
+        const int16_t* h = reinterpret_cast<const int16_t*>(&raw);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) q[c][j] = static_cast<float>(h[j]);
+      }
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const float* m = a.dequant + c_dq_off[v.code] + c * W * H + vv * W + u0;
+        const float4 m0 = __ldg(reinterpret_cast<const float4*>(m));
+        const float4 m1 = __ldg(reinterpret_cast<const float4*>(m + 4));
+        const float mm[8] = {m0.x, m0.y, m0.z, m0.w, m1.x, m1.y, m1.z, m1.w};
+        const float omb = a.one_minus_bias[c];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const float qq = q[c][j];
+          const float adj = fabsf(qq) <= 1.f ? qq * omb : qq - __fdividef(0.145f, qq);
+          out[c][j] = adj * v.acmul * mm[j];
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const bool llf = (u0 + j) < cxl && vv < cyl;
+        if (llf) {
+          const float dx = a.m_dc[0] * q[0][j], dy = a.m_dc[1] * q[1][j], db = a.m_dc[2] * q[2][j];
+          out[0][j] = fmaf(a.kx_dc, dy, dx);
+          out[1][j] = dy;
+          out[2][j] = fmaf(a.kb_dc, dy, db);
+        } else {
+          out[0][j] = fmaf(kx, out[1][j], out[0][j]);
+          out[2][j] = fmaf(kb, out[1][j], out[2][j]);
+        }
+      }
+    } else {
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) out[c][j] = 0.f;
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      float4* d = reinterpret_cast<float4*>(&S[c][y][8 * k]);
+      d[0] = make_float4(out[c][0], out[c][1], out[c][2], out[c][3]);
+      d[1] = make_float4(out[c][4], out[c][5], out[c][6], out[c][7]);
+    }
+  }
+  __syncthreads();
+
+  // ---- I.2.7 LLF from DC, and the DC pre-steps of DCT4 / 8x4 / 4x8 -------
+  if (tid < 3 * cs.nvb) {
+    const CellVB v = cs.vb[tid / 3];
+    const int c = tid % 3;
+    float* s = &S[c][8 * v.by][8 * v.bx];
+    const int cxl = c_shape_w[v.code] >> 3, cyl = c_shape_h[v.code] >> 3;
+    const int n = cxl * cyl;
+    if (n > 1) {
+      const float* mp = c_llf + llf_map_index_dev(cxl, cyl) * 256;
+      float dc[16], r[16];
+      for (int i = 0; i < n; ++i) dc[i] = s[(i / cxl) * kRS + i % cxl];
+      for (int j = 0; j < n; ++j) {
+        float acc = 0.f;
+        for (int i = 0; i < n; ++i) acc = fmaf(mp[j * 16 + i], dc[i], acc);
+        r[j] = acc;
+      }
+      for (int j = 0; j < n; ++j) s[(j / cxl) * kRS + j % cxl] = r[j];
+    } else if (v.code == kDCT4) {
+      const float c00 = s[0], c01 = s[1], c10 = s[kRS], c11 = s[kRS + 1];
+      s[0] = c00 + c01 + c10 + c11;
+      s[1] = c00 + c01 - c10 - c11;
+      s[kRS] = c00 - c01 + c10 - c11;
+      s[kRS + 1] = c00 - c01 - c10 + c11;
+    } else if (v.code == kDCT8x4) {
+      const float c0 = s[0], c1 = s[1];
+      s[0] = c0 + c1;
+      s[1] = c0 - c1;
+    } else if (v.code == kDCT4x8) {
+      const float c0 = s[0], c1 = s[kRS];
+      s[0] = c0 + c1;
+      s[kRS] = c0 - c1;
+    }
+  }
+  __syncthreads();
+
+  // ---- I.2.4 row pass ------------------------------------------------------
+  {
+    const int total = cs.row_pre[cs.nvb];
+    int vi = 0;
+    for (int it = tid; it < total; it += blockDim.x) {
+      while (it >= cs.row_pre[vi + 1]) ++vi;
+      row_item(S, T, cs.vb[vi], it - cs.row_pre[vi]);
+    }
+  }
+  __syncthreads();
+  // ---- column pass ---------------------------------------------------------
+  {
+    const int total = cs.col_pre[cs.nvb];
+    int vi = 0;
+    for (int it = tid; it < total; it += blockDim.x) {
+      while (it >= cs.col_pre[vi + 1]) ++vi;
+      col_item(S, T, cs.vb[vi], it - cs.col_pre[vi]);
+    }
+  }
+  __syncthreads();
+
+  // ---- output ---------------------------------------------------------------
+  if (a.write_xyb) {
+    // planar XYB [3][hp][wp], float4 per thread step
+    for (int i = tid; i < 3 * 32 * 8; i += blockDim.x) {
+      const int c = i / 256, y = (i >> 3) & 31, k4 = i & 7;
+      const int gy = py0 + y, gx = px0 + 4 * k4;
+      if (gy < a.hp && gx < a.wp) {
+        const float4 v4 = *reinterpret_cast<const float4*>(&S[c][y][4 * k4]);
+        *reinterpret_cast<float4*>(a.xyb + (static_cast<size_t>(c) * a.hp + gy) * a.wp + gx) = v4;
+      }
+    }
+    if (a.sigma)
+      cell_sigma(S, cs, a.sp, gbx0, gby0, a.xs, a.ys, a.bw, a.bh, a.acmul, a.sharp, a.sigma);
+  } else {
+    for (int i = tid; i < 32 * 8; i += blockDim.x) {
+      const int y = i >> 3, k4 = i & 7;
+      const int gy = py0 + y, gx = px0 + 4 * k4;
+      if (gy < a.ys && gx < a.xs) {
+        const int n = min(4, a.xs - gx);
+        emit4(a.cp, a.out, gx, gy, n, &S[0][y][4 * k4], &S[1][y][4 * k4], &S[2][y][4 * k4]);
+      }
+    }
+  }
+}
+
+void launch_recon(const ReconArgs& a, cudaStream_t s) {
+  dim3 grid((a.wp + 31) / 32, (a.hp + 31) / 32);
+  k_recon<<<grid, 128, 0, s>>>(a);
+}
+
+// ---------------------------------------------------------------------------
+// k_sigma: J.2.4 sigma from caller-supplied XYB
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(128) k_sigma(const SigmaArgs a) {
+  __shared__ __align__(16) float S[3][32][kRS];
+  __shared__ CellState cs;
+  const int tid = threadIdx.x;
+  const int gbx0 = blockIdx.x * 4, gby0 = blockIdx.y * 4;
+  cell_setup(cs, a.vmap, a.acmul, gbx0, gby0, a.bw, a.bh);
+  for (int i = tid; i < 3 * 32 * 32; i += blockDim.x) {
+    const int c = i >> 10, y = (i >> 5) & 31, x = i & 31;
+    const int gy = gby0 * 8 + y, gx = gbx0 * 8 + x;
+    S[c][y][x] = (gy < a.ys && gx < a.xs) ? a.xyb[c * a.pstride + gy * a.rstride + gx] : 0.f;
+  }
+  __syncthreads();
+  cell_sigma(S, cs, a.sp, gbx0, gby0, a.xs, a.ys, a.bw, a.bh, a.acmul, a.sharp, a.sigma);
+}
+
+void launch_sigma(const SigmaArgs& a, cudaStream_t s) {
+  dim3 grid((a.bw + 3) / 4, (a.bh + 3) / 4);
+  k_sigma<<<grid, 128, 0, s>>>(a);
+}
+
+// ---------------------------------------------------------------------------
+// k_filter: EPF (J.2) + Gaborish (J.4) + colour (L.2) on a 32 x 32 tile
+// ---------------------------------------------------------------------------
+constexpr int kTW = 32, kTH = 32;
+constexpr int kGX = 5, kGY = 5;                 // halo before the tile
+constexpr int kGW = kTW + 12, kGH = kTH + 10;   // guide/sample window
+constexpr int kEW = kTW + 2, kEH = kTH + 2;     // EPF output with a 1-sample ring
+
+__global__ void __launch_bounds__(256) k_filter(const FilterArgs a) {
+  __shared__ float F[3][kGH][kGW];
+  __shared__ uint32_t G[kGH][kGW];
+  __shared__ float E[3][kEH][kEW];
+  const int tid = threadIdx.x;
+  const int x0 = blockIdx.x * kTW, y0 = blockIdx.y * kTH;
+  const int wx0 = x0 - kGX, wy0 = y0 - kGY;     // window origin (image coords)
+
+  // ---- load the window with mirrored coordinates (6.5) --------------------
+  for (int i = tid; i < kGH * kGW; i += blockDim.x) {
+    const int ly = i / kGW, lx = i % kGW;
+    const int gy = mirror_coord(wy0 + ly, a.ys), gx = mirror_coord(wx0 + lx, a.xs);
+    const size_t off = static_cast<size_t>(gy) * a.rstride + gx;
+    float v[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      v[c] = __ldg(a.xyb + c * a.pstride + off);
+      F[c][ly][lx] = v[c];
+    }
+    if (a.epf) {
+      uint32_t g = 0;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const float s = fminf(fmaxf(guide_scaled(a.sp, c, v[c]), 0.f), 255.f);
+        g |= static_cast<uint32_t>(s) << (8 * c);
+      }
+      G[ly][lx] = g;
+    }
+  }
+  __syncthreads();
+
+  // ---- J.2 on the tile plus a one-sample ring ------------------------------
+  const int R = a.gab ? 1 : 0;
+  if (a.epf) {
+    const int ew = kTW + 2 * R, eh = kTH + 2 * R;
+    for (int i = tid; i < ew * eh; i += blockDim.x) {
+      const int qy = i / ew - R, qx = i % ew - R;          // tile-relative
+      const int gy = y0 + qy, gx = x0 + qx;
+      if (gy >= a.ys + 1 || gx >= a.xs + 1) continue;      // beyond the ring
+      const int cy = mirror_coord(gy, a.ys), cx = mirror_coord(gx, a.xs);
+      const int ly = cy - wy0, lx = cx - wx0;              // window coords
+      const int sigma = min(max(static_cast<int>(a.sigma[(cy >> 3) * a.bw + (cx >> 3)]), 0), 672);
+      float rx, ry, rb;
+      if (sigma < 16) {
+        rx = F[0][ly][lx]; ry = F[1][ly][lx]; rb = F[2][ly][lx];
+      } else {
+        const int M = 16 * c_mul4[sigma];
+        uint32_t own[3][4];
+#pragma unroll
+        for (int iy = 0; iy < 3; ++iy)
+#pragma unroll
+          for (int ix = 0; ix < 4; ++ix) own[iy][ix] = G[ly + iy - 1][lx + ix - 1];
+        float ax = 0.f, ay = 0.f, ab = 0.f, ws = 0.f;
+#pragma unroll 1
+        for (int oy = -3; oy <= 3; ++oy) {
+          uint32_t sad[8];
+#pragma unroll
+          for (int o = 0; o < 8; ++o) sad[o] = 0;
+#pragma unroll
+          for (int iy = 0; iy < 3; ++iy) {
+            const uint32_t* row = &G[ly + oy + iy - 1][lx - 4];
+            uint32_t r[11];
+#pragma unroll
+            for (int j = 0; j < 11; ++j) r[j] = row[j];
+#pragma unroll
+            for (int o = 0; o < 8; ++o)
+#pragma unroll
+              for (int ix = 0; ix < 4; ++ix)
+                sad[o] = __dp4a(__vabsdiffu4(own[iy][ix], r[o + ix]), 0x01010101u, sad[o]);
+          }
+#pragma unroll
+          for (int o = 0; o < 8; ++o) {
+            const int s = min(static_cast<int>(sad[o]), 507);
+            uint32_t bits = (0x3F800000u + static_cast<uint32_t>(s * M)) & 0xFFFF0000u;
+            if (bits < a.wmin_bits) bits = 0;
+            const float w = __uint_as_float(bits);
+            const int sy = ly + oy, sx = lx + o - 3;
+            ax = fmaf(w, F[0][sy][sx], ax);
+            ay = fmaf(w, F[1][sy][sx], ay);
+            ab = fmaf(w, F[2][sy][sx], ab);
+            ws += w;
+          }
+        }
+        const float inv = 1.f / ws;
+        rx = ax * inv; ry = ay * inv; rb = ab * inv;
+      }
+      E[0][qy + R][qx + R] = rx;
+      E[1][qy + R][qx + R] = ry;
+      E[2][qy + R][qx + R] = rb;
+    }
+    __syncthreads();
+  }
+
+  // ---- J.4 Gaborish + L.2 + store: 4 pixels per item ----------------------
+  for (int i = tid; i < kTH * (kTW / 4); i += blockDim.x) {
+    const int ty = i / (kTW / 4), tx = 4 * (i % (kTW / 4));
+    const int gy = y0 + ty, gx = x0 + tx;
+    if (gy >= a.ys || gx >= a.xs) continue;
+    const int n = min(4, a.xs - gx);
+    float X[4], Y[4], B[4];
+    float* dst[3] = {X, Y, B};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        float v;
+        if (a.gab) {
+          // source sample (dy, dx) around the pixel, mirrored at the image
+          // border (J.4); E holds the ring, F the unfiltered window
+          float acc = 0.f;
+#pragma unroll
+          for (int dy = -1; dy <= 1; ++dy) {
+#pragma unroll
+            for (int dx = -1; dx <= 1; ++dx) {
+              const int wgt = (dx != 0) + (dy != 0);
+              float sv;
+              // F already holds mirrored samples at window coordinates
+              sv = a.epf ? E[c][ty + dy + 1][tx + j + dx + 1]
+                         : F[c][ty + dy + kGY][tx + j + dx + kGX];
+              acc = fmaf(a.gw[c][wgt], sv, acc);
+            }
+          }
+          v = acc;
+        } else if (a.epf) {
+          v = E[c][ty][tx + j];
+        } else {
+          v = F[c][ty + kGY][tx + j + kGX];
+        }
+        dst[c][j] = v;
+      }
+    }
+    emit4(a.cp, a.out, gx, gy, n, X, Y, B);
+  }
+}
+
+void launch_filter(const FilterArgs& a, cudaStream_t s) {
+  dim3 grid((a.xs + kTW - 1) / kTW, (a.ys + kTH - 1) / kTH);
+  k_filter<<<grid, 256, 0, s>>>(a);
+}
+
+}  // namespace jxlr

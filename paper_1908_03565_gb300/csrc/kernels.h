@@ -1,0 +1,81 @@
+// Launch parameters of the reconstruction kernels (device-side layout).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+namespace jxlr {
+
+// L.2 colour transform with the output scale folded in: rgb01 = m * mix,
+// mix = gamma^3 + bias.
+struct ColorParams {
+  float m[9];
+  float bias[3];
+};
+
+// J.2.2 guide and J.2.4 sigma parameters (binary32, the kernels' precision).
+struct SigmaParams {
+  float gmin[3];        // min[c] of J.2.2
+  float gscale[3];      // epf_scale
+  float range_max, range_mul, quant_mul, sigma_max;
+  float lut[8];
+};
+
+struct OutParams {
+  void* data;
+  size_t stride;        // bytes per row
+  int dtype;            // jxlr_out_dtype
+};
+
+struct ReconArgs {
+  const int16_t* coef[3];
+  size_t cstride;             // elements per coefficient row
+  const uint8_t* vmap;        // [bh][bw]
+  const float* acmul;         // [bh][bw]
+  const float* cfl;           // [th][tw][2]
+  const uint8_t* sharp;       // [bh][bw] (EPF only)
+  const float* dequant;       // prescaled matrices, dequant_offset layout
+  int xs, ys, wp, hp, bw, bh, tw;
+  float m_dc[3];
+  float kx_dc, kb_dc;
+  float one_minus_bias[3];
+  int write_xyb;              // 1: planar XYB to xyb; 0: final pixels to out
+  float* xyb;                 // [3][hp][wp]
+  int16_t* sigma;             // [bh][bw] or nullptr (no EPF)
+  SigmaParams sp;
+  ColorParams cp;
+  OutParams out;
+};
+
+struct SigmaArgs {
+  const float* xyb;
+  size_t rstride, pstride;    // elements per row / per plane
+  const uint8_t* vmap;
+  const float* acmul;
+  const uint8_t* sharp;
+  int xs, ys, bw, bh;
+  int16_t* sigma;
+  SigmaParams sp;
+};
+
+struct FilterArgs {
+  const float* xyb;
+  size_t rstride, pstride;
+  int xs, ys, bw;
+  const int16_t* sigma;
+  int epf, gab;
+  float gw[3][3];             // Gaborish: centre, side, corner weights per channel
+  uint32_t wmin_bits;         // smallest binary32 pattern with value >= epf_weight_min
+  SigmaParams sp;             // guide parameters
+  ColorParams cp;
+  OutParams out;
+};
+
+void launch_validate(const uint8_t* vmap, int bw, int bh, unsigned* status, cudaStream_t s);
+void launch_recon(const ReconArgs& a, cudaStream_t s);
+void launch_sigma(const SigmaArgs& a, cudaStream_t s);
+void launch_filter(const FilterArgs& a, cudaStream_t s);
+
+}  // namespace jxlr

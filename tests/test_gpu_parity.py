@@ -1,0 +1,346 @@
+"""Parity of the CUDA library (through its C ABI) with the FP64 oracle.
+
+Tolerances (written here, derived in the design doc):
+  * linear RGB in [0, 1]: max |gpu - oracle| <= 1e-4 on clamp(., 0, 1);
+  * 8-bit sRGB: every sample within +-1 of the oracle's;
+  * f16 output: <= half an f16 ulp of the value + 1e-4;
+  * XYB before the filters: <= XYB_TOL absolute (FP32 transforms of O(1)
+    samples).
+The EPF decides integers (guide bytes, sigma) from real numbers; the oracle
+takes those decisions in binary32 like the kernels, so the filter stage is
+compared on identical input samples (the GPU's own XYB).  From-scratch
+comparisons exclude, and count, only pixels whose EPF window saw a guide
+byte or sigma that differs between the two XYB images.
+"""
+import numpy as np
+import pytest
+
+from oracle import recon as R
+from paper_1908_03565_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL01 = 1e-4
+XYB_TOL = 2e-5
+
+F32, F16, U8, XYB = 0, 1, 2, 3
+
+
+def params_pair(B, epf=False, gab=False, kx_dc=0.0, kb_dc=0.0):
+    """Matching oracle and library parameter sets (draft defaults)."""
+    p = R.Params(epf=epf, gab=gab, kx_dc=kx_dc, kb_dc=kb_dc)
+    lp = B.filter_defaults(epf=int(epf), gab=int(gab))
+    return p, lp
+
+
+@pytest.fixture(scope="module")
+def B():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("GPU test without CUDA")
+    from paper_1908_03565_gb300 import binding
+    binding.load()
+    return binding
+
+
+@pytest.fixture(scope="module")
+def ctx(B):
+    c = B.Context(max_slots=2)
+    yield c
+    c.close()
+
+
+def run(B, ctx, img, lp, dtype, device_io=True, kx_dc=0.0, kb_dc=0.0):
+    import torch
+    shape, npd = B.out_shape(img, dtype)
+    if device_io:
+        dimg = B.to_device(img, torch)
+        tdt = {np.float32: torch.float32, np.float16: torch.float16, np.uint8: torch.uint8}[npd]
+        out = torch.full(shape, 7, dtype=tdt, device="cuda")
+        t = ctx.submit(dimg, lp, out, dtype, on_device=True, kx_dc=kx_dc, kb_dc=kb_dc)
+        ctx.poll(t)
+        return out.cpu().numpy()
+    out = np.full(shape, 7, dtype=npd)
+    t = ctx.submit(img, lp, out, dtype, on_device=False, out_on_device=False,
+                   kx_dc=kx_dc, kb_dc=kb_dc)
+    ctx.poll(t)
+    return out
+
+
+def oracle_xyb(img, p):
+    xyb = R.reconstruct_xyb(img['coeffs'], img['vmap'], img['acmul'], img['cfl'], p)
+    return xyb[:, :img['ysize'], :img['xsize']]
+
+
+def check_rgb01(got, want, tol=TOL01):
+    err = np.abs(np.clip(got.astype(np.float64), 0, 1) - np.clip(want, 0, 1))
+    assert err.max() <= tol, f"max err {err.max():.3g} at {np.unravel_index(err.argmax(), err.shape)}"
+    return err.max()
+
+
+def check_u8(got, want01):
+    want = R.srgb_u8(want01).astype(np.int64)
+    d = np.abs(got.astype(np.int64) - want)
+    assert d.max() <= 1, f"u8 off by {d.max()} at {np.unravel_index(d.argmax(), d.shape)}"
+
+
+# ---------------------------------------------------------------------------
+# linear path: dequantisation, CfL, LLF, transforms, colour
+# ---------------------------------------------------------------------------
+def test_config0_dct8_256(B, ctx):
+    """256x256, all DCT8, AcMul 1, no CfL, no filters, f32 output."""
+    img = synth.make_image(256, 256, 0, mix='dct8', acmul=1.0, cfl=False)
+    p, lp = params_pair(B)
+    want_xyb = oracle_xyb(img, p)
+    got_xyb = run(B, ctx, img, lp, XYB)
+    np.testing.assert_allclose(got_xyb.transpose(2, 0, 1), want_xyb, rtol=0, atol=XYB_TOL)
+    want = R.xyb_to_linear01(want_xyb, p)
+    check_rgb01(run(B, ctx, img, lp, F32), want)
+    check_u8(run(B, ctx, img, lp, U8), want)
+
+
+@pytest.mark.parametrize("code", list(range(15)))
+def test_every_shape(B, ctx, code):
+    """An image tiled with one varblock shape (DCT8 where it does not fit),
+    with quant field and CfL drawn as in the mixed workload."""
+    img = synth.make_image(72, 80, 100 + code, mix=code, y_dc_offset_q=200)
+    p, lp = params_pair(B)
+    want_xyb = oracle_xyb(img, p)
+    got = run(B, ctx, img, lp, XYB).transpose(2, 0, 1)
+    np.testing.assert_allclose(got, want_xyb, rtol=0, atol=XYB_TOL)
+
+
+@pytest.mark.parametrize("xs,ys", [(1, 1), (7, 9), (8, 8), (33, 17), (95, 64), (200, 136)])
+def test_ragged_sizes_all_outputs(B, ctx, xs, ys):
+    img = synth.make_image(xs, ys, xs * 1000 + ys, y_dc_offset_q=200)
+    p, lp = params_pair(B)
+    want_xyb = oracle_xyb(img, p)
+    np.testing.assert_allclose(run(B, ctx, img, lp, XYB).transpose(2, 0, 1), want_xyb,
+                               rtol=0, atol=XYB_TOL)
+    want = R.xyb_to_linear01(want_xyb, p)
+    check_rgb01(run(B, ctx, img, lp, F32), want)
+    check_u8(run(B, ctx, img, lp, U8), want)
+    h = run(B, ctx, img, lp, F16).astype(np.float64)
+    tol = np.abs(want) * 2.0 ** -11 + TOL01
+    assert np.all(np.abs(h - want) <= tol)
+
+
+def test_dc_cfl_factors(B, ctx):
+    img = synth.make_image(64, 48, 77, y_dc_offset_q=200)
+    p, lp = params_pair(B, kx_dc=0.25, kb_dc=0.9)
+    want = oracle_xyb(img, p)
+    got = run(B, ctx, img, lp, XYB, kx_dc=0.25, kb_dc=0.9).transpose(2, 0, 1)
+    np.testing.assert_allclose(got, want, rtol=0, atol=XYB_TOL)
+
+
+def test_host_io_equals_device_io(B, ctx):
+    img = synth.make_image(150, 70, 5, y_dc_offset_q=200)
+    for epf, gab in ((False, False), (True, True)):
+        _, lp = params_pair(B, epf=epf, gab=gab)
+        a = run(B, ctx, img, lp, F32, device_io=True)
+        b = run(B, ctx, img, lp, F32, device_io=False)
+        np.testing.assert_array_equal(a, b)
+
+
+# ---------------------------------------------------------------------------
+# filters: EPF and Gaborish
+# ---------------------------------------------------------------------------
+def _filters_on_gpu_xyb(B, ctx, img, lp, epf, gab, dtype=F32):
+    """Runs the filter + colour stage of the library on the GPU's own XYB."""
+    import torch
+    xs, ys = img['xsize'], img['ysize']
+    _, lp0 = params_pair(B)
+    xyb = run(B, ctx, img, lp0, XYB).transpose(2, 0, 1).copy()      # (3, ys, xs) f32
+    dx = torch.from_numpy(xyb).cuda()
+    shape, npd = B.out_shape(img, dtype)
+    tdt = {np.float32: torch.float32, np.float16: torch.float16, np.uint8: torch.uint8}[npd]
+    out = torch.empty(shape, dtype=tdt, device="cuda")
+    dimg = B.to_device(img, torch)
+    t = ctx.submit_xyb(dx, xs, ys, dimg['vmap'], dimg['acmul'], dimg['sharpness'], lp, out, dtype)
+    ctx.poll(t)
+    return xyb, out.cpu().numpy()
+
+
+def _oracle_filters(img, xyb, p, region=None):
+    x = xyb.astype(np.float64)
+    if p.epf:
+        x = R.epf(x, img['vmap'], img['acmul'], img['sharpness'], p)
+    if p.gab:
+        x = R.gaborish(x, p)
+    return x
+
+
+@pytest.mark.parametrize("epf,gab", [(True, False), (False, True), (True, True)])
+@pytest.mark.parametrize("xs,ys", [(64, 64), (131, 77), (9, 13)])
+def test_filter_stage_on_identical_samples(B, ctx, epf, gab, xs, ys):
+    """J.2 + J.4 + L.2 on the same binary32 XYB on both sides: every integer
+    decision agrees, so the result is within float rounding."""
+    img = synth.make_image(xs, ys, 31 * xs + ys, y_dc_offset_q=200)
+    p, lp = params_pair(B, epf=epf, gab=gab)
+    xyb, got = _filters_on_gpu_xyb(B, ctx, img, lp, epf, gab, XYB)
+    want = _oracle_filters(img, xyb, p)
+    np.testing.assert_allclose(got.transpose(2, 0, 1), want, rtol=0, atol=5e-6)
+
+
+def test_full_path_equals_staged_path(B, ctx):
+    """Submit with filters == recon to XYB then the filter entry point."""
+    img = synth.make_image(200, 136, 9, y_dc_offset_q=200)
+    p, lp = params_pair(B, epf=True, gab=True)
+    _, staged = _filters_on_gpu_xyb(B, ctx, img, lp, True, True, F32)
+    full = run(B, ctx, img, lp, F32)
+    np.testing.assert_array_equal(full, staged)
+
+
+def _ambiguous_mask(img, xyb_a, xyb_b, p):
+    """Pixels whose EPF+Gaborish window (x -5..+6, y -5..+5) contains a guide
+    byte or a block sigma that differs between two XYB images."""
+    ga, gb = R.guide(xyb_a, p), R.guide(xyb_b, p)
+    diff = np.any(ga != gb, axis=0)
+    sa = R.epf_sigma(xyb_a, img['vmap'], img['acmul'], img['sharpness'], p)
+    sb = R.epf_sigma(xyb_b, img['vmap'], img['acmul'], img['sharpness'], p)
+    sd = np.repeat(np.repeat(sa != sb, 8, 0), 8, 1)[:diff.shape[0], :diff.shape[1]]
+    bad = diff | sd
+    out = np.zeros_like(bad)
+    ys, xs = bad.shape
+    for dy in range(-5, 6):
+        for dx in range(-5, 7):
+            out |= bad[R.mirror(np.arange(ys)[:, None] - dy, ys), R.mirror(np.arange(xs)[None, :] - dx, xs)]
+    return out
+
+
+def test_config1_statistics_from_scratch(B, ctx):
+    """Mixed tiling, quant field, CfL, EPF + Gaborish, f32 and u8 outputs,
+    against the oracle run from the coefficients."""
+    img = synth.make_image(320, 200, 1001, y_dc_offset_q=200)
+    p, lp = params_pair(B, epf=True, gab=True)
+    ref = R.reconstruct(img, p)
+    gpu_xyb = run(B, ctx, img, params_pair(B)[1], XYB).transpose(2, 0, 1)
+    np.testing.assert_allclose(gpu_xyb, ref['xyb_padded'][:, :200, :320], rtol=0, atol=XYB_TOL)
+    amb = _ambiguous_mask(img, ref['xyb_padded'][:, :200, :320], gpu_xyb.astype(np.float64), p)
+    got = run(B, ctx, img, lp, F32)
+    err = np.abs(np.clip(got, 0, 1) - np.clip(ref['rgb01'], 0, 1)).max(axis=2)
+    assert err[~amb].max() <= TOL01
+    assert amb.mean() < 0.25, amb.mean()
+    u8 = run(B, ctx, img, lp, U8).astype(np.int64)
+    d = np.abs(u8 - R.srgb_u8(ref['rgb01']).astype(np.int64)).max(axis=2)
+    assert d[~amb].max() <= 1
+
+
+def test_config1_full_size_sampled(B, ctx):
+    """1920x1088 at the mixed statistics with both filters: the linear part
+    everywhere; the filters on windows (corners, edges, interior) computed
+    by the oracle from the GPU's XYB."""
+    xs, ys = 1920, 1088
+    img = synth.make_image(xs, ys, 1000)
+    p, lp = params_pair(B, epf=True, gab=True)
+    gpu_xyb = run(B, ctx, img, params_pair(B)[1], XYB).transpose(2, 0, 1)
+    want = R.reconstruct_xyb(img['coeffs'], img['vmap'], img['acmul'], img['cfl'], p)
+    np.testing.assert_allclose(gpu_xyb, want[:, :ys, :xs], rtol=0, atol=XYB_TOL)
+    got = run(B, ctx, img, lp, F32)
+    x64 = gpu_xyb.astype(np.float64)
+    for (x0, y0) in [(0, 0), (xs - 40, 0), (0, ys - 40), (xs - 40, ys - 40), (960, 544)]:
+        region = (x0, y0, x0 + 40, y0 + 40)
+        e = R.epf(x64, img['vmap'], img['acmul'], img['sharpness'], p,
+                  region=(max(0, x0 - 1), max(0, y0 - 1), min(xs, x0 + 41), min(ys, y0 + 41)))
+        ref = R.xyb_to_linear01(_gab_window(x64, e, region, p, img), p)
+        check_rgb01(got[y0:y0 + 40, x0:x0 + 40], ref, tol=TOL01)
+
+
+def _gab_window(x64, e, region, p, img):
+    """Gaborish of the EPF output on `region`, given the EPF output `e` on the
+    region grown by one sample (clipped to the image)."""
+    xs, ys = x64.shape[2], x64.shape[1]
+    x0, y0, x1, y1 = region
+    ex0, ey0 = max(0, x0 - 1), max(0, y0 - 1)
+    out = np.zeros((3, y1 - y0, x1 - x0))
+    for c in range(3):
+        w1, w2 = p.gab_w1[c], p.gab_w2[c]
+        n = 1 + 4 * w1 + 4 * w2
+        for dy in (-1, 0, 1):
+            for dx in (-1, 0, 1):
+                wt = (1.0, w1, w2)[abs(dx) + abs(dy)] / n
+                yy = R.mirror(np.arange(y0, y1)[:, None] + dy, ys) - ey0
+                xx = R.mirror(np.arange(x0, x1)[None, :] + dx, xs) - ex0
+                out[c] += wt * e[c][yy, xx]
+    return out
+
+
+# ---------------------------------------------------------------------------
+# boundary behaviour
+# ---------------------------------------------------------------------------
+def test_invalid_maps_rejected(B, ctx):
+    import torch
+    img = synth.make_image(64, 64, 3)
+    _, lp = params_pair(B)
+    bad = dict(img)
+    vm = img['vmap'].copy()
+    vm[0, 0] = 5          # DCT32 at (0,0) overlapping whatever is there
+    vm[1, 1] = 0
+    bad['vmap'] = vm
+    out = np.zeros((64, 64, 3), np.float32)
+    with pytest.raises(B.JxlrError) as e:
+        ctx.submit(bad, lp, out, F32, on_device=False, out_on_device=False)
+    assert e.value.status == B.JXLR_EINVAL
+    # device inputs: reported by poll
+    dimg = B.to_device(bad, torch)
+    dout = torch.empty((64, 64, 3), dtype=torch.float32, device="cuda")
+    t = ctx.submit(dimg, lp, dout, F32, on_device=True)
+    with pytest.raises(B.JxlrError) as e:
+        ctx.poll(t)
+    assert e.value.status == B.JXLR_EINVAL
+    vm2 = img['vmap'].copy()
+    vm2[3, 3] = 16        # no such code
+    bad['vmap'] = vm2
+    dimg = B.to_device(bad, torch)
+    t = ctx.submit(dimg, lp, dout, F32, on_device=True)
+    with pytest.raises(B.JxlrError):
+        ctx.poll(t)
+    # the context still works
+    assert np.isfinite(run(B, ctx, img, lp, F32)).all()
+
+
+def test_dequant_override(B, ctx):
+    """A caller matrix table replaces C.6.1.1's defaults."""
+    from oracle import tables as T
+    img = synth.make_image(64, 64, 8, y_dc_offset_q=200)
+    p, lp = params_pair(B)
+    tab = []
+    for code in range(15):
+        for c in range(3):
+            tab.append(T.dequant_matrix(code, c).reshape(-1) * (1.5 if c == 1 else 0.75))
+    tab = np.concatenate(tab).astype(np.float32)
+    assert tab.size == 10560
+    tab[~np.isfinite(tab)] = 1.0
+    lp.dequant = tab.ctypes.data
+    got = run(B, ctx, img, lp, XYB).transpose(2, 0, 1)
+    orig = T.dequant_matrix
+    try:
+        T.dequant_matrix = lambda code, c: orig(code, c) * (1.5 if c == 1 else 0.75)
+        want = oracle_xyb(img, p)
+    finally:
+        T.dequant_matrix = orig
+    np.testing.assert_allclose(got, want, rtol=0, atol=XYB_TOL)
+    bad = tab.copy()
+    bad[100] = -1.0
+    lp.dequant = bad.ctypes.data
+    with pytest.raises(B.JxlrError):
+        run(B, ctx, img, lp, XYB)
+    lp.dequant = None
+
+
+def test_hbm_cap_admission(B):
+    img = synth.make_image(256, 256, 4)
+    _, lp = params_pair(B, epf=True, gab=True)
+    with B.Context(max_slots=1, hbm_cap_bytes=1 << 20) as c:
+        out = np.zeros((256, 256, 3), np.float32)
+        with pytest.raises(B.JxlrError) as e:
+            c.submit(img, lp, out, F32, on_device=False, out_on_device=False)
+        assert e.value.status == B.JXLR_ENOMEM
+    with B.Context(max_slots=1) as c:
+        out = np.zeros((256, 256, 3), np.float32)
+        t = c.submit(img, lp, out, F32, on_device=False, out_on_device=False)
+        with pytest.raises(B.JxlrError) as e:
+            c.submit(img, lp, out, F32, on_device=False, out_on_device=False)
+        assert e.value.status == B.JXLR_EBUSY
+        c.poll(t)
+        assert c.launch_count() >= 2
