@@ -36,7 +36,7 @@ OUT_BPP = 12.0
 # separable 3x4 patch sums on packed guide bytes, J.2.4 weight, J.2.5
 # accumulation, guide, Gaborish, colour); derivation in the design doc
 FILTER_OPS_PER_PX = 56 * 14 + 4 + 17 + 27 + 20
-CPU_SAMPLE = 640          # oracle sample: one 640x640 image, same statistics
+CPU_SAMPLE = 1024         # oracle sample: one 1024x1024 image, same statistics
 
 
 def env_int(k, d):
@@ -61,7 +61,7 @@ def clocks_start():
              "--query-gpu=clocks.sm,clocks.max.sm,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
-             "--format=csv,noheader,nounits", "-lms", "200"],
+             "--format=csv,noheader,nounits", "-lms", "100"],
             stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
     except OSError:
         return None
@@ -136,8 +136,10 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--size", default=None,
+                    help="WxH instead of 4096x4096 (profiling captures only)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
@@ -147,6 +149,9 @@ def main():
     import torch
     from paper_1908_03565_gb300 import binding, synth
 
+    global XS, YS
+    if args.size:
+        XS, YS = (int(v) for v in args.size.lower().split("x"))
     world = env_int("WORLD_SIZE", 1)
     rank = env_int("RANK", 0)
     local = env_int("LOCAL_RANK", 0)
@@ -160,7 +165,10 @@ def main():
     img = synth.make_image(XS, YS, SEED + rank)
     dimg = binding.to_device(img, torch)
     out = torch.empty((YS, XS, 3), dtype=torch.float32, device="cuda")
-    stream = torch.cuda.current_stream()
+    # a created stream (not the legacy default stream, whose handle is 0):
+    # every request and the timing events go on it, in order
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
     ctx = binding.Context(device=local, max_slots=2, timing=True, stream=stream.cuda_stream)
     params = binding.filter_defaults(epf=1, gab=1)
 
@@ -196,9 +204,9 @@ def main():
         return float(t.item())
 
     # ---- device-resident timing -----------------------------------------
+    clk = clocks_start()          # sampled through warm-up and timed steps
     run_steps(max(3, args.warmup))
     barrier()
-    clk = clocks_start()
     l0 = ctx.launch_count()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -257,14 +265,15 @@ def main():
         if world == 1 and not args.no_cpu_baseline:
             cb = cpu_baseline_run()
         line = {
-            "metric": "recon Mpx/s at 4096^2", "value": round(value, 1), "unit": "Mpx/s",
+            "metric": f"recon Mpx/s at {XS}x{YS}", "value": round(value, 1), "unit": "Mpx/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "4096x4096 mixed varblocks (config-1 statistics), "
+            "config": {"workload": f"{XS}x{YS} mixed varblocks (config-1 statistics), "
                                    "EPF+Gaborish, f32 linear RGB out",
                        "global_batch": world, "image": f"{XS}x{YS}",
-                       "l2": "inputs larger than L2 (100.7 MB coefficients, 201 MB output)",
+                       "l2": f"inputs larger than L2 ({6 * px / 1e6:.1f} MB coefficients, "
+                             f"{12 * px / 1e6:.1f} MB output, {12 * px / 1e6:.1f} MB XYB scratch)",
                        "parallelism": f"replicas x{world}"},
             "roofline": roof,
             "hbm_roofline_frac_step": round(step_hbm_frac, 4),
