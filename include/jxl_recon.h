@@ -206,6 +206,39 @@ jxlr_status jxl_recon_destroy(jxl_recon_ctx* ctx);
 /* Message of the last error on the calling thread ("" if none). */
 const char* jxl_recon_last_error(const jxl_recon_ctx* ctx);
 
+/* Size of the fixed device scratch of jxl_recon_run_noalloc(). */
+#define JXL_RECON_NOALLOC_SCRATCH_BYTES ((size_t)64 << 20)
+
+/* Reconstruction for callers that cannot allocate device memory.  (The
+ * draft has no counterpart: this is a deployment variant of the submit
+ * path.)  Some callers may not call cudaMalloc: a framework or service that
+ * must account for every device byte through its own allocator, or code
+ * for which an allocation's implicit device synchronisation is not
+ * allowed.  This call creates no context and allocates nothing, on the
+ * host or the device: the scratch of the transform kernel (planar XYB and
+ * per-block EPF sigma, 12 B per padded pixel + 2 B per 8x8 block) is a
+ * fixed array of JXL_RECON_NOALLOC_SCRATCH_BYTES inside the library, held
+ * by every GPU that loads it until the process exits; a padded image that
+ * needs more (about 5.5 Mpx with a loop filter on; no limit with both off)
+ * is rejected with JXLR_EINVAL.
+ * Inputs as for jxl_recon_submit() and all on the device (coeffs->on_device
+ * = 1, out->on_device = 1); filter_params->dequant must be NULL (default
+ * matrices).  The map is not validated: an ill-formed map gives unspecified
+ * pixels but no out-of-bounds access.  The kernels are enqueued on
+ * cuda_stream (a cudaStream_t; NULL = the legacy default stream) of the
+ * current device and the call returns without waiting.
+ * The first call on a device copies the constant tables to it and looks up
+ * the scratch address; make that first call before any stream capture.
+ * All calls share the scratch: calls whose work overlaps on the GPU race and
+ * give wrong pixels, so order them on one stream.  Nothing needs clearing
+ * between calls (every scratch element read is written first).
+ * Returns JXLR_OK, JXLR_EINVAL (message in jxl_recon_last_error(NULL)) or
+ * JXLR_ECUDA. */
+jxlr_status jxl_recon_run_noalloc(const jxl_recon_coeffs* coeffs, const uint8_t* varblock_map,
+                                  const float* quant_field, const jxl_recon_cfl* cfl_map,
+                                  const jxl_recon_filter_params* filter_params,
+                                  const jxl_recon_output* out, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

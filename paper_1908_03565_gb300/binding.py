@@ -22,7 +22,7 @@ OUT_BYTES = {OUT_F32_LINEAR: 12, OUT_F16_LINEAR: 6, OUT_U8_SRGB: 3, OUT_F32_XYB:
 EXPORTS = ("jxl_recon_filter_defaults", "jxl_recon_create", "jxl_recon_submit",
            "jxl_recon_submit_xyb", "jxl_recon_poll", "jxl_recon_stage_ms",
            "jxl_recon_launch_count", "jxl_recon_device_bytes", "jxl_recon_destroy",
-           "jxl_recon_last_error")
+           "jxl_recon_last_error", "jxl_recon_run_noalloc")
 
 
 class Config(ctypes.Structure):
@@ -263,3 +263,32 @@ def decode(ctx, img, params, dtype=OUT_F32_LINEAR, device_io=True):
     t = ctx.submit(img, params, out, dtype, on_device=False, out_on_device=False)
     ctx.poll(t)
     return out
+
+
+def run_noalloc(img, params, out, out_dtype, stream=0, kx_dc=0.0, kb_dc=0.0, out_stride=None):
+    """jxl_recon_run_noalloc: for callers that cannot allocate device memory.
+    Everything (img's arrays as torch CUDA tensors, out) is on the device;
+    the work is enqueued on ``stream`` (raw cudaStream_t, 0 = legacy default
+    stream) and this returns without waiting.  The library's fixed scratch
+    is shared by every call: order overlapping calls on one stream."""
+    lib = load()
+    fn = lib.jxl_recon_run_noalloc
+    P = ctypes.POINTER
+    fn.argtypes = [P(Coeffs), ctypes.c_void_p, ctypes.c_void_p, P(Cfl), P(FilterParams),
+                   P(Output), ctypes.c_void_p]
+    fn.restype = ctypes.c_int
+    xs, ys = img['xsize'], img['ysize']
+    co = img['coeffs']
+    planes = (ctypes.c_void_p * 3)(*[_ptr(co[c]) for c in range(3)])
+    c = Coeffs(xs, ys, planes, co.shape[2], 1)
+    cfl = Cfl(_ptr(img['cfl']), kx_dc, kb_dc)
+    if params.epf:
+        params.sharpness = _ptr(img['sharpness'])
+    if out_stride is None:
+        out_stride = OUT_BYTES[out_dtype] * xs
+    o = Output(_ptr(out), out_stride, out_dtype, 1)
+    st = fn(ctypes.byref(c), _ptr(img['vmap']), _ptr(img['acmul']), ctypes.byref(cfl),
+            ctypes.byref(params), ctypes.byref(o), stream or None)
+    if st != JXLR_OK:
+        lib.jxl_recon_last_error.restype = ctypes.c_char_p
+        raise JxlrError(st, lib.jxl_recon_last_error(None).decode())

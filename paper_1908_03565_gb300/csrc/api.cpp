@@ -42,6 +42,12 @@ size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 using Clock = std::chrono::steady_clock;
 
+}  // namespace
+
+void jxlr::set_last_error(const std::string& msg) { g_err = msg; }
+
+namespace {
+
 struct Slot {
   cudaStream_t stream = nullptr;
   bool own_stream = true;

@@ -3,6 +3,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <string>
 
 namespace jxlr {
 
@@ -54,6 +55,9 @@ void mul_table4(int32_t* out /* 673 */);
 
 // AFV basis of I.2.2, [coefficient][sample], 16 x 16.
 extern const double kAfvBasis[16][16];
+
+// Sets the message jxl_recon_last_error() returns on this thread (api.cpp).
+void set_last_error(const std::string& msg);
 
 // Device-side constant setup (kernels.cu): copies the tables above into
 // __constant__ memory of the current device.
