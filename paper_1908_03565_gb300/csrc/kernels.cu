@@ -23,6 +23,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <vector>
 
 #include "internal.h"
 #include "kernels.h"
@@ -878,7 +879,241 @@ __global__ void __launch_bounds__(256) k_filter(const FilterArgs a) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// k_epf: J.2 with shared per-offset patch sums, then J.4 + L.2 (30x30 tile)
+//
+// The 3x4 patch SAD of J.2.3 is a box sum of the per-offset distance image
+// D_o(q) = sum_c |g_c(q) - g_c(q + o)|.  For each horizontal offset ox the
+// CTA first writes, for all 7 vertical offsets, the horizontal 4-sums
+// H_o(q) = D_o(q-1) + D_o(q) + D_o(q+1) + D_o(q+2) of its region to shared
+// memory as 16-bit values (at most 3060); then each thread walks a column
+// strip of 8 pixels, forms sad = H_o(y-1) + H_o(y) + H_o(y+1) by a sliding
+// sum, turns it into the J.2.4 weight and accumulates the J.2.5 sums, with
+// the strip's sample column for this ox held in registers.  Integer sums are
+// exact in any order, so every weight equals the per-pixel definition.
+//
+// Cut-off without a compare: with C = bits(1.0f) and M = 16 * (4 mul) < 0,
+// Weight() has bits floor16(C + sad * M); it is >= the cut-off pattern T
+// exactly when sad <= vmax = floor((C - ceil16(T)) / -M).  With
+// the weight bits are (C + sad M) & 0xFFFF0000 & ~((vmax - sad) >> 31) (the
+// product may wrap only when sad > vmax, where the mask clears it).  When
+// some sigma has
+// vmax >= 507 the clamp of Weight() matters and the kClamp variant is used.
+// ---------------------------------------------------------------------------
+constexpr int kET = 30;                  // output tile
+constexpr int kER = 32;                  // EPF region: tile plus a 1-sample ring
+constexpr int kHR = 34;                  // rows of horizontal sums
+constexpr int kWW = 42, kWH = 40;        // sample / guide window, origin (x0-5, y0-5)
+constexpr int kGS = 65;                  // guide row stride (words), = 1 mod 32
+
+template <bool kClamp>
+__global__ void __launch_bounds__(128, 4) k_epf(const FilterArgs a) {
+  __shared__ float F[3][kWH][kWW];
+  __shared__ uint32_t G[kWH][kGS];
+  __shared__ __align__(16) uint16_t Hb[7][kHR][kER];
+  const int tid = threadIdx.x;
+  const int x0 = blockIdx.x * kET, y0 = blockIdx.y * kET;
+  const int wx0 = x0 - 5, wy0 = y0 - 5;
+
+  // ---- window of mirrored samples and packed guide bytes (6.5, J.2.2) ----
+  for (int i = tid; i < kWH * kWW; i += 128) {
+    const int ly = i / kWW, lx = i - ly * kWW;
+    const int gy = mirror_coord(wy0 + ly, a.ys), gx = mirror_coord(wx0 + lx, a.xs);
+    const size_t off = static_cast<size_t>(gy) * a.rstride + gx;
+    uint32_t g = 0;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const float v = __ldg(a.xyb + c * a.pstride + off);
+      F[c][ly][lx] = v;
+      const float sc = fminf(fmaxf(guide_scaled(a.sp, c, v), 0.f), 255.f);
+      g |= static_cast<uint32_t>(sc) << (8 * c);
+    }
+    G[ly][lx] = g;
+  }
+
+  // ---- per-pixel weight parameters of this thread's strip ------------------
+  const int cx = tid & 31, ry0 = (tid >> 5) * 8;   // EPF-region column, first row
+  int Mneg[8], vmax[8];
+  bool pass[8];
+#pragma unroll
+  for (int r = 0; r < 8; ++r) {
+    const int qx = min(max(x0 - 1 + cx, 0), a.xs - 1);
+    const int qy = min(max(y0 - 1 + ry0 + r, 0), a.ys - 1);
+    const int sg = min(max(static_cast<int>(a.sigma[(qy >> 3) * a.bw + (qx >> 3)]), 0), 672);
+    pass[r] = sg < 16;
+    const int M = 16 * c_mul4[max(sg, 16)];           // < 0
+    Mneg[r] = -M;
+    const int C = 0x3F800000;
+    const int T16 = static_cast<int>((a.wmin_bits + 0xFFFFu) & 0xFFFF0000u);
+    vmax[r] = C >= T16 ? (C - T16) / (-M) : -1;
+  }
+  float ax[8], ay[8], ab[8], ws[8];
+#pragma unroll
+  for (int r = 0; r < 8; ++r) { ax[r] = ay[r] = ab[r] = ws[r] = 0.f; }
+
+  __syncthreads();
+  // own guide bytes of this thread's run of horizontal sums (row hy, 8k..8k+7)
+  const int hy = tid >> 2, k8 = 8 * (tid & 3);
+  uint32_t own[11];
+#pragma unroll
+  for (int j = 0; j < 11; ++j) own[j] = G[hy + 3][k8 + 3 + j];
+
+#pragma unroll 1
+  for (int g = 0; g < 8; ++g) {
+    const int ox = g - 3;
+    // ---- step 1: horizontal 4-sums of D_o for the 7 offsets (ox, oy) ------
+#pragma unroll
+    for (int oi = 0; oi < 7; ++oi) {
+      const uint32_t* nb = &G[hy + oi][k8 + 3 + ox];
+      uint32_t d[11];
+#pragma unroll
+      for (int j = 0; j < 11; ++j) d[j] = __dp4a(__vabsdiffu4(own[j], nb[j]), 0x01010101u, 0u);
+      uint32_t h[8];
+      h[0] = d[0] + d[1] + d[2] + d[3];
+#pragma unroll
+      for (int i = 1; i < 8; ++i) h[i] = h[i - 1] + d[i + 3] - d[i - 1];
+      *reinterpret_cast<uint4*>(&Hb[oi][hy][k8]) =
+          make_uint4(h[0] | (h[1] << 16), h[2] | (h[3] << 16), h[4] | (h[5] << 16),
+                     h[6] | (h[7] << 16));
+    }
+    // rows 32 and 33 of the sums: 8 runs x 7 offsets spread over threads 72..127
+    if (tid >= 72) {
+      const int it = tid - 72, run = it / 7, oi = it - 7 * run;
+      const int hy2 = 32 + (run >> 2), kk = 8 * (run & 3);
+      const uint32_t* ow = &G[hy2 + 3][kk + 3];
+      const uint32_t* nb = &G[hy2 + oi][kk + 3 + ox];
+      uint32_t d[11];
+#pragma unroll
+      for (int j = 0; j < 11; ++j) d[j] = __dp4a(__vabsdiffu4(ow[j], nb[j]), 0x01010101u, 0u);
+      uint32_t h[8];
+      h[0] = d[0] + d[1] + d[2] + d[3];
+#pragma unroll
+      for (int i = 1; i < 8; ++i) h[i] = h[i - 1] + d[i + 3] - d[i - 1];
+      *reinterpret_cast<uint4*>(&Hb[oi][hy2][kk]) =
+          make_uint4(h[0] | (h[1] << 16), h[2] | (h[3] << 16), h[4] | (h[5] << 16),
+                     h[6] | (h[7] << 16));
+    }
+    __syncthreads();
+
+    // ---- step 2: vertical 3-sums, weights, weighted sums --------------------
+    // samples of column cx + ox for rows ry0 - 3 .. ry0 + 10 of the region
+    float sx[14], sy[14], sb[14];
+#pragma unroll
+    for (int j = 0; j < 14; ++j) {
+      sx[j] = F[0][ry0 + j + 1][cx + ox + 4];
+      sy[j] = F[1][ry0 + j + 1][cx + ox + 4];
+      sb[j] = F[2][ry0 + j + 1][cx + ox + 4];
+    }
+#pragma unroll
+    for (int oi = 0; oi < 7; ++oi) {
+      int hv[10];
+#pragma unroll
+      for (int j = 0; j < 10; ++j) hv[j] = Hb[oi][ry0 + j][cx];
+      int v = hv[0] + hv[1] + hv[2];
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        if (r > 0) v += hv[r + 2] - hv[r - 1];
+        uint32_t bits;
+        if (kClamp) {
+          const int s = min(v, 507);
+          bits = static_cast<uint32_t>(0x3F800000 - s * Mneg[r]) & 0xFFFF0000u;
+          if (bits < a.wmin_bits) bits = 0;
+        } else {
+          // may wrap when v > vmax; the mask then clears it
+          bits = (0x3F800000u - static_cast<uint32_t>(v) * static_cast<uint32_t>(Mneg[r])) &
+                 0xFFFF0000u & ~static_cast<uint32_t>((vmax[r] - v) >> 31);
+        }
+        const float w = __uint_as_float(bits);
+        ax[r] = fmaf(w, sx[r + oi], ax[r]);
+        ay[r] = fmaf(w, sy[r + oi], ay[r]);
+        ab[r] = fmaf(w, sb[r + oi], ab[r]);
+        ws[r] += w;
+      }
+    }
+    __syncthreads();
+  }
+
+  // ---- EPF result into E (aliases the sums), ring fix-up at image borders --
+  float (*E)[kER][kER] = reinterpret_cast<float (*)[kER][kER]>(&Hb[0][0][0]);
+#pragma unroll
+  for (int r = 0; r < 8; ++r) {
+    const int ly = ry0 + r + 4, lx = cx + 4;
+    float ex, ey, eb;
+    if (pass[r]) {
+      ex = F[0][ly][lx]; ey = F[1][ly][lx]; eb = F[2][ly][lx];
+    } else {
+      const float inv = 1.f / ws[r];
+      ex = ax[r] * inv; ey = ay[r] * inv; eb = ab[r] * inv;
+    }
+    E[0][ry0 + r][cx] = ex;
+    E[1][ry0 + r][cx] = ey;
+    E[2][ry0 + r][cx] = eb;
+  }
+  __syncthreads();
+  // positions of the ring outside the image take the value at the mirrored
+  // position, which is inside the image and inside the region
+  for (int i = tid; i < kER * kER; i += 128) {
+    const int ey = i >> 5, ex = i & 31;
+    const int gy = y0 - 1 + ey, gx = x0 - 1 + ex;
+    if (gy > a.ys || gx > a.xs) continue;
+    if (gy >= 0 && gx >= 0 && gy < a.ys && gx < a.xs) continue;
+    const int my = mirror_coord(gy, a.ys) - (y0 - 1), mx = mirror_coord(gx, a.xs) - (x0 - 1);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) E[c][ey][ex] = E[c][my][mx];
+  }
+  __syncthreads();
+
+  // ---- J.4 Gaborish + L.2 + store, one pixel per item ----------------------
+  for (int i = tid; i < kET * kET; i += 128) {
+    const int ty = i / kET, tx = i - ty * kET;
+    const int gy = y0 + ty, gx = x0 + tx;
+    if (gy >= a.ys || gx >= a.xs) continue;
+    float v[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      if (a.gab) {
+        float acc = 0.f;
+#pragma unroll
+        for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+          for (int dx = -1; dx <= 1; ++dx)
+            acc = fmaf(a.gw[c][(dx != 0) + (dy != 0)], E[c][ty + 1 + dy][tx + 1 + dx], acc);
+        v[c] = acc;
+      } else {
+        v[c] = E[c][ty + 1][tx + 1];
+      }
+    }
+    float X[4] = {v[0], 0.f, 0.f, 0.f}, Y[4] = {v[1], 0.f, 0.f, 0.f}, B[4] = {v[2], 0.f, 0.f, 0.f};
+    emit4(a.cp, a.out, gx, gy, 1, X, Y, B);
+  }
+}
+
+// True when Weight()'s clamp of sad at 507 can change a weight that survives
+// the cut-off, for some sigma the request can produce.
+static bool epf_needs_clamp(const FilterArgs& a, const int32_t* mul4) {
+  const long long C = 0x3F800000LL;
+  const long long T16 = (static_cast<long long>(a.wmin_bits) + 0xFFFF) & ~0xFFFFLL;
+  const int smax = static_cast<int>(a.sp.sigma_max) < 672 ? static_cast<int>(a.sp.sigma_max) : 672;
+  for (int s = 16; s <= smax; ++s) {
+    const long long M = 16LL * mul4[s];
+    if (M >= 0) return true;
+    if ((C - T16) / (-M) >= 507) return true;
+  }
+  return false;
+}
+
 void launch_filter(const FilterArgs& a, cudaStream_t s) {
+  if (a.epf) {
+    static const std::vector<int32_t> mul4 = [] {
+      std::vector<int32_t> t(673);
+      mul_table4(t.data());
+      return t;
+    }();
+    dim3 grid((a.xs + kET - 1) / kET, (a.ys + kET - 1) / kET);
+    if (epf_needs_clamp(a, mul4.data())) k_epf<true><<<grid, 128, 0, s>>>(a);
+    else k_epf<false><<<grid, 128, 0, s>>>(a);
+    return;
+  }
   dim3 grid((a.xs + kTW - 1) / kTW, (a.ys + kTH - 1) / kTH);
   k_filter<<<grid, 256, 0, s>>>(a);
 }
