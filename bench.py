@@ -96,6 +96,54 @@ def clocks_stop(p):
             "samples": len(sm)}
 
 
+def serve_leg(binding, torch, n_req, loads, pool_n=24, seed=4000, slots=8):
+    """Config-4 style serving: a pool of images with sides log-uniform in
+    [32, 8192] (config-1 statistics, EPF + Gaborish, u8 sRGB out) resident on
+    the device, requests drawn from it, Poisson arrivals at a fraction of the
+    measured capacity; the native request loop with `slots` concurrent
+    requests (continuous batching) against the plain path (one request at a
+    time), both under a 40 GB HBM cap."""
+    import math
+    from paper_1908_03565_gb300 import synth
+    rng = np.random.default_rng(seed)
+    sides = np.exp(rng.uniform(math.log(32), math.log(8192), size=(pool_n, 2))).astype(int)
+    pool, outs = [], []
+    for i, (xs, ys) in enumerate(sides):
+        pool.append(binding.to_device(synth.make_image(int(xs), int(ys), seed + i), torch))
+        outs.append(torch.empty((int(ys), int(xs), 3), dtype=torch.uint8, device="cuda"))
+    params = binding.filter_defaults(epf=1, gab=1)
+    idx = rng.integers(0, pool_n, n_req)
+    jobs = [(pool[k], params, outs[k], binding.OUT_U8_SRGB) for k in idx]
+    px = sum(pool[k]['xsize'] * pool[k]['ysize'] for k in idx)
+    cap = 40 << 30
+    res = {"requests": n_req, "pool": pool_n, "mean_mpx": round(px / n_req / 1e6, 3),
+           "slots": slots, "hbm_cap_gb": 40, "output": "u8 sRGB"}
+    with binding.Context(max_slots=slots, hbm_cap_bytes=cap) as cont, \
+            binding.Context(max_slots=1, hbm_cap_bytes=cap) as plain:
+        for c in (cont, plain):
+            c.serve(jobs[:16], np.zeros(16))
+        _, st = cont.serve(jobs, np.zeros(n_req))
+        cap_rps = n_req / st["makespan_s"]
+        _, stp = plain.serve(jobs, np.zeros(n_req))
+        res["capacity_rps"] = round(cap_rps, 1)
+        res["capacity_mpx_s"] = round(px / st["makespan_s"] / 1e6, 1)
+        res["plain_capacity_rps"] = round(n_req / stp["makespan_s"], 1)
+        res["plain_capacity_mpx_s"] = round(px / stp["makespan_s"] / 1e6, 1)
+        res["loads"] = []
+        for load in loads:
+            arr = np.cumsum(rng.exponential(1.0 / (load * cap_rps), n_req))
+            arr -= arr[0]
+            row = {"load": load}
+            for name, c in (("continuous", cont), ("plain", plain)):
+                lat, st = c.serve(jobs, arr)
+                row[name] = {"p50_ms": round(float(np.percentile(lat, 50)), 3),
+                             "p99_ms": round(float(np.percentile(lat, 99)), 3),
+                             "mpx_s": round(px / st["makespan_s"] / 1e6, 1),
+                             "max_in_flight": st["max_in_flight"]}
+            res["loads"].append(row)
+    return res
+
+
 def cpu_baseline_run(steps=1):
     """Times the FP64 oracle on a bounded sample of the workload."""
     from oracle import recon as R
@@ -142,6 +190,10 @@ def main():
                     help="WxH instead of 4096x4096 (profiling captures only)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=600,
+                    help="requests per serving run (0 = skip; 20000 = the full workload)")
+    ap.add_argument("--serve-loads", default="0.5,0.9",
+                    help="offered loads as fractions of the measured capacity")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -260,6 +312,11 @@ def main():
                "ms_per_step": round(ems, 4), "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(hout.nbytes)}
 
+    served = None
+    if rank == 0 and args.serve_requests > 0:
+        served = serve_leg(binding, torch, args.serve_requests,
+                           [float(v) for v in args.serve_loads.split(",")])
+
     if rank == 0:
         cb = None
         if world == 1 and not args.no_cpu_baseline:
@@ -281,7 +338,7 @@ def main():
                          "recon_gbs": round(recon_gbs, 1)},
             "peaks": peak_kind,
             "clocks": clocks, "e2e": e2e, "gpu_launches": int(launches),
-            "cpu_baseline": cb,
+            "cpu_baseline": cb, "served": served,
         }
         print(json.dumps(line), flush=True)
     ctx.close()

@@ -193,6 +193,37 @@ jxlr_status jxl_recon_poll(jxl_recon_ctx* ctx, uint64_t ticket, int64_t timeout_
  * the values stay until the next completed request of that slot. */
 jxlr_status jxl_recon_stage_ms(jxl_recon_ctx* ctx, uint64_t ticket, float ms[4]);
 
+/* One request of a serving schedule: the arguments of jxl_recon_submit(). */
+typedef struct {
+  const jxl_recon_coeffs* coeffs;
+  const uint8_t* varblock_map;
+  const float* quant_field;
+  const jxl_recon_cfl* cfl_map;
+  const jxl_recon_filter_params* filter_params;
+  const jxl_recon_output* out;
+} jxl_recon_request;
+
+typedef struct {
+  double makespan_s;       /* first arrival to last completion                  */
+  uint64_t busy_refusals;  /* admissions refused (no slot / HBM) and retried     */
+  uint64_t completed;      /* requests finished                                  */
+  uint32_t max_in_flight;  /* most requests running at once                      */
+} jxl_recon_serve_stats;
+
+/* Request loop (the draft's data-parallel decoding of independent images,
+ * 6.2 / 6.4, as a service).  Replays reqs[0..n) arriving at arrival_s[i]
+ * seconds after the call (non-decreasing): each arrived request is admitted
+ * in order as soon as the context has a free slot and room under its HBM cap
+ * (a refused request waits at the head of the queue until one in flight
+ * completes); admitted requests run concurrently on their slots' streams.
+ * latency_ms[i] receives completion - arrival of request i (queueing
+ * included).  Blocks until every request finished.  With max_slots = 1 the
+ * loop is the plain one-image-at-a-time path.  Returns JXLR_OK, or the first
+ * error a request produced (the others still complete). */
+jxlr_status jxl_recon_serve(jxl_recon_ctx* ctx, const jxl_recon_request* reqs, size_t n,
+                            const double* arrival_s, double* latency_ms,
+                            jxl_recon_serve_stats* stats);
+
 /* Number of kernels the context has launched so far. */
 uint64_t jxl_recon_launch_count(const jxl_recon_ctx* ctx);
 

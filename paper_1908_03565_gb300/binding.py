@@ -22,7 +22,7 @@ OUT_BYTES = {OUT_F32_LINEAR: 12, OUT_F16_LINEAR: 6, OUT_U8_SRGB: 3, OUT_F32_XYB:
 EXPORTS = ("jxl_recon_filter_defaults", "jxl_recon_create", "jxl_recon_submit",
            "jxl_recon_submit_xyb", "jxl_recon_poll", "jxl_recon_stage_ms",
            "jxl_recon_launch_count", "jxl_recon_device_bytes", "jxl_recon_destroy",
-           "jxl_recon_last_error", "jxl_recon_run_noalloc")
+           "jxl_recon_last_error", "jxl_recon_run_noalloc", "jxl_recon_serve")
 
 
 class Config(ctypes.Structure):
@@ -56,6 +56,17 @@ class FilterParams(ctypes.Structure):
 class Output(ctypes.Structure):
     _fields_ = [("data", ctypes.c_void_p), ("row_stride_bytes", ctypes.c_size_t),
                 ("dtype", ctypes.c_int), ("on_device", ctypes.c_int)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("coeffs", ctypes.c_void_p), ("varblock_map", ctypes.c_void_p),
+                ("quant_field", ctypes.c_void_p), ("cfl_map", ctypes.c_void_p),
+                ("filter_params", ctypes.c_void_p), ("out", ctypes.c_void_p)]
+
+
+class ServeStats(ctypes.Structure):
+    _fields_ = [("makespan_s", ctypes.c_double), ("busy_refusals", ctypes.c_uint64),
+                ("completed", ctypes.c_uint64), ("max_in_flight", ctypes.c_uint32)]
 
 
 _lib = None
@@ -96,6 +107,9 @@ def load(path=LIB_PATH):
     lib.jxl_recon_destroy.restype = ctypes.c_int
     lib.jxl_recon_last_error.argtypes = [ctypes.c_void_p]
     lib.jxl_recon_last_error.restype = ctypes.c_char_p
+    lib.jxl_recon_serve.argtypes = [ctypes.c_void_p, P(Request), ctypes.c_size_t,
+                                    P(ctypes.c_double), P(ctypes.c_double), P(ServeStats)]
+    lib.jxl_recon_serve.restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -216,6 +230,37 @@ class Context:
         if st != JXLR_OK:
             raise JxlrError(st, self.last_error())
         return st, lat.value
+
+    def serve(self, jobs, arrival_s):
+        """jobs: list of (img, params, out, out_dtype) with device-resident
+        arrays (torch CUDA tensors).  Replays the arrival schedule through the
+        native request loop; returns (latency_ms array, stats dict)."""
+        n = len(jobs)
+        keep = []
+        reqs = (Request * n)()
+        for i, (img, params, out, dtype) in enumerate(jobs):
+            co = img['coeffs']
+            planes = (ctypes.c_void_p * 3)(*[_ptr(co[c]) for c in range(3)])
+            c = Coeffs(img['xsize'], img['ysize'], planes, co.shape[2], 1)
+            cfl = Cfl(_ptr(img['cfl']), 0.0, 0.0)
+            p = FilterParams()
+            ctypes.pointer(p)[0] = params
+            if p.epf:
+                p.sharpness = _ptr(img['sharpness'])
+            o = Output(_ptr(out), OUT_BYTES[dtype] * img['xsize'], dtype, 1)
+            keep += [planes, c, cfl, p, o, img, out]
+            reqs[i] = Request(ctypes.addressof(c), _ptr(img['vmap']), _ptr(img['acmul']),
+                              ctypes.addressof(cfl), ctypes.addressof(p), ctypes.addressof(o))
+        arr = (ctypes.c_double * n)(*arrival_s)
+        lat = (ctypes.c_double * n)()
+        stats = ServeStats()
+        st = self.lib.jxl_recon_serve(self.h, reqs, n, arr, lat, ctypes.byref(stats))
+        if st != JXLR_OK:
+            raise JxlrError(st, self.last_error())
+        return np.array(lat[:]), {"makespan_s": stats.makespan_s,
+                                  "busy_refusals": stats.busy_refusals,
+                                  "completed": stats.completed,
+                                  "max_in_flight": stats.max_in_flight}
 
     def stage_ms(self, ticket):
         ms = (ctypes.c_float * 4)()
