@@ -144,6 +144,63 @@ def serve_leg(binding, torch, n_req, loads, pool_n=24, seed=4000, slots=8):
     return res
 
 
+def batch_leg(binding, torch, n_img=512, pool_n=64, seed=3000, reps=10):
+    """Config-3 style batching: 512 images with sides log-uniform in
+    [64, 2048] (multiples of 8; drawn from a pool of 64 distinct images with
+    config-1 statistics), EPF + Gaborish, half u8 sRGB and half f16 linear
+    outputs; one multi-image launch per kernel kind, autotuned grids, replayed
+    as a CUDA graph; against the plain path (one submit + poll per image)."""
+    import math
+    from paper_1908_03565_gb300 import synth
+    rng = np.random.default_rng(seed)
+    sides = (np.exp(rng.uniform(math.log(64), math.log(2048), size=(pool_n, 2))) // 8 * 8).astype(int)
+    pool = [binding.to_device(synth.make_image(int(x), int(y), seed + i), torch)
+            for i, (x, y) in enumerate(sides)]
+    params = binding.filter_defaults(epf=1, gab=1)
+    jobs = []
+    for i, k in enumerate(rng.integers(0, pool_n, n_img)):
+        img = pool[k]
+        if i % 2 == 0:
+            dt, tdt = binding.OUT_U8_SRGB, torch.uint8
+        else:
+            dt, tdt = binding.OUT_F16_LINEAR, torch.float16
+        out = torch.empty((img['ysize'], img['xsize'], 3), dtype=tdt, device="cuda")
+        jobs.append((img, params, out, dt))
+    px = sum(j[0]['xsize'] * j[0]['ysize'] for j in jobs)
+    stream = torch.cuda.Stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with binding.Context(max_slots=1, stream=stream.cuda_stream) as ctx:
+        b = ctx.batch(jobs, autotune=True)
+        for _ in range(3):
+            b.launch(stream.cuda_stream)
+        stream.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            b.launch(stream.cuda_stream)
+        e1.record(stream)
+        stream.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        info = b.info()
+        b.close()
+        # plain per-image path
+        for img, p, out, dt in jobs[:8]:
+            ctx.poll(ctx.submit(img, p, out, dt, on_device=True))
+        stream.synchronize()
+        e0.record(stream)
+        for img, p, out, dt in jobs:
+            ctx.poll(ctx.submit(img, p, out, dt, on_device=True))
+        e1.record(stream)
+        stream.synchronize()
+        pms = e0.elapsed_time(e1)
+    return {"images": n_img, "mpx_per_batch": round(px / 1e6, 2),
+            "batch_ms": round(ms, 3), "batch_mpx_s": round(px / ms / 1e3, 1),
+            "plain_ms": round(pms, 3), "plain_mpx_s": round(px / pms / 1e3, 1),
+            "graph_kernels": info["kernels_per_launch"],
+            "grids": [info["recon_grid"], info["epf_grid"], info["filter_grid"]],
+            "work_items": [info["recon_items"], info["epf_items"], info["filter_items"]],
+            "autotuned": info["autotuned"], "outputs": "u8 sRGB / f16 linear alternating"}
+
+
 def cpu_baseline_run(steps=1):
     """Times the FP64 oracle on a bounded sample of the workload."""
     from oracle import recon as R
@@ -192,6 +249,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=600,
                     help="requests per serving run (0 = skip; 20000 = the full workload)")
+    ap.add_argument("--batch-images", type=int, default=512,
+                    help="images in the multi-image batch leg (0 = skip)")
     ap.add_argument("--serve-loads", default="0.5,0.9",
                     help="offered loads as fractions of the measured capacity")
     args = ap.parse_args()
@@ -312,6 +371,9 @@ def main():
                "ms_per_step": round(ems, 4), "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(hout.nbytes)}
 
+    batched = None
+    if rank == 0 and args.batch_images > 0:
+        batched = batch_leg(binding, torch, args.batch_images)
     served = None
     if rank == 0 and args.serve_requests > 0:
         served = serve_leg(binding, torch, args.serve_requests,
@@ -338,7 +400,7 @@ def main():
                          "recon_gbs": round(recon_gbs, 1)},
             "peaks": peak_kind,
             "clocks": clocks, "e2e": e2e, "gpu_launches": int(launches),
-            "cpu_baseline": cb, "served": served,
+            "cpu_baseline": cb, "batched": batched, "served": served,
         }
         print(json.dumps(line), flush=True)
     ctx.close()

@@ -224,6 +224,37 @@ jxlr_status jxl_recon_serve(jxl_recon_ctx* ctx, const jxl_recon_request* reqs, s
                             const double* arrival_s, double* latency_ms,
                             jxl_recon_serve_stats* stats);
 
+/* Multi-image batches (the draft's independent groups, 6.2, taken across
+ * images): many uneven images reconstructed by one launch per kernel kind,
+ * captured once in a CUDA graph and replayed by jxl_recon_batch_launch().
+ * Every request must be device-resident (inputs and output) with the
+ * default dequantisation matrices; the batch owns the XYB/sigma scratch of
+ * all its images (allocated at creation).  Maps are validated at creation
+ * (JXLR_EINVAL).  With JXLR_BATCH_AUTOTUNE the grid of each kernel is
+ * chosen by timing candidates on this batch (remembered per batch shape in
+ * the process and in $JXLR_AUTOTUNE_CACHE if set); otherwise a remembered
+ * choice is used, else one CTA per work item.  The inputs and outputs of
+ * the requests must stay valid for the batch's lifetime. */
+typedef struct jxl_recon_batch jxl_recon_batch;
+#define JXLR_BATCH_AUTOTUNE 1
+
+typedef struct {
+  uint32_t images;
+  uint64_t pixels;
+  uint32_t recon_items, epf_items, filter_items;   /* cells / tiles */
+  int recon_grid, epf_grid, filter_grid;           /* CTAs per launch */
+  int kernels_per_launch;
+  int autotuned;                                   /* 0 no, 1 tuned now, 2 cached */
+} jxl_recon_batch_info;
+
+jxlr_status jxl_recon_batch_create(jxl_recon_ctx* ctx, const jxl_recon_request* reqs, size_t n,
+                                   int flags, jxl_recon_batch** out);
+/* Enqueues the whole batch on cuda_stream (a cudaStream_t; NULL = legacy
+ * default stream) and returns; completion is the stream's. */
+jxlr_status jxl_recon_batch_launch(jxl_recon_batch* batch, void* cuda_stream);
+jxlr_status jxl_recon_batch_query(const jxl_recon_batch* batch, jxl_recon_batch_info* info);
+jxlr_status jxl_recon_batch_destroy(jxl_recon_batch* batch);
+
 /* Number of kernels the context has launched so far. */
 uint64_t jxl_recon_launch_count(const jxl_recon_ctx* ctx);
 

@@ -22,7 +22,9 @@ OUT_BYTES = {OUT_F32_LINEAR: 12, OUT_F16_LINEAR: 6, OUT_U8_SRGB: 3, OUT_F32_XYB:
 EXPORTS = ("jxl_recon_filter_defaults", "jxl_recon_create", "jxl_recon_submit",
            "jxl_recon_submit_xyb", "jxl_recon_poll", "jxl_recon_stage_ms",
            "jxl_recon_launch_count", "jxl_recon_device_bytes", "jxl_recon_destroy",
-           "jxl_recon_last_error", "jxl_recon_run_noalloc", "jxl_recon_serve")
+           "jxl_recon_last_error", "jxl_recon_run_noalloc", "jxl_recon_serve",
+           "jxl_recon_batch_create", "jxl_recon_batch_launch", "jxl_recon_batch_query",
+           "jxl_recon_batch_destroy")
 
 
 class Config(ctypes.Structure):
@@ -69,6 +71,15 @@ class ServeStats(ctypes.Structure):
                 ("completed", ctypes.c_uint64), ("max_in_flight", ctypes.c_uint32)]
 
 
+class BatchInfo(ctypes.Structure):
+    _fields_ = [("images", ctypes.c_uint32), ("pixels", ctypes.c_uint64),
+                ("recon_items", ctypes.c_uint32), ("epf_items", ctypes.c_uint32),
+                ("filter_items", ctypes.c_uint32), ("recon_grid", ctypes.c_int),
+                ("epf_grid", ctypes.c_int), ("filter_grid", ctypes.c_int),
+                ("kernels_per_launch", ctypes.c_int), ("autotuned", ctypes.c_int)]
+
+
+BATCH_AUTOTUNE = 1
 _lib = None
 
 
@@ -110,6 +121,15 @@ def load(path=LIB_PATH):
     lib.jxl_recon_serve.argtypes = [ctypes.c_void_p, P(Request), ctypes.c_size_t,
                                     P(ctypes.c_double), P(ctypes.c_double), P(ServeStats)]
     lib.jxl_recon_serve.restype = ctypes.c_int
+    lib.jxl_recon_batch_create.argtypes = [ctypes.c_void_p, P(Request), ctypes.c_size_t,
+                                           ctypes.c_int, P(ctypes.c_void_p)]
+    lib.jxl_recon_batch_create.restype = ctypes.c_int
+    lib.jxl_recon_batch_launch.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+    lib.jxl_recon_batch_launch.restype = ctypes.c_int
+    lib.jxl_recon_batch_query.argtypes = [ctypes.c_void_p, P(BatchInfo)]
+    lib.jxl_recon_batch_query.restype = ctypes.c_int
+    lib.jxl_recon_batch_destroy.argtypes = [ctypes.c_void_p]
+    lib.jxl_recon_batch_destroy.restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -236,21 +256,7 @@ class Context:
         arrays (torch CUDA tensors).  Replays the arrival schedule through the
         native request loop; returns (latency_ms array, stats dict)."""
         n = len(jobs)
-        keep = []
-        reqs = (Request * n)()
-        for i, (img, params, out, dtype) in enumerate(jobs):
-            co = img['coeffs']
-            planes = (ctypes.c_void_p * 3)(*[_ptr(co[c]) for c in range(3)])
-            c = Coeffs(img['xsize'], img['ysize'], planes, co.shape[2], 1)
-            cfl = Cfl(_ptr(img['cfl']), 0.0, 0.0)
-            p = FilterParams()
-            ctypes.pointer(p)[0] = params
-            if p.epf:
-                p.sharpness = _ptr(img['sharpness'])
-            o = Output(_ptr(out), OUT_BYTES[dtype] * img['xsize'], dtype, 1)
-            keep += [planes, c, cfl, p, o, img, out]
-            reqs[i] = Request(ctypes.addressof(c), _ptr(img['vmap']), _ptr(img['acmul']),
-                              ctypes.addressof(cfl), ctypes.addressof(p), ctypes.addressof(o))
+        reqs, keep = requests(jobs)
         arr = (ctypes.c_double * n)(*arrival_s)
         lat = (ctypes.c_double * n)()
         stats = ServeStats()
@@ -261,6 +267,10 @@ class Context:
                                   "busy_refusals": stats.busy_refusals,
                                   "completed": stats.completed,
                                   "max_in_flight": stats.max_in_flight}
+
+    def batch(self, jobs, autotune=True):
+        """A multi-image batch (CUDA graph) over device-resident jobs."""
+        return Batch(self, jobs, autotune)
 
     def stage_ms(self, ticket):
         ms = (ctypes.c_float * 4)()
@@ -274,6 +284,64 @@ class Context:
 
     def device_bytes(self):
         return self.lib.jxl_recon_device_bytes(self.h)
+
+
+def requests(jobs):
+    """Request array for (img, params, out, out_dtype) device jobs, plus the
+    ctypes objects that must stay alive with it."""
+    n = len(jobs)
+    keep = []
+    reqs = (Request * n)()
+    for i, (img, params, out, dtype) in enumerate(jobs):
+        co = img['coeffs']
+        planes = (ctypes.c_void_p * 3)(*[_ptr(co[c]) for c in range(3)])
+        c = Coeffs(img['xsize'], img['ysize'], planes, co.shape[2], 1)
+        cfl = Cfl(_ptr(img['cfl']), 0.0, 0.0)
+        p = FilterParams()
+        ctypes.pointer(p)[0] = params
+        if p.epf:
+            p.sharpness = _ptr(img['sharpness'])
+        o = Output(_ptr(out), OUT_BYTES[dtype] * img['xsize'], dtype, 1)
+        keep += [planes, c, cfl, p, o, img, out]
+        reqs[i] = Request(ctypes.addressof(c), _ptr(img['vmap']), _ptr(img['acmul']),
+                          ctypes.addressof(cfl), ctypes.addressof(p), ctypes.addressof(o))
+    return reqs, keep
+
+
+class Batch:
+    """jxl_recon_batch: create once, launch (graph replay) many times."""
+
+    def __init__(self, ctx, jobs, autotune=True):
+        self.ctx = ctx
+        self.lib = ctx.lib
+        self.reqs, self.keep = requests(jobs)
+        h = ctypes.c_void_p()
+        st = self.lib.jxl_recon_batch_create(ctx.h, self.reqs, len(jobs),
+                                             BATCH_AUTOTUNE if autotune else 0, ctypes.byref(h))
+        if st != JXLR_OK:
+            raise JxlrError(st, ctx.last_error())
+        self.h = h
+
+    def launch(self, stream=0):
+        st = self.lib.jxl_recon_batch_launch(self.h, stream or None)
+        if st != JXLR_OK:
+            raise JxlrError(st, self.ctx.last_error())
+
+    def info(self):
+        i = BatchInfo()
+        self.lib.jxl_recon_batch_query(self.h, ctypes.byref(i))
+        return {k: getattr(i, k) for k, _ in BatchInfo._fields_}
+
+    def close(self):
+        if self.h:
+            self.lib.jxl_recon_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def to_device(img, torch_module, device="cuda"):

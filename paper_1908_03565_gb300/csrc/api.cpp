@@ -82,6 +82,12 @@ struct jxl_recon_ctx {
   std::unordered_map<uint64_t, Timing> timings;
 };
 
+namespace jxlr {
+const float* ctx_default_dequant(const jxl_recon_ctx* c) { return c->d_dequant; }
+int ctx_device(const jxl_recon_ctx* c) { return c->device; }
+void ctx_count_launches(jxl_recon_ctx* c, int n) { c->launches += n; }
+}  // namespace jxlr
+
 extern "C" {
 
 void jxl_recon_filter_defaults(jxl_recon_filter_params* p) {
@@ -220,55 +226,6 @@ bool host_map_valid(const uint8_t* vmap, int bw, int bh, std::string* why) {
   for (auto c : cov)
     if (c != 1) { *why = "blocks not covered by exactly one varblock"; return false; }
   return true;
-}
-
-ColorParams color_params(const jxl_recon_filter_params& p) {
-  ColorParams cp;
-  const double div = p.target_nits_div50 * 50.0 / 250.0 * 255.0;
-  for (int i = 0; i < 9; ++i) cp.m[i] = static_cast<float>(p.inv_opsin[i] / div);
-  for (int i = 0; i < 3; ++i) cp.bias[i] = p.opsin_bias[i];
-  return cp;
-}
-
-SigmaParams sigma_params(const jxl_recon_filter_params& p) {
-  SigmaParams sp;
-  const double im3 = std::cbrt(p.target_nits_div50 * 50.0 / 250.0);
-  for (int c = 0; c < 3; ++c) {
-    sp.gmin[c] = static_cast<float>((c == 0 ? -0.03 : 0.0) * im3);
-    sp.gscale[c] = p.epf_scale[c];
-  }
-  sp.range_max = p.epf_range_max;
-  sp.range_mul = p.epf_range_mul;
-  sp.quant_mul = p.epf_quant_mul;
-  sp.sigma_max = static_cast<float>(p.epf_sigma_max);
-  for (int i = 0; i < 8; ++i) sp.lut[i] = p.epf_sharp_lut[i];
-  return sp;
-}
-
-uint32_t weight_min_bits(float wmin) {
-  // smallest binary32 value >= wmin (weights below it are dropped, J.2.5)
-  if (!(wmin > 0)) return 0;
-  uint32_t b;
-  std::memcpy(&b, &wmin, 4);
-  return b;
-}
-
-FilterArgs filter_args(const jxl_recon_filter_params& p) {
-  FilterArgs f;
-  std::memset(&f, 0, sizeof(f));
-  f.epf = p.epf != 0;
-  f.gab = p.gab != 0;
-  for (int c = 0; c < 3; ++c) {
-    const double w1 = p.gab_w1[c], w2 = p.gab_w2[c];
-    const double n = 1.0 + 4.0 * w1 + 4.0 * w2;
-    f.gw[c][0] = static_cast<float>(1.0 / n);
-    f.gw[c][1] = static_cast<float>(w1 / n);
-    f.gw[c][2] = static_cast<float>(w2 / n);
-  }
-  f.wmin_bits = weight_min_bits(p.epf_weight_min);
-  f.sp = sigma_params(p);
-  f.cp = color_params(p);
-  return f;
 }
 
 // Finds a free slot and makes sure its arena holds `need` bytes within the

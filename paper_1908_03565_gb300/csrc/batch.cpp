@@ -1,0 +1,385 @@
+// Multi-image batches: one launch per kernel kind for many uneven images,
+// captured once in a CUDA graph and replayed.
+//
+// Every image keeps its own parameter block (sizes, pointers, filters,
+// output encoding) in device memory; the multi-image kernels map their work
+// items (32x32 cells for the transforms, filter tiles) to (image, cell) by a
+// prefix array.  The grid of each kernel (one CTA per item, or a persistent
+// multiple of the resident CTAs) is chosen by timing on the batch itself
+// when JXLR_BATCH_AUTOTUNE is set, and remembered per batch shape (in this
+// process, and in the file named by $JXLR_AUTOTUNE_CACHE if set).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <fstream>
+#include <map>
+#include <mutex>
+#include <sstream>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/jxl_recon.h"
+#include "internal.h"
+#include "kernels.h"
+
+using namespace jxlr;
+
+struct jxl_recon_batch {
+  jxl_recon_ctx* ctx = nullptr;
+  int device = 0;
+  uint32_t n = 0;
+  uint64_t pixels = 0;
+  char* dmem = nullptr;
+  ReconArgs* d_rargs = nullptr;
+  int* d_rprefix = nullptr;
+  int rtotal = 0;
+  FilterArgs* d_eargs = nullptr;   // images with the EPF
+  int* d_eprefix = nullptr;
+  int ne = 0, etotal = 0;
+  bool clamp = false;
+  FilterArgs* d_fargs = nullptr;   // images with Gaborish only
+  int* d_fprefix = nullptr;
+  int nf = 0, ftotal = 0;
+  int grid[3] = {0, 0, 0};         // recon, epf, filter
+  int autotuned = 0;
+  cudaStream_t cap = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int kernels = 0;
+};
+
+namespace {
+
+size_t up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+jxlr_status bfail(jxlr_status s, const std::string& m) {
+  set_last_error(m);
+  return s;
+}
+
+void enqueue(const jxl_recon_batch* b, const int* grid, cudaStream_t s) {
+  if (b->rtotal) launch_recon_batch(b->d_rargs, b->d_rprefix, static_cast<int>(b->n), b->rtotal,
+                                    grid[0], s);
+  if (b->etotal) launch_filter_batch(b->d_eargs, b->d_eprefix, b->ne, b->etotal, true, b->clamp,
+                                     grid[1], s);
+  if (b->ftotal) launch_filter_batch(b->d_fargs, b->d_fprefix, b->nf, b->ftotal, false, false,
+                                     grid[2], s);
+}
+
+using Key = std::tuple<uint32_t, int, int, int>;
+std::mutex g_tune_mu;
+std::map<Key, std::vector<int>> g_tuned;
+
+bool tuned_lookup(const Key& k, int* grid) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  auto it = g_tuned.find(k);
+  if (it == g_tuned.end()) {
+    const char* path = std::getenv("JXLR_AUTOTUNE_CACHE");
+    if (!path) return false;
+    std::ifstream f(path);
+    uint32_t n;
+    int a, b, c, g0, g1, g2;
+    while (f >> n >> a >> b >> c >> g0 >> g1 >> g2)
+      g_tuned[Key(n, a, b, c)] = {g0, g1, g2};
+    it = g_tuned.find(k);
+    if (it == g_tuned.end()) return false;
+  }
+  for (int i = 0; i < 3; ++i) grid[i] = it->second[i];
+  return true;
+}
+
+void tuned_store(const Key& k, const int* grid) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  g_tuned[k] = {grid[0], grid[1], grid[2]};
+  if (const char* path = std::getenv("JXLR_AUTOTUNE_CACHE")) {
+    std::ofstream f(path, std::ios::app);
+    f << std::get<0>(k) << ' ' << std::get<1>(k) << ' ' << std::get<2>(k) << ' '
+      << std::get<3>(k) << ' ' << grid[0] << ' ' << grid[1] << ' ' << grid[2] << '\n';
+  }
+}
+
+// Times candidate grids for each kernel kind on the batch itself and keeps
+// the fastest (median of 3 after a warm-up).
+jxlr_status autotune(jxl_recon_batch* b) {
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
+  const int kinds[3] = {0, b->clamp ? 2 : 1, 3};
+  const int totals[3] = {b->rtotal, b->etotal, b->ftotal};
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  for (int k = 0; k < 3; ++k) {
+    if (!totals[k]) continue;
+    const int res = sms * batch_blocks_per_sm(kinds[k]);
+    std::vector<int> cand = {totals[k]};
+    for (int f : {1, 2, 4})
+      if (f * res < totals[k]) cand.push_back(f * res);
+    float best = 1e30f;
+    int bestg = totals[k];
+    for (int g : cand) {
+      int grid[3] = {b->grid[0], b->grid[1], b->grid[2]};
+      grid[k] = g;
+      std::vector<float> t;
+      for (int rep = 0; rep < 4; ++rep) {
+        cudaEventRecord(e0, b->cap);
+        if (k == 0) launch_recon_batch(b->d_rargs, b->d_rprefix, b->n, b->rtotal, g, b->cap);
+        else if (k == 1)
+          launch_filter_batch(b->d_eargs, b->d_eprefix, b->ne, b->etotal, true, b->clamp, g, b->cap);
+        else launch_filter_batch(b->d_fargs, b->d_fprefix, b->nf, b->ftotal, false, false, g, b->cap);
+        cudaEventRecord(e1, b->cap);
+        cudaEventSynchronize(e1);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (rep) t.push_back(ms);
+      }
+      std::sort(t.begin(), t.end());
+      if (t[1] < best) {
+        best = t[1];
+        bestg = g;
+      }
+    }
+    b->grid[k] = bestg;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? JXLR_OK : bfail(JXLR_ECUDA, std::string("autotune: ") + cudaGetErrorString(e));
+}
+
+}  // namespace
+
+extern "C" jxlr_status jxl_recon_batch_destroy(jxl_recon_batch* b) {
+  if (!b) return JXLR_OK;
+  cudaSetDevice(b->device);
+  if (b->cap) cudaStreamSynchronize(b->cap);
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  if (b->cap) cudaStreamDestroy(b->cap);
+  if (b->dmem) cudaFree(b->dmem);
+  delete b;
+  return JXLR_OK;
+}
+
+extern "C" jxlr_status jxl_recon_batch_create(jxl_recon_ctx* ctx, const jxl_recon_request* reqs,
+                                              size_t n, int flags, jxl_recon_batch** out) {
+  if (!ctx || !reqs || !out || n == 0 || n > (1u << 20))
+    return bfail(JXLR_EINVAL, "batch_create: bad arguments");
+  const int dev = ctx_device(ctx);
+  if (cudaSetDevice(dev) != cudaSuccess) return bfail(JXLR_ECUDA, "batch_create: set device");
+  std::vector<ReconArgs> ra(n);
+  std::vector<FilterArgs> ea, fa;
+  std::vector<int> rpre(1, 0), epre(1, 0), fpre(1, 0);
+  std::vector<size_t> scratch_off(n, 0), sig_off(n, 0);
+  std::vector<int> eimg, fimg;
+  size_t scratch = 0;
+  uint64_t pixels = 0;
+  for (size_t i = 0; i < n; ++i) {
+    const jxl_recon_request& r = reqs[i];
+    const jxl_recon_coeffs* co = r.coeffs;
+    const jxl_recon_filter_params* fp = r.filter_params;
+    const jxl_recon_output* o = r.out;
+    if (!co || !fp || !o || !r.varblock_map || !r.quant_field || !r.cfl_map || !r.cfl_map->k)
+      return bfail(JXLR_EINVAL, "batch_create: null field in request " + std::to_string(i));
+    if (!co->on_device || !o->on_device || fp->dequant)
+      return bfail(JXLR_EINVAL, "batch_create: requests must be device-resident with default matrices");
+    const int xs = static_cast<int>(co->xsize), ys = static_cast<int>(co->ysize);
+    if (xs <= 0 || ys <= 0 || xs > 65536 || ys > 65536)
+      return bfail(JXLR_EINVAL, "batch_create: image size");
+    const int wp = (xs + 7) & ~7, hp = (ys + 7) & ~7, bw = wp / 8, bh = hp / 8;
+    if (co->row_stride_elems < size_t(wp) || co->row_stride_elems % 8)
+      return bfail(JXLR_EINVAL, "batch_create: coefficient row stride");
+    for (int c = 0; c < 3; ++c)
+      if (!co->plane[c] || (reinterpret_cast<uintptr_t>(co->plane[c]) & 15))
+        return bfail(JXLR_EINVAL, "batch_create: coefficient planes must be 16-byte aligned");
+    const size_t px_bytes = o->dtype == 1 ? 6 : o->dtype == 2 ? 3 : 12;
+    if (o->dtype < 0 || o->dtype > 3 || !o->data || o->row_stride_bytes < px_bytes * xs)
+      return bfail(JXLR_EINVAL, "batch_create: bad output");
+    if (fp->epf && !fp->sharpness) return bfail(JXLR_EINVAL, "batch_create: EPF needs sharpness");
+    pixels += uint64_t(xs) * ys;
+    ReconArgs& a = ra[i];
+    std::memset(&a, 0, sizeof(a));
+    for (int c = 0; c < 3; ++c) a.coef[c] = co->plane[c];
+    a.cstride = co->row_stride_elems;
+    a.vmap = r.varblock_map;
+    a.acmul = r.quant_field;
+    a.cfl = r.cfl_map->k;
+    a.sharp = fp->sharpness;
+    a.dequant = ctx_default_dequant(ctx);
+    a.xs = xs; a.ys = ys; a.wp = wp; a.hp = hp; a.bw = bw; a.bh = bh; a.tw = (wp + 63) / 64;
+    const double bias[3] = {0.05465007330715401, 0.07005449891748593, 0.049935103337343655};
+    for (int c = 0; c < 3; ++c) {
+      a.m_dc[c] = fp->m_dc[c];
+      a.one_minus_bias[c] = static_cast<float>(1.0 - bias[c]);
+    }
+    a.kx_dc = r.cfl_map->kx_dc;
+    a.kb_dc = r.cfl_map->kb_dc;
+    a.sp = sigma_params(*fp);
+    a.cp = color_params(*fp);
+    OutParams op;
+    op.data = o->data;
+    op.stride = o->row_stride_bytes;
+    op.dtype = o->dtype;
+    rpre.push_back(rpre.back() + ((wp + 31) / 32) * ((hp + 31) / 32));
+    if (fp->epf || fp->gab) {
+      a.write_xyb = 1;
+      scratch = up(scratch, 256);
+      scratch_off[i] = scratch;
+      scratch += sizeof(float) * 3 * size_t(wp) * hp;
+      if (fp->epf) {
+        scratch = up(scratch, 256);
+        sig_off[i] = scratch;
+        scratch += sizeof(int16_t) * size_t(bw) * bh;
+      }
+      FilterArgs f = filter_args(*fp);
+      f.rstride = wp;
+      f.pstride = size_t(wp) * hp;
+      f.xs = xs; f.ys = ys; f.bw = bw;
+      f.out = op;
+      if (fp->epf) {
+        ea.push_back(f);
+        eimg.push_back(static_cast<int>(i));
+        epre.push_back(epre.back() + filter_tiles(f));
+      } else {
+        fa.push_back(f);
+        fimg.push_back(static_cast<int>(i));
+        fpre.push_back(fpre.back() + filter_tiles(f));
+      }
+    } else {
+      a.write_xyb = 0;
+      a.out = op;
+    }
+  }
+  auto* b = new jxl_recon_batch();
+  b->ctx = ctx;
+  b->device = dev;
+  b->n = static_cast<uint32_t>(n);
+  b->pixels = pixels;
+  b->ne = static_cast<int>(ea.size());
+  b->nf = static_cast<int>(fa.size());
+  b->rtotal = rpre.back();
+  b->etotal = epre.back();
+  b->ftotal = fpre.back();
+  // one device allocation: parameter blocks, prefixes, statuses, scratch
+  size_t off = 0;
+  auto take = [&](size_t bytes) { off = up(off, 256); size_t o = off; off += bytes; return o; };
+  const size_t o_r = take(sizeof(ReconArgs) * n), o_rp = take(sizeof(int) * rpre.size());
+  const size_t o_e = take(sizeof(FilterArgs) * ea.size()), o_ep = take(sizeof(int) * epre.size());
+  const size_t o_f = take(sizeof(FilterArgs) * fa.size()), o_fp = take(sizeof(int) * fpre.size());
+  const size_t o_st = take(sizeof(unsigned) * 4 * n);
+  const size_t o_sc = take(scratch);
+  cudaError_t e = cudaMalloc(&b->dmem, up(off, 256));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    jxl_recon_batch_destroy(b);
+    return bfail(JXLR_ENOMEM, "batch_create: device allocation failed");
+  }
+  char* base = b->dmem;
+  for (size_t i = 0; i < n; ++i) {
+    if (ra[i].write_xyb) {
+      ra[i].xyb = reinterpret_cast<float*>(base + o_sc + scratch_off[i]);
+      ra[i].sigma = reqs[i].filter_params->epf
+                        ? reinterpret_cast<int16_t*>(base + o_sc + sig_off[i]) : nullptr;
+    }
+  }
+  for (size_t j = 0; j < ea.size(); ++j) {
+    ea[j].xyb = ra[eimg[j]].xyb;
+    ea[j].sigma = ra[eimg[j]].sigma;
+    b->clamp = b->clamp || filter_needs_clamp(ea[j]);
+  }
+  for (size_t j = 0; j < fa.size(); ++j) fa[j].xyb = ra[fimg[j]].xyb;
+  b->d_rargs = reinterpret_cast<ReconArgs*>(base + o_r);
+  b->d_rprefix = reinterpret_cast<int*>(base + o_rp);
+  b->d_eargs = reinterpret_cast<FilterArgs*>(base + o_e);
+  b->d_eprefix = reinterpret_cast<int*>(base + o_ep);
+  b->d_fargs = reinterpret_cast<FilterArgs*>(base + o_f);
+  b->d_fprefix = reinterpret_cast<int*>(base + o_fp);
+  unsigned* d_status = reinterpret_cast<unsigned*>(base + o_st);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+  auto h2d = [&](void* d, const void* h, size_t bytes) {
+    if (e == cudaSuccess && bytes) e = cudaMemcpyAsync(d, h, bytes, cudaMemcpyHostToDevice, b->cap);
+  };
+  h2d(b->d_rargs, ra.data(), sizeof(ReconArgs) * n);
+  h2d(b->d_rprefix, rpre.data(), sizeof(int) * rpre.size());
+  h2d(b->d_eargs, ea.data(), sizeof(FilterArgs) * ea.size());
+  h2d(b->d_eprefix, epre.data(), sizeof(int) * epre.size());
+  h2d(b->d_fargs, fa.data(), sizeof(FilterArgs) * fa.size());
+  h2d(b->d_fprefix, fpre.data(), sizeof(int) * fpre.size());
+  // C.5.4 validation of every map, once, at creation
+  if (e == cudaSuccess) e = cudaMemsetAsync(d_status, 0, sizeof(unsigned) * 4 * n, b->cap);
+  for (size_t i = 0; i < n && e == cudaSuccess; ++i)
+    launch_validate(reqs[i].varblock_map, ra[i].bw, ra[i].bh, d_status + 4 * i, b->cap);
+  std::vector<unsigned> st(4 * n);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(st.data(), d_status, sizeof(unsigned) * 4 * n, cudaMemcpyDeviceToHost, b->cap);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->cap);
+  if (e != cudaSuccess) {
+    jxl_recon_batch_destroy(b);
+    return bfail(JXLR_ECUDA, std::string("batch_create: ") + cudaGetErrorString(e));
+  }
+  for (size_t i = 0; i < n; ++i)
+    if (st[4 * i] != 0) {
+      jxl_recon_batch_destroy(b);
+      return bfail(JXLR_EINVAL, "batch_create: DctSelect map of request " + std::to_string(i) +
+                                    " is ill-formed");
+    }
+  ctx_count_launches(ctx, static_cast<int>(n));
+  // grids: cached tuning, fresh tuning, or one CTA per work item
+  b->grid[0] = b->rtotal;
+  b->grid[1] = b->etotal;
+  b->grid[2] = b->ftotal;
+  const Key key(b->n, b->rtotal, b->etotal, b->ftotal);
+  if (tuned_lookup(key, b->grid)) {
+    b->autotuned = 2;
+  } else if (flags & JXLR_BATCH_AUTOTUNE) {
+    jxlr_status ts = autotune(b);
+    if (ts != JXLR_OK) {
+      jxl_recon_batch_destroy(b);
+      return ts;
+    }
+    tuned_store(key, b->grid);
+    b->autotuned = 1;
+  }
+  for (int k = 0; k < 3; ++k) b->grid[k] = std::max(1, b->grid[k]);
+  // capture the launches once
+  e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    enqueue(b, b->grid, b->cap);
+    e = cudaStreamEndCapture(b->cap, &b->graph);
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+  if (e != cudaSuccess) {
+    jxl_recon_batch_destroy(b);
+    return bfail(JXLR_ECUDA, std::string("batch graph: ") + cudaGetErrorString(e));
+  }
+  b->kernels = (b->rtotal > 0) + (b->etotal > 0) + (b->ftotal > 0);
+  *out = b;
+  return JXLR_OK;
+}
+
+extern "C" jxlr_status jxl_recon_batch_launch(jxl_recon_batch* b, void* cuda_stream) {
+  if (!b) return bfail(JXLR_EINVAL, "batch_launch: null batch");
+  if (cudaSetDevice(b->device) != cudaSuccess) return bfail(JXLR_ECUDA, "batch_launch: set device");
+  cudaError_t e = cudaGraphLaunch(b->exec, static_cast<cudaStream_t>(cuda_stream));
+  if (e != cudaSuccess) return bfail(JXLR_ECUDA, std::string("batch_launch: ") + cudaGetErrorString(e));
+  ctx_count_launches(b->ctx, b->kernels);
+  return JXLR_OK;
+}
+
+extern "C" jxlr_status jxl_recon_batch_query(const jxl_recon_batch* b, jxl_recon_batch_info* info) {
+  if (!b || !info) return bfail(JXLR_EINVAL, "batch_query: null argument");
+  info->images = b->n;
+  info->pixels = b->pixels;
+  info->recon_items = b->rtotal;
+  info->epf_items = b->etotal;
+  info->filter_items = b->ftotal;
+  info->recon_grid = b->grid[0];
+  info->epf_grid = b->grid[1];
+  info->filter_grid = b->grid[2];
+  info->kernels_per_launch = b->kernels;
+  info->autotuned = b->autotuned;
+  return JXLR_OK;
+}

@@ -5,6 +5,8 @@
 #include <cstdint>
 #include <string>
 
+#include "../../include/jxl_recon.h"
+
 namespace jxlr {
 
 constexpr int kNumCodes = 15;          // DctSelect codes 0..14 (C.5.4)
@@ -55,6 +57,24 @@ void mul_table4(int32_t* out /* 673 */);
 
 // AFV basis of I.2.2, [coefficient][sample], 16 x 16.
 extern const double kAfvBasis[16][16];
+
+// Kernel parameter blocks from the C-ABI parameters (params.cpp).
+struct ColorParams;
+struct SigmaParams;
+struct FilterArgs;
+ColorParams color_params(const jxl_recon_filter_params& p);
+SigmaParams sigma_params(const jxl_recon_filter_params& p);
+uint32_t weight_min_bits(float wmin);
+FilterArgs filter_args(const jxl_recon_filter_params& p);
+
+// Context internals used by the batch path (api.cpp).
+const float* ctx_default_dequant(const jxl_recon_ctx* c);
+int ctx_device(const jxl_recon_ctx* c);
+void ctx_count_launches(jxl_recon_ctx* c, int n);
+
+// Resident CTAs per SM of the multi-image kernels (kernels.cu):
+// kind 0 recon, 1 EPF, 2 EPF exact-clamp, 3 Gaborish/colour only.
+int batch_blocks_per_sm(int kind);
 
 // Sets the message jxl_recon_last_error() returns on this thread (api.cpp).
 void set_last_error(const std::string& msg);

@@ -553,12 +553,13 @@ __device__ void cell_setup(CellState& cs, const uint8_t* __restrict__ vmap,
   __syncthreads();
 }
 
-__global__ void __launch_bounds__(128) k_recon(const ReconArgs a) {
+// One 32x32 cell (cell coordinates cxi, cyi) of image a; 128 threads.
+__device__ __forceinline__ void recon_cell(const ReconArgs& a, int cxi, int cyi) {
   __shared__ __align__(16) float S[3][32][kRS];
   __shared__ __align__(16) float T[3][32][kRS];
   __shared__ CellState cs;
   const int tid = threadIdx.x;
-  const int gbx0 = blockIdx.x * 4, gby0 = blockIdx.y * 4;
+  const int gbx0 = cxi * 4, gby0 = cyi * 4;
   const int px0 = gbx0 * 8, py0 = gby0 * 8;
 
   cell_setup(cs, a.vmap, a.acmul, gbx0, gby0, a.bw, a.bh);
@@ -708,9 +709,47 @@ __global__ void __launch_bounds__(128) k_recon(const ReconArgs a) {
   }
 }
 
+__global__ void __launch_bounds__(128) k_recon(const __grid_constant__ ReconArgs a) {
+  recon_cell(a, blockIdx.x, blockIdx.y);
+}
+
+// Multi-image form: work item w is cell (w - prefix[i]) of image i, cells in
+// raster order; CTAs stride over the items.
+__global__ void __launch_bounds__(128) k_recon_batch(const ReconArgs* __restrict__ args,
+                                                     const int* __restrict__ prefix, int nimg,
+                                                     int total) {
+  __shared__ ReconArgs sa;
+  __shared__ int s_img;
+  for (int w = blockIdx.x; w < total; w += gridDim.x) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int lo = 0, hi = nimg;            // largest i with prefix[i] <= w
+      while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (prefix[mid] <= w) lo = mid; else hi = mid;
+      }
+      s_img = lo;
+    }
+    __syncthreads();
+    const int img = s_img;
+    static_assert(sizeof(ReconArgs) % 4 == 0, "word copy");
+    for (int k = threadIdx.x; k < int(sizeof(ReconArgs) / 4); k += blockDim.x)
+      reinterpret_cast<int*>(&sa)[k] = reinterpret_cast<const int*>(&args[img])[k];
+    __syncthreads();
+    const int local = w - prefix[img];
+    const int cells_x = (sa.wp + 31) / 32;
+    recon_cell(sa, local % cells_x, local / cells_x);
+  }
+}
+
 void launch_recon(const ReconArgs& a, cudaStream_t s) {
   dim3 grid((a.wp + 31) / 32, (a.hp + 31) / 32);
   k_recon<<<grid, 128, 0, s>>>(a);
+}
+
+void launch_recon_batch(const ReconArgs* args, const int* prefix, int nimg, int total, int grid,
+                        cudaStream_t s) {
+  k_recon_batch<<<grid, 128, 0, s>>>(args, prefix, nimg, total);
 }
 
 // ---------------------------------------------------------------------------
@@ -744,12 +783,12 @@ constexpr int kGX = 5, kGY = 5;                 // halo before the tile
 constexpr int kGW = kTW + 12, kGH = kTH + 10;   // guide/sample window
 constexpr int kEW = kTW + 2, kEH = kTH + 2;     // EPF output with a 1-sample ring
 
-__global__ void __launch_bounds__(256) k_filter(const FilterArgs a) {
+__device__ __forceinline__ void filter_tile(const FilterArgs& a, int tbx, int tby) {
   __shared__ float F[3][kGH][kGW];
   __shared__ uint32_t G[kGH][kGW];
   __shared__ float E[3][kEH][kEW];
   const int tid = threadIdx.x;
-  const int x0 = blockIdx.x * kTW, y0 = blockIdx.y * kTH;
+  const int x0 = tbx * kTW, y0 = tby * kTH;
   const int wx0 = x0 - kGX, wy0 = y0 - kGY;     // window origin (image coords)
 
   // ---- load the window with mirrored coordinates (6.5) --------------------
@@ -907,12 +946,12 @@ constexpr int kWW = 42, kWH = 40;        // sample / guide window, origin (x0-5,
 constexpr int kGS = 65;                  // guide row stride (words), = 1 mod 32
 
 template <bool kClamp>
-__global__ void __launch_bounds__(128, 4) k_epf(const FilterArgs a) {
+__device__ __forceinline__ void epf_tile(const FilterArgs& a, int tbx, int tby) {
   __shared__ float F[3][kWH][kWW];
   __shared__ uint32_t G[kWH][kGS];
   __shared__ __align__(16) uint16_t Hb[7][kHR][kER];
   const int tid = threadIdx.x;
-  const int x0 = blockIdx.x * kET, y0 = blockIdx.y * kET;
+  const int x0 = tbx * kET, y0 = tby * kET;
   const int wx0 = x0 - 5, wy0 = y0 - 5;
 
   // ---- window of mirrored samples and packed guide bytes (6.5, J.2.2) ----
@@ -1100,6 +1139,80 @@ static bool epf_needs_clamp(const FilterArgs& a, const int32_t* mul4) {
     if ((C - T16) / (-M) >= 507) return true;
   }
   return false;
+}
+
+__global__ void __launch_bounds__(256) k_filter(const __grid_constant__ FilterArgs a) {
+  filter_tile(a, blockIdx.x, blockIdx.y);
+}
+
+template <bool kClamp>
+__global__ void __launch_bounds__(128, 4) k_epf(const __grid_constant__ FilterArgs a) {
+  epf_tile<kClamp>(a, blockIdx.x, blockIdx.y);
+}
+
+// Multi-image forms of the two filter kernels (tiles in raster order per
+// image, CTAs striding over work items).
+template <bool kEpf, bool kClamp>
+__global__ void __launch_bounds__(kEpf ? 128 : 256, kEpf ? 4 : 1)
+    k_filter_batch(const FilterArgs* __restrict__ args, const int* __restrict__ prefix, int nimg,
+                   int total) {
+  __shared__ FilterArgs sa;
+  __shared__ int s_img;
+  for (int w = blockIdx.x; w < total; w += gridDim.x) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int lo = 0, hi = nimg;
+      while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (prefix[mid] <= w) lo = mid; else hi = mid;
+      }
+      s_img = lo;
+    }
+    __syncthreads();
+    const int img = s_img;
+    static_assert(sizeof(FilterArgs) % 4 == 0, "word copy");
+    for (int k = threadIdx.x; k < int(sizeof(FilterArgs) / 4); k += blockDim.x)
+      reinterpret_cast<int*>(&sa)[k] = reinterpret_cast<const int*>(&args[img])[k];
+    __syncthreads();
+    const int local = w - prefix[img];
+    const int tw = kEpf ? (sa.xs + kET - 1) / kET : (sa.xs + kTW - 1) / kTW;
+    if (kEpf) epf_tile<kClamp>(sa, local % tw, local / tw);
+    else filter_tile(sa, local % tw, local / tw);
+  }
+}
+
+bool filter_needs_clamp(const FilterArgs& a) {
+  static const std::vector<int32_t> mul4 = [] {
+    std::vector<int32_t> t(673);
+    mul_table4(t.data());
+    return t;
+  }();
+  return epf_needs_clamp(a, mul4.data());
+}
+
+void launch_filter_batch(const FilterArgs* args, const int* prefix, int nimg, int total,
+                         bool epf, bool clamp, int grid, cudaStream_t s) {
+  if (!epf) k_filter_batch<false, false><<<grid, 256, 0, s>>>(args, prefix, nimg, total);
+  else if (clamp) k_filter_batch<true, true><<<grid, 128, 0, s>>>(args, prefix, nimg, total);
+  else k_filter_batch<true, false><<<grid, 128, 0, s>>>(args, prefix, nimg, total);
+}
+
+int batch_blocks_per_sm(int kind) {
+  int n = 0;
+  cudaError_t e = cudaSuccess;
+  if (kind == 0) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_recon_batch, 128, 0);
+  else if (kind == 1)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_filter_batch<true, false>, 128, 0);
+  else if (kind == 2)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_filter_batch<true, true>, 128, 0);
+  else
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_filter_batch<false, false>, 256, 0);
+  return e == cudaSuccess && n > 0 ? n : 1;
+}
+
+int filter_tiles(const FilterArgs& a) {
+  return a.epf ? ((a.xs + kET - 1) / kET) * ((a.ys + kET - 1) / kET)
+               : ((a.xs + kTW - 1) / kTW) * ((a.ys + kTH - 1) / kTH);
 }
 
 void launch_filter(const FilterArgs& a, cudaStream_t s) {

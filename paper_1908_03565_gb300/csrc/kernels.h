@@ -78,4 +78,15 @@ void launch_recon(const ReconArgs& a, cudaStream_t s);
 void launch_sigma(const SigmaArgs& a, cudaStream_t s);
 void launch_filter(const FilterArgs& a, cudaStream_t s);
 
+// Multi-image launches: args[i] per image (device array), prefix[i] = first
+// work item of image i (prefix[nimg] = total), grid CTAs striding over items.
+void launch_recon_batch(const ReconArgs* args, const int* prefix, int nimg, int total, int grid,
+                        cudaStream_t s);
+void launch_filter_batch(const FilterArgs* args, const int* prefix, int nimg, int total,
+                         bool epf, bool clamp, int grid, cudaStream_t s);
+// Work items (tiles) of the filter kernel that handles a, and whether the
+// EPF needs its exact-clamp variant for a's parameters.
+int filter_tiles(const FilterArgs& a);
+bool filter_needs_clamp(const FilterArgs& a);
+
 }  // namespace jxlr

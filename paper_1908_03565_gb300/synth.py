@@ -119,15 +119,17 @@ def tiling(bw, bh, rng, mix='mixed'):
 
 def coefficient_positions(vmap):
     """Per-sample (u, v) position inside the varblock's coefficient matrix,
-    with the 8x8 matrix of 8x8-class shapes."""
+    with the 8x8 matrix of 8x8-class shapes; and the top-left block of each
+    block's varblock."""
     bh, bw = vmap.shape
     ox = np.zeros((bh, bw), dtype=np.int64)
     oy = np.zeros((bh, bw), dtype=np.int64)
-    tl = np.argwhere(vmap != COVERED)
-    for by, bx in tl:
-        w, h = SHAPE_WH[int(vmap[by, bx])]
-        ox[by:by + h // 8, bx:bx + w // 8] = bx
-        oy[by:by + h // 8, bx:bx + w // 8] = by
+    for code, (w, h) in SHAPE_WH.items():
+        ty, tx = np.nonzero(vmap == code)
+        for dy in range(h // 8):
+            for dx in range(w // 8):
+                ox[ty + dy, tx + dx] = tx
+                oy[ty + dy, tx + dx] = ty
     Hp, Wp = 8 * bh, 8 * bw
     x0 = np.repeat(np.repeat(ox, 8, 0), 8, 1) * 8
     y0 = np.repeat(np.repeat(oy, 8, 0), 8, 1) * 8
@@ -153,11 +155,17 @@ def make_image(xsize, ysize, seed, mix='mixed', acmul=None, cfl=True,
     lap = rng.laplace(0.0, 1.0, size=(3, Hp, Wp)) * scale[None]
     coeffs = np.clip(np.rint(lap), -32768, 32767).astype(np.int16)
     if y_dc_offset_q:
-        tl = np.argwhere(vmap != COVERED)
-        for by, bx in tl:
-            cw, ch = SHAPE_WH[int(vmap[by, bx])]
-            sl = coeffs[1, 8 * by:8 * by + ch // 8, 8 * bx:8 * bx + cw // 8]
-            sl[...] = np.clip(sl.astype(np.int64) + y_dc_offset_q, -32768, 32767)
+        # LLF slots: u < W/8 and v < H/8 of the sample's varblock
+        wv = np.zeros((bh, bw), dtype=np.int64)
+        hv = np.zeros((bh, bw), dtype=np.int64)
+        for code, (w, h) in SHAPE_WH.items():
+            sel = vmap[oy, ox] == code
+            wv[sel], hv[sel] = w, h
+        wv = np.repeat(np.repeat(wv, 8, 0), 8, 1)
+        hv = np.repeat(np.repeat(hv, 8, 0), 8, 1)
+        llf = (u < wv // 8) & (v < hv // 8)
+        y = coeffs[1].astype(np.int64)
+        coeffs[1] = np.where(llf, np.clip(y + y_dc_offset_q, -32768, 32767), y)
     if acmul is None:
         per_vb = np.exp(rng.uniform(math.log(0.5), math.log(4.0), size=(bh, bw)))
         am = per_vb[oy, ox].astype(np.float32)
