@@ -38,8 +38,11 @@ __constant__ int c_shape_w[kNumCodes];
 __constant__ int c_shape_h[kNumCodes];
 __constant__ int c_dq_off[kNumCodes];
 
+static void prefer_shared_carveout();
+
 bool upload_constants(const float* llf, const float* odd, const int32_t* mul4,
                       const float* afv) {
+  prefer_shared_carveout();
   int offs[kNumCodes];
   for (int c = 0; c < kNumCodes; ++c) offs[c] = dequant_offset(c, 0);
   return cudaMemcpyToSymbol(c_llf, llf, sizeof(float) * kLlfMaps * 256) == cudaSuccess &&
@@ -502,52 +505,59 @@ __device__ void cell_sigma(float (*S)[32][kRS], CellState& cs, const SigmaParams
   }
 }
 
-// Loads the cell's map entries and builds the varblock list (sorted by code
-// so that warps of the transform passes mostly share a shape).
+// Loads the cell's map entries and builds the varblock list, sorted by code
+// so that warps of the transform passes mostly share a shape.  Warp 0 does
+// it in parallel: lane b < 16 owns block b of the cell; its rank in the
+// sorted list and its item prefix sums come from shuffles.
 __device__ void cell_setup(CellState& cs, const uint8_t* __restrict__ vmap,
                            const float* __restrict__ acmul, int gbx0, int gby0, int bw,
                            int bh) {
-  __shared__ int s_code[16];
-  __shared__ float s_am[16];
   const int tid = threadIdx.x;
-  if (tid < 16) {
-    const int gbx = gbx0 + (tid & 3), gby = gby0 + (tid >> 2);
+  if (tid < 32) {
+    const unsigned full = 0xffffffffu;
+    const int b = tid & 15, bx = b & 3, by = b >> 2;
+    const int gbx = gbx0 + bx, gby = gby0 + by;
     int code = kCovered;
     float am = 1.f;
-    if (gbx < bw && gby < bh) {
+    if (tid < 16 && gbx < bw && gby < bh) {
       code = vmap[gby * bw + gbx];
       am = acmul[gby * bw + gbx];
     }
-    s_code[tid] = code;
-    s_am[tid] = am;
-    cs.owner[tid] = -1;
-  }
-  __syncthreads();
-  if (tid == 0) {
-    int n = 0;
-    for (int b = 0; b < 16; ++b) {
-      const int code = s_code[b];
-      if (code >= kNumCodes) continue;
-      const int bx = b & 3, by = b >> 2;
-      const int w8 = c_shape_w[code] / 8, h8 = c_shape_h[code] / 8;
+    bool valid = false;
+    int ri = 0, ci = 0, w8 = 1, h8 = 1;
+    if (tid < 16 && code < kNumCodes) {
+      w8 = c_shape_w[code] / 8;
+      h8 = c_shape_h[code] / 8;
       // ill-formed placements are reported by k_validate; skip them here
-      if (bx % w8 || by % h8 || bx + w8 > 4 || by + h8 > 4) continue;
-      if (gbx0 + bx + w8 > bw || gby0 + by + h8 > bh) continue;
-      CellVB v;
-      v.code = code; v.bx = bx; v.by = by; v.acmul = s_am[b];
-      int i = n++;
-      while (i > 0 && cs.vb[i - 1].code > code) { cs.vb[i] = cs.vb[i - 1]; --i; }
-      cs.vb[i] = v;
+      valid = !(bx % w8 || by % h8 || bx + w8 > 4 || by + h8 > 4 || gbx0 + bx + w8 > bw ||
+                gby0 + by + h8 > bh);
+      ri = row_items(code);
+      ci = col_items(code);
     }
-    cs.nvb = n;
-    cs.row_pre[0] = cs.col_pre[0] = 0;
-    for (int i = 0; i < n; ++i) {
-      const CellVB& v = cs.vb[i];
-      const int w8 = c_shape_w[v.code] / 8, h8 = c_shape_h[v.code] / 8;
+    const int key = valid ? code * 16 + b : 0x7fffffff;
+    int rank = 0, pr = 0, pc = 0;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      const int kj = __shfl_sync(full, key, j);
+      const int rj = __shfl_sync(full, ri, j);
+      const int cj = __shfl_sync(full, ci, j);
+      if (kj < key) { ++rank; pr += rj; pc += cj; }
+    }
+    const int n = __popc(__ballot_sync(full, valid));
+    if (tid < 16) cs.owner[tid] = -1;
+    if (tid == 0) {
+      cs.nvb = n;
+      cs.row_pre[0] = cs.col_pre[0] = 0;
+    }
+    __syncwarp();
+    if (valid) {
+      CellVB v;
+      v.code = code; v.bx = bx; v.by = by; v.acmul = am;
+      cs.vb[rank] = v;
+      cs.row_pre[rank + 1] = pr + ri;
+      cs.col_pre[rank + 1] = pc + ci;
       for (int yy = 0; yy < h8; ++yy)
-        for (int xx = 0; xx < w8; ++xx) cs.owner[(v.by + yy) * 4 + v.bx + xx] = i;
-      cs.row_pre[i + 1] = cs.row_pre[i] + row_items(v.code);
-      cs.col_pre[i + 1] = cs.col_pre[i] + col_items(v.code);
+        for (int xx = 0; xx < w8; ++xx) cs.owner[(by + yy) * 4 + bx + xx] = rank;
     }
   }
   __syncthreads();
@@ -562,16 +572,24 @@ __device__ __forceinline__ void recon_cell(const ReconArgs& a, int cxi, int cyi)
   const int gbx0 = cxi * 4, gby0 = cyi * 4;
   const int px0 = gbx0 * 8, py0 = gby0 * 8;
 
+  // the coefficient loads do not depend on the map: issue them first
+  const int y = tid >> 2, k = tid & 3;     // cell row, 8-column chunk
+  const int gy = py0 + y, gx = px0 + 8 * k;
+  const bool inb = gy < a.hp && gx < a.wp;
+  int4 raw[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+    raw[c] = inb ? __ldg(reinterpret_cast<const int4*>(a.coef[c] + gy * a.cstride + gx))
+                 : make_int4(0, 0, 0, 0);
+
   cell_setup(cs, a.vmap, a.acmul, gbx0, gby0, a.bw, a.bh);
 
   // ---- F.2 / F.3 / G: one 8-sample row chunk of all three channels -------
   {
-    const int y = tid >> 2, k = tid & 3;   // cell row, 8-column chunk
-    const int gy = py0 + y, gx = px0 + 8 * k;
     const int b = (y >> 3) * 4 + k;
     const int o = cs.owner[b];
     float out[3][8];
-    if (o >= 0 && gy < a.hp && gx < a.wp) {
+    if (o >= 0 && inb) {
       const CellVB v = cs.vb[o];
       const int W = c_shape_w[v.code], H = c_shape_h[v.code];
       const int u0 = 8 * k - 8 * v.bx, vv = y - 8 * v.by;
@@ -581,8 +599,7 @@ __device__ __forceinline__ void recon_cell(const ReconArgs& a, int cxi, int cyi)
       float q[3][8];
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        const int4 raw = __ldg(reinterpret_cast<const int4*>(a.coef[c] + gy * a.cstride + gx));
-        const int16_t* h = reinterpret_cast<const int16_t*>(&raw);
+        const int16_t* h = reinterpret_cast<const int16_t*>(&raw[c]);
 #pragma unroll
         for (int j = 0; j < 8; ++j) q[c][j] = static_cast<float>(h[j]);
       }
@@ -709,13 +726,13 @@ __device__ __forceinline__ void recon_cell(const ReconArgs& a, int cxi, int cyi)
   }
 }
 
-__global__ void __launch_bounds__(128) k_recon(const __grid_constant__ ReconArgs a) {
+__global__ void __launch_bounds__(128, 6) k_recon(const __grid_constant__ ReconArgs a) {
   recon_cell(a, blockIdx.x, blockIdx.y);
 }
 
 // Multi-image form: work item w is cell (w - prefix[i]) of image i, cells in
 // raster order; CTAs stride over the items.
-__global__ void __launch_bounds__(128) k_recon_batch(const ReconArgs* __restrict__ args,
+__global__ void __launch_bounds__(128, 6) k_recon_batch(const ReconArgs* __restrict__ args,
                                                      const int* __restrict__ prefix, int nimg,
                                                      int total) {
   __shared__ ReconArgs sa;
@@ -1195,6 +1212,20 @@ void launch_filter_batch(const FilterArgs* args, const int* prefix, int nimg, in
   if (!epf) k_filter_batch<false, false><<<grid, 256, 0, s>>>(args, prefix, nimg, total);
   else if (clamp) k_filter_batch<true, true><<<grid, 128, 0, s>>>(args, prefix, nimg, total);
   else k_filter_batch<true, false><<<grid, 128, 0, s>>>(args, prefix, nimg, total);
+}
+
+// The kernels use static shared memory; ask for the largest carveout so the
+// register limit, not the L1/shared split, bounds resident CTAs.
+static void prefer_shared_carveout() {
+  const int pct = cudaSharedmemCarveoutMaxShared;
+  cudaFuncSetAttribute(k_recon, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+  cudaFuncSetAttribute(k_recon_batch, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+  cudaFuncSetAttribute(k_epf<false>, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+  cudaFuncSetAttribute(k_epf<true>, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+  cudaFuncSetAttribute(k_filter_batch<true, false>, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+  cudaFuncSetAttribute(k_filter_batch<true, true>, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+  cudaFuncSetAttribute(k_filter, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+  cudaGetLastError();
 }
 
 int batch_blocks_per_sm(int kind) {
