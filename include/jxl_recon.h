@@ -68,7 +68,12 @@ typedef enum {
 } jxlr_out_dtype;
 
 typedef enum {
-  JXLR_PREC_FP32 = 0       /* every stage on FP32 CUDA cores */
+  JXLR_PREC_FP32 = 0,      /* every stage on FP32 CUDA cores                    */
+  JXLR_PREC_TC_F16X3 = 1   /* the separable passes of varblocks larger than 8x8
+                              (I.2.4.1) run on the tensor cores as FP16 hi/lo
+                              split products (hi*hi + hi*lo + lo*hi) with FP32
+                              accumulation, each operand row scaled by a power
+                              of two; everything else as in FP32 mode         */
 } jxlr_precision;
 
 typedef struct {

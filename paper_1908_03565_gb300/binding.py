@@ -17,6 +17,7 @@ LIB_PATH = os.path.join(HERE, "libjxlrecon.so")
 JXLR_OK, JXLR_EAGAIN, JXLR_EINVAL, JXLR_ENOMEM = 0, 1, -1, -2
 JXLR_EBUSY, JXLR_ECUDA, JXLR_ETIMEDOUT, JXLR_ECANCELLED = -3, -4, -5, -6
 OUT_F32_LINEAR, OUT_F16_LINEAR, OUT_U8_SRGB, OUT_F32_XYB = 0, 1, 2, 3
+PREC_FP32, PREC_TC_F16X3 = 0, 1
 OUT_BYTES = {OUT_F32_LINEAR: 12, OUT_F16_LINEAR: 6, OUT_U8_SRGB: 3, OUT_F32_XYB: 12}
 
 EXPORTS = ("jxl_recon_filter_defaults", "jxl_recon_create", "jxl_recon_submit",
@@ -167,10 +168,12 @@ def _ptr(a):
 class Context:
     """One jxl_recon_ctx.  Methods mirror the C entry points."""
 
-    def __init__(self, device=0, max_slots=1, hbm_cap_bytes=0, timing=False, stream=None):
-        """stream: optional raw cudaStream_t (int) every request runs on."""
+    def __init__(self, device=0, max_slots=1, hbm_cap_bytes=0, timing=False, stream=None,
+                 precision=PREC_FP32):
+        """stream: optional raw cudaStream_t (int) every request runs on;
+        precision: PREC_FP32 or PREC_TC_F16X3."""
         self.lib = load()
-        cfg = Config(device, hbm_cap_bytes, max_slots, 0, int(timing), stream)
+        cfg = Config(device, hbm_cap_bytes, max_slots, precision, int(timing), stream)
         h = ctypes.c_void_p()
         st = self.lib.jxl_recon_create(ctypes.byref(cfg), ctypes.byref(h))
         if st != JXLR_OK:

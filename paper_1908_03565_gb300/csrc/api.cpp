@@ -75,6 +75,8 @@ struct jxl_recon_ctx {
   bool timing = false;
   std::vector<Slot> slots;
   float* d_dequant = nullptr;        // prescaled default matrices
+  int precision = JXLR_PREC_FP32;
+  unsigned char* d_tcb = nullptr;    // tensor-core basis tables
   std::mutex mu;
   std::atomic<uint64_t> next_ticket{1};
   std::atomic<uint64_t> launches{0};
@@ -132,7 +134,8 @@ size_t jxl_recon_device_bytes(const jxl_recon_ctx* ctx) { return ctx ? ctx->byte
 jxlr_status jxl_recon_create(const jxl_recon_config* cfg, jxl_recon_ctx** out) {
   if (!cfg || !out) return fail(JXLR_EINVAL, "create: null argument");
   if (cfg->max_slots < 1 || cfg->max_slots > 256) return fail(JXLR_EINVAL, "create: max_slots out of [1, 256]");
-  if (cfg->precision != JXLR_PREC_FP32) return fail(JXLR_EINVAL, "create: unsupported precision");
+  if (cfg->precision != JXLR_PREC_FP32 && cfg->precision != JXLR_PREC_TC_F16X3)
+    return fail(JXLR_EINVAL, "create: unsupported precision");
   int ndev = 0;
   CK(cudaGetDeviceCount(&ndev));
   if (cfg->device < 0 || cfg->device >= ndev) return fail(JXLR_EINVAL, "create: bad device");
@@ -156,10 +159,18 @@ jxlr_status jxl_recon_create(const jxl_recon_config* cfg, jxl_recon_ctx** out) {
   ctx->device = cfg->device;
   ctx->cap = cfg->hbm_cap_bytes;
   ctx->timing = cfg->timing != 0;
+  ctx->precision = cfg->precision;
   cudaError_t e = cudaMalloc(&ctx->d_dequant, sizeof(float) * kDequantFloats);
   if (e == cudaSuccess)
     e = cudaMemcpy(ctx->d_dequant, scaled.data(), sizeof(float) * kDequantFloats,
                    cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && ctx->precision == JXLR_PREC_TC_F16X3) {
+    std::vector<unsigned char> tcb(kTcBasisBytes);
+    tc_basis_tables(tcb.data());
+    e = cudaMalloc(&ctx->d_tcb, kTcBasisBytes);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(ctx->d_tcb, tcb.data(), kTcBasisBytes, cudaMemcpyHostToDevice);
+  }
   ctx->slots.resize(cfg->max_slots);
   for (auto& s : ctx->slots) {
     if (cfg->cuda_stream) {
@@ -194,6 +205,7 @@ jxlr_status jxl_recon_destroy(jxl_recon_ctx* ctx) {
     if (s.stream && s.own_stream) cudaStreamDestroy(s.stream);
   }
   if (ctx->d_dequant) cudaFree(ctx->d_dequant);
+  if (ctx->d_tcb) cudaFree(ctx->d_tcb);
   delete ctx;
   return JXLR_OK;
 }
@@ -434,6 +446,9 @@ extern "C" jxlr_status jxl_recon_submit(jxl_recon_ctx* ctx, const jxl_recon_coef
   ra.kb_dc = cfl->kb_dc;
   ra.sp = sigma_params(*fp);
   ra.cp = color_params(*fp);
+  ra.tcb = ctx->d_tcb;
+  ra.err = d_status + 3;
+  const bool tc = ctx->precision == JXLR_PREC_TC_F16X3;
 
   OutParams op;
   char* d_out = nullptr;
@@ -452,7 +467,8 @@ extern "C" jxlr_status jxl_recon_submit(jxl_recon_ctx* ctx, const jxl_recon_coef
     ra.write_xyb = 1;
     ra.xyb = xyb;
     ra.sigma = sig;
-    launch_recon(ra, s);
+    if (tc) launch_recon_tc(ra, s);
+    else launch_recon(ra, s);
     ctx->launches++;
     mark(slot, 3);
     FilterArgs fa = filter_args(*fp);
@@ -467,7 +483,8 @@ extern "C" jxlr_status jxl_recon_submit(jxl_recon_ctx* ctx, const jxl_recon_coef
   } else {
     ra.write_xyb = 0;
     ra.out = op;
-    launch_recon(ra, s);
+    if (tc) launch_recon_tc(ra, s);
+    else launch_recon(ra, s);
     ctx->launches++;
     mark(slot, 3);
   }
@@ -590,6 +607,8 @@ extern "C" jxlr_status jxl_recon_poll(jxl_recon_ctx* ctx, uint64_t ticket, int64
     if (ctx->timings.size() > 4096) ctx->timings.clear();
     ctx->timings[ticket] = t;
   }
+  if (slot->h_status[3] != 0)
+    return fail(JXLR_ETIMEDOUT, "tensor-core completion wait expired in the transform kernel");
   if (slot->check_status && slot->h_status[0] != 0) {
     char buf[96];
     std::snprintf(buf, sizeof(buf), "device validation: DctSelect map ill-formed (flags 0x%x)",

@@ -55,6 +55,11 @@ void odd_tables(float* out);
 // 4 * mul_table[sigma] of J.2.4 for sigma in [0, 672]; entries below 16 are 0.
 void mul_table4(int32_t* out /* 673 */);
 
+// Tensor-core basis tables: for N = 8 (padded to 16), 16, 32 at byte offsets
+// 0, 1024, 2048, the FP16 hi then lo parts of B[n][k] = cos((2n+1)k pi/2N)
+// in the canonical K-major no-swizzle operand layout (6144 bytes).
+void tc_basis_tables(unsigned char* out);
+
 // AFV basis of I.2.2, [coefficient][sample], 16 x 16.
 extern const double kAfvBasis[16][16];
 

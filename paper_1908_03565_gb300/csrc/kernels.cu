@@ -306,6 +306,9 @@ __device__ __forceinline__ bool separable(int code) {
   return code != kIdentity && code != kDCT2 && code != kAFV;
 }
 
+// Varblocks whose separable passes the tensor-core variant takes over.
+__device__ __forceinline__ bool tc_shape(int code) { return code >= kDCT16 && code <= kDCT16x32; }
+
 __device__ __forceinline__ int row_items(int code) {
   if (code == kIdentity || code == kDCT2) return 3;   // whole block per channel
   if (code == kAFV) return 12;                          // 4 quadrants x 3 channels
@@ -511,7 +514,7 @@ __device__ void cell_sigma(float (*S)[32][kRS], CellState& cs, const SigmaParams
 // sorted list and its item prefix sums come from shuffles.
 __device__ void cell_setup(CellState& cs, const uint8_t* __restrict__ vmap,
                            const float* __restrict__ acmul, int gbx0, int gby0, int bw,
-                           int bh) {
+                           int bh, bool tc = false) {
   const int tid = threadIdx.x;
   if (tid < 32) {
     const unsigned full = 0xffffffffu;
@@ -531,8 +534,8 @@ __device__ void cell_setup(CellState& cs, const uint8_t* __restrict__ vmap,
       // ill-formed placements are reported by k_validate; skip them here
       valid = !(bx % w8 || by % h8 || bx + w8 > 4 || by + h8 > 4 || gbx0 + bx + w8 > bw ||
                 gby0 + by + h8 > bh);
-      ri = row_items(code);
-      ci = col_items(code);
+      ri = tc && tc_shape(code) ? 0 : row_items(code);
+      ci = tc && tc_shape(code) ? 0 : col_items(code);
     }
     const int key = valid ? code * 16 + b : 0x7fffffff;
     int rank = 0, pr = 0, pc = 0;
@@ -563,7 +566,161 @@ __device__ void cell_setup(CellState& cs, const uint8_t* __restrict__ vmap,
   __syncthreads();
 }
 
+// ---------------------------------------------------------------------------
+// Tensor-core separable pass (tcgen05, cta_group::1, kind::f16)
+//
+// One pass of one varblock is D[m][n] = sum_k A[m][k] B[n][k] with M = 128
+// rows (3 channels x H rows for the row pass, 3 x W columns for the column
+// pass; unused rows zero), K = N = the transform size (8 is padded to 16)
+// and B the unscaled cosine basis.  Each row of A is scaled by a power of two
+// so its largest entry lies in [2^13, 2^14), split into FP16 hi + lo, and
+// D = A_hi B_hi + A_hi B_lo + A_lo B_hi accumulates in FP32 in tensor memory
+// (128 lanes x 32 columns).  Operands use the canonical K-major layout
+// without swizzle: element (r, k) at (r/8)*SBO + (k/8)*128 + (r%8)*16 +
+// (k%8)*2 bytes, SBO = (Kp/8)*128.
+// ---------------------------------------------------------------------------
+struct TcShared {
+  unsigned char a_hi[8192];
+  unsigned char a_lo[8192];
+  unsigned char b_hi[2048];
+  unsigned char b_lo[2048];
+  unsigned long long mbar;
+  uint32_t tmem;
+};
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ unsigned long long umma_desc(uint32_t addr, int sbo) {
+  unsigned long long d = (addr >> 4) & 0x3FFF;
+  d |= static_cast<unsigned long long>((128 >> 4) & 0x3FFF) << 16;   // LBO: K direction
+  d |= static_cast<unsigned long long>((sbo >> 4) & 0x3FFF) << 32;   // SBO: M/N direction
+  d |= 1ull << 46;                                                   // sm_100 family
+  return d;
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// src / dst: element (row m = c*G + i, index k) at base + c*cstr + i*rstr + k*estr.
+__device__ void tc_pass(TcShared& ts, uint32_t& phase, unsigned* err, int nrows, int G, int K,
+                        const unsigned char* __restrict__ basis, const float* src, float* dst,
+                        int cstr, int rstr, int estr) {
+  const int m = threadIdx.x;
+  const int Kp = K < 16 ? 16 : K;
+  const int sbo = (Kp / 8) * 128;
+  // ---- stage A (hi, lo) row m ----
+  {
+    float v[32];
+    float amax = 0.f;
+    const int c = m / G, i = m - (m / G) * G;
+#pragma unroll
+    for (int k = 0; k < 32; ++k) {
+      float x = 0.f;
+      if (m < nrows && k < K) x = src[c * cstr + i * rstr + k * estr];
+      v[k] = x;
+      amax = fmaxf(amax, fabsf(x));
+    }
+    int e = 0;
+    frexpf(amax, &e);
+    const float sc = amax > 0.f ? ldexpf(1.f, 14 - e) : 1.f;
+#pragma unroll
+    for (int g = 0; g < 4; ++g) {
+      if (g * 8 >= Kp) break;
+      uint32_t hw[4], lw[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const float x0 = v[g * 8 + 2 * j] * sc, x1 = v[g * 8 + 2 * j + 1] * sc;
+        const __half h0 = __float2half_rn(x0), h1 = __float2half_rn(x1);
+        const __half l0 = __float2half_rn(x0 - __half2float(h0));
+        const __half l1 = __float2half_rn(x1 - __half2float(h1));
+        hw[j] = static_cast<uint32_t>(__half_as_ushort(h0)) |
+                (static_cast<uint32_t>(__half_as_ushort(h1)) << 16);
+        lw[j] = static_cast<uint32_t>(__half_as_ushort(l0)) |
+                (static_cast<uint32_t>(__half_as_ushort(l1)) << 16);
+      }
+      const int off = (m >> 3) * sbo + g * 128 + (m & 7) * 16;
+      *reinterpret_cast<uint4*>(ts.a_hi + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+      *reinterpret_cast<uint4*>(ts.a_lo + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+    }
+    // ---- stage B (hi, lo), already canonical in global memory ----
+    const int bbytes = Kp * Kp * 2;
+    for (int o = m * 16; o < bbytes; o += 128 * 16) {
+      *reinterpret_cast<uint4*>(ts.b_hi + o) = *reinterpret_cast<const uint4*>(basis + o);
+      *reinterpret_cast<uint4*>(ts.b_lo + o) = *reinterpret_cast<const uint4*>(basis + bbytes + o);
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (m == 0) {
+      const uint32_t idesc = (1u << 4) | (static_cast<uint32_t>(Kp >> 3) << 17) |
+                             (static_cast<uint32_t>(128 >> 4) << 24);
+      const uint32_t ah = smem_addr(ts.a_hi), al = smem_addr(ts.a_lo);
+      const uint32_t bh = smem_addr(ts.b_hi), bl = smem_addr(ts.b_lo);
+      uint32_t acc = 0;
+      for (int ks = 0; ks < Kp / 16; ++ks) {
+        const uint32_t o = ks * 256;
+        const unsigned long long da[3] = {umma_desc(ah + o, sbo), umma_desc(ah + o, sbo),
+                                          umma_desc(al + o, sbo)};
+        const unsigned long long db[3] = {umma_desc(bh + o, sbo), umma_desc(bl + o, sbo),
+                                          umma_desc(bh + o, sbo)};
+#pragma unroll
+        for (int t = 0; t < 3; ++t) {
+          asm volatile(
+              "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+              "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+              :: "r"(ts.tmem), "l"(da[t]), "l"(db[t]), "r"(idesc), "r"(acc));
+          acc = 1;
+        }
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                   :: "r"(smem_addr(&ts.mbar)) : "memory");
+    }
+    // bounded wait for the products
+    uint32_t done = 0;
+    for (int it = 0; it < (1 << 24) && !done; ++it) {
+      asm volatile("{\n.reg .pred q;\nmbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\n"
+                   "selp.u32 %0, 1, 0, q;\n}\n"
+                   : "=r"(done) : "r"(smem_addr(&ts.mbar)), "r"(phase) : "memory");
+    }
+    phase ^= 1u;
+    tc_fence_after();
+    if (!done) {
+      if (m == 0) atomicOr(err, 4u);
+    } else {
+      uint32_t r[32];
+      const uint32_t taddr = ts.tmem + (static_cast<uint32_t>(m & ~31) << 16);
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,"
+          "%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+            "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]),
+            "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]),
+            "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+            "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]),
+            "=r"(r[30]), "=r"(r[31])
+          : "r"(taddr));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      const float inv = amax > 0.f ? ldexpf(1.f, e - 14) : 1.f;
+      if (m < nrows) {
+#pragma unroll
+        for (int n = 0; n < 32; ++n)
+          if (n < K) dst[c * cstr + i * rstr + n * estr] = __uint_as_float(r[n]) * inv;
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+}
+
 // One 32x32 cell (cell coordinates cxi, cyi) of image a; 128 threads.
+template <bool kTC = false>
 __device__ __forceinline__ void recon_cell(const ReconArgs& a, int cxi, int cyi) {
   __shared__ __align__(16) float S[3][32][kRS];
   __shared__ __align__(16) float T[3][32][kRS];
@@ -582,7 +739,21 @@ __device__ __forceinline__ void recon_cell(const ReconArgs& a, int cxi, int cyi)
     raw[c] = inb ? __ldg(reinterpret_cast<const int4*>(a.coef[c] + gy * a.cstride + gx))
                  : make_int4(0, 0, 0, 0);
 
-  cell_setup(cs, a.vmap, a.acmul, gbx0, gby0, a.bw, a.bh);
+  extern __shared__ __align__(1024) unsigned char tc_dyn[];
+  TcShared& ts = *reinterpret_cast<TcShared*>(tc_dyn);
+  uint32_t phase = 0;
+  if (kTC) {
+    if (tid == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_addr(&ts.mbar)));
+    if (tid < 32) {
+      asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 32;"
+                   :: "r"(smem_addr(&ts.tmem)));
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    tc_fence_before();
+  }
+  cell_setup(cs, a.vmap, a.acmul, gbx0, gby0, a.bw, a.bh, kTC);
+  if (kTC) tc_fence_after();
 
   // ---- F.2 / F.3 / G: one 8-sample row chunk of all three channels -------
   {
@@ -680,6 +851,25 @@ __device__ __forceinline__ void recon_cell(const ReconArgs& a, int cxi, int cyi)
   }
   __syncthreads();
 
+  // ---- tensor-core passes of the varblocks larger than 8x8 ----------------
+  if (kTC) {
+    for (int vi = 0; vi < cs.nvb; ++vi) {
+      const CellVB v = cs.vb[vi];
+      if (!tc_shape(v.code)) continue;
+      const int W = c_shape_w[v.code], H = c_shape_h[v.code];
+      const int x0 = 8 * v.bx, y0 = 8 * v.by;
+      const int bw_idx = W == 8 ? 0 : W == 16 ? 1 : 2;
+      const int bh_idx = H == 8 ? 0 : H == 16 ? 1 : 2;
+      const int boff[3] = {0, 1024, 2048};
+      // rows: S -> T
+      tc_pass(ts, phase, a.err, 3 * H, H, W, a.tcb + boff[bw_idx], &S[0][y0][x0], &T[0][y0][x0],
+              32 * kRS, kRS, 1);
+      // columns: T -> S
+      tc_pass(ts, phase, a.err, 3 * W, W, H, a.tcb + boff[bh_idx], &T[0][y0][x0], &S[0][y0][x0],
+              32 * kRS, 1, kRS);
+    }
+  }
+
   // ---- I.2.4 row pass ------------------------------------------------------
   {
     const int total = cs.row_pre[cs.nvb];
@@ -724,6 +914,12 @@ __device__ __forceinline__ void recon_cell(const ReconArgs& a, int cxi, int cyi)
       }
     }
   }
+  if (kTC) {
+    tc_fence_before();
+    __syncthreads();
+    if (tid < 32)
+      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;" :: "r"(ts.tmem));
+  }
 }
 
 __global__ void __launch_bounds__(128, 6) k_recon(const __grid_constant__ ReconArgs a) {
@@ -757,6 +953,15 @@ __global__ void __launch_bounds__(128, 6) k_recon_batch(const ReconArgs* __restr
     const int cells_x = (sa.wp + 31) / 32;
     recon_cell(sa, local % cells_x, local / cells_x);
   }
+}
+
+__global__ void __launch_bounds__(128, 4) k_recon_tc(const __grid_constant__ ReconArgs a) {
+  recon_cell<true>(a, blockIdx.x, blockIdx.y);
+}
+
+void launch_recon_tc(const ReconArgs& a, cudaStream_t s) {
+  dim3 grid((a.wp + 31) / 32, (a.hp + 31) / 32);
+  k_recon_tc<<<grid, 128, sizeof(TcShared) + 1024, s>>>(a);
 }
 
 void launch_recon(const ReconArgs& a, cudaStream_t s) {
@@ -1219,6 +1424,9 @@ void launch_filter_batch(const FilterArgs* args, const int* prefix, int nimg, in
 static void prefer_shared_carveout() {
   const int pct = cudaSharedmemCarveoutMaxShared;
   cudaFuncSetAttribute(k_recon, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+  cudaFuncSetAttribute(k_recon_tc, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+  cudaFuncSetAttribute(k_recon_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       static_cast<int>(sizeof(TcShared) + 1024));
   cudaFuncSetAttribute(k_recon_batch, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
   cudaFuncSetAttribute(k_epf<false>, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
   cudaFuncSetAttribute(k_epf<true>, cudaFuncAttributePreferredSharedMemoryCarveout, pct);

@@ -47,6 +47,8 @@ struct ReconArgs {
   SigmaParams sp;
   ColorParams cp;
   OutParams out;
+  const unsigned char* tcb;   // tensor-core basis tables (tensor-core variant only)
+  unsigned* err;              // error flags of the tensor-core variant
 };
 
 struct SigmaArgs {
@@ -75,6 +77,10 @@ struct FilterArgs {
 
 void launch_validate(const uint8_t* vmap, int bw, int bh, unsigned* status, cudaStream_t s);
 void launch_recon(const ReconArgs& a, cudaStream_t s);
+// Variant whose separable passes of the varblocks larger than 8x8 run as
+// FP16 hi/lo split products on the tensor cores (tcgen05, FP32 accumulate).
+void launch_recon_tc(const ReconArgs& a, cudaStream_t s);
+constexpr int kTcBasisBytes = 6144;
 void launch_sigma(const SigmaArgs& a, cudaStream_t s);
 void launch_filter(const FilterArgs& a, cudaStream_t s);
 

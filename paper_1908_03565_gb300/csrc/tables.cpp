@@ -8,6 +8,8 @@
 //  * LLF from DC: I.2.7, as the exact inverse of the 8x8 box mean of I.2.6
 //  * mul_table: J.2.4 with kSigmaShift = 2
 //  * AFV basis: I.2.2 (two rows printed with a surplus 0.0, repaired)
+#include <cuda_fp16.h>
+
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -503,6 +505,27 @@ void mul_table4(int32_t* out) {
   for (int sigma = 16; sigma < 672; sigma += gap) {
     const int32_t step = (out[sigma + gap] - out[sigma]) / gap;  // = mul_step * 4
     for (int i = 1; i < gap; ++i) out[sigma + i] = out[sigma] + i * step;
+  }
+}
+
+void tc_basis_tables(unsigned char* out) {
+  std::memset(out, 0, 6144);
+  const int sizes[3] = {8, 16, 32};
+  const int offs[3] = {0, 1024, 2048};
+  for (int t = 0; t < 3; ++t) {
+    const int N = sizes[t], Kp = N < 16 ? 16 : N, sbo = (Kp / 8) * 128;
+    unsigned char* hi = out + offs[t];
+    unsigned char* lo = hi + Kp * Kp * 2;
+    for (int n = 0; n < Kp; ++n) {
+      for (int k = 0; k < Kp; ++k) {
+        const double v = (n < N && k < N) ? std::cos((2 * n + 1) * k * kPi / (2.0 * N)) : 0.0;
+        const __half h = __double2half(v);
+        const __half l = __double2half(v - static_cast<double>(__half2float(h)));
+        const int off = (n / 8) * sbo + (k / 8) * 128 + (n % 8) * 16 + (k % 8) * 2;
+        std::memcpy(hi + off, &h, 2);
+        std::memcpy(lo + off, &l, 2);
+      }
+    }
   }
 }
 
