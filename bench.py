@@ -201,6 +201,68 @@ def batch_leg(binding, torch, n_img=512, pool_n=64, seed=3000, reps=10):
             "autotuned": info["autotuned"], "outputs": "u8 sRGB / f16 linear alternating"}
 
 
+def precision_leg(binding, torch, steps, sample=1024):
+    """Config-2 style precision study: the FP32 CUDA-core path against the
+    tensor-core FP16 hi/lo path.  Time: 4096x4096 with both filters (f32 out),
+    CUDA events.  Error: max |XYB - oracle| relative to the local magnitude,
+    max |RGB01 - oracle| and the share of u8 samples within +-1 of the
+    oracle's, on a sample image of the same statistics without the filters
+    (so the comparison isolates the transforms)."""
+    from oracle import recon as R
+    from paper_1908_03565_gb300 import synth
+    from scipy.ndimage import maximum_filter
+    res = {}
+    img = synth.make_image(XS, YS, SEED)
+    dimg = binding.to_device(img, torch)
+    out = torch.empty((YS, XS, 3), dtype=torch.float32, device="cuda")
+    stream = torch.cuda.Stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    small = synth.make_image(sample, sample, SEED + 77, y_dc_offset_q=200)
+    want = R.reconstruct_xyb(small['coeffs'], small['vmap'], small['acmul'], small['cfl'],
+                             R.Params())[:, :sample, :sample]
+    mag = maximum_filter(np.abs(want), size=(1, 33, 33), mode='nearest')
+    ref01 = R.xyb_to_linear01(want, R.Params())
+    ref8 = R.srgb_u8(ref01).astype(np.int64)
+    dsmall = binding.to_device(small, torch)
+    for name, prec in (("fp32", binding.PREC_FP32), ("tc_f16x3", binding.PREC_TC_F16X3)):
+        with binding.Context(stream=stream.cuda_stream, timing=True, precision=prec) as ctx:
+            p = binding.filter_defaults(epf=1, gab=1)
+            for _ in range(3):
+                ctx.poll(ctx.submit(dimg, p, out, binding.OUT_F32_LINEAR, on_device=True))
+            stream.synchronize()
+            tickets = []
+            e0.record(stream)
+            for _ in range(steps):
+                t = ctx.submit(dimg, p, out, binding.OUT_F32_LINEAR, on_device=True)
+                ctx.poll(t)
+                tickets.append(t)
+            e1.record(stream)
+            stream.synchronize()
+            ms = e0.elapsed_time(e1) / steps
+            recon_ms = float(np.mean([ctx.stage_ms(t)[1] for t in tickets]))
+            q = binding.filter_defaults()
+            outs = {}
+            for dt, tdt in ((binding.OUT_F32_XYB, torch.float32),
+                            (binding.OUT_F32_LINEAR, torch.float32),
+                            (binding.OUT_U8_SRGB, torch.uint8)):
+                o = torch.empty((sample, sample, 3), dtype=tdt, device="cuda")
+                ctx.poll(ctx.submit(dsmall, q, o, dt, on_device=True))
+                outs[dt] = o.cpu().numpy()
+        xyb = outs[binding.OUT_F32_XYB].transpose(2, 0, 1).astype(np.float64)
+        rel = float((np.abs(xyb - want) / np.maximum(mag, 1e-30)).max())
+        plain = mag.max(axis=0) < 4.0       # realistic XYB magnitudes around the pixel
+        e01 = np.abs(np.clip(outs[binding.OUT_F32_LINEAR], 0, 1) - np.clip(ref01, 0, 1)).max(axis=2)
+        d8 = np.abs(outs[binding.OUT_U8_SRGB].astype(np.int64) - ref8)
+        res[name] = {"ms_per_4096_step": round(ms, 4), "recon_ms": round(recon_ms, 4),
+                     "mpx_s": round(XS * YS / ms / 1e3, 1),
+                     "xyb_max_err_rel_local": rel,
+                     "xyb_max_abs_err_where_local_abs_xyb_lt_4": float(np.abs(xyb - want).max(axis=0)[plain].max()),
+                     "rgb01_max_abs_err_where_local_abs_xyb_lt_4": float(e01[plain].max()),
+                     "u8_within_1": float((d8 <= 1).mean())}
+    res["error_sample"] = f"{sample}x{sample} mixed varblocks, no filters, vs FP64 oracle"
+    return res
+
+
 def cpu_baseline_run(steps=1):
     """Times the FP64 oracle on a bounded sample of the workload."""
     from oracle import recon as R
@@ -249,6 +311,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=600,
                     help="requests per serving run (0 = skip; 20000 = the full workload)")
+    ap.add_argument("--precision-steps", type=int, default=20,
+                    help="timed steps of the FP32 vs tensor-core comparison (0 = skip)")
     ap.add_argument("--batch-images", type=int, default=512,
                     help="images in the multi-image batch leg (0 = skip)")
     ap.add_argument("--serve-loads", default="0.5,0.9",
@@ -371,6 +435,9 @@ def main():
                "ms_per_step": round(ems, 4), "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(hout.nbytes)}
 
+    precision = None
+    if rank == 0 and args.precision_steps > 0:
+        precision = precision_leg(binding, torch, args.precision_steps)
     batched = None
     if rank == 0 and args.batch_images > 0:
         batched = batch_leg(binding, torch, args.batch_images)
@@ -400,7 +467,7 @@ def main():
                          "recon_gbs": round(recon_gbs, 1)},
             "peaks": peak_kind,
             "clocks": clocks, "e2e": e2e, "gpu_launches": int(launches),
-            "cpu_baseline": cb, "batched": batched, "served": served,
+            "cpu_baseline": cb, "precision": precision, "batched": batched, "served": served,
         }
         print(json.dumps(line), flush=True)
     ctx.close()
