@@ -327,9 +327,8 @@ def main():
     global XS, YS
     if args.size:
         XS, YS = (int(v) for v in args.size.lower().split("x"))
-    world = env_int("WORLD_SIZE", 1)
-    rank = env_int("RANK", 0)
-    local = env_int("LOCAL_RANK", 0)
+    from paper_1908_03565_gb300 import replicas
+    world, rank, local = replicas.rank_env()
     torch.cuda.set_device(local)
     dist = None
     if world > 1:
@@ -372,11 +371,7 @@ def main():
         torch.cuda.synchronize()
 
     def max_over_ranks(v):
-        if dist is None:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return replicas.max_over_ranks(v, dist, "cuda")
 
     # ---- device-resident timing -----------------------------------------
     clk = clocks_start()          # sampled through warm-up and timed steps
@@ -395,7 +390,7 @@ def main():
     recon_ms, filter_ms = float(stage[:, 1].mean()), float(stage[:, 2].mean())
 
     px = XS * YS
-    value = world * px / (ms * 1e-3) / 1e6
+    value = replicas.whole_job_rate(px, ms * 1e-3, world) / 1e6
     hbm_peak = peaks["hbm_gbs"]
     sm_count = torch.cuda.get_device_properties(local).multi_processor_count
     sm_mhz = peaks.get("sm_max_mhz", 2070.0)
