@@ -1165,7 +1165,8 @@ constexpr int kET = 30;                  // output tile
 constexpr int kER = 32;                  // EPF region: tile plus a 1-sample ring
 constexpr int kHR = 34;                  // rows of horizontal sums
 constexpr int kWW = 42, kWH = 40;        // sample / guide window, origin (x0-5, y0-5)
-constexpr int kGS = 65;                  // guide row stride (words), = 1 mod 32
+constexpr int kGS = 49;                  // guide row stride (words), = 17 mod 32: the
+                                         // 8 rows x 4 runs a warp reads hit 32 banks
 
 template <bool kClamp>
 __device__ __forceinline__ void epf_tile(const FilterArgs& a, int tbx, int tby) {
@@ -1177,36 +1178,64 @@ __device__ __forceinline__ void epf_tile(const FilterArgs& a, int tbx, int tby) 
   const int wx0 = x0 - 5, wy0 = y0 - 5;
 
   // ---- window of mirrored samples and packed guide bytes (6.5, J.2.2) ----
-  for (int i = tid; i < kWH * kWW; i += 128) {
-    const int ly = i / kWW, lx = i - ly * kWW;
-    const int gy = mirror_coord(wy0 + ly, a.ys), gx = mirror_coord(wx0 + lx, a.xs);
-    const size_t off = static_cast<size_t>(gy) * a.rstride + gx;
-    uint32_t g = 0;
+  // all of a thread's loads are issued before any is used (latency overlap)
+  const bool inner = wx0 >= 0 && wy0 >= 0 && wx0 + kWW <= a.xs && wy0 + kWH <= a.ys;
+  constexpr int kPer = (kWH * kWW + 127) / 128;
+  {
+    float wv[kPer][3];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      const float v = __ldg(a.xyb + c * a.pstride + off);
-      F[c][ly][lx] = v;
-      const float sc = fminf(fmaxf(guide_scaled(a.sp, c, v), 0.f), 255.f);
-      g |= static_cast<uint32_t>(sc) << (8 * c);
+    for (int j = 0; j < kPer; ++j) {
+      const int i = tid + 128 * j;
+      if (i < kWH * kWW) {
+        const int ly = i / kWW, lx = i - ly * kWW;
+        const int gy = inner ? wy0 + ly : mirror_coord(wy0 + ly, a.ys);
+        const int gx = inner ? wx0 + lx : mirror_coord(wx0 + lx, a.xs);
+        const size_t off = static_cast<size_t>(gy) * a.rstride + gx;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) wv[j][c] = __ldg(a.xyb + c * a.pstride + off);
+      }
     }
-    G[ly][lx] = g;
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) {
+      const int i = tid + 128 * j;
+      if (i < kWH * kWW) {
+        const int ly = i / kWW, lx = i - ly * kWW;
+        uint32_t g = 0;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          F[c][ly][lx] = wv[j][c];
+          const float sc = fminf(fmaxf(guide_scaled(a.sp, c, wv[j][c]), 0.f), 255.f);
+          g |= static_cast<uint32_t>(sc) << (8 * c);
+        }
+        G[ly][lx] = g;
+      }
+    }
   }
 
   // ---- per-pixel weight parameters of this thread's strip ------------------
   const int cx = tid & 31, ry0 = (tid >> 5) * 8;   // EPF-region column, first row
   int Mneg[8], vmax[8];
   bool pass[8];
-#pragma unroll
-  for (int r = 0; r < 8; ++r) {
-    const int qx = min(max(x0 - 1 + cx, 0), a.xs - 1);
-    const int qy = min(max(y0 - 1 + ry0 + r, 0), a.ys - 1);
-    const int sg = min(max(static_cast<int>(a.sigma[(qy >> 3) * a.bw + (qx >> 3)]), 0), 672);
-    pass[r] = sg < 16;
-    const int M = 16 * c_mul4[max(sg, 16)];           // < 0
-    Mneg[r] = -M;
+  {
     const int C = 0x3F800000;
     const int T16 = static_cast<int>((a.wmin_bits + 0xFFFFu) & 0xFFFF0000u);
-    vmax[r] = C >= T16 ? (C - T16) / (-M) : -1;
+    int prev = -1;
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const int qx = min(max(x0 - 1 + cx, 0), a.xs - 1);
+      const int qy = min(max(y0 - 1 + ry0 + r, 0), a.ys - 1);
+      const int sg = min(max(static_cast<int>(a.sigma[(qy >> 3) * a.bw + (qx >> 3)]), 0), 672);
+      pass[r] = sg < 16;
+      if (r > 0 && sg == prev) {          // the strip mostly stays in one block
+        Mneg[r] = Mneg[r - 1];
+        vmax[r] = vmax[r - 1];
+      } else {
+        const int M = 16 * c_mul4[max(sg, 16)];         // < 0
+        Mneg[r] = -M;
+        vmax[r] = C >= T16 ? (C - T16) / (-M) : -1;
+      }
+      prev = sg;
+    }
   }
   float ax[8], ay[8], ab[8], ws[8];
 #pragma unroll
@@ -1313,7 +1342,8 @@ __device__ __forceinline__ void epf_tile(const FilterArgs& a, int tbx, int tby) 
   __syncthreads();
   // positions of the ring outside the image take the value at the mirrored
   // position, which is inside the image and inside the region
-  for (int i = tid; i < kER * kER; i += 128) {
+  const bool ring_inside = x0 >= 1 && y0 >= 1 && x0 + kET < a.xs && y0 + kET < a.ys;
+  for (int i = ring_inside ? kER * kER : tid; i < kER * kER; i += 128) {
     const int ey = i >> 5, ex = i & 31;
     const int gy = y0 - 1 + ey, gx = x0 - 1 + ex;
     if (gy > a.ys || gx > a.xs) continue;
@@ -1324,28 +1354,41 @@ __device__ __forceinline__ void epf_tile(const FilterArgs& a, int tbx, int tby) 
   }
   __syncthreads();
 
-  // ---- J.4 Gaborish + L.2 + store, one pixel per item ----------------------
-  for (int i = tid; i < kET * kET; i += 128) {
-    const int ty = i / kET, tx = i - ty * kET;
-    const int gy = y0 + ty, gx = x0 + tx;
-    if (gy >= a.ys || gx >= a.xs) continue;
-    float v[3];
+  // ---- J.4 Gaborish + L.2 + store: each thread walks a column of up to 8
+  // pixels keeping the centre and the left+right sum of the previous, current
+  // and next rows (3 shared loads per pixel and channel) ------------------
+  {
+    const int tx = tid & 31, ty0 = (tid >> 5) * 8;
+    const int gx = x0 + tx;
+    if (tx < kET && gx < a.xs) {
+      float bp[3], sp[3], bc[3], sc[3];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      if (a.gab) {
-        float acc = 0.f;
+      for (int c = 0; c < 3; ++c) {
+        bp[c] = E[c][ty0][tx + 1];
+        sp[c] = E[c][ty0][tx] + E[c][ty0][tx + 2];
+        bc[c] = E[c][ty0 + 1][tx + 1];
+        sc[c] = E[c][ty0 + 1][tx] + E[c][ty0 + 1][tx + 2];
+      }
 #pragma unroll
-        for (int dy = -1; dy <= 1; ++dy)
+      for (int r = 0; r < 8; ++r) {
+        const int ty = ty0 + r, gy = y0 + ty;
+        if (ty >= kET || gy >= a.ys) break;
+        float v[3];
 #pragma unroll
-          for (int dx = -1; dx <= 1; ++dx)
-            acc = fmaf(a.gw[c][(dx != 0) + (dy != 0)], E[c][ty + 1 + dy][tx + 1 + dx], acc);
-        v[c] = acc;
-      } else {
-        v[c] = E[c][ty + 1][tx + 1];
+        for (int c = 0; c < 3; ++c) {
+          const float bn = E[c][ty + 2][tx + 1];
+          const float sn = E[c][ty + 2][tx] + E[c][ty + 2][tx + 2];
+          v[c] = a.gab ? fmaf(a.gw[c][0], bc[c],
+                              fmaf(a.gw[c][1], bp[c] + bn + sc[c], a.gw[c][2] * (sp[c] + sn)))
+                       : bc[c];
+          bp[c] = bc[c]; sp[c] = sc[c];
+          bc[c] = bn; sc[c] = sn;
+        }
+        float X[4] = {v[0], 0.f, 0.f, 0.f}, Y[4] = {v[1], 0.f, 0.f, 0.f};
+        float B[4] = {v[2], 0.f, 0.f, 0.f};
+        emit4(a.cp, a.out, gx, gy, 1, X, Y, B);
       }
     }
-    float X[4] = {v[0], 0.f, 0.f, 0.f}, Y[4] = {v[1], 0.f, 0.f, 0.f}, B[4] = {v[2], 0.f, 0.f, 0.f};
-    emit4(a.cp, a.out, gx, gy, 1, X, Y, B);
   }
 }
 
