@@ -56,6 +56,8 @@ class Params:
         self.inv_opsin = T.INV_OPSIN
         self.opsin_bias = T.OPSIN_BIAS
         self.target_nits_div50 = T.TARGET_NITS_DIV50
+        self.dc_smooth = False        # F.2 adaptive DC smoothing
+        self.lf_predict = False       # Annex H AC prediction
         for k, v in kw.items():
             if not hasattr(self, k):
                 raise KeyError(k)
@@ -108,7 +110,7 @@ def owner_map(vmap):
 # ---------------------------------------------------------------------------
 # F.2 + G + I.2.7 + F.3 + G: coefficients of every varblock
 # ---------------------------------------------------------------------------
-def dequantize(coeffs, vmap, acmul, cfl, params):
+def dequantize(coeffs, vmap, acmul, cfl, params, diag=None):
     """Dequantised, chroma-from-luma-corrected coefficient planes (FP64), in
     the same footprint layout as ``coeffs``, with each varblock's LLF slots
     holding its LLF coefficients."""
@@ -150,18 +152,202 @@ def dequantize(coeffs, vmap, acmul, cfl, params):
     kb = np.repeat(np.repeat(cfl[..., 1].astype(np.float64), 64, 0), 64, 1)[:Hp, :Wp]
     out[0] = out[0] + kx * out[1]
     out[2] = out[2] + kb * out[1]
-    # F.2 DC dequantisation and G for DC
-    dc = np.stack([params.m_dc[c] * q[c] for c in range(3)])
-    dc[0] = dc[0] + params.kx_dc * dc[1]
-    dc[2] = dc[2] + params.kb_dc * dc[1]
+    # F.2 DC dequantisation per 8x8 block (and adaptive smoothing), then G
+    if params.dc_smooth:
+        dcf = dc_smooth(dc_image(coeffs, vmap, params), params).astype(np.float64)
+    else:
+        dcf = dc_image(coeffs, vmap, params, dtype=np.float64)
+    dcf[0] = dcf[0] + params.kx_dc * dcf[1]
+    dcf[2] = dcf[2] + params.kb_dc * dcf[1]
     # I.2.7 LLF from DC, per varblock
     for c_, bx, by in varblocks(vmap):
         W, H = T.SHAPE_WH[c_]
-        x_0, y_0 = 8 * bx, 8 * by
         for c in range(3):
-            d = dc[c, y_0:y_0 + H // 8, x_0:x_0 + W // 8]
-            out[c, y_0:y_0 + H // 8, x_0:x_0 + W // 8] = TR.llf_from_dc(d)
+            out[c, 8 * by:8 * by + H // 8, 8 * bx:8 * bx + W // 8] = \
+                TR.llf_from_dc(dcf[c, by:by + H // 8, bx:bx + W // 8])
+    # Annex H: prediction of the remaining W/4 x H/4 coefficients
+    if params.lf_predict:
+        info = ac_prediction(out, vmap, dcf, params)
+        if diag is not None:
+            diag.update(info)
     return out
+
+
+# ---------------------------------------------------------------------------
+# F.2 adaptive DC smoothing
+# ---------------------------------------------------------------------------
+DC_SMOOTH_W = (0.05226273532324128, 0.20345139757231578, 0.0334829185968739)
+
+
+def dc_image(coeffs, vmap, params, dtype=np.float32):
+    """Dequantised DC samples per 8x8 block, (3, Hp/8, Wp/8), before chroma
+    from luma (F.2 with extra_levels 0): the DC of block (bx0+u, by0+v) of a
+    varblock sits at its LLF slot (u, v).  binary32 when the samples feed
+    the smoothing decision (one rounding of q * m_DC, as in the kernels)."""
+    bh, bw = vmap.shape
+    out = np.zeros((3, bh, bw), dtype=dtype)
+    for c_, bx, by in varblocks(vmap):
+        W, H = T.SHAPE_WH[c_]
+        for c in range(3):
+            q = coeffs[c, 8 * by:8 * by + H // 8, 8 * bx:8 * bx + W // 8].astype(dtype)
+            out[c, by:by + H // 8, bx:bx + W // 8] = q * dtype(params.m_dc[c])
+    return out
+
+
+def dc_smooth(dc, params):
+    """F.2: each DC sample not on the first/last row/column of the DC image
+    becomes the 3x3 weighted average wa of its neighbourhood (weights for
+    the centre, the 4 edge and the 4 corner neighbours) when
+    s - dcq/2 <= wa <= s + dcq/2.  READINGS: the averages read the
+    unsmoothed image; dcq, the DcQuantField of C.5.2, is m_DC of the channel
+    (no extra levels); the average and the comparison are evaluated in
+    binary32 in the order centre, then edges (N, W, E, S), then corners
+    (NW, NE, SW, SE), as the kernels do, so that both take the same
+    decisions."""
+    dc = dc.astype(np.float32)
+    out = dc.copy()
+    _, bh, bw = dc.shape
+    if bh < 3 or bw < 3:
+        return out
+    w0, w1, w2 = (np.float32(w) for w in DC_SMOOTH_W)
+    for c in range(3):
+        d = dc[c]
+        s_ = d[1:-1, 1:-1]
+        edges = ((d[:-2, 1:-1] + d[1:-1, :-2]) + d[1:-1, 2:]) + d[2:, 1:-1]
+        corners = ((d[:-2, :-2] + d[:-2, 2:]) + d[2:, :-2]) + d[2:, 2:]
+        wa = (w0 * s_ + w1 * edges) + w2 * corners
+        half = np.float32(0.5) * np.float32(params.m_dc[c])
+        keep = (s_ - half <= wa) & (wa <= s_ + half)
+        out[c, 1:-1, 1:-1] = np.where(keep, wa, s_)
+    return out
+
+
+# ---------------------------------------------------------------------------
+# Annex H AC prediction (with I.2.6 / I.2.7 at N = 4)
+# ---------------------------------------------------------------------------
+LF_SMOOTH_W = (0.12, 0.2, 0.02)
+LF_SMOOTH_RANGE = 1.7
+GROUP_BLOCKS = 32            # 256 x 256 sample groups (6.2), in 8x8 blocks
+_DCT_SHAPES = (T.DCT8, T.DCT16, T.DCT32, 6, 7, 8, 9, 10, 11)
+
+
+def downsample4(code, llf):
+    """I.2.6 with N = 4 from the LLF coefficients alone (the other
+    coefficients zero): the 4x4 box means of that reconstruction, the
+    reading pinned at N = 8 against the printed ScaleF form; for the 8x8-class
+    shapes every cell is the (0, 0) coefficient (I.2.6.3)."""
+    W, H = T.SHAPE_WH[code]
+    if code in _DCT_SHAPES:
+        coef = np.zeros((H, W))
+        coef[:H // 8, :W // 8] = llf
+        return TR.idct_2d(coef).reshape(H // 4, 4, W // 4, 4).mean(axis=(1, 3))
+    return np.full((2, 2), llf[0, 0])
+
+
+_LF4_INV = {}
+
+
+def half_mean_scale():
+    """The coefficient of frequency 1 of the 8-point IDCT whose two 4-sample
+    halves average to +1 and -1 (the factor I.2.7.3 writes ScaleF(2, 8, 1);
+    READING: the exact inverse of the half means, like R11 at N = 8)."""
+    return 1.0 / TR.idct_matrix(8)[:4, 1].mean()
+
+
+def lf_from_image4(code, img):
+    """I.2.7 with N = 4: the top-left H/4 x W/4 coefficients from an
+    H/4 x W/4 image of 4x4 means.  DCT shapes: the exact inverse of the 4x4
+    box mean of the reconstruction from those coefficients (I.2.7.1 defines
+    I.2.7 as the inverse of I.2.6).  Identity, DCT2, DCT4, AFV: AuxDCT2x2
+    (I.2.3.2).  DCT8x4 / DCT4x8: half means and half differences
+    (I.2.7.3; READING: the second formula printed for "DCT 8 x 4" is the
+    4x8 one and its block11 is input(1, 1))."""
+    W, H = T.SHAPE_WH[code]
+    if code in _DCT_SHAPES:
+        if code not in _LF4_INV:
+            cx, cy = W // 4, H // 4
+            M = np.zeros((cx * cy, cx * cy))
+            for j in range(cx * cy):
+                coef = np.zeros((H, W))
+                coef[j // cx, j % cx] = 1.0
+                M[:, j] = TR.idct_2d(coef).reshape(cy, 4, cx, 4).mean(axis=(1, 3)).reshape(-1)
+            _LF4_INV[code] = np.linalg.inv(M)
+        return (_LF4_INV[code] @ img.reshape(-1)).reshape(H // 4, W // 4)
+    if code in (T.IDENTITY, T.DCT2, T.DCT4, T.AFV):
+        return TR.aux_dct2x2(img, 2)
+    s = half_mean_scale()
+    tl, tr, bl, br = img[0, 0], img[0, 1], img[1, 0], img[1, 1]
+    out = np.zeros((2, 2))
+    if code == T.DCT8X4:          # two 8-tall, 4-wide halves side by side
+        dc0, ac0 = (tl + bl) / 2, (tl - bl) / 2
+        dc1, ac1 = (tr + br) / 2, (tr - br) / 2
+        out[0, 0], out[0, 1] = (dc0 + dc1) / 2, (dc0 - dc1) / 2
+        out[1, 0], out[1, 1] = ac0 * s, ac1 * s
+    else:                         # DCT4x8: two 4-tall, 8-wide halves stacked
+        dc0, ac0 = (tl + tr) / 2, (tl - tr) / 2
+        dc1, ac1 = (bl + br) / 2, (bl - br) / 2
+        out[0, 0], out[1, 0] = (dc0 + dc1) / 2, (dc0 - dc1) / 2
+        out[0, 1], out[1, 1] = ac0 * s, ac1 * s
+    return out
+
+
+def lf_smooth(img, dcq):
+    """Annex H smoothing of one group's DC2x2 image (2-sample ring
+    included): samples off the 2-wide ring become the 3x3 weighted average
+    wa when |wa - s| <= 1.7 dcq.  Returns the smoothed interior and the
+    distance of wa from the nearer threshold (for tests)."""
+    wc, we, wd = LF_SMOOTH_W
+    s_ = img[2:-2, 2:-2]
+    edges = img[1:-3, 2:-2] + img[2:-2, 1:-3] + img[2:-2, 3:-1] + img[3:-1, 2:-2]
+    corners = img[1:-3, 1:-3] + img[1:-3, 3:-1] + img[3:-1, 1:-3] + img[3:-1, 3:-1]
+    wa = wc * s_ + we * edges + wd * corners
+    t = LF_SMOOTH_RANGE * dcq
+    keep = (s_ - t <= wa) & (wa <= s_ + t)
+    margin = np.minimum(np.abs(wa - (s_ - t)), np.abs(s_ + t - wa))
+    return np.where(keep, wa, s_), margin
+
+
+def ac_prediction(out, vmap, dcf, params):
+    """Annex H on the dequantised coefficient planes ``out`` (in place):
+    per 256 x 256 group, the DC2x2 image of the varblocks' 4x downsamples
+    with a ring of the 1-block border of DC samples (mirrored at the image
+    bounds, 6.5), each repeated 2x2; smoothing; then the W/4 x H/4
+    coefficients of I.2.7 (N = 4) added outside the LLF corner.
+    READINGS: the group size is counted in 8x8 blocks of the padded image;
+    the ring and the DC2x2 image use the DC samples after F.2 and G; the
+    prediction is added to coefficients after G, in the same colour
+    space as the DC it derives from.  Returns the smoothed image and the
+    threshold margins, (3, 2 bh, 2 bw) each."""
+    bh, bw = vmap.shape
+    U = np.zeros((3, 2 * bh, 2 * bw))
+    for code, bx, by in varblocks(vmap):
+        W, H = T.SHAPE_WH[code]
+        for c in range(3):
+            llf = out[c, 8 * by:8 * by + H // 8, 8 * bx:8 * bx + W // 8]
+            U[c, 2 * by:2 * by + H // 4, 2 * bx:2 * bx + W // 4] = downsample4(code, llf)
+    Us = np.zeros_like(U)
+    margin = np.zeros_like(U)
+    G = GROUP_BLOCKS
+    for gy0 in range(0, bh, G):
+        for gx0 in range(0, bw, G):
+            gbw, gbh = min(G, bw - gx0), min(G, bh - gy0)
+            ys = mirror(np.arange(gy0 - 1, gy0 + gbh + 1), bh)
+            xs = mirror(np.arange(gx0 - 1, gx0 + gbw + 1), bw)
+            sl = (slice(2 * gy0, 2 * (gy0 + gbh)), slice(2 * gx0, 2 * (gx0 + gbw)))
+            for c in range(3):
+                ring = dcf[c][np.ix_(ys, xs)]
+                img = np.repeat(np.repeat(ring, 2, 0), 2, 1)
+                img[2:-2, 2:-2] = U[c][sl]
+                Us[c][sl], margin[c][sl] = lf_smooth(img, params.m_dc[c])
+    for code, bx, by in varblocks(vmap):
+        W, H = T.SHAPE_WH[code]
+        mask = np.ones((H // 4, W // 4), dtype=bool)
+        mask[:H // 8, :W // 8] = False
+        for c in range(3):
+            lf = lf_from_image4(code, Us[c, 2 * by:2 * by + H // 4, 2 * bx:2 * bx + W // 4])
+            blk = out[c, 8 * by:8 * by + H // 4, 8 * bx:8 * bx + W // 4]
+            blk[mask] += lf[mask]
+    return {'lf_image': Us, 'lf_margin': margin}
 
 
 # ---------------------------------------------------------------------------
@@ -220,9 +406,10 @@ def inverse_transform_literal(dq, vmap):
     return out
 
 
-def reconstruct_xyb(coeffs, vmap, acmul, cfl, params):
-    """Steps F, G, I: XYB samples of the padded image (FP64)."""
-    return inverse_transform(dequantize(coeffs, vmap, acmul, cfl, params), vmap)
+def reconstruct_xyb(coeffs, vmap, acmul, cfl, params, diag=None):
+    """Steps F, G, H, I: XYB samples of the padded image (FP64).  ``diag``
+    (a dict) receives the Annex H intermediates when that step runs."""
+    return inverse_transform(dequantize(coeffs, vmap, acmul, cfl, params, diag), vmap)
 
 
 # ---------------------------------------------------------------------------
@@ -408,10 +595,10 @@ def srgb_u8(lin01):
 # ---------------------------------------------------------------------------
 # Whole path
 # ---------------------------------------------------------------------------
-def reconstruct(inp, params):
+def reconstruct(inp, params, diag=None):
     """Returns a dict with the padded XYB before filters, the cropped XYB
     after filters, and linear RGB in [0, 1] (h, w, 3)."""
-    xyb = reconstruct_xyb(inp['coeffs'], inp['vmap'], inp['acmul'], inp['cfl'], params)
+    xyb = reconstruct_xyb(inp['coeffs'], inp['vmap'], inp['acmul'], inp['cfl'], params, diag)
     ys, xs = inp['ysize'], inp['xsize']
     img = xyb[:, :ys, :xs]
     if params.epf:

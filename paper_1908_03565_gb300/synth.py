@@ -138,14 +138,32 @@ def coefficient_positions(vmap):
     return u, v, ox, oy
 
 
+def llf_slots(vmap, u, v, ox, oy):
+    """Boolean (Hp, Wp) mask of the LLF slots (u < W/8 and v < H/8 of the
+    sample's varblock), which hold the quantised DC samples."""
+    bh, bw = vmap.shape
+    wv = np.zeros((bh, bw), dtype=np.int64)
+    hv = np.zeros((bh, bw), dtype=np.int64)
+    for code, (w, h) in SHAPE_WH.items():
+        sel = vmap[oy, ox] == code
+        wv[sel], hv[sel] = w, h
+    wv = np.repeat(np.repeat(wv, 8, 0), 8, 1)
+    hv = np.repeat(np.repeat(hv, 8, 0), 8, 1)
+    return (u < wv // 8) & (v < hv // 8)
+
+
 def make_image(xsize, ysize, seed, mix='mixed', acmul=None, cfl=True,
-               coef_scale=64.0, y_dc_offset_q=0):
+               coef_scale=64.0, y_dc_offset_q=0, dc='noise', ac=True):
     """One synthetic image.  Returns a dict with xsize, ysize, coeffs
     (int16, 3 x Hp x Wp), vmap (uint8, Hp/8 x Wp/8), acmul (float32, per
     block), cfl (float32, ceil(Hp/64) x ceil(Wp/64) x 2), sharpness (uint8).
     ``acmul`` None draws the log-uniform quant field, a number fixes it;
     ``cfl`` False sets kX = kB = 0; ``y_dc_offset_q`` adds a constant to the
-    quantised DC of the Y channel."""
+    quantised DC of the Y channel.  ``dc='smooth'`` replaces the quantised
+    DC samples by a slowly varying field (amplitude 40 steps, period 48
+    blocks) plus Gaussian noise of 0.7 steps, so that the DC and DC2x2
+    smoothing steps keep some samples and change others; ``ac=False``
+    zeroes every coefficient outside the LLF slots."""
     rng = np.random.default_rng(seed)
     Wp, Hp = 8 * ((xsize + 7) // 8), 8 * ((ysize + 7) // 8)
     bw, bh = Wp // 8, Hp // 8
@@ -154,16 +172,24 @@ def make_image(xsize, ysize, seed, mix='mixed', acmul=None, cfl=True,
     scale = coef_scale / (1.0 + u + v)
     lap = rng.laplace(0.0, 1.0, size=(3, Hp, Wp)) * scale[None]
     coeffs = np.clip(np.rint(lap), -32768, 32767).astype(np.int16)
+    llf = None
+    if dc == 'smooth' or not ac:
+        llf = llf_slots(vmap, u, v, ox, oy)
+    if dc == 'smooth':
+        # block index of the DC sample in each LLF slot
+        bxs = np.repeat(np.repeat(ox, 8, 0), 8, 1) + u
+        bys = np.repeat(np.repeat(oy, 8, 0), 8, 1) + v
+        phase = rng.uniform(0, 2 * math.pi, size=(3, 2))
+        for c in range(3):
+            f = 40.0 * np.sin(2 * math.pi * bxs / 48.0 + phase[c, 0]) * \
+                np.cos(2 * math.pi * bys / 48.0 + phase[c, 1])
+            f = np.rint(f + rng.normal(0.0, 0.7, size=f.shape)).astype(np.int16)
+            coeffs[c] = np.where(llf, f, coeffs[c])
+    if not ac:
+        coeffs = np.where(llf[None], coeffs, 0).astype(np.int16)
     if y_dc_offset_q:
-        # LLF slots: u < W/8 and v < H/8 of the sample's varblock
-        wv = np.zeros((bh, bw), dtype=np.int64)
-        hv = np.zeros((bh, bw), dtype=np.int64)
-        for code, (w, h) in SHAPE_WH.items():
-            sel = vmap[oy, ox] == code
-            wv[sel], hv[sel] = w, h
-        wv = np.repeat(np.repeat(wv, 8, 0), 8, 1)
-        hv = np.repeat(np.repeat(hv, 8, 0), 8, 1)
-        llf = (u < wv // 8) & (v < hv // 8)
+        if llf is None:
+            llf = llf_slots(vmap, u, v, ox, oy)
         y = coeffs[1].astype(np.int64)
         coeffs[1] = np.where(llf, np.clip(y + y_dc_offset_q, -32768, 32767), y)
     if acmul is None:

@@ -376,3 +376,160 @@ def test_srgb_encoding_values():
     v = R.srgb_u8(np.array([0.0, 1.0, 0.5, 0.002, -1.0, 2.0]))
     assert list(v) == [0, 255, 188, 7, 0, 255]
 
+
+
+# --------------------------------------------------------------------------
+# F.2 adaptive DC smoothing
+# --------------------------------------------------------------------------
+def test_dc_smoothing_weights_and_invariants():
+    """The nine weights of F.2 sum to one, so constant and linear DC images
+    are fixed points; borders are untouched; a lone spike is smoothed only
+    when the average stays within half a quantisation step."""
+    w0, w1, w2 = R.DC_SMOOTH_W
+    assert w0 + 4 * w1 + 4 * w2 == pytest.approx(1.0, abs=1e-15)
+    p = R.Params(m_dc=(0.1, 0.1, 0.1))
+    yy, xx = np.mgrid[0:9, 0:11]
+    ramp = np.stack([0.01 * xx + 0.02 * yy, np.full((9, 11), 0.3), -0.01 * yy]).astype(np.float32)
+    np.testing.assert_allclose(R.dc_smooth(ramp, p), ramp, atol=1e-6)
+    spike = np.zeros((3, 5, 5), np.float32)
+    spike[:, 2, 2] = 0.04          # wa = w0 * 0.04, deviation 0.038 < 0.05: smoothed
+    out = R.dc_smooth(spike, p)
+    assert out[0, 2, 2] == pytest.approx(w0 * 0.04, rel=1e-6)
+    assert out[0, 1, 2] == pytest.approx(w1 * 0.04, rel=1e-6)
+    assert out[0, 1, 1] == pytest.approx(w2 * 0.04, rel=1e-6)
+    spike[:, 2, 2] = 0.2           # deviation 0.19 > 0.05: kept
+    out = R.dc_smooth(spike, p)
+    assert out[0, 2, 2] == pytest.approx(0.2)
+    assert out[0, 0, 2] == 0.0 and out[0, 4, 4] == 0.0   # border samples untouched
+
+
+def test_dc_smoothing_reaches_the_pixels():
+    """With smoothing the DC samples of the varblocks change as F.2 says, and
+    the box means of the reconstruction follow them (I.2.6/I.2.7)."""
+    im = synth.make_image(64, 48, 11, dc='smooth')
+    p = R.Params(dc_smooth=True)
+    raw = R.dc_image(im['coeffs'], im['vmap'], p)
+    dci = R.dc_smooth(raw, p)
+    assert 0.2 < np.mean(dci != raw) < 0.8      # the workload exercises both outcomes
+    x = R.reconstruct_xyb(im['coeffs'], im['vmap'], im['acmul'], np.zeros_like(im['cfl']), p)
+    # AC contributes zero mean to every 8x8 block of a DCT8 varblock
+    for by, bx in zip(*np.nonzero(im['vmap'] == 0)):
+        mean = x[:, 8 * by:8 * by + 8, 8 * bx:8 * bx + 8].mean(axis=(1, 2))
+        np.testing.assert_allclose(mean, dci[:, by, bx], atol=1e-9)
+
+
+# --------------------------------------------------------------------------
+# Annex H AC prediction; I.2.6 / I.2.7 at N = 4
+# --------------------------------------------------------------------------
+def _inverse_any(code, coef):
+    return TR.idct_2d(coef) if code in R._DCT_SHAPES else TR.idct_8x8_class(code, coef)
+
+
+@pytest.mark.parametrize('code', range(15))
+def test_lf_from_image4_inverts_the_4x4_means(code):
+    """I.2.7.1: the N = 4 coefficients reproduce the given 4x4 means when
+    reconstructed by the shape's own inverse transform (I.2.4), for every
+    DctSelect code, the printed 8x4 / 4x8 / AFV forms included."""
+    W, H = T.SHAPE_WH[code]
+    img = np.random.default_rng(code).normal(size=(H // 4, W // 4))
+    c = R.lf_from_image4(code, img)
+    coef = np.zeros((H, W))
+    coef[:H // 4, :W // 4] = c
+    means = _inverse_any(code, coef).reshape(H // 4, 4, W // 4, 4).mean(axis=(1, 3))
+    np.testing.assert_allclose(means, img, atol=1e-12)
+
+
+def test_half_mean_scale_is_the_printed_scalef():
+    """The 8x4 / 4x8 factor read as an exact inverse equals the printed
+    ScaleF(2, 8, 1) of I.2.7.3."""
+    assert R.half_mean_scale() == pytest.approx(T.ScaleF(2, 8, 1), rel=1e-14)
+
+
+@pytest.mark.parametrize('code', R._DCT_SHAPES)
+def test_downsample4_matches_printed_scalef(code):
+    """I.2.6.2 as printed with N = 4 (ScaleF, then an IDCT of the LF size)
+    equals the 4x4 box means of the LLF-only reconstruction; and the 2x2
+    means of the 4x image are the 8x DC samples (I.2.7 at N = 8)."""
+    W, H = T.SHAPE_WH[code]
+    rng = np.random.default_rng(100 + code)
+    dc = rng.normal(size=(H // 8, W // 8))
+    llf = TR.llf_from_dc(dc)
+    d4 = R.downsample4(code, llf)
+    coef = np.zeros((H, W))
+    coef[:H // 8, :W // 8] = llf
+    np.testing.assert_allclose(TR.downsample_scalef(coef, N=4), d4, atol=1e-13)
+    np.testing.assert_allclose(d4.reshape(H // 8, 2, W // 8, 2).mean(axis=(1, 3)), dc, atol=1e-13)
+
+
+def test_lf_smoothing_weights_and_threshold():
+    """Annex H smoothing: weights sum to one (constant and linear images are
+    fixed points); a spike is averaged with 0.12 / 0.2 / 0.02 only within
+    1.7 dcq; the 2-sample ring is never changed."""
+    wc, we, wd = R.LF_SMOOTH_W
+    assert wc + 4 * we + 4 * wd == pytest.approx(1.0, abs=1e-15)
+    yy, xx = np.mgrid[0:10, 0:12]
+    ramp = 0.3 + 0.01 * xx - 0.02 * yy
+    sm, _ = R.lf_smooth(ramp, 0.1)
+    np.testing.assert_allclose(sm, ramp[2:-2, 2:-2], atol=1e-15)
+    img = np.zeros((7, 7))
+    img[3, 3] = 0.1                          # |wa - s| = 0.088 <= 0.17: averaged
+    sm, _ = R.lf_smooth(img, 0.1)
+    assert sm[1, 1] == pytest.approx(0.012)
+    assert sm[0, 1] == pytest.approx(0.02) and sm[0, 0] == pytest.approx(0.002)
+    img[3, 3] = 1.0                          # |wa - s| = 0.88 > 0.17: kept
+    sm, _ = R.lf_smooth(img, 0.1)
+    assert sm[1, 1] == 1.0
+    assert sm.shape == (3, 3)
+
+
+@pytest.mark.parametrize('mix', ['mixed', 3, 12, 13, 14, 1, 2])
+def test_ac_prediction_closes_the_loop(mix):
+    """With only DC transmitted, the W/4 x H/4 coefficients that the
+    reconstruction's own 4x4 means imply (I.2.7 at N = 4) are the LLF
+    coefficients from the DC samples in the LLF corner and those of the
+    smoothed DC2x2 image outside it (Annex H + I.2.4); a constant DC image
+    yields no prediction at all."""
+    im = synth.make_image(72, 56, 5, mix=mix, dc='smooth', ac=False)
+    p = R.Params(dc_smooth=True, lf_predict=True)
+    diag = {}
+    x = R.reconstruct_xyb(im['coeffs'], im['vmap'], im['acmul'], im['cfl'], p, diag)
+    base = R.dequantize(im['coeffs'], im['vmap'], im['acmul'], im['cfl'], R.Params(dc_smooth=True))
+    _, Hp, Wp = x.shape
+    means = x.reshape(3, Hp // 4, 4, Wp // 4, 4).mean(axis=(2, 4))
+    us = diag['lf_image']
+    assert np.abs(us - means).max() > 1e-4          # the prediction did something
+    for code, bx, by in R.varblocks(im['vmap']):
+        W, H = T.SHAPE_WH[code]
+        llf = np.zeros((H // 4, W // 4), dtype=bool)
+        llf[:H // 8, :W // 8] = True
+        for c in range(3):
+            area = (slice(2 * by, 2 * by + H // 4), slice(2 * bx, 2 * bx + W // 4))
+            got = R.lf_from_image4(code, means[c][area])
+            want = np.where(llf, base[c, 8 * by:8 * by + H // 4, 8 * bx:8 * bx + W // 4],
+                            R.lf_from_image4(code, us[c][area]))
+            np.testing.assert_allclose(got, want, atol=1e-12)
+    u, v, ox, oy = synth.coefficient_positions(im['vmap'])
+    slots = synth.llf_slots(im['vmap'], u, v, ox, oy)
+    q = np.broadcast_to(np.where(slots, 7, 0), im['coeffs'].shape).astype(np.int16)
+    a = R.dequantize(q, im['vmap'], im['acmul'], np.zeros_like(im['cfl']), R.Params())
+    b = R.dequantize(q, im['vmap'], im['acmul'], np.zeros_like(im['cfl']),
+                     R.Params(lf_predict=True))
+    np.testing.assert_allclose(a, b, atol=1e-15)
+
+
+def test_ac_prediction_ring_reads_only_the_border_dc():
+    """A group's prediction depends on its own varblocks and the 1-block ring
+    of DC samples around it, not on anything further out: two images that
+    agree on group 0 (256 x 256) and its ring agree there; a change inside
+    the ring does reach group 0."""
+    im = synth.make_image(280, 64, 9, mix='dct8', dc='smooth')
+    p = R.Params(lf_predict=True)
+    base = R.dequantize(im['coeffs'], im['vmap'], im['acmul'], im['cfl'], p)
+    far = im['coeffs'].copy()
+    far[:, :, 8 * 34:] += 5                   # blocks 34.. (beyond the ring at 32)
+    other = R.dequantize(far, im['vmap'], im['acmul'], im['cfl'], p)
+    np.testing.assert_array_equal(other[:, :, :256], base[:, :, :256])
+    near = im['coeffs'].copy()
+    near[:, ::8, 8 * 32] += 5                 # DC of the ring column (block 32)
+    other = R.dequantize(near, im['vmap'], im['acmul'], im['cfl'], p)
+    assert np.abs(other[:, :, 248:256] - base[:, :, 248:256]).max() > 0
