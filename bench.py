@@ -263,6 +263,43 @@ def precision_leg(binding, torch, steps, sample=1024):
     return res
 
 
+def dc_lf_leg(binding, torch, steps):
+    """Cost of the DC-domain steps (F.2 adaptive DC smoothing, Annex H AC
+    prediction) on a 4096x4096 image with a smooth DC field: the same step
+    (EPF + Gaborish, f32 out) without them, with F.2, and with F.2 + H.
+    CUDA events over the timed steps; the recon stage includes the DC-domain
+    kernels."""
+    from paper_1908_03565_gb300 import synth
+    img = synth.make_image(XS, YS, SEED + 5, dc='smooth')
+    dimg = binding.to_device(img, torch)
+    out = torch.empty((YS, XS, 3), dtype=torch.float32, device="cuda")
+    stream = torch.cuda.Stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    res = {}
+    with binding.Context(stream=stream.cuda_stream, timing=True) as ctx:
+        for name, sm, lf in (("plain", 0, 0), ("dc_smooth", 1, 0), ("dc_smooth+lf_predict", 1, 1)):
+            p = binding.filter_defaults(epf=1, gab=1, dc_smooth=sm, lf_predict=lf)
+            for _ in range(3):
+                ctx.poll(ctx.submit(dimg, p, out, binding.OUT_F32_LINEAR, on_device=True))
+            stream.synchronize()
+            l0 = ctx.launch_count()
+            tickets = []
+            e0.record(stream)
+            for _ in range(steps):
+                t = ctx.submit(dimg, p, out, binding.OUT_F32_LINEAR, on_device=True)
+                ctx.poll(t)
+                tickets.append(t)
+            e1.record(stream)
+            stream.synchronize()
+            ms = e0.elapsed_time(e1) / steps
+            res[name] = {"ms_per_step": round(ms, 4),
+                         "recon_stage_ms": round(float(np.mean([ctx.stage_ms(t)[1] for t in tickets])), 4),
+                         "mpx_s": round(XS * YS / ms / 1e3, 1),
+                         "launches_per_step": (ctx.launch_count() - l0) / steps}
+    res["input"] = f"{XS}x{YS} mixed varblocks, smooth DC field (synth dc='smooth')"
+    return res
+
+
 def cpu_baseline_run(steps=1):
     """Times the FP64 oracle on a bounded sample of the workload."""
     from oracle import recon as R
@@ -315,6 +352,8 @@ def main():
                     help="timed steps of the FP32 vs tensor-core comparison (0 = skip)")
     ap.add_argument("--batch-images", type=int, default=512,
                     help="images in the multi-image batch leg (0 = skip)")
+    ap.add_argument("--dclf-steps", type=int, default=20,
+                    help="timed steps of the DC smoothing / AC prediction leg (0 = skip)")
     ap.add_argument("--serve-loads", default="0.5,0.9",
                     help="offered loads as fractions of the measured capacity")
     args = ap.parse_args()
@@ -433,6 +472,9 @@ def main():
     precision = None
     if rank == 0 and args.precision_steps > 0:
         precision = precision_leg(binding, torch, args.precision_steps)
+    dclf = None
+    if rank == 0 and args.dclf_steps > 0:
+        dclf = dc_lf_leg(binding, torch, args.dclf_steps)
     batched = None
     if rank == 0 and args.batch_images > 0:
         batched = batch_leg(binding, torch, args.batch_images)
@@ -462,7 +504,7 @@ def main():
                          "recon_gbs": round(recon_gbs, 1)},
             "peaks": peak_kind,
             "clocks": clocks, "e2e": e2e, "gpu_launches": int(launches),
-            "cpu_baseline": cb, "precision": precision, "batched": batched, "served": served,
+            "cpu_baseline": cb, "precision": precision, "dc_lf": dclf, "batched": batched, "served": served,
         }
         print(json.dumps(line), flush=True)
     ctx.close()

@@ -135,6 +135,13 @@ typedef struct {
   float opsin_bias[3];
   uint32_t target_nits_div50;
   const float* dequant;
+  /* F.2 adaptive DC smoothing: 1 applies it, 0 skips it (the effect of
+   * kSkipAdaptiveDCSmoothing).  The window half-width is m_dc / 2 (DC
+   * quantisation without extra levels, C.5.2). */
+  int dc_smooth;
+  /* Annex H AC prediction from the DC2x2 image of each 256 x 256 group:
+   * 1 applies it, 0 skips it (the effect of kSkipPredictLf). */
+  int lf_predict;
 } jxl_recon_filter_params;
 
 /* Caller-owned output buffer of ysize rows, row_stride_bytes apart. */
@@ -147,7 +154,8 @@ typedef struct {
 } jxl_recon_output;
 
 /* Fills *p with the defaults of C.10, C.4.1 (m_DC of the synthetic
- * workloads: (0.02, 0.2, 0.2) / (64 sqrt 2)) and L.2; both filters off. */
+ * workloads: (0.02, 0.2, 0.2) / (64 sqrt 2)) and L.2; both filters, DC
+ * smoothing and AC prediction off. */
 void jxl_recon_filter_defaults(jxl_recon_filter_params* p);
 
 /* Creates a context on config->device: builds the constant tables (C.6.1

@@ -16,6 +16,7 @@
 #include "../../include/jxl_recon.h"
 #include "internal.h"
 #include "kernels.h"
+#include "lf.h"
 
 using namespace jxlr;
 
@@ -153,6 +154,11 @@ jxlr_status jxl_recon_create(const jxl_recon_config* cfg, jxl_recon_ctx** out) {
   for (int j = 0; j < 16; ++j)
     for (int i = 0; i < 16; ++i) afv[j * 16 + i] = static_cast<float>(kAfvBasis[j][i]);
   if (!upload_constants(llf.data(), odd.data(), mul4.data(), afv.data()))
+    return fail(JXLR_ECUDA, "create: constant upload failed");
+  std::vector<float> lf_up(kLfUpFloats), lf_inv(kLfInvFloats);
+  float lf_half = 0.f;
+  lf_tables(lf_up.data(), lf_inv.data(), &lf_half);
+  if (!upload_lf_constants(lf_up.data(), lf_inv.data(), lf_half))
     return fail(JXLR_ECUDA, "create: constant upload failed");
 
   auto* ctx = new jxl_recon_ctx();
@@ -371,6 +377,16 @@ extern "C" jxlr_status jxl_recon_submit(jxl_recon_ctx* ctx, const jxl_recon_coef
   if (fp->dequant) add(sizeof(float) * kDequantFloats);
   if (filters) add(sizeof(float) * 3 * wp * hp);
   if (fp->epf) add(sizeof(int16_t) * bw * bh);
+  const bool dcsteps = fp->dc_smooth || fp->lf_predict;
+  const size_t nblk = static_cast<size_t>(bw) * bh;
+  if (dcsteps) {
+    add(nblk);                                        // owner bytes
+    add(sizeof(float) * 3 * nblk);                    // DC after F.2 and G
+  }
+  if (fp->lf_predict) {
+    add(sizeof(float) * 12 * nblk);                   // DC2x2 image
+    add(sizeof(float) * 12 * nblk);                   // predicted coefficients
+  }
   const size_t out_bytes = out->row_stride_bytes * (ys - 1) + px_bytes * xs;
   if (!out->on_device) add(out_bytes);
   need = align_up(need, 256);
@@ -449,6 +465,32 @@ extern "C" jxlr_status jxl_recon_submit(jxl_recon_ctx* ctx, const jxl_recon_coef
   ra.tcb = ctx->d_tcb;
   ra.err = d_status + 3;
   const bool tc = ctx->precision == JXLR_PREC_TC_F16X3;
+  if (dcsteps) {
+    LfArgs la;
+    std::memset(&la, 0, sizeof(la));
+    for (int c = 0; c < 3; ++c) {
+      la.coef[c] = ra.coef[c];
+      la.m_dc[c] = fp->m_dc[c];
+    }
+    la.cstride = ra.cstride;
+    la.vmap = ra.vmap;
+    la.bw = bw;
+    la.bh = bh;
+    la.bpl = nblk;
+    la.kx_dc = cfl->kx_dc;
+    la.kb_dc = cfl->kb_dc;
+    la.smooth = fp->dc_smooth != 0;
+    la.predict = fp->lf_predict != 0;
+    la.own = cv.take<uint8_t>(nblk);
+    la.d1 = cv.take<float>(3 * nblk);
+    if (la.predict) {
+      la.u = cv.take<float>(12 * nblk);
+      la.us = cv.take<float>(12 * nblk);
+    }
+    ctx->launches += launch_lf(la, s);
+    ra.dc1 = la.d1;
+    ra.lfp = la.us;
+  }
 
   OutParams op;
   char* d_out = nullptr;

@@ -52,6 +52,17 @@ void llf_maps(float* out /* kLlfMaps * 256 */);
 constexpr int kOddFloats = 256 + 64 + 16 + 4 + 1;
 void odd_tables(float* out);
 
+// Annex H maps on the unscaled cosine basis, for N = 8, 16, 32 packed in
+// that order: up (N/4 x N/8 each, 42 floats) takes the N/8 DC samples of a
+// varblock axis to the 4-sample means of its LLF-only reconstruction (I.2.6
+// at N = 4); inv (N/4 x N/4 each, 84 floats) takes N/4 such means to the
+// N/4 lowest coefficients (I.2.7 at N = 4, the exact inverse); half is the
+// coefficient of 8-point frequency 1 whose 4-sample halves average to +-1
+// (I.2.7.3 for DCT8x4 / DCT4x8).
+constexpr int kLfUpFloats = 42;
+constexpr int kLfInvFloats = 84;
+void lf_tables(float* up, float* inv, float* half);
+
 // 4 * mul_table[sigma] of J.2.4 for sigma in [0, 672]; entries below 16 are 0.
 void mul_table4(int32_t* out /* 673 */);
 
@@ -88,5 +99,7 @@ void set_last_error(const std::string& msg);
 // __constant__ memory of the current device.
 bool upload_constants(const float* llf, const float* odd, const int32_t* mul4,
                       const float* afv);
+// The same for the Annex H kernels (lf.cu).
+bool upload_lf_constants(const float* up, const float* inv, float half);
 
 }  // namespace jxlr

@@ -720,7 +720,9 @@ __device__ void tc_pass(TcShared& ts, uint32_t& phase, unsigned* err, int nrows,
 }
 
 // One 32x32 cell (cell coordinates cxi, cyi) of image a; 128 threads.
-template <bool kTC = false>
+// kDc: whether the DC-domain inputs (dc1, lfp) may be set (single-image
+// launches only).
+template <bool kTC = false, bool kDc = true>
 __device__ __forceinline__ void recon_cell(const ReconArgs& a, int cxi, int cyi) {
   __shared__ __align__(16) float S[3][32][kRS];
   __shared__ __align__(16) float T[3][32][kRS];
@@ -751,6 +753,24 @@ __device__ __forceinline__ void recon_cell(const ReconArgs& a, int cxi, int cyi)
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     tc_fence_before();
+  }
+  // DC after F.2 and G, and the Annex H coefficients, of this cell's blocks
+  // (published by the barrier that ends cell_setup)
+  __shared__ float sdc[kDc ? 3 : 1][4][4];
+  __shared__ __align__(8) float slp[kDc ? 3 : 1][8][8];
+  const size_t bpl = static_cast<size_t>(a.bw) * a.bh;
+  if (kDc && a.dc1 && tid < 48) {
+    const int c = tid >> 4, bx = gbx0 + (tid & 3), by = gby0 + ((tid >> 2) & 3);
+    sdc[c][(tid >> 2) & 3][tid & 3] =
+        bx < a.bw && by < a.bh ? a.dc1[c * bpl + static_cast<size_t>(by) * a.bw + bx] : 0.f;
+  }
+  if (kDc && a.lfp && tid >= 32) {
+    const int i = tid - 32, c = i >> 5, r = (i >> 2) & 7, q = i & 3;
+    const int x = 2 * gbx0 + 2 * q, y = 2 * gby0 + r;
+    float2 v = make_float2(0.f, 0.f);
+    if (x < 2 * a.bw && y < 2 * a.bh)
+      v = *reinterpret_cast<const float2*>(a.lfp + 4 * c * bpl + static_cast<size_t>(y) * (2 * a.bw) + x);
+    *reinterpret_cast<float2*>(&slp[c][r][2 * q]) = v;
   }
   cell_setup(cs, a.vmap, a.acmul, gbx0, gby0, a.bw, a.bh, kTC);
   if (kTC) tc_fence_after();
@@ -792,13 +812,23 @@ __device__ __forceinline__ void recon_cell(const ReconArgs& a, int cxi, int cyi)
       for (int j = 0; j < 8; ++j) {
         const bool llf = (u0 + j) < cxl && vv < cyl;
         if (llf) {
-          const float dx = a.m_dc[0] * q[0][j], dy = a.m_dc[1] * q[1][j], db = a.m_dc[2] * q[2][j];
-          out[0][j] = fmaf(a.kx_dc, dy, dx);
-          out[1][j] = dy;
-          out[2][j] = fmaf(a.kb_dc, dy, db);
+          if (kDc && a.dc1) {   // F.2 smoothing and G already applied per block
+#pragma unroll
+            for (int c = 0; c < 3; ++c) out[c][j] = sdc[c][v.by + vv][v.bx + u0 + j];
+          } else {
+            const float dx = a.m_dc[0] * q[0][j], dy = a.m_dc[1] * q[1][j],
+                        db = a.m_dc[2] * q[2][j];
+            out[0][j] = fmaf(a.kx_dc, dy, dx);
+            out[1][j] = dy;
+            out[2][j] = fmaf(a.kb_dc, dy, db);
+          }
         } else {
           out[0][j] = fmaf(kx, out[1][j], out[0][j]);
           out[2][j] = fmaf(kb, out[1][j], out[2][j]);
+          if (kDc && a.lfp && (u0 + j) < 2 * cxl && vv < 2 * cyl) {   // Annex H prediction
+#pragma unroll
+            for (int c = 0; c < 3; ++c) out[c][j] += slp[c][2 * v.by + vv][2 * v.bx + u0 + j];
+          }
         }
       }
     } else {
@@ -951,7 +981,7 @@ __global__ void __launch_bounds__(128, 6) k_recon_batch(const ReconArgs* __restr
     __syncthreads();
     const int local = w - prefix[img];
     const int cells_x = (sa.wp + 31) / 32;
-    recon_cell(sa, local % cells_x, local / cells_x);
+    recon_cell<false, false>(sa, local % cells_x, local / cells_x);
   }
 }
 

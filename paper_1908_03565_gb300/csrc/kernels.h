@@ -49,6 +49,8 @@ struct ReconArgs {
   OutParams out;
   const unsigned char* tcb;   // tensor-core basis tables (tensor-core variant only)
   unsigned* err;              // error flags of the tensor-core variant
+  const float* dc1;           // [3][bh][bw] DC after F.2 smoothing and G, or nullptr
+  const float* lfp;           // [3][2bh][2bw] Annex H coefficients, or nullptr
 };
 
 struct SigmaArgs {

@@ -127,6 +127,8 @@ extern "C" jxlr_status jxl_recon_run_noalloc(const jxl_recon_coeffs* co, const u
     return noalloc_fail(JXLR_EINVAL, "run_noalloc: output stride too small");
   if (fp->epf && !fp->sharpness)
     return noalloc_fail(JXLR_EINVAL, "run_noalloc: EPF needs the sharpness map");
+  if (fp->dc_smooth || fp->lf_predict)
+    return noalloc_fail(JXLR_EINVAL, "run_noalloc: DC smoothing and AC prediction run on the submit path only");
 
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);

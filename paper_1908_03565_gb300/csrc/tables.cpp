@@ -426,6 +426,42 @@ void prescale_dequant(const float* raw, float* scaled) {
   }
 }
 
+namespace {
+// Mean of the unscaled cosine f_k(n) = cos((2n+1) k pi / 2N) over n in
+// [s, s + len).
+double cos_mean(int N, int k, int s, int len) {
+  double acc = 0;
+  for (int n = s; n < s + len; ++n) acc += std::cos((2 * n + 1) * k * kPi / (2.0 * N));
+  return acc / len;
+}
+}  // namespace
+
+void lf_tables(float* up, float* inv, float* half) {
+  int uo = 0, io = 0;
+  for (int N = 8; N <= 32; N *= 2) {
+    const int n4 = N / 4, n8 = N / 8;
+    // M8[b][k]: 8-sample means of the LLF frequencies; M4L[q][k]: 4-sample
+    // means of the same; M4[q][k]: 4-sample means of the N/4 LF frequencies.
+    std::vector<double> m8(n8 * n8), m4(n4 * n4);
+    for (int b = 0; b < n8; ++b)
+      for (int k = 0; k < n8; ++k) m8[b * n8 + k] = cos_mean(N, k, 8 * b, 8);
+    for (int q = 0; q < n4; ++q)
+      for (int k = 0; k < n4; ++k) m4[q * n4 + k] = cos_mean(N, k, 4 * q, 4);
+    invert(m8.data(), n8);
+    for (int q = 0; q < n4; ++q)
+      for (int b = 0; b < n8; ++b) {
+        double acc = 0;
+        for (int k = 0; k < n8; ++k) acc += cos_mean(N, k, 4 * q, 4) * m8[k * n8 + b];
+        up[uo + q * n8 + b] = static_cast<float>(acc);
+      }
+    invert(m4.data(), n4);
+    for (int i = 0; i < n4 * n4; ++i) inv[io + i] = static_cast<float>(m4[i]);
+    uo += n4 * n8;
+    io += n4 * n4;
+  }
+  *half = static_cast<float>(1.0 / cos_mean(8, 1, 0, 4));
+}
+
 int llf_map_index(int cx, int cy) {
   // (cx, cy) in {1,2,4}^2 minus (1,1) and (1,... ) combinations that occur
   if (cx == 2 && cy == 2) return 0;
