@@ -34,14 +34,29 @@ __constant__ float c_llf[kLlfMaps * 256];
 __constant__ float c_odd[kOddFloats];
 __constant__ int32_t c_mul4[673];
 __constant__ float c_afv[256];
-__constant__ int c_shape_w[kNumCodes];
-__constant__ int c_shape_h[kNumCodes];
 __constant__ int c_dq_off[kNumCodes];
+
+// log2(W / 8) and log2(H / 8) per DctSelect code, two bits per code: lanes
+// holding different codes look their shape up without a memory access (a
+// constant-bank table serialises divergent lanes).
+constexpr uint32_t shape_bits(bool width) {
+  constexpr int lw[kNumCodes] = {0, 0, 0, 0, 1, 2, 0, 1, 0, 2, 1, 2, 0, 0, 0};
+  constexpr int lh[kNumCodes] = {0, 0, 0, 0, 1, 2, 1, 0, 2, 0, 2, 1, 0, 0, 0};
+  uint32_t m = 0;
+  for (int i = 0; i < kNumCodes; ++i) m |= static_cast<uint32_t>(width ? lw[i] : lh[i]) << (2 * i);
+  return m;
+}
+constexpr uint32_t kW8Bits = shape_bits(true), kH8Bits = shape_bits(false);
+__device__ __forceinline__ int lg_w8(int code) { return (kW8Bits >> (2 * code)) & 3; }
+__device__ __forceinline__ int lg_h8(int code) { return (kH8Bits >> (2 * code)) & 3; }
 
 static void prefer_shared_carveout();
 
 bool upload_constants(const float* llf, const float* odd, const int32_t* mul4,
                       const float* afv) {
+  for (int c = 0; c < kNumCodes; ++c)   // the packed shape bits agree with the shape table
+    if ((8 << ((kW8Bits >> (2 * c)) & 3)) != kShapeW[c] || (8 << ((kH8Bits >> (2 * c)) & 3)) != kShapeH[c])
+      return false;
   prefer_shared_carveout();
   int offs[kNumCodes];
   for (int c = 0; c < kNumCodes; ++c) offs[c] = dequant_offset(c, 0);
@@ -49,8 +64,6 @@ bool upload_constants(const float* llf, const float* odd, const int32_t* mul4,
          cudaMemcpyToSymbol(c_odd, odd, sizeof(float) * kOddFloats) == cudaSuccess &&
          cudaMemcpyToSymbol(c_mul4, mul4, sizeof(int32_t) * 673) == cudaSuccess &&
          cudaMemcpyToSymbol(c_afv, afv, sizeof(float) * 256) == cudaSuccess &&
-         cudaMemcpyToSymbol(c_shape_w, kShapeW, sizeof(int) * kNumCodes) == cudaSuccess &&
-         cudaMemcpyToSymbol(c_shape_h, kShapeH, sizeof(int) * kNumCodes) == cudaSuccess &&
          cudaMemcpyToSymbol(c_dq_off, offs, sizeof(int) * kNumCodes) == cudaSuccess;
 }
 
@@ -247,7 +260,7 @@ __global__ void k_validate(const uint8_t* __restrict__ vmap, int bw, int bh, uns
       if (code >= kNumCodes) {
         err |= 1;
       } else {
-        const int w8 = c_shape_w[code] / 8, h8 = c_shape_h[code] / 8;
+        const int w8 = 1 << lg_w8(code), h8 = 1 << lg_h8(code);
         if (bx % w8 || by % h8) {
           err |= 2;
         } else if (bx + w8 > bw || by + h8 > bh) {
@@ -291,6 +304,9 @@ constexpr int kRS = 36;  // shared row stride in floats: 16-byte rows, no bank
 struct CellVB {
   int code, bx, by;      // code and top-left block inside the cell (0..3)
   float acmul;
+  int lw, lh;            // log2 of the width and height in samples
+  int dqoff;             // offset of the code's matrices in the dequant table
+  int pad;
 };
 
 struct CellState {
@@ -312,10 +328,10 @@ __device__ __forceinline__ bool tc_shape(int code) { return code >= kDCT16 && co
 __device__ __forceinline__ int row_items(int code) {
   if (code == kIdentity || code == kDCT2) return 3;   // whole block per channel
   if (code == kAFV) return 12;                          // 4 quadrants x 3 channels
-  return 3 * c_shape_h[code];
+  return 3 * (8 << lg_h8(code));
 }
 
-__device__ __forceinline__ int col_items(int code) { return 3 * c_shape_w[code]; }
+__device__ __forceinline__ int col_items(int code) { return 3 * (8 << lg_w8(code)); }
 
 // Row pass of one item.  S: coefficients, T: output of the pass.
 __device__ void row_item(float (*S)[32][kRS], float (*T)[32][kRS], const CellVB& v, int k) {
@@ -403,8 +419,7 @@ __device__ void row_item(float (*S)[32][kRS], float (*T)[32][kRS], const CellVB&
     return;
   }
   // separable shapes: item = (channel, row)
-  const int H = c_shape_h[code];
-  const int c = k / H, r = k % H;
+  const int c = k >> v.lh, r = k & ((1 << v.lh) - 1);
   const float* src = &S[c][y0 + r][x0];
   float* dst = &T[c][y0 + r][x0];
   switch (code) {
@@ -419,8 +434,7 @@ __device__ void row_item(float (*S)[32][kRS], float (*T)[32][kRS], const CellVB&
 // Column pass of one item: T -> S.
 __device__ void col_item(float (*S)[32][kRS], float (*T)[32][kRS], const CellVB& v, int k) {
   const int code = v.code;
-  const int W = c_shape_w[code];
-  const int c = k / W, col = k % W;
+  const int c = k >> v.lw, col = k & ((1 << v.lw) - 1);
   const int x0 = 8 * v.bx, y0 = 8 * v.by;
   const float* src = &T[c][y0][x0 + col];
   float* dst = &S[c][y0][x0 + col];
@@ -490,7 +504,7 @@ __device__ void cell_sigma(float (*S)[32][kRS], CellState& cs, const SigmaParams
       sigma[gby * bw + gbx] = 0;   // not covered (ill-formed map): unfiltered
     } else if (o >= 0 && gbx < bw && gby < bh && gbx * 8 < xs && gby * 8 < ys) {
       const CellVB& v = cs.vb[o];
-      const int w8 = c_shape_w[v.code] / 8, h8 = c_shape_h[v.code] / 8;
+      const int w8 = 1 << (v.lw - 3), h8 = 1 << (v.lh - 3);
       float rng = 0.f;
       for (int yy = 0; yy < h8; ++yy)
         for (int xx = 0; xx < w8; ++xx) rng = fmaxf(rng, cs.brange[(v.by + yy) * 4 + v.bx + xx]);
@@ -529,8 +543,8 @@ __device__ void cell_setup(CellState& cs, const uint8_t* __restrict__ vmap,
     bool valid = false;
     int ri = 0, ci = 0, w8 = 1, h8 = 1;
     if (tid < 16 && code < kNumCodes) {
-      w8 = c_shape_w[code] / 8;
-      h8 = c_shape_h[code] / 8;
+      w8 = 1 << lg_w8(code);
+      h8 = 1 << lg_h8(code);
       // ill-formed placements are reported by k_validate; skip them here
       valid = !(bx % w8 || by % h8 || bx + w8 > 4 || by + h8 > 4 || gbx0 + bx + w8 > bw ||
                 gby0 + by + h8 > bh);
@@ -556,6 +570,9 @@ __device__ void cell_setup(CellState& cs, const uint8_t* __restrict__ vmap,
     if (valid) {
       CellVB v;
       v.code = code; v.bx = bx; v.by = by; v.acmul = am;
+      v.lw = 3 + lg_w8(code); v.lh = 3 + lg_h8(code);
+      v.dqoff = c_dq_off[code];
+      v.pad = 0;
       cs.vb[rank] = v;
       cs.row_pre[rank + 1] = pr + ri;
       cs.col_pre[rank + 1] = pc + ci;
@@ -782,7 +799,7 @@ __device__ __forceinline__ void recon_cell(const ReconArgs& a, int cxi, int cyi)
     float out[3][8];
     if (o >= 0 && inb) {
       const CellVB v = cs.vb[o];
-      const int W = c_shape_w[v.code], H = c_shape_h[v.code];
+      const int W = 1 << v.lw, H = 1 << v.lh;
       const int u0 = 8 * k - 8 * v.bx, vv = y - 8 * v.by;
       const int cxl = W >> 3, cyl = H >> 3;
       const int tile = (gy >> 6) * a.tw + (gx >> 6);
@@ -796,7 +813,7 @@ __device__ __forceinline__ void recon_cell(const ReconArgs& a, int cxi, int cyi)
       }
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        const float* m = a.dequant + c_dq_off[v.code] + c * W * H + vv * W + u0;
+        const float* m = a.dequant + v.dqoff + ((c * H + vv) << v.lw) + u0;
         const float4 m0 = __ldg(reinterpret_cast<const float4*>(m));
         const float4 m1 = __ldg(reinterpret_cast<const float4*>(m + 4));
         const float mm[8] = {m0.x, m0.y, m0.z, m0.w, m1.x, m1.y, m1.z, m1.w};
@@ -851,18 +868,22 @@ __device__ __forceinline__ void recon_cell(const ReconArgs& a, int cxi, int cyi)
     const CellVB v = cs.vb[tid / 3];
     const int c = tid % 3;
     float* s = &S[c][8 * v.by][8 * v.bx];
-    const int cxl = c_shape_w[v.code] >> 3, cyl = c_shape_h[v.code] >> 3;
+    const int cxl = 1 << (v.lw - 3), cyl = 1 << (v.lh - 3);
     const int n = cxl * cyl;
     if (n > 1) {
       const float* mp = c_llf + llf_map_index_dev(cxl, cyl) * 256;
-      float dc[16], r[16];
-      for (int i = 0; i < n; ++i) dc[i] = s[(i / cxl) * kRS + i % cxl];
+      const int lcx = v.lw - 3;
+      // dc is indexed statically (guarded) so that it stays in registers; it
+      // is read in full before the first output overwrites the LLF slots
+      float dc[16];
+#pragma unroll
+      for (int i = 0; i < 16; ++i) dc[i] = i < n ? s[(i >> lcx) * kRS + (i & (cxl - 1))] : 0.f;
       for (int j = 0; j < n; ++j) {
         float acc = 0.f;
-        for (int i = 0; i < n; ++i) acc = fmaf(mp[j * 16 + i], dc[i], acc);
-        r[j] = acc;
+#pragma unroll
+        for (int i = 0; i < 16; ++i) acc = fmaf(mp[j * 16 + i], dc[i], acc);
+        s[(j >> lcx) * kRS + (j & (cxl - 1))] = acc;
       }
-      for (int j = 0; j < n; ++j) s[(j / cxl) * kRS + j % cxl] = r[j];
     } else if (v.code == kDCT4) {
       const float c00 = s[0], c01 = s[1], c10 = s[kRS], c11 = s[kRS + 1];
       s[0] = c00 + c01 + c10 + c11;
@@ -886,17 +907,15 @@ __device__ __forceinline__ void recon_cell(const ReconArgs& a, int cxi, int cyi)
     for (int vi = 0; vi < cs.nvb; ++vi) {
       const CellVB v = cs.vb[vi];
       if (!tc_shape(v.code)) continue;
-      const int W = c_shape_w[v.code], H = c_shape_h[v.code];
+      const int W = 1 << v.lw, H = 1 << v.lh;
       const int x0 = 8 * v.bx, y0 = 8 * v.by;
-      const int bw_idx = W == 8 ? 0 : W == 16 ? 1 : 2;
-      const int bh_idx = H == 8 ? 0 : H == 16 ? 1 : 2;
-      const int boff[3] = {0, 1024, 2048};
       // rows: S -> T
-      tc_pass(ts, phase, a.err, 3 * H, H, W, a.tcb + boff[bw_idx], &S[0][y0][x0], &T[0][y0][x0],
-              32 * kRS, kRS, 1);
+      // basis tables at byte offsets 0, 1024, 2048 for N = 8, 16, 32
+      tc_pass(ts, phase, a.err, 3 * H, H, W, a.tcb + 1024 * (v.lw - 3), &S[0][y0][x0],
+              &T[0][y0][x0], 32 * kRS, kRS, 1);
       // columns: T -> S
-      tc_pass(ts, phase, a.err, 3 * W, W, H, a.tcb + boff[bh_idx], &T[0][y0][x0], &S[0][y0][x0],
-              32 * kRS, 1, kRS);
+      tc_pass(ts, phase, a.err, 3 * W, W, H, a.tcb + 1024 * (v.lh - 3), &T[0][y0][x0],
+              &S[0][y0][x0], 32 * kRS, 1, kRS);
     }
   }
 
