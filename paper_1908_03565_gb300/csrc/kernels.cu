@@ -300,6 +300,9 @@ void launch_validate(const uint8_t* vmap, int bw, int bh, unsigned* status, cuda
 // ---------------------------------------------------------------------------
 constexpr int kRS = 36;  // shared row stride in floats: 16-byte rows, no bank
                          // conflicts for row-per-thread float4 access
+constexpr int kPR = 34;  // rows per channel plane (32 + 2 padding): the plane
+                         // stride is 8 banks, so the three channels of a column
+                         // group hit different banks in the column pass
 
 struct CellVB {
   int code, bx, by;      // code and top-left block inside the cell (0..3)
@@ -334,7 +337,7 @@ __device__ __forceinline__ int row_items(int code) {
 __device__ __forceinline__ int col_items(int code) { return 3 * (8 << lg_w8(code)); }
 
 // Row pass of one item.  S: coefficients, T: output of the pass.
-__device__ void row_item(float (*S)[32][kRS], float (*T)[32][kRS], const CellVB& v, int k) {
+__device__ void row_item(float (*S)[kPR][kRS], float (*T)[kPR][kRS], const CellVB& v, int k) {
   const int code = v.code;
   const int x0 = 8 * v.bx, y0 = 8 * v.by;
   if (code == kDCT2) {
@@ -432,7 +435,7 @@ __device__ void row_item(float (*S)[32][kRS], float (*T)[32][kRS], const CellVB&
 }
 
 // Column pass of one item: T -> S.
-__device__ void col_item(float (*S)[32][kRS], float (*T)[32][kRS], const CellVB& v, int k) {
+__device__ void col_item(float (*S)[kPR][kRS], float (*T)[kPR][kRS], const CellVB& v, int k) {
   const int code = v.code;
   const int c = k >> v.lw, col = k & ((1 << v.lw) - 1);
   const int x0 = 8 * v.bx, y0 = 8 * v.by;
@@ -452,7 +455,7 @@ __device__ void col_item(float (*S)[32][kRS], float (*T)[32][kRS], const CellVB&
 
 // J.2.4 per-block sigma for the 16 blocks of the cell held in S (channel
 // planes, 32 x 32).  Requires cs.owner and cs.vb; 128 threads.
-__device__ void cell_sigma(float (*S)[32][kRS], CellState& cs, const SigmaParams& sp,
+__device__ void cell_sigma(float (*S)[kPR][kRS], CellState& cs, const SigmaParams& sp,
                            int gbx0, int gby0, int xs, int ys, int bw, int bh,
                            const float* __restrict__ acmul, const uint8_t* __restrict__ sharp,
                            int16_t* __restrict__ sigma) {
@@ -741,8 +744,8 @@ __device__ void tc_pass(TcShared& ts, uint32_t& phase, unsigned* err, int nrows,
 // launches only).
 template <bool kTC = false, bool kDc = true>
 __device__ __forceinline__ void recon_cell(const ReconArgs& a, int cxi, int cyi) {
-  __shared__ __align__(16) float S[3][32][kRS];
-  __shared__ __align__(16) float T[3][32][kRS];
+  __shared__ __align__(16) float S[3][kPR][kRS];
+  __shared__ __align__(16) float T[3][kPR][kRS];
   __shared__ CellState cs;
   const int tid = threadIdx.x;
   const int gbx0 = cxi * 4, gby0 = cyi * 4;
@@ -912,10 +915,10 @@ __device__ __forceinline__ void recon_cell(const ReconArgs& a, int cxi, int cyi)
       // rows: S -> T
       // basis tables at byte offsets 0, 1024, 2048 for N = 8, 16, 32
       tc_pass(ts, phase, a.err, 3 * H, H, W, a.tcb + 1024 * (v.lw - 3), &S[0][y0][x0],
-              &T[0][y0][x0], 32 * kRS, kRS, 1);
+              &T[0][y0][x0], kPR * kRS, kRS, 1);
       // columns: T -> S
       tc_pass(ts, phase, a.err, 3 * W, W, H, a.tcb + 1024 * (v.lh - 3), &T[0][y0][x0],
-              &S[0][y0][x0], 32 * kRS, 1, kRS);
+              &S[0][y0][x0], kPR * kRS, 1, kRS);
     }
   }
 
@@ -1027,7 +1030,7 @@ void launch_recon_batch(const ReconArgs* args, const int* prefix, int nimg, int 
 // k_sigma: J.2.4 sigma from caller-supplied XYB
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(128) k_sigma(const SigmaArgs a) {
-  __shared__ __align__(16) float S[3][32][kRS];
+  __shared__ __align__(16) float S[3][kPR][kRS];
   __shared__ CellState cs;
   const int tid = threadIdx.x;
   const int gbx0 = blockIdx.x * 4, gby0 = blockIdx.y * 4;
