@@ -58,6 +58,8 @@ class Params:
         self.target_nits_div50 = T.TARGET_NITS_DIV50
         self.dc_smooth = False        # F.2 adaptive DC smoothing
         self.lf_predict = False       # Annex H AC prediction
+        self.qco = False              # J.3 quantization constraint (with EPF)
+        self.qco_interval_mul = T.QCO_INTERVAL_MUL
         for k, v in kw.items():
             if not hasattr(self, k):
                 raise KeyError(k)
@@ -548,6 +550,65 @@ def epf(img, vmap, acmul, sharpness, params, region=None):
 
 
 # ---------------------------------------------------------------------------
+# J.3 quantization constraint
+# ---------------------------------------------------------------------------
+_FORWARD_8X8 = {T.DCT2: TR.dct_dct2, T.DCT4: TR.dct_dct4, T.IDENTITY: TR.dct_identity,
+                T.DCT8X4: TR.dct_dct8x4, T.DCT4X8: TR.dct_dct4x8, T.AFV: TR.dct_afv}
+
+
+def forward_transform(code, samples):
+    """I.2.3: the coefficients whose I.2.4 reconstruction is ``samples``
+    (the DCT shapes: the 2-D DCT divided by the sample count, the exact
+    inverse of the IDCT's orthogonal cosine sums)."""
+    if code in _DCT_SHAPES:
+        H, W = samples.shape
+        return TR.dct_2d(samples) / (H * W)
+    return _FORWARD_8X8[code](samples)
+
+
+def inverse_any(code, coef):
+    """I.2.4 for one varblock of any shape."""
+    return TR.idct_2d(coef) if code in _DCT_SHAPES else TR.idct_8x8_class(code, coef)
+
+
+def qco(filtered, original, vmap, acmul, params):
+    """J.3 on the EPF output ``filtered`` (3, ys, xs) with the EPF input
+    ``original`` (padded, 3 x Hp x Wp): per varblock and channel, the DCT of
+    the filter residual (I.2.3), its LLF turned into DC samples (I.2.6), each
+    value clamped to +-qco_interval_mul x interval, DC back to LLF (I.2.7),
+    the inverse transform (I.2.4) added to the EPF input.  READINGS: the
+    interval of an HF coefficient is the dequantisation step of F.3, AcMul x
+    the C.6.1 matrix entry (the text divides by AcMul while F.3 multiplies);
+    that of a DC sample is m_DC (DcQuantField without extra levels); samples
+    of a varblock outside the cropped image have zero residual.  Returns the
+    cropped result."""
+    _, ys, xs = filtered.shape
+    _, Hp, Wp = original.shape
+    res = np.zeros((3, Hp, Wp))
+    res[:, :ys, :xs] = filtered - original[:, :ys, :xs]
+    out = original.copy()
+    mul = params.qco_interval_mul
+    for code, bx, by in varblocks(vmap):
+        W, H = T.SHAPE_WH[code]
+        cx, cy = W // 8, H // 8
+        sl = (slice(8 * by, 8 * by + H), slice(8 * bx, 8 * bx + W))
+        am = float(acmul[by, bx])
+        for c in range(3):
+            coef = forward_transform(code, res[c][sl])
+            lim = mul * am * T.dequant_matrix(code, c)
+            clamped = np.clip(coef, -lim, lim)
+            if code in _DCT_SHAPES:
+                dc = (TR.box_mean_map(W, H) @ coef[:cy, :cx].reshape(-1)).reshape(cy, cx)
+            else:
+                dc = coef[:1, :1].copy()
+            t = mul * params.m_dc[c]
+            dc = np.clip(dc, -t, t)
+            clamped[:cy, :cx] = TR.llf_from_dc(dc) if code in _DCT_SHAPES else dc
+            out[c][sl] = original[c][sl] + inverse_any(code, clamped)
+    return out[:, :ys, :xs]
+
+
+# ---------------------------------------------------------------------------
 # J.4 Gaborish
 # ---------------------------------------------------------------------------
 def gaborish(img, params, region=None):
@@ -603,6 +664,8 @@ def reconstruct(inp, params, diag=None):
     img = xyb[:, :ys, :xs]
     if params.epf:
         img = epf(img, inp['vmap'], inp['acmul'], inp['sharpness'], params)
+        if params.qco:
+            img = qco(img, xyb, inp['vmap'], inp['acmul'], params)
     if params.gab:
         img = gaborish(img, params)
     return {'xyb_padded': xyb, 'xyb': img, 'rgb01': xyb_to_linear01(img, params)}

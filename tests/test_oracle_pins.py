@@ -533,3 +533,75 @@ def test_ac_prediction_ring_reads_only_the_border_dc():
     near[:, ::8, 8 * 32] += 5                 # DC of the ring column (block 32)
     other = R.dequantize(near, im['vmap'], im['acmul'], im['cfl'], p)
     assert np.abs(other[:, :, 248:256] - base[:, :, 248:256]).max() > 0
+
+
+# --------------------------------------------------------------------------
+# J.3 quantization constraint
+# --------------------------------------------------------------------------
+def _qco_case(mix, seed=3, xs=72, ys=56):
+    im = synth.make_image(xs, ys, seed, mix=mix)
+    p = R.Params()
+    orig = R.reconstruct_xyb(im['coeffs'], im['vmap'], im['acmul'], im['cfl'], p)
+    rng = np.random.default_rng(seed + 1)
+    filt = orig[:, :ys, :xs] + rng.normal(0, 0.02, size=(3, ys, xs)) * \
+        np.abs(orig[:, :ys, :xs]).mean(axis=(1, 2), keepdims=True)
+    return im, orig, filt
+
+
+@pytest.mark.parametrize('code', range(15))
+def test_forward_transform_inverts_every_shape(code):
+    """I.2.3 against I.2.4: the forward transform of every shape is the exact
+    inverse of its reconstruction procedure."""
+    W, H = T.SHAPE_WH[code]
+    x = np.random.default_rng(code).normal(size=(H, W))
+    np.testing.assert_allclose(R.inverse_any(code, R.forward_transform(code, x)), x, atol=1e-12)
+
+
+@pytest.mark.parametrize('mix', ['mixed', 1, 2, 3, 12, 13, 14])
+def test_qco_limits_and_invariants(mix):
+    """J.3: with an unbounded interval the filter output passes unchanged;
+    with a zero interval the filter input comes back; the output residual's
+    coefficients lie inside the intervals (DC samples within the DC
+    interval); applying the constraint twice changes nothing."""
+    im, orig, filt = _qco_case(mix)
+    ys, xs = filt.shape[1:]
+    big = R.Params(qco_interval_mul=1e12)
+    np.testing.assert_allclose(R.qco(filt, orig, im['vmap'], im['acmul'], big), filt, atol=1e-9)
+    zero = R.Params(qco_interval_mul=0.0)
+    np.testing.assert_allclose(R.qco(filt, orig, im['vmap'], im['acmul'], zero),
+                               orig[:, :ys, :xs], atol=1e-12)
+    p = R.Params()
+    out = R.qco(filt, orig, im['vmap'], im['acmul'], p)
+    assert np.abs(out - filt).max() > 1e-6          # something was clamped
+    np.testing.assert_allclose(R.qco(out, orig, im['vmap'], im['acmul'], p), out, atol=1e-10)
+    res = np.zeros_like(orig)
+    res[:, :ys, :xs] = out - orig[:, :ys, :xs]
+    for code, bx, by in R.varblocks(im['vmap']):
+        W, H = T.SHAPE_WH[code]
+        cx, cy = W // 8, H // 8
+        for c in range(3):
+            coef = R.forward_transform(code, res[c, 8 * by:8 * by + H, 8 * bx:8 * bx + W])
+            lim = 0.5 * im['acmul'][by, bx] * T.dequant_matrix(code, c)
+            hf = np.ones((H, W), bool)
+            hf[:cy, :cx] = False
+            assert np.all(np.abs(coef[hf]) <= lim[hf] * (1 + 1e-9) + 1e-12)
+            if code in R._DCT_SHAPES:
+                dc = TR.box_mean_map(W, H) @ coef[:cy, :cx].reshape(-1)
+            else:
+                dc = coef[:1, :1].reshape(-1)
+            assert np.all(np.abs(dc) <= 0.5 * p.m_dc[c] * (1 + 1e-9) + 1e-15)
+
+
+def test_qco_dc_interval_is_the_block_mean():
+    """A residual that is constant over an 8x8 DCT8 block is pure DC: it is
+    clamped to +-mul x m_DC of the channel, whatever its AC intervals."""
+    im = synth.make_image(16, 16, 1, mix='dct8', acmul=1.0)
+    p = R.Params()
+    orig = np.zeros((3, 16, 16))
+    filt = np.zeros((3, 16, 16))
+    filt[:, :8, :8] = 1.0
+    out = R.qco(filt, orig, im['vmap'], im['acmul'], p)
+    for c in range(3):
+        np.testing.assert_allclose(out[c, :8, :8], 0.5 * p.m_dc[c], rtol=1e-9)
+    np.testing.assert_allclose(out[:, 8:, :], 0.0, atol=1e-15)
+    np.testing.assert_allclose(out[:, :, 8:], 0.0, atol=1e-15)
