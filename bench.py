@@ -263,12 +263,12 @@ def precision_leg(binding, torch, steps, sample=1024):
     return res
 
 
-def dc_lf_leg(binding, torch, steps):
-    """Cost of the DC-domain steps (F.2 adaptive DC smoothing, Annex H AC
-    prediction) on a 4096x4096 image with a smooth DC field: the same step
-    (EPF + Gaborish, f32 out) without them, with F.2, and with F.2 + H.
-    CUDA events over the timed steps; the recon stage includes the DC-domain
-    kernels."""
+def extra_steps_leg(binding, torch, steps):
+    """Cost of the optional steps on a 4096x4096 image with a smooth DC
+    field: the same step (EPF + Gaborish, f32 out) plain, with F.2 adaptive
+    DC smoothing, with F.2 + Annex H AC prediction, and with the J.3
+    quantization constraint.  CUDA events over the timed steps; the recon
+    stage includes the DC-domain kernels, the filter stage the J.3 chain."""
     from paper_1908_03565_gb300 import synth
     img = synth.make_image(XS, YS, SEED + 5, dc='smooth')
     dimg = binding.to_device(img, torch)
@@ -277,8 +277,9 @@ def dc_lf_leg(binding, torch, steps):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     res = {}
     with binding.Context(stream=stream.cuda_stream, timing=True) as ctx:
-        for name, sm, lf in (("plain", 0, 0), ("dc_smooth", 1, 0), ("dc_smooth+lf_predict", 1, 1)):
-            p = binding.filter_defaults(epf=1, gab=1, dc_smooth=sm, lf_predict=lf)
+        for name, sm, lf, qc in (("plain", 0, 0, 0), ("dc_smooth", 1, 0, 0),
+                                 ("dc_smooth+lf_predict", 1, 1, 0), ("qco", 0, 0, 1)):
+            p = binding.filter_defaults(epf=1, gab=1, dc_smooth=sm, lf_predict=lf, qco=qc)
             for _ in range(3):
                 ctx.poll(ctx.submit(dimg, p, out, binding.OUT_F32_LINEAR, on_device=True))
             stream.synchronize()
@@ -294,6 +295,7 @@ def dc_lf_leg(binding, torch, steps):
             ms = e0.elapsed_time(e1) / steps
             res[name] = {"ms_per_step": round(ms, 4),
                          "recon_stage_ms": round(float(np.mean([ctx.stage_ms(t)[1] for t in tickets])), 4),
+                         "filter_stage_ms": round(float(np.mean([ctx.stage_ms(t)[2] for t in tickets])), 4),
                          "mpx_s": round(XS * YS / ms / 1e3, 1),
                          "launches_per_step": (ctx.launch_count() - l0) / steps}
     res["input"] = f"{XS}x{YS} mixed varblocks, smooth DC field (synth dc='smooth')"
@@ -352,8 +354,8 @@ def main():
                     help="timed steps of the FP32 vs tensor-core comparison (0 = skip)")
     ap.add_argument("--batch-images", type=int, default=512,
                     help="images in the multi-image batch leg (0 = skip)")
-    ap.add_argument("--dclf-steps", type=int, default=20,
-                    help="timed steps of the DC smoothing / AC prediction leg (0 = skip)")
+    ap.add_argument("--extra-steps", type=int, default=20,
+                    help="timed steps of the optional-steps leg: F.2, Annex H, J.3 (0 = skip)")
     ap.add_argument("--serve-loads", default="0.5,0.9",
                     help="offered loads as fractions of the measured capacity")
     args = ap.parse_args()
@@ -473,8 +475,8 @@ def main():
     if rank == 0 and args.precision_steps > 0:
         precision = precision_leg(binding, torch, args.precision_steps)
     dclf = None
-    if rank == 0 and args.dclf_steps > 0:
-        dclf = dc_lf_leg(binding, torch, args.dclf_steps)
+    if rank == 0 and args.extra_steps > 0:
+        dclf = extra_steps_leg(binding, torch, args.extra_steps)
     batched = None
     if rank == 0 and args.batch_images > 0:
         batched = batch_leg(binding, torch, args.batch_images)
@@ -504,7 +506,7 @@ def main():
                          "recon_gbs": round(recon_gbs, 1)},
             "peaks": peak_kind,
             "clocks": clocks, "e2e": e2e, "gpu_launches": int(launches),
-            "cpu_baseline": cb, "precision": precision, "dc_lf": dclf, "batched": batched, "served": served,
+            "cpu_baseline": cb, "precision": precision, "extra_steps": dclf, "batched": batched, "served": served,
         }
         print(json.dumps(line), flush=True)
     ctx.close()

@@ -142,6 +142,11 @@ typedef struct {
   /* Annex H AC prediction from the DC2x2 image of each 256 x 256 group:
    * 1 applies it, 0 skips it (the effect of kSkipPredictLf). */
   int lf_predict;
+  /* J.3 quantization constraint after the EPF (only with epf != 0): 1
+   * applies it, clamping each coefficient of the filter residual to
+   * +-qco_interval_mul times its interval (C.10: default 0.5). */
+  int qco;
+  float qco_interval_mul;
 } jxl_recon_filter_params;
 
 /* Caller-owned output buffer of ysize rows, row_stride_bytes apart. */
@@ -155,7 +160,7 @@ typedef struct {
 
 /* Fills *p with the defaults of C.10, C.4.1 (m_DC of the synthetic
  * workloads: (0.02, 0.2, 0.2) / (64 sqrt 2)) and L.2; both filters, DC
- * smoothing and AC prediction off. */
+ * smoothing, AC prediction and the quantization constraint off. */
 void jxl_recon_filter_defaults(jxl_recon_filter_params* p);
 
 /* Creates a context on config->device: builds the constant tables (C.6.1

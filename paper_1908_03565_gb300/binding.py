@@ -54,7 +54,8 @@ class FilterParams(ctypes.Structure):
                 ("m_dc", ctypes.c_float * 3), ("inv_opsin", ctypes.c_float * 9),
                 ("opsin_bias", ctypes.c_float * 3), ("target_nits_div50", ctypes.c_uint32),
                 ("dequant", ctypes.c_void_p), ("dc_smooth", ctypes.c_int),
-                ("lf_predict", ctypes.c_int)]
+                ("lf_predict", ctypes.c_int), ("qco", ctypes.c_int),
+                ("qco_interval_mul", ctypes.c_float)]
 
 
 class Output(ctypes.Structure):

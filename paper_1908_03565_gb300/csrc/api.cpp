@@ -124,6 +124,8 @@ void jxl_recon_filter_defaults(jxl_recon_filter_params* p) {
   p->opsin_bias[2] = -0.00094081f;
   p->target_nits_div50 = 5;
   p->dequant = nullptr;
+  p->qco = 0;
+  p->qco_interval_mul = 0.5f;
 }
 
 const char* jxl_recon_last_error(const jxl_recon_ctx*) { return g_err.c_str(); }
@@ -146,14 +148,15 @@ jxlr_status jxl_recon_create(const jxl_recon_config* cfg, jxl_recon_ctx** out) {
   std::vector<float> raw(kDequantFloats), scaled(kDequantFloats);
   if (!default_dequant(raw.data())) return fail(JXLR_EINVAL, "default dequant matrices ill-formed");
   prescale_dequant(raw.data(), scaled.data());
-  std::vector<float> llf(kLlfMaps * 256), odd(kOddFloats), afv(256);
+  std::vector<float> llf(kLlfMaps * 256), box(kLlfMaps * 256), odd(kOddFloats), afv(256);
   std::vector<int32_t> mul4(673);
   llf_maps(llf.data());
+  llf_box_maps(box.data());
   odd_tables(odd.data());
   mul_table4(mul4.data());
   for (int j = 0; j < 16; ++j)
     for (int i = 0; i < 16; ++i) afv[j * 16 + i] = static_cast<float>(kAfvBasis[j][i]);
-  if (!upload_constants(llf.data(), odd.data(), mul4.data(), afv.data()))
+  if (!upload_constants(llf.data(), box.data(), odd.data(), mul4.data(), afv.data()))
     return fail(JXLR_ECUDA, "create: constant upload failed");
   std::vector<float> lf_up(kLfUpFloats), lf_inv(kLfInvFloats);
   float lf_half = 0.f;
@@ -323,6 +326,41 @@ jxlr_status finish_submit(jxl_recon_ctx* ctx, Slot* slot, unsigned* d_status, ui
 
 }  // namespace
 
+// J.2 into eo, J.3 in place on eo, then J.4 / L.2 from eo (three launches).
+// fa: the filter arguments of the plain path (EPF on); orig = fa.xyb.
+static void launch_qco_chain(const FilterArgs& fa, float* eo, const uint8_t* vmap,
+                             const float* acmul, const float* dequant, int bh,
+                             const jxl_recon_filter_params& fp, cudaStream_t s) {
+  const size_t wp = static_cast<size_t>(fa.bw) * 8, hp = static_cast<size_t>(bh) * 8;
+  FilterArgs e = fa;
+  e.epf_out = eo;
+  e.ors = wp;
+  e.ops = wp * hp;
+  launch_filter(e, s);
+  QcoArgs q;
+  std::memset(&q, 0, sizeof(q));
+  q.orig = fa.xyb;
+  q.ors = fa.rstride;
+  q.ops = fa.pstride;
+  q.f = eo;
+  q.frs = wp;
+  q.fps = wp * hp;
+  q.vmap = vmap;
+  q.acmul = acmul;
+  q.dequant = dequant;
+  q.xs = fa.xs; q.ys = fa.ys; q.bw = fa.bw; q.bh = bh;
+  for (int c = 0; c < 3; ++c) q.m_dc[c] = fp.m_dc[c];
+  q.mul = fp.qco_interval_mul;
+  launch_qco(q, s);
+  FilterArgs g = fa;
+  g.epf = 0;
+  g.sigma = nullptr;
+  g.xyb = eo;
+  g.rstride = wp;
+  g.pstride = wp * hp;
+  launch_filter(g, s);
+}
+
 extern "C" jxlr_status jxl_recon_submit(jxl_recon_ctx* ctx, const jxl_recon_coeffs* co,
                                         const uint8_t* vmap, const float* qf,
                                         const jxl_recon_cfl* cfl,
@@ -387,6 +425,8 @@ extern "C" jxlr_status jxl_recon_submit(jxl_recon_ctx* ctx, const jxl_recon_coef
     add(sizeof(float) * 12 * nblk);                   // DC2x2 image
     add(sizeof(float) * 12 * nblk);                   // predicted coefficients
   }
+  const bool qco = fp->epf && fp->qco;
+  if (qco) add(sizeof(float) * 3 * wp * hp);         // EPF output for J.3
   const size_t out_bytes = out->row_stride_bytes * (ys - 1) + px_bytes * xs;
   if (!out->on_device) add(out_bytes);
   need = align_up(need, 256);
@@ -520,8 +560,14 @@ extern "C" jxlr_status jxl_recon_submit(jxl_recon_ctx* ctx, const jxl_recon_coef
     fa.xs = xs; fa.ys = ys; fa.bw = bw;
     fa.sigma = sig;
     fa.out = op;
-    launch_filter(fa, s);
-    ctx->launches++;
+    if (qco) {
+      float* eo = cv.take<float>(static_cast<size_t>(3) * wp * hp);
+      launch_qco_chain(fa, eo, ra.vmap, ra.acmul, ra.dequant, bh, *fp, s);
+      ctx->launches += 3;
+    } else {
+      launch_filter(fa, s);
+      ctx->launches++;
+    }
   } else {
     ra.write_xyb = 0;
     ra.out = op;
@@ -553,7 +599,11 @@ extern "C" jxlr_status jxl_recon_submit_xyb(jxl_recon_ctx* ctx, const float* xyb
   if (out->dtype < 0 || out->dtype > 3 || !out->data || !out->on_device)
     return fail(JXLR_EINVAL, "submit_xyb: output must be a device buffer");
   const int bw = (xs + 7) / 8, bh = (ys + 7) / 8;
+  const bool qco = fp->epf && fp->qco;
+  if (qco && fp->dequant)
+    return fail(JXLR_EINVAL, "submit_xyb: the quantization constraint uses the default matrices here");
   size_t need = 256 + (fp->epf ? align_up(sizeof(int16_t) * bw * bh, 256) : 0);
+  if (qco) need += align_up(sizeof(float) * 3 * 64 * static_cast<size_t>(bw) * bh, 256);
   std::lock_guard<std::mutex> lock(ctx->mu);
   CK(cudaSetDevice(ctx->device));
   Slot* slot = nullptr;
@@ -598,8 +648,14 @@ extern "C" jxlr_status jxl_recon_submit_xyb(jxl_recon_ctx* ctx, const float* xyb
   fa.out.data = out->data;
   fa.out.stride = out->row_stride_bytes;
   fa.out.dtype = out->dtype;
-  launch_filter(fa, s);
-  ctx->launches++;
+  if (qco) {
+    float* eo = cv.take<float>(static_cast<size_t>(3) * 64 * bw * bh);
+    launch_qco_chain(fa, eo, vmap, qf, ctx->d_dequant, bh, *fp, s);
+    ctx->launches += 3;
+  } else {
+    launch_filter(fa, s);
+    ctx->launches++;
+  }
   mark(slot, 4);
   slot->check_status = fp->epf != 0;
   return finish_submit(ctx, slot, d_status, ticket);

@@ -46,6 +46,9 @@ bool dequant_valid(const float* table);
 constexpr int kLlfMaps = 8;
 int llf_map_index(int cx, int cy);
 void llf_maps(float* out /* kLlfMaps * 256 */);
+// The maps those invert (I.2.6 at N = 8 on the unscaled cosine basis):
+// dc[i] = sum_j B[i][j] llf[j], B[i][j] at i * 16 + j, same index.
+void llf_box_maps(float* out /* kLlfMaps * 256 */);
 
 // Odd-part matrices of the unscaled N-point inverse DCT for N = 2..32:
 // O_N[n][j] = cos((2n+1)(2j+1) pi / 2N), n, j < N/2, packed N = 32, 16, 8, 4, 2.
@@ -97,8 +100,8 @@ void set_last_error(const std::string& msg);
 
 // Device-side constant setup (kernels.cu): copies the tables above into
 // __constant__ memory of the current device.
-bool upload_constants(const float* llf, const float* odd, const int32_t* mul4,
-                      const float* afv);
+bool upload_constants(const float* llf, const float* box, const float* odd,
+                      const int32_t* mul4, const float* afv);
 // The same for the Annex H kernels (lf.cu).
 bool upload_lf_constants(const float* up, const float* inv, float half);
 

@@ -31,6 +31,7 @@
 namespace jxlr {
 
 __constant__ float c_llf[kLlfMaps * 256];
+__constant__ float c_box[kLlfMaps * 256];
 __constant__ float c_odd[kOddFloats];
 __constant__ int32_t c_mul4[673];
 __constant__ float c_afv[256];
@@ -52,8 +53,8 @@ __device__ __forceinline__ int lg_h8(int code) { return (kH8Bits >> (2 * code)) 
 
 static void prefer_shared_carveout();
 
-bool upload_constants(const float* llf, const float* odd, const int32_t* mul4,
-                      const float* afv) {
+bool upload_constants(const float* llf, const float* box, const float* odd,
+                      const int32_t* mul4, const float* afv) {
   for (int c = 0; c < kNumCodes; ++c)   // the packed shape bits agree with the shape table
     if ((8 << ((kW8Bits >> (2 * c)) & 3)) != kShapeW[c] || (8 << ((kH8Bits >> (2 * c)) & 3)) != kShapeH[c])
       return false;
@@ -61,6 +62,7 @@ bool upload_constants(const float* llf, const float* odd, const int32_t* mul4,
   int offs[kNumCodes];
   for (int c = 0; c < kNumCodes; ++c) offs[c] = dequant_offset(c, 0);
   return cudaMemcpyToSymbol(c_llf, llf, sizeof(float) * kLlfMaps * 256) == cudaSuccess &&
+         cudaMemcpyToSymbol(c_box, box, sizeof(float) * kLlfMaps * 256) == cudaSuccess &&
          cudaMemcpyToSymbol(c_odd, odd, sizeof(float) * kOddFloats) == cudaSuccess &&
          cudaMemcpyToSymbol(c_mul4, mul4, sizeof(int32_t) * 673) == cudaSuccess &&
          cudaMemcpyToSymbol(c_afv, afv, sizeof(float) * 256) == cudaSuccess &&
@@ -447,6 +449,197 @@ __device__ void col_item(float (*S)[kPR][kRS], float (*T)[kPR][kRS], const CellV
     case kDCT32: case kDCT32x8: case kDCT32x16: col_idct<32>(src, dst, kRS); break;
     case kDCT4: case kDCT4x8: pair4(src, kRS, dst, kRS); break;
     default:  // Identity, DCT2, AFV: the row pass already produced samples
+#pragma unroll
+      for (int i = 0; i < 8; ++i) dst[i * kRS] = src[i * kRS];
+      break;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// I.2.3 forward transforms in the kernels' coefficient convention: for the
+// unscaled inverse x_n = sum_k c_k cos((2n+1) k pi / 2N), the forward is
+// c_0 = (1/N) sum_n x_n and c_k = (2/N) sum_n x_n cos((2n+1) k pi / 2N); the
+// raw sums A^T x come from the transpose of the even/odd recursion.
+// ---------------------------------------------------------------------------
+template <int N>
+__device__ __forceinline__ void fdct1d_raw(float (&x)[N]) {
+  if constexpr (N > 1) {
+    constexpr int H = N / 2;
+    float e[H], d[H];
+#pragma unroll
+    for (int n = 0; n < H; ++n) {
+      e[n] = x[n] + x[N - 1 - n];
+      d[n] = x[n] - x[N - 1 - n];
+    }
+    fdct1d_raw<H>(e);
+#pragma unroll
+    for (int j = 0; j < H; ++j) {
+      float acc = 0.f;
+#pragma unroll
+      for (int n = 0; n < H; ++n) acc = fmaf(d[n], c_odd[OddOff<N>::v + n * H + j], acc);
+      x[2 * j + 1] = acc;
+    }
+#pragma unroll
+    for (int j = 0; j < H; ++j) x[2 * j] = e[j];
+  }
+}
+
+template <int N>
+__device__ __forceinline__ void fdct1d(float (&x)[N]) {
+  fdct1d_raw<N>(x);
+  x[0] *= 1.f / N;
+#pragma unroll
+  for (int k = 1; k < N; ++k) x[k] *= 2.f / N;
+}
+
+template <int N>
+__device__ __forceinline__ void row_fdct(const float* src, float* dst) {
+  float x[N];
+#pragma unroll
+  for (int i = 0; i < N; i += 4) {
+    float4 v = *reinterpret_cast<const float4*>(src + i);
+    x[i] = v.x; x[i + 1] = v.y; x[i + 2] = v.z; x[i + 3] = v.w;
+  }
+  fdct1d<N>(x);
+#pragma unroll
+  for (int i = 0; i < N; i += 4)
+    *reinterpret_cast<float4*>(dst + i) = make_float4(x[i], x[i + 1], x[i + 2], x[i + 3]);
+}
+
+template <int N>
+__device__ __forceinline__ void col_fdct(const float* src, float* dst, int stride) {
+  float x[N];
+#pragma unroll
+  for (int i = 0; i < N; ++i) x[i] = src[i * stride];
+  fdct1d<N>(x);
+#pragma unroll
+  for (int i = 0; i < N; ++i) dst[i * stride] = x[i];
+}
+
+// Forward of pair4: samples 0..3 -> even entries, samples 4..7 -> odd entries.
+__device__ __forceinline__ void fpair4(const float* src, int sstride, float* dst, int dstride) {
+  float a[4], b[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    a[i] = src[i * sstride];
+    b[i] = src[(4 + i) * sstride];
+  }
+  fdct1d<4>(a);
+  fdct1d<4>(b);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    dst[(2 * i) * dstride] = a[i];
+    dst[(2 * i + 1) * dstride] = b[i];
+  }
+}
+
+// AuxDCT2x2 of I.2.3.2 on the top-left 2h x 2h of src (row stride kRS),
+// the exact inverse of one AuxIDCT2x2 level.
+__device__ __forceinline__ void aux_fwd(const float* src, float* dst, int h) {
+  for (int y = 0; y < h; ++y)
+    for (int x = 0; x < h; ++x) {
+      const float o00 = src[(2 * y) * kRS + 2 * x], o01 = src[(2 * y) * kRS + 2 * x + 1];
+      const float o10 = src[(2 * y + 1) * kRS + 2 * x], o11 = src[(2 * y + 1) * kRS + 2 * x + 1];
+      dst[y * kRS + x] = 0.25f * ((o00 + o01) + (o10 + o11));
+      dst[y * kRS + h + x] = 0.25f * ((o00 + o01) - (o10 + o11));
+      dst[(y + h) * kRS + x] = 0.25f * ((o00 - o01) + (o10 - o11));
+      dst[(y + h) * kRS + h + x] = 0.25f * ((o00 - o01) - (o10 - o11));
+    }
+}
+
+// Forward row pass of one item: S (samples) -> T.  Items as in row_item.
+// AFV leaves each quadrant's DC term at its corner position and Identity
+// writes its AuxDCT2x2 corner; the corner steps of DCT4 / 8x4 / 4x8 / AFV
+// follow the column pass (qco_corner_in).
+__device__ void fwd_row_item(float (*S)[kPR][kRS], float (*T)[kPR][kRS], const CellVB& v, int k) {
+  const int code = v.code;
+  const int x0 = 8 * v.bx, y0 = 8 * v.by;
+  if (code == kDCT2) {
+    // levels S = 8, 4, 2; the inverse of row_item's three AuxIDCT2x2 levels
+    const int c = k;
+    float* s = &S[c][y0][x0];
+    float* t = &T[c][y0][x0];
+    aux_fwd(s, t, 4);                     // 8x8: S -> T
+    aux_fwd(t, s, 2);                     // top-left 4x4: T -> S
+    aux_fwd(s, t, 1);                     // top-left 2x2: S -> T
+    for (int y = 0; y < 4; ++y)           // rest of the 4x4 from S
+      for (int x = 0; x < 4; ++x)
+        if (y >= 2 || x >= 2) t[y * kRS + x] = s[y * kRS + x];
+    return;
+  }
+  if (code == kIdentity) {
+    const int c = k;
+    const float* s = &S[c][y0][x0];
+    float* t = &T[c][y0][x0];
+    float dcs[2][2];
+    for (int y = 0; y < 2; ++y)
+      for (int x = 0; x < 2; ++x) {
+        const float* p = s + (4 * y) * kRS + 4 * x;
+        const float s11 = p[kRS + 1];
+        float sum = 0.f;
+        for (int iy = 0; iy < 4; ++iy)
+          for (int ix = 0; ix < 4; ++ix) {
+            const float pv = p[iy * kRS + ix];
+            sum += pv;
+            if ((ix == 0 && iy == 0) || (ix == 1 && iy == 1)) continue;
+            t[(y + 2 * iy) * kRS + x + 2 * ix] = pv - s11;
+          }
+        t[(y + 2) * kRS + x + 2] = p[0] - s11;
+        dcs[y][x] = sum * (1.f / 16.f);
+      }
+    const float o00 = dcs[0][0], o01 = dcs[0][1], o10 = dcs[1][0], o11 = dcs[1][1];
+    t[0] = 0.25f * ((o00 + o01) + (o10 + o11));
+    t[1] = 0.25f * ((o00 + o01) - (o10 + o11));
+    t[kRS] = 0.25f * ((o00 - o01) + (o10 - o11));
+    t[kRS + 1] = 0.25f * ((o00 - o01) - (o10 - o11));
+    return;
+  }
+  if (code == kAFV) {
+    const int c = k / 4, q = k % 4, qx = q & 1, qy = q >> 1;
+    const float* s = &S[c][y0][x0];
+    float* t = &T[c][y0][x0];
+    float smp[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      const int sx = i & 3, sy = i >> 2;
+      const int ix = qx ? 3 - sx : sx, iy = qy ? 3 - sy : sy;
+      smp[i] = s[(4 * qy + iy) * kRS + 4 * qx + ix];
+    }
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      float acc = 0.f;
+#pragma unroll
+      for (int i = 0; i < 16; ++i) acc = fmaf(smp[i], c_afv[j * 16 + i], acc);
+      const int ix = j & 3, iy = j >> 2;
+      t[(qy + 2 * iy) * kRS + qx + 2 * ix] = acc;   // j = 0: the quadrant's DC term
+    }
+    return;
+  }
+  const int c = k >> v.lh, r = k & ((1 << v.lh) - 1);
+  const float* src = &S[c][y0 + r][x0];
+  float* dst = &T[c][y0 + r][x0];
+  switch (code) {
+    case kDCT8: case kDCT16x8: case kDCT32x8: case kDCT4x8: row_fdct<8>(src, dst); break;
+    case kDCT16: case kDCT8x16: case kDCT32x16: row_fdct<16>(src, dst); break;
+    case kDCT32: case kDCT8x32: case kDCT16x32: row_fdct<32>(src, dst); break;
+    case kDCT4: case kDCT8x4: fpair4(src, 1, dst, 1); break;
+    default: break;
+  }
+}
+
+// Forward column pass of one item: T -> S.
+__device__ void fwd_col_item(float (*S)[kPR][kRS], float (*T)[kPR][kRS], const CellVB& v, int k) {
+  const int code = v.code;
+  const int c = k >> v.lw, col = k & ((1 << v.lw) - 1);
+  const int x0 = 8 * v.bx, y0 = 8 * v.by;
+  const float* src = &T[c][y0][x0 + col];
+  float* dst = &S[c][y0][x0 + col];
+  switch (code) {
+    case kDCT8: case kDCT8x16: case kDCT8x32: case kDCT8x4: col_fdct<8>(src, dst, kRS); break;
+    case kDCT16: case kDCT16x8: case kDCT16x32: col_fdct<16>(src, dst, kRS); break;
+    case kDCT32: case kDCT32x8: case kDCT32x16: col_fdct<32>(src, dst, kRS); break;
+    case kDCT4: case kDCT4x8: fpair4(src, kRS, dst, kRS); break;
+    default:
 #pragma unroll
       for (int i = 0; i < 8; ++i) dst[i * kRS] = src[i * kRS];
       break;
@@ -1027,6 +1220,180 @@ void launch_recon_batch(const ReconArgs* args, const int* prefix, int nimg, int 
 }
 
 // ---------------------------------------------------------------------------
+// k_qco: J.3 per 32x32 cell (whole varblocks), 128 threads.  The residual
+// EPF output - EPF input goes through the forward passes (I.2.3), the corner
+// steps turn LLF into DC (I.2.6) and clamp it, every other coefficient is
+// clamped to +-mul x AcMul x (prescaled) matrix entry, then DC back to LLF
+// (I.2.7), the inverse passes (I.2.4) and the sum with the EPF input.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float clampf(float v, float t) { return fminf(fmaxf(v, -t), t); }
+
+__global__ void __launch_bounds__(128, 6) k_qco(const __grid_constant__ QcoArgs a) {
+  __shared__ __align__(16) float S[3][kPR][kRS];
+  __shared__ __align__(16) float T[3][kPR][kRS];
+  __shared__ CellState cs;
+  const int tid = threadIdx.x;
+  const int gbx0 = blockIdx.x * 4, gby0 = blockIdx.y * 4;
+  const int px0 = gbx0 * 8, py0 = gby0 * 8;
+  cell_setup(cs, a.vmap, a.acmul, gbx0, gby0, a.bw, a.bh);
+
+  // residual; zero outside the cropped image
+  for (int i = tid; i < 3 * 32 * 32; i += 128) {
+    const int c = i >> 10, y = (i >> 5) & 31, x = i & 31;
+    const int gy = py0 + y, gx = px0 + x;
+    float r = 0.f;
+    if (gy < a.ys && gx < a.xs)
+      r = a.f[c * a.fps + static_cast<size_t>(gy) * a.frs + gx] -
+          a.orig[c * a.ops + static_cast<size_t>(gy) * a.ors + gx];
+    S[c][y][x] = r;
+  }
+  __syncthreads();
+  {
+    const int total = cs.row_pre[cs.nvb];
+    int vi = 0;
+    for (int it = tid; it < total; it += blockDim.x) {
+      while (it >= cs.row_pre[vi + 1]) ++vi;
+      fwd_row_item(S, T, cs.vb[vi], it - cs.row_pre[vi]);
+    }
+  }
+  __syncthreads();
+  {
+    const int total = cs.col_pre[cs.nvb];
+    int vi = 0;
+    for (int it = tid; it < total; it += blockDim.x) {
+      while (it >= cs.col_pre[vi + 1]) ++vi;
+      fwd_col_item(S, T, cs.vb[vi], it - cs.col_pre[vi]);
+    }
+  }
+  __syncthreads();
+
+  // corner steps: undo the DC pre-steps, LLF -> DC, clamp DC, DC -> LLF
+  if (tid < 3 * cs.nvb) {
+    const CellVB v = cs.vb[tid / 3];
+    const int c = tid % 3;
+    float* s = &S[c][8 * v.by][8 * v.bx];
+    const int code = v.code;
+    if (code == kDCT4 || code == kAFV) {
+      const float o00 = s[0], o01 = s[1], o10 = s[kRS], o11 = s[kRS + 1];
+      const float k4 = code == kAFV ? 1.f / 16.f : 0.25f;
+      s[0] = k4 * ((o00 + o01) + (o10 + o11));
+      s[1] = k4 * ((o00 + o01) - (o10 + o11));
+      s[kRS] = k4 * ((o00 - o01) + (o10 - o11));
+      s[kRS + 1] = k4 * ((o00 - o01) - (o10 - o11));
+    } else if (code == kDCT8x4) {
+      const float s0 = s[0], s1 = s[1];
+      s[0] = 0.5f * (s0 + s1);
+      s[1] = 0.5f * (s0 - s1);
+    } else if (code == kDCT4x8) {
+      const float s0 = s[0], s1 = s[kRS];
+      s[0] = 0.5f * (s0 + s1);
+      s[kRS] = 0.5f * (s0 - s1);
+    }
+    const float t = a.mul * a.m_dc[c];
+    const int cxl = 1 << (v.lw - 3), cyl = 1 << (v.lh - 3);
+    const int n = cxl * cyl;
+    if (n > 1) {
+      const int m = llf_map_index_dev(cxl, cyl) * 256;
+      const int lcx = v.lw - 3;
+      float llf[16], dc[16];
+#pragma unroll
+      for (int i = 0; i < 16; ++i) llf[i] = i < n ? s[(i >> lcx) * kRS + (i & (cxl - 1))] : 0.f;
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        float acc = 0.f;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) acc = fmaf(c_box[m + i * 16 + j], llf[j], acc);
+        dc[i] = clampf(acc, t);
+      }
+      for (int j = 0; j < n; ++j) {
+        float acc = 0.f;
+#pragma unroll
+        for (int i = 0; i < 16; ++i) acc = fmaf(c_llf[m + j * 16 + i], dc[i], acc);
+        s[(j >> lcx) * kRS + (j & (cxl - 1))] = acc;
+      }
+    } else {
+      s[0] = clampf(s[0], t);
+    }
+  }
+  __syncthreads();
+
+  // clamp of every coefficient outside the LLF slots: one 8-sample chunk
+  {
+    const int y = tid >> 2, k = tid & 3;
+    const int o = cs.owner[(y >> 3) * 4 + k];
+    if (o >= 0) {
+      const CellVB v = cs.vb[o];
+      const int u0 = 8 * k - 8 * v.bx, vv = y - 8 * v.by;
+      const int cxl = 1 << (v.lw - 3), cyl = 1 << (v.lh - 3);
+      const float am = a.mul * v.acmul;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const float* m = a.dequant + v.dqoff + ((c * (1 << v.lh) + vv) << v.lw) + u0;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          if ((u0 + j) < cxl && vv < cyl) continue;
+          S[c][y][8 * k + j] = clampf(S[c][y][8 * k + j], am * __ldg(m + j));
+        }
+      }
+    }
+  }
+  __syncthreads();
+
+  // DC pre-steps of DCT4 / 8x4 / 4x8 (as in the reconstruction)
+  if (tid < 3 * cs.nvb) {
+    const CellVB v = cs.vb[tid / 3];
+    const int c = tid % 3;
+    float* s = &S[c][8 * v.by][8 * v.bx];
+    if (v.code == kDCT4) {
+      const float c00 = s[0], c01 = s[1], c10 = s[kRS], c11 = s[kRS + 1];
+      s[0] = c00 + c01 + c10 + c11;
+      s[1] = c00 + c01 - c10 - c11;
+      s[kRS] = c00 - c01 + c10 - c11;
+      s[kRS + 1] = c00 - c01 - c10 + c11;
+    } else if (v.code == kDCT8x4) {
+      const float c0 = s[0], c1 = s[1];
+      s[0] = c0 + c1;
+      s[1] = c0 - c1;
+    } else if (v.code == kDCT4x8) {
+      const float c0 = s[0], c1 = s[kRS];
+      s[0] = c0 + c1;
+      s[kRS] = c0 - c1;
+    }
+  }
+  __syncthreads();
+  {
+    const int total = cs.row_pre[cs.nvb];
+    int vi = 0;
+    for (int it = tid; it < total; it += blockDim.x) {
+      while (it >= cs.row_pre[vi + 1]) ++vi;
+      row_item(S, T, cs.vb[vi], it - cs.row_pre[vi]);
+    }
+  }
+  __syncthreads();
+  {
+    const int total = cs.col_pre[cs.nvb];
+    int vi = 0;
+    for (int it = tid; it < total; it += blockDim.x) {
+      while (it >= cs.col_pre[vi + 1]) ++vi;
+      col_item(S, T, cs.vb[vi], it - cs.col_pre[vi]);
+    }
+  }
+  __syncthreads();
+  for (int i = tid; i < 3 * 32 * 32; i += 128) {
+    const int c = i >> 10, y = (i >> 5) & 31, x = i & 31;
+    const int gy = py0 + y, gx = px0 + x;
+    if (gy < a.ys && gx < a.xs && cs.owner[(y >> 3) * 4 + (x >> 3)] >= 0)
+      a.f[c * a.fps + static_cast<size_t>(gy) * a.frs + gx] =
+          a.orig[c * a.ops + static_cast<size_t>(gy) * a.ors + gx] + S[c][y][x];
+  }
+}
+
+void launch_qco(const QcoArgs& a, cudaStream_t s) {
+  dim3 grid((a.bw + 3) / 4, (a.bh + 3) / 4);
+  k_qco<<<grid, 128, 0, s>>>(a);
+}
+
+// ---------------------------------------------------------------------------
 // k_sigma: J.2.4 sigma from caller-supplied XYB
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(128) k_sigma(const SigmaArgs a) {
@@ -1405,6 +1772,19 @@ __device__ __forceinline__ void epf_tile(const FilterArgs& a, int tbx, int tby) 
     for (int c = 0; c < 3; ++c) E[c][ey][ex] = E[c][my][mx];
   }
   __syncthreads();
+
+  if (a.epf_out) {   // EPF result only (the quantization constraint follows)
+    for (int i = tid; i < kET * kET; i += 128) {
+      const int ty = i / kET, tx = i - ty * kET;
+      const int gy = y0 + ty, gx = x0 + tx;
+      if (gy < a.ys && gx < a.xs) {
+        float* o = a.epf_out + static_cast<size_t>(gy) * a.ors + gx;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) o[c * a.ops] = E[c][ty + 1][tx + 1];
+      }
+    }
+    return;
+  }
 
   // ---- J.4 Gaborish + L.2 + store: each thread walks a column of up to 8
   // pixels keeping the centre and the left+right sum of the previous, current

@@ -75,6 +75,22 @@ struct FilterArgs {
   SigmaParams sp;             // guide parameters
   ColorParams cp;
   OutParams out;
+  float* epf_out;             // non-null: write the EPF result here (planar XYB,
+  size_t ors, ops;            // row / plane stride in elements) and stop before J.4
+};
+
+// J.3 on the EPF output f, in place, with the EPF input orig (planar XYB).
+struct QcoArgs {
+  const float* orig;
+  size_t ors, ops;            // row / plane stride of orig (elements)
+  float* f;
+  size_t frs, fps;            // row / plane stride of f
+  const uint8_t* vmap;        // [bh][bw]
+  const float* acmul;         // [bh][bw]
+  const float* dequant;       // prescaled matrices, dequant_offset layout
+  int xs, ys, bw, bh;
+  float m_dc[3];
+  float mul;                  // qco_interval_mul
 };
 
 void launch_validate(const uint8_t* vmap, int bw, int bh, unsigned* status, cudaStream_t s);
@@ -84,6 +100,7 @@ void launch_recon(const ReconArgs& a, cudaStream_t s);
 void launch_recon_tc(const ReconArgs& a, cudaStream_t s);
 constexpr int kTcBasisBytes = 6144;
 void launch_sigma(const SigmaArgs& a, cudaStream_t s);
+void launch_qco(const QcoArgs& a, cudaStream_t s);
 void launch_filter(const FilterArgs& a, cudaStream_t s);
 
 // Multi-image launches: args[i] per image (device array), prefix[i] = first

@@ -59,14 +59,15 @@ jxlr_status setup_device(int dev) {
   std::vector<float> raw(kDequantFloats), scaled(kDequantFloats);
   if (!default_dequant(raw.data())) return noalloc_fail(JXLR_EINVAL, "default matrices ill-formed");
   prescale_dequant(raw.data(), scaled.data());
-  std::vector<float> llf(kLlfMaps * 256), odd(kOddFloats), afv(256);
+  std::vector<float> llf(kLlfMaps * 256), box(kLlfMaps * 256), odd(kOddFloats), afv(256);
   std::vector<int32_t> mul4(673);
   llf_maps(llf.data());
+  llf_box_maps(box.data());
   odd_tables(odd.data());
   mul_table4(mul4.data());
   for (int j = 0; j < 16; ++j)
     for (int i = 0; i < 16; ++i) afv[j * 16 + i] = static_cast<float>(kAfvBasis[j][i]);
-  if (!upload_constants(llf.data(), odd.data(), mul4.data(), afv.data()))
+  if (!upload_constants(llf.data(), box.data(), odd.data(), mul4.data(), afv.data()))
     return noalloc_fail(JXLR_ECUDA, "noalloc setup: constant upload failed");
   cudaError_t e = cudaMemcpyToSymbol(g_noalloc_dequant, scaled.data(),
                                      sizeof(float) * kDequantFloats);
@@ -127,8 +128,8 @@ extern "C" jxlr_status jxl_recon_run_noalloc(const jxl_recon_coeffs* co, const u
     return noalloc_fail(JXLR_EINVAL, "run_noalloc: output stride too small");
   if (fp->epf && !fp->sharpness)
     return noalloc_fail(JXLR_EINVAL, "run_noalloc: EPF needs the sharpness map");
-  if (fp->dc_smooth || fp->lf_predict)
-    return noalloc_fail(JXLR_EINVAL, "run_noalloc: DC smoothing and AC prediction run on the submit path only");
+  if (fp->dc_smooth || fp->lf_predict || (fp->epf && fp->qco))
+    return noalloc_fail(JXLR_EINVAL, "run_noalloc: DC smoothing, AC prediction and the quantization constraint run on the submit path only");
 
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);

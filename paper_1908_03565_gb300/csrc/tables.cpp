@@ -475,6 +475,28 @@ int llf_map_index(int cx, int cy) {
   return -1;
 }
 
+void llf_box_maps(float* out) {
+  const int dims[kLlfMaps][2] = {{2, 2}, {4, 4}, {1, 2}, {2, 1},
+                                 {1, 4}, {4, 1}, {2, 4}, {4, 2}};
+  std::memset(out, 0, sizeof(float) * kLlfMaps * 256);
+  for (int m = 0; m < kLlfMaps; ++m) {
+    const int cx = dims[m][0], cy = dims[m][1], W = 8 * cx, H = 8 * cy;
+    const int n = cx * cy;
+    for (int i = 0; i < n; ++i) {
+      const int bx = i % cx, by = i / cx;
+      for (int j = 0; j < n; ++j) {
+        const int u = j % cx, v = j / cx;
+        double sx = 0, sy = 0;
+        for (int k = 0; k < 8; ++k) {
+          sx += std::cos((2 * (8 * bx + k) + 1) * u * kPi / (2.0 * W));
+          sy += std::cos((2 * (8 * by + k) + 1) * v * kPi / (2.0 * H));
+        }
+        out[m * 256 + i * 16 + j] = static_cast<float>((sx / 8) * (sy / 8));
+      }
+    }
+  }
+}
+
 void llf_maps(float* out) {
   const int dims[kLlfMaps][2] = {{2, 2}, {4, 4}, {1, 2}, {2, 1},
                                  {1, 4}, {4, 1}, {2, 4}, {4, 2}};

@@ -201,6 +201,21 @@ def test_filter_stage_on_identical_samples(B, ctx, epf, gab, xs, ys):
     assert_xyb_close(got.transpose(2, 0, 1), want, abs_tol=5e-6, radius=8)
 
 
+@pytest.mark.parametrize("epf,gab", [(True, False), (True, True)])
+@pytest.mark.parametrize("xs,ys,mix", [(136, 104, 'mixed'), (97, 61, 3), (64, 64, 14)])
+def test_filter_stage_where_the_epf_acts(B, ctx, epf, gab, xs, ys, mix):
+    """As above on inputs where most EPF weights survive the cut-off (small
+    AC, smooth DC, AcMul 0.5): with the workload's coefficient statistics
+    the EPF leaves almost every sample unchanged."""
+    img = synth.make_image(xs, ys, 13 * xs + ys, mix=mix, coef_scale=2.0, acmul=0.5, dc='smooth')
+    p, lp = params_pair(B, epf=epf, gab=gab)
+    xyb, got = _filters_on_gpu_xyb(B, ctx, img, lp, epf, gab, XYB)
+    want = _oracle_filters(img, xyb, p)
+    assert np.mean(np.abs(R.epf(xyb.astype(np.float64), img['vmap'], img['acmul'],
+                                img["sharpness"], p) - xyb) > 1e-7) > 0.03
+    assert_xyb_close(got.transpose(2, 0, 1), want, abs_tol=5e-6, radius=8)
+
+
 def test_full_path_equals_staged_path(B, ctx):
     """Submit with filters == recon to XYB then the filter entry point."""
     img = synth.make_image(200, 136, 9, y_dc_offset_q=200)
