@@ -34,7 +34,9 @@ IN_BPP = 6.0 + 1 / 64 + 4 / 64 + 1 / 64 + 8 / 4096
 OUT_BPP = 12.0
 # algorithmic lane operations per pixel of the filter+colour kernel (EPF with
 # separable 3x4 patch sums on packed guide bytes, J.2.4 weight, J.2.5
-# accumulation, guide, Gaborish, colour); derivation in the design doc
+# accumulation, guide, Gaborish, colour): per offset absdiff 1, channel sum 1,
+# horizontal and vertical sliding sums 4, weight 4, accumulation 4 (x 56);
+# normalisation 4; guide 17; Gaborish 27; colour 20
 FILTER_OPS_PER_PX = 56 * 14 + 4 + 17 + 27 + 20
 CPU_SAMPLE = 1024         # oracle sample: one 1024x1024 image, same statistics
 

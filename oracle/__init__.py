@@ -12,6 +12,6 @@ Pinning status: every function is pinned by ``tests/test_oracle_pins.py``
 against closed forms, round trips and invariants the draft fixes, except the
 reading of the garbled numerator formula of C.6.1 (its 4-point and
 rectangular cases), which no independent value in the draft pins ("parity
-unpinned" for those matrix entries; see DESIGN.md).
+unpinned" for those matrix entries).
 """
 from . import tables, transforms, recon  # noqa: F401

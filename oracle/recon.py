@@ -418,7 +418,8 @@ def reconstruct_xyb(coeffs, vmap, acmul, cfl, params, diag=None):
 # J.2 edge-preserving filter
 # ---------------------------------------------------------------------------
 K_SIGMA_SHIFT = 2  # READING: undefined in the draft; 2 makes mul = -32768 the
-                   # exact bound for the smallest sigma
+                   # exact bound for the smallest sigma (Weight(16 >> 2, -32768)
+                   # is exactly 0.5)
 
 
 def weight_bits(sad, mul4):

@@ -1,6 +1,6 @@
 """Parity of the CUDA library (through its C ABI) with the FP64 oracle.
 
-Tolerances (written here, derived in the design doc):
+Tolerances (written here; derived from binary32 arithmetic):
   * linear RGB in [0, 1]: max |gpu - oracle| <= 1e-4 on clamp(., 0, 1);
   * 8-bit sRGB: every sample within +-1 of the oracle's;
   * f16 output: <= half an f16 ulp of the value + 1e-4;
