@@ -1,6 +1,6 @@
 """FP64 CPU oracle of VarDCT pixel reconstruction (JPEG XL committee draft,
-ISO/IEC 18181 CD 2019: Annexes F, G, I.2, J.2, J.4, L.2; tables of C.6.1 and
-C.10).
+ISO/IEC 18181 CD 2019: Annexes F, G, H, I.2, J.2-J.4, L.2; tables of C.6.1
+and C.10) and of JPEG1 direct rasterisation (M.6).
 
 TEST INFRASTRUCTURE. This package is the independent reference that the CUDA
 library is checked against. It is plain, slow, FP64 numpy written from the
@@ -14,4 +14,4 @@ reading of the garbled numerator formula of C.6.1 (its 4-point and
 rectangular cases), which no independent value in the draft pins ("parity
 unpinned" for those matrix entries).
 """
-from . import tables, transforms, recon  # noqa: F401
+from . import tables, transforms, recon, jpeg1  # noqa: F401

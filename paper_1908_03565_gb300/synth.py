@@ -216,3 +216,46 @@ def shape_area_fractions(vmap):
         tot[c] = tot.get(c, 0) + w * h
     area = 64 * vmap.size
     return {c: a / area for c, a in sorted(tot.items())}
+
+
+def make_jpeg(xsize, ysize, seed, sampling='420', gab=False):
+    """A synthetic JPEG1 coefficient stream (the input of direct
+    rasterisation).  ``sampling``: '420' (Y 2x2, Cb and Cr 1x1), '444' or
+    'grey'.  Quantisation tables: 3 + 2 (u + v) for Y and 4 + 3 (u + v) for
+    chroma (synthetic, index 8u + v).  Quantised DC: a slow field of
+    amplitude 200 steps (period 40 blocks) plus Gaussian noise of 2 steps;
+    AC: Laplace(0, 6 / (1 + u + v)) rounded.  ``gab`` adds the block-
+    conditional Gaborish side channel (w1 118/1024, w2 63/1024, threshold
+    2.5, limit 20) to every component.  Returns a dict with xsize, ysize and
+    components (coeffs int16 (bh, bw, 64), quant uint16 (64,), h_samp,
+    v_samp, gab)."""
+    rng = np.random.default_rng(seed)
+    if sampling == '420':
+        samp = [(2, 2), (1, 1), (1, 1)]
+    elif sampling == '444':
+        samp = [(1, 1), (1, 1), (1, 1)]
+    elif sampling == 'grey':
+        samp = [(1, 1)]
+    else:
+        raise ValueError(sampling)
+    hmax = max(s[0] for s in samp)
+    vmax = max(s[1] for s in samp)
+    mx = -(-xsize // (8 * hmax))
+    my = -(-ysize // (8 * vmax))
+    uu, vv = np.divmod(np.arange(64), 8)
+    comps = []
+    for ci, (h, v) in enumerate(samp):
+        bw, bh = mx * h, my * v
+        base = 3 if ci == 0 else 4
+        step = 2 if ci == 0 else 3
+        quant = (base + step * (uu + vv)).astype(np.uint16)
+        ac = rng.laplace(0.0, 1.0, size=(bh, bw, 64)) * (6.0 / (1.0 + uu + vv))
+        q = np.rint(ac)
+        by, bx = np.mgrid[0:bh, 0:bw]
+        ph = rng.uniform(0, 2 * math.pi, size=2)
+        dc = 200.0 * np.sin(2 * math.pi * bx / 40.0 + ph[0]) * np.cos(2 * math.pi * by / 40.0 + ph[1])
+        q[:, :, 0] = np.rint(dc + rng.normal(0.0, 2.0, size=(bh, bw)))
+        comps.append({'coeffs': np.clip(q, -32768, 32767).astype(np.int16), 'quant': quant,
+                      'h_samp': h, 'v_samp': v,
+                      'gab': (118 / 1024, 63 / 1024, 40 / 16, 20) if gab else None})
+    return {'xsize': xsize, 'ysize': ysize, 'components': comps}
