@@ -304,6 +304,37 @@ def extra_steps_leg(binding, torch, steps):
     return res
 
 
+def jpeg1_leg(binding, torch, steps, peak_gbs):
+    """JPEG1 direct rasterisation (M.6) of a 4096x4096 4:2:0 stream (synthetic
+    coefficients, no side channel), u8 and f32 RGB out, device-resident
+    coefficients; CUDA events.  Algorithmic bytes per pixel: coefficients
+    2 (Y) + 1 (Cb, Cr at quarter resolution) in, 3 (u8) or 12 (f32) out."""
+    from paper_1908_03565_gb300 import synth
+    st = binding.jpeg_to_device(synth.make_jpeg(XS, YS, SEED + 9, sampling='420'), torch)
+    stream = torch.cuda.Stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    res = {"input": f"{XS}x{YS} 4:2:0 synthetic JPEG1 coefficients"}
+    with binding.Context(stream=stream.cuda_stream) as ctx:
+        for name, dt, tdt, ob in (("u8", binding.OUT_U8_SRGB, torch.uint8, 3),
+                                  ("f32", binding.OUT_F32_LINEAR, torch.float32, 12)):
+            out = torch.empty((YS, XS, 3), dtype=tdt, device="cuda")
+            for _ in range(3):
+                ctx.poll(ctx.submit_jpeg(st, out, dt))
+            stream.synchronize()
+            l0 = ctx.launch_count()
+            e0.record(stream)
+            for _ in range(steps):
+                ctx.poll(ctx.submit_jpeg(st, out, dt))
+            e1.record(stream)
+            stream.synchronize()
+            ms = e0.elapsed_time(e1) / steps
+            gbs = XS * YS * (3 + ob) / (ms * 1e-3) / 1e9
+            res[name] = {"ms_per_step": round(ms, 4), "mpx_s": round(XS * YS / ms / 1e3, 1),
+                         "algorithmic_gbs": round(gbs, 1), "hbm_frac": round(gbs / peak_gbs, 4),
+                         "launches_per_step": (ctx.launch_count() - l0) / steps}
+    return res
+
+
 def cpu_baseline_run(steps=1):
     """Times the FP64 oracle on a bounded sample of the workload."""
     from oracle import recon as R
@@ -356,6 +387,8 @@ def main():
                     help="timed steps of the FP32 vs tensor-core comparison (0 = skip)")
     ap.add_argument("--batch-images", type=int, default=512,
                     help="images in the multi-image batch leg (0 = skip)")
+    ap.add_argument("--jpeg-steps", type=int, default=20,
+                    help="timed steps of the JPEG1 rasterisation leg (0 = skip)")
     ap.add_argument("--extra-steps", type=int, default=20,
                     help="timed steps of the optional-steps leg: F.2, Annex H, J.3 (0 = skip)")
     ap.add_argument("--serve-loads", default="0.5,0.9",
@@ -479,6 +512,9 @@ def main():
     dclf = None
     if rank == 0 and args.extra_steps > 0:
         dclf = extra_steps_leg(binding, torch, args.extra_steps)
+    jpeg = None
+    if rank == 0 and args.jpeg_steps > 0:
+        jpeg = jpeg1_leg(binding, torch, args.jpeg_steps, hbm_peak)
     batched = None
     if rank == 0 and args.batch_images > 0:
         batched = batch_leg(binding, torch, args.batch_images)
@@ -508,7 +544,7 @@ def main():
                          "recon_gbs": round(recon_gbs, 1)},
             "peaks": peak_kind,
             "clocks": clocks, "e2e": e2e, "gpu_launches": int(launches),
-            "cpu_baseline": cb, "precision": precision, "extra_steps": dclf, "batched": batched, "served": served,
+            "cpu_baseline": cb, "precision": precision, "extra_steps": dclf, "jpeg1": jpeg, "batched": batched, "served": served,
         }
         print(json.dumps(line), flush=True)
     ctx.close()

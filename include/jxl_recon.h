@@ -196,6 +196,49 @@ jxlr_status jxl_recon_submit_xyb(jxl_recon_ctx* ctx, const float* xyb,
                                  const jxl_recon_filter_params* filter_params,
                                  const jxl_recon_output* out, uint64_t* ticket);
 
+/* ---- JPEG1 direct rasterisation (M.6) ------------------------------------
+ * One component of a JPEG1 coefficient stream.  coeffs: int16
+ * [height_in_blocks][width_in_blocks][64] in the natural order of M.6.1
+ * (index 8u + v, u the vertical and v the horizontal frequency), in the
+ * memory space the stream's on_device names; quant: the component's 64
+ * quantisation factors in the same order, always host memory.  h_samp,
+ * v_samp: sampling factors (1 or 2); a component whose factor is below the
+ * largest one is upsampled 2x along that axis (M.6.4).  gab: 1 when the
+ * block-conditional Gaborish side channel of M.6.3 is present, with its
+ * decoded weights (u(8) / 1024), threshold (u(8) / 16) and limit. */
+typedef struct {
+  uint32_t width_in_blocks, height_in_blocks;
+  uint32_t h_samp, v_samp;
+  const int16_t* coeffs;
+  const uint16_t* quant;
+  int gab;
+  float gab_w1, gab_w2, gab_threshold;
+  int gab_limit;
+} jxl_jpeg_component;
+
+/* num_components: 1 (grey) or 3 (Y, Cb, Cr).  The block grids must cover
+ * the image: 8 x width_in_blocks x (largest h_samp / h_samp) >= xsize, and
+ * likewise vertically.  on_device: 1 = coeffs are device pointers that stay
+ * valid until poll returns something other than JXLR_EAGAIN; 0 = host. */
+typedef struct {
+  uint32_t xsize, ysize;
+  uint32_t num_components;
+  jxl_jpeg_component comp[3];
+  int on_device;
+} jxl_jpeg_stream;
+
+/* Enqueues M.6.1 (dequantisation), M.6.2 (IDCT_2D), M.6.3, M.6.4, M.6.5
+ * (YCbCr -> RGB) and M.6.6 (cropping) for one stream.  The optional DC/AC
+ * conditioning of M.6.1.1 and the HDR transform of M.6.5.1 are not
+ * performed.  Output: JXLR_OUT_U8_SRGB gives the rasterised samples
+ * clamped to [0, 255] and rounded half up (no transfer function is applied:
+ * the samples are already in the JPEG's colour encoding); F32_LINEAR and
+ * F16_LINEAR give sample / 255 unclamped; F32_XYB is rejected.  Same ticket
+ * semantics as jxl_recon_submit.  Returns JXLR_OK, JXLR_EINVAL, JXLR_EBUSY,
+ * JXLR_ENOMEM or JXLR_ECUDA. */
+jxlr_status jxl_recon_submit_jpeg(jxl_recon_ctx* ctx, const jxl_jpeg_stream* stream,
+                                  const jxl_recon_output* out, uint64_t* ticket);
+
 /* Waits up to timeout_us (0 = just test, < 0 = forever) for a ticket.
  * JXLR_OK when done (the ticket is then released; *latency_ms, if not
  * NULL, receives submit-to-completion time), JXLR_EAGAIN / JXLR_ETIMEDOUT

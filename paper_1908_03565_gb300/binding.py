@@ -25,7 +25,7 @@ EXPORTS = ("jxl_recon_filter_defaults", "jxl_recon_create", "jxl_recon_submit",
            "jxl_recon_launch_count", "jxl_recon_device_bytes", "jxl_recon_destroy",
            "jxl_recon_last_error", "jxl_recon_run_noalloc", "jxl_recon_serve",
            "jxl_recon_batch_create", "jxl_recon_batch_launch", "jxl_recon_batch_query",
-           "jxl_recon_batch_destroy")
+           "jxl_recon_batch_destroy", "jxl_recon_submit_jpeg")
 
 
 class Config(ctypes.Structure):
@@ -56,6 +56,20 @@ class FilterParams(ctypes.Structure):
                 ("dequant", ctypes.c_void_p), ("dc_smooth", ctypes.c_int),
                 ("lf_predict", ctypes.c_int), ("qco", ctypes.c_int),
                 ("qco_interval_mul", ctypes.c_float)]
+
+
+class JpegComponent(ctypes.Structure):
+    _fields_ = [("width_in_blocks", ctypes.c_uint32), ("height_in_blocks", ctypes.c_uint32),
+                ("h_samp", ctypes.c_uint32), ("v_samp", ctypes.c_uint32),
+                ("coeffs", ctypes.c_void_p), ("quant", ctypes.c_void_p), ("gab", ctypes.c_int),
+                ("gab_w1", ctypes.c_float), ("gab_w2", ctypes.c_float),
+                ("gab_threshold", ctypes.c_float), ("gab_limit", ctypes.c_int)]
+
+
+class JpegStream(ctypes.Structure):
+    _fields_ = [("xsize", ctypes.c_uint32), ("ysize", ctypes.c_uint32),
+                ("num_components", ctypes.c_uint32), ("comp", JpegComponent * 3),
+                ("on_device", ctypes.c_int)]
 
 
 class Output(ctypes.Structure):
@@ -108,6 +122,9 @@ def load(path=LIB_PATH):
                                          ctypes.c_void_p, P(FilterParams), P(Output),
                                          P(ctypes.c_uint64)]
     lib.jxl_recon_submit_xyb.restype = ctypes.c_int
+    lib.jxl_recon_submit_jpeg.argtypes = [ctypes.c_void_p, P(JpegStream), P(Output),
+                                          P(ctypes.c_uint64)]
+    lib.jxl_recon_submit_jpeg.restype = ctypes.c_int
     lib.jxl_recon_poll.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int64,
                                    P(ctypes.c_double)]
     lib.jxl_recon_poll.restype = ctypes.c_int
@@ -244,6 +261,40 @@ class Context:
         self._keep[t.value] = (xyb, vmap, acmul, sharpness, params, out, o)
         return t.value
 
+    def submit_jpeg(self, stream, out, out_dtype, on_device=True, out_on_device=True,
+                    out_stride=None):
+        """stream: a synth.make_jpeg dict (coeffs as CUDA tensors when
+        on_device, numpy arrays otherwise; quant always numpy)."""
+        xs, ys = stream['xsize'], stream['ysize']
+        st = JpegStream()
+        st.xsize, st.ysize = xs, ys
+        comps = stream['components']
+        st.num_components = len(comps)
+        keep = [stream]
+        for i, c in enumerate(comps):
+            k = st.comp[i]
+            bh, bw = c['coeffs'].shape[:2]
+            k.width_in_blocks, k.height_in_blocks = bw, bh
+            k.h_samp, k.v_samp = c['h_samp'], c['v_samp']
+            k.coeffs = _ptr(c['coeffs'])
+            q = np.ascontiguousarray(c['quant'], dtype=np.uint16)
+            keep.append(q)
+            k.quant = q.ctypes.data
+            if c.get('gab') is not None:
+                k.gab = 1
+                k.gab_w1, k.gab_w2, k.gab_threshold, k.gab_limit = c['gab']
+        st.on_device = 1 if on_device else 0
+        if out_stride is None:
+            out_stride = OUT_BYTES[out_dtype] * xs
+        o = Output(_ptr(out), out_stride, out_dtype, 1 if out_on_device else 0)
+        t = ctypes.c_uint64()
+        r = self.lib.jxl_recon_submit_jpeg(self.h, ctypes.byref(st), ctypes.byref(o),
+                                           ctypes.byref(t))
+        if r != JXLR_OK:
+            raise JxlrError(r, self.last_error())
+        self._keep[t.value] = (keep, st, out, o)
+        return t.value
+
     def poll(self, ticket, timeout_us=-1):
         """Returns (status, latency_ms); raises on errors other than
         EAGAIN/ETIMEDOUT."""
@@ -355,6 +406,17 @@ def to_device(img, torch_module, device="cuda"):
     out = dict(img)
     for k in ('coeffs', 'vmap', 'acmul', 'cfl', 'sharpness'):
         out[k] = t.from_numpy(np.ascontiguousarray(img[k])).to(device)
+    return out
+
+
+def jpeg_to_device(stream, torch_module, device="cuda"):
+    """Copies a JPEG1 stream's coefficient arrays to device tensors."""
+    out = dict(stream)
+    out['components'] = []
+    for c in stream['components']:
+        d = dict(c)
+        d['coeffs'] = torch_module.from_numpy(np.ascontiguousarray(c['coeffs'])).to(device)
+        out['components'].append(d)
     return out
 
 

@@ -2,6 +2,7 @@
 // admission under an HBM cap, request tickets.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <atomic>
 #include <chrono>
 #include <cmath>
@@ -16,6 +17,7 @@
 #include "../../include/jxl_recon.h"
 #include "internal.h"
 #include "kernels.h"
+#include "jpeg1.h"
 #include "lf.h"
 
 using namespace jxlr;
@@ -163,6 +165,19 @@ jxlr_status jxl_recon_create(const jxl_recon_config* cfg, jxl_recon_ctx** out) {
   lf_tables(lf_up.data(), lf_inv.data(), &lf_half);
   if (!upload_lf_constants(lf_up.data(), lf_inv.data(), lf_half))
     return fail(JXLR_ECUDA, "create: constant upload failed");
+  {
+    // odd parts of the unscaled 8- and 4-point inverse DCT (M.6.2)
+    const double pi = 3.14159265358979323846;
+    float odd8[16], odd4[4];
+    for (int n = 0; n < 4; ++n)
+      for (int j = 0; j < 4; ++j)
+        odd8[n * 4 + j] = static_cast<float>(std::cos((2 * n + 1) * (2 * j + 1) * pi / 16.0));
+    for (int n = 0; n < 2; ++n)
+      for (int j = 0; j < 2; ++j)
+        odd4[n * 2 + j] = static_cast<float>(std::cos((2 * n + 1) * (2 * j + 1) * pi / 8.0));
+    if (!upload_jpeg_constants(odd8, odd4, static_cast<float>(std::cos(pi / 4.0))))
+      return fail(JXLR_ECUDA, "create: constant upload failed");
+  }
 
   auto* ctx = new jxl_recon_ctx();
   ctx->device = cfg->device;
@@ -723,4 +738,146 @@ extern "C" jxlr_status jxl_recon_stage_ms(jxl_recon_ctx* ctx, uint64_t ticket, f
   if (it == ctx->timings.end()) return fail(JXLR_EINVAL, "stage_ms: no timing for this ticket");
   std::memcpy(ms, it->second.ms, sizeof(float) * 4);
   return JXLR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// JPEG1 direct rasterisation (M.6)
+// ---------------------------------------------------------------------------
+extern "C" jxlr_status jxl_recon_submit_jpeg(jxl_recon_ctx* ctx, const jxl_jpeg_stream* st,
+                                             const jxl_recon_output* out, uint64_t* ticket) {
+  if (!ctx || !st || !out || !ticket) return fail(JXLR_EINVAL, "submit_jpeg: null argument");
+  const int xs = static_cast<int>(st->xsize), ys = static_cast<int>(st->ysize);
+  if (xs <= 0 || ys <= 0 || xs > 65536 || ys > 65536)
+    return fail(JXLR_EINVAL, "submit_jpeg: image size out of [1, 65536]");
+  const int nc = static_cast<int>(st->num_components);
+  if (nc != 1 && nc != 3) return fail(JXLR_EINVAL, "submit_jpeg: 1 or 3 components");
+  if (out->dtype < 0 || out->dtype > 2 || !out->data)
+    return fail(JXLR_EINVAL, "submit_jpeg: output must be f32, f16 or u8");
+  const size_t px_bytes = out->dtype == 1 ? 6 : out->dtype == 2 ? 3 : 12;
+  if (out->row_stride_bytes < px_bytes * xs) return fail(JXLR_EINVAL, "submit_jpeg: output stride too small");
+  int hmax = 1, vmax = 1;
+  for (int c = 0; c < nc; ++c) {
+    const jxl_jpeg_component& k = st->comp[c];
+    if (k.h_samp < 1 || k.h_samp > 2 || k.v_samp < 1 || k.v_samp > 2)
+      return fail(JXLR_EINVAL, "submit_jpeg: sampling factors must be 1 or 2");
+    hmax = std::max(hmax, static_cast<int>(k.h_samp));
+    vmax = std::max(vmax, static_cast<int>(k.v_samp));
+  }
+  for (int c = 0; c < nc; ++c) {
+    const jxl_jpeg_component& k = st->comp[c];
+    if (!k.coeffs || !k.quant) return fail(JXLR_EINVAL, "submit_jpeg: null coefficients or table");
+    if (k.width_in_blocks == 0 || k.height_in_blocks == 0 || k.width_in_blocks > 8192 ||
+        k.height_in_blocks > 8192)
+      return fail(JXLR_EINVAL, "submit_jpeg: block grid out of [1, 8192]");
+    const long long cw = 8LL * k.width_in_blocks * (hmax / k.h_samp);
+    const long long ch = 8LL * k.height_in_blocks * (vmax / k.v_samp);
+    if (cw < xs || ch < ys) return fail(JXLR_EINVAL, "submit_jpeg: block grid does not cover the image");
+    if (st->on_device && (reinterpret_cast<uintptr_t>(k.coeffs) & 15))
+      return fail(JXLR_EINVAL, "submit_jpeg: device coefficients must be 16-byte aligned");
+    if (k.gab && !(k.gab_limit >= 0 && std::isfinite(k.gab_w1) && std::isfinite(k.gab_w2) &&
+                   std::isfinite(k.gab_threshold) && 1.0 + 4.0 * k.gab_w1 + 4.0 * k.gab_w2 != 0.0))
+      return fail(JXLR_EINVAL, "submit_jpeg: bad Gaborish side channel");
+  }
+
+  size_t need = 0;
+  auto add = [&](size_t bytes) { need = align_up(need, 256) + bytes; };
+  add(16);
+  for (int c = 0; c < nc; ++c) {
+    const size_t nb = static_cast<size_t>(st->comp[c].width_in_blocks) * st->comp[c].height_in_blocks;
+    if (!st->on_device) add(nb * 128);
+    add(nb * 256);                                    // sample plane
+    if (st->comp[c].gab) add(nb * 256);               // after M.6.3
+  }
+  const size_t out_bytes = out->row_stride_bytes * (ys - 1) + px_bytes * xs;
+  if (!out->on_device) add(out_bytes);
+  need = align_up(need, 256);
+
+  std::lock_guard<std::mutex> lock(ctx->mu);
+  CK(cudaSetDevice(ctx->device));
+  Slot* slot = nullptr;
+  jxlr_status status = acquire_slot(ctx, need, &slot);
+  if (status != JXLR_OK) return status;
+  slot->timed = ctx->timing;
+  slot->t_submit = Clock::now();
+  cudaStream_t s = slot->stream;
+  Carve cv(slot->arena);
+  unsigned* d_status = cv.take<unsigned>(4);
+  CK(cudaMemsetAsync(d_status, 0, 16, s));
+  mark(slot, 0);
+  const int16_t* coef[3] = {nullptr, nullptr, nullptr};
+  for (int c = 0; c < nc; ++c) {
+    const size_t nb = static_cast<size_t>(st->comp[c].width_in_blocks) * st->comp[c].height_in_blocks;
+    if (st->on_device) {
+      coef[c] = st->comp[c].coeffs;
+    } else {
+      int16_t* d = cv.take<int16_t>(nb * 64);
+      CK(cudaMemcpyAsync(d, st->comp[c].coeffs, nb * 128, cudaMemcpyHostToDevice, s));
+      coef[c] = d;
+    }
+  }
+  mark(slot, 1);
+  mark(slot, 2);
+  JpegColorArgs ca;
+  std::memset(&ca, 0, sizeof(ca));
+  for (int c = 0; c < nc; ++c) {
+    const jxl_jpeg_component& k = st->comp[c];
+    const int bw = static_cast<int>(k.width_in_blocks), bh = static_cast<int>(k.height_in_blocks);
+    JpegIdctArgs ia;
+    ia.coef = coef[c];
+    ia.bw = bw;
+    ia.bh = bh;
+    // M.6.1 I(8,u) I(8,v) times the scale of the unscaled cosine sums:
+    // I(8,u) S_8(u) = eps(u) / 2 with eps(0) = sqrt(1/2)
+    for (int u = 0; u < 8; ++u)
+      for (int v = 0; v < 8; ++v) {
+        const double eu = u == 0 ? std::sqrt(0.5) : 1.0, ev = v == 0 ? std::sqrt(0.5) : 1.0;
+        ia.dq[8 * u + v] = static_cast<float>(k.quant[8 * u + v] * eu * ev / 4.0);
+      }
+    ia.plane = cv.take<float>(static_cast<size_t>(bw) * bh * 64);
+    launch_jpeg_idct(ia, s);
+    ctx->launches++;
+    const float* plane = ia.plane;
+    if (k.gab) {
+      JpegGabArgs ga;
+      ga.src = ia.plane;
+      ga.dst = cv.take<float>(static_cast<size_t>(bw) * bh * 64);
+      ga.bw = bw;
+      ga.bh = bh;
+      const double norm = 1.0 + 4.0 * k.gab_w1 + 4.0 * k.gab_w2;
+      ga.w0n = static_cast<float>(1.0 / norm);
+      ga.w1n = static_cast<float>(k.gab_w1 / norm);
+      ga.w2n = static_cast<float>(k.gab_w2 / norm);
+      ga.threshold = k.gab_threshold;
+      ga.limit = k.gab_limit;
+      launch_jpeg_gab(ga, s);
+      ctx->launches++;
+      plane = ga.dst;
+    }
+    ca.p[c].data = plane;
+    ca.p[c].w = 8 * bw;
+    ca.p[c].h = 8 * bh;
+    ca.p[c].up_x = static_cast<int>(k.h_samp) != hmax;
+    ca.p[c].up_y = static_cast<int>(k.v_samp) != vmax;
+  }
+  mark(slot, 3);
+  ca.ncomp = nc;
+  ca.xs = xs;
+  ca.ys = ys;
+  char* d_out = nullptr;
+  if (out->on_device) {
+    ca.out = out->data;
+  } else {
+    d_out = cv.take<char>(out_bytes);
+    ca.out = d_out;
+  }
+  ca.stride = out->row_stride_bytes;
+  ca.dtype = out->dtype;
+  launch_jpeg_color(ca, s);
+  ctx->launches++;
+  mark(slot, 4);
+  if (!out->on_device)
+    CK(cudaMemcpy2DAsync(out->data, out->row_stride_bytes, d_out, out->row_stride_bytes,
+                         px_bytes * xs, ys, cudaMemcpyDeviceToHost, s));
+  slot->check_status = false;
+  return finish_submit(ctx, slot, d_status, ticket);
 }

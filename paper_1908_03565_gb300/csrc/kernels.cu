@@ -1293,18 +1293,24 @@ __global__ void __launch_bounds__(128, 6) k_qco(const __grid_constant__ QcoArgs 
     const int cxl = 1 << (v.lw - 3), cyl = 1 << (v.lh - 3);
     const int n = cxl * cyl;
     if (n > 1) {
+      // lanes of a warp hold different shapes, so the maps are read n rows
+      // at a time (n x 16 constant loads, not 256); the clamped DC goes to
+      // the same positions of T, free after the column pass
       const int m = llf_map_index_dev(cxl, cyl) * 256;
       const int lcx = v.lw - 3;
-      float llf[16], dc[16];
+      float* tdc = &T[c][8 * v.by][8 * v.bx];
+      float llf[16];
 #pragma unroll
       for (int i = 0; i < 16; ++i) llf[i] = i < n ? s[(i >> lcx) * kRS + (i & (cxl - 1))] : 0.f;
-#pragma unroll
-      for (int i = 0; i < 16; ++i) {
+      for (int i = 0; i < n; ++i) {
         float acc = 0.f;
 #pragma unroll
         for (int j = 0; j < 16; ++j) acc = fmaf(c_box[m + i * 16 + j], llf[j], acc);
-        dc[i] = clampf(acc, t);
+        tdc[(i >> lcx) * kRS + (i & (cxl - 1))] = clampf(acc, t);
       }
+      float dc[16];
+#pragma unroll
+      for (int i = 0; i < 16; ++i) dc[i] = i < n ? tdc[(i >> lcx) * kRS + (i & (cxl - 1))] : 0.f;
       for (int j = 0; j < n; ++j) {
         float acc = 0.f;
 #pragma unroll

@@ -218,13 +218,13 @@ def shape_area_fractions(vmap):
     return {c: a / area for c, a in sorted(tot.items())}
 
 
-def make_jpeg(xsize, ysize, seed, sampling='420', gab=False):
+def make_jpeg(xsize, ysize, seed, sampling='420', gab=False, ac_scale=6.0):
     """A synthetic JPEG1 coefficient stream (the input of direct
     rasterisation).  ``sampling``: '420' (Y 2x2, Cb and Cr 1x1), '444' or
     'grey'.  Quantisation tables: 3 + 2 (u + v) for Y and 4 + 3 (u + v) for
     chroma (synthetic, index 8u + v).  Quantised DC: a slow field of
     amplitude 200 steps (period 40 blocks) plus Gaussian noise of 2 steps;
-    AC: Laplace(0, 6 / (1 + u + v)) rounded.  ``gab`` adds the block-
+    AC: Laplace(0, ac_scale / (1 + u + v)) rounded.  ``gab`` adds the block-
     conditional Gaborish side channel (w1 118/1024, w2 63/1024, threshold
     2.5, limit 20) to every component.  Returns a dict with xsize, ysize and
     components (coeffs int16 (bh, bw, 64), quant uint16 (64,), h_samp,
@@ -249,7 +249,7 @@ def make_jpeg(xsize, ysize, seed, sampling='420', gab=False):
         base = 3 if ci == 0 else 4
         step = 2 if ci == 0 else 3
         quant = (base + step * (uu + vv)).astype(np.uint16)
-        ac = rng.laplace(0.0, 1.0, size=(bh, bw, 64)) * (6.0 / (1.0 + uu + vv))
+        ac = rng.laplace(0.0, 1.0, size=(bh, bw, 64)) * (ac_scale / (1.0 + uu + vv))
         q = np.rint(ac)
         by, bx = np.mgrid[0:bh, 0:bw]
         ph = rng.uniform(0, 2 * math.pi, size=2)
