@@ -366,6 +366,9 @@ static void launch_qco_chain(const FilterArgs& fa, float* eo, const uint8_t* vma
   q.xs = fa.xs; q.ys = fa.ys; q.bw = fa.bw; q.bh = bh;
   for (int c = 0; c < 3; ++c) q.m_dc[c] = fp.m_dc[c];
   q.mul = fp.qco_interval_mul;
+  q.vec = (q.ors % 4 == 0 && q.ops % 4 == 0 && q.frs % 4 == 0 && q.fps % 4 == 0 &&
+           (reinterpret_cast<uintptr_t>(q.orig) & 15) == 0 &&
+           (reinterpret_cast<uintptr_t>(q.f) & 15) == 0) ? 1 : 0;
   launch_qco(q, s);
   FilterArgs g = fa;
   g.epf = 0;

@@ -1237,15 +1237,39 @@ __global__ void __launch_bounds__(128, 6) k_qco(const __grid_constant__ QcoArgs 
   const int px0 = gbx0 * 8, py0 = gby0 * 8;
   cell_setup(cs, a.vmap, a.acmul, gbx0, gby0, a.bw, a.bh);
 
-  // residual; zero outside the cropped image
-  for (int i = tid; i < 3 * 32 * 32; i += 128) {
-    const int c = i >> 10, y = (i >> 5) & 31, x = i & 31;
-    const int gy = py0 + y, gx = px0 + x;
-    float r = 0.f;
-    if (gy < a.ys && gx < a.xs)
-      r = a.f[c * a.fps + static_cast<size_t>(gy) * a.frs + gx] -
-          a.orig[c * a.ops + static_cast<size_t>(gy) * a.ors + gx];
-    S[c][y][x] = r;
+  // residual, zero outside the cropped image: thread (row y, chunk k) loads
+  // its 8 samples of both images in all three channels at once
+  const int cy_ = tid >> 2, ck = tid & 3;
+  const int cgy = py0 + cy_, cgx = px0 + 8 * ck;
+  const bool full = cgy < a.ys && cgx + 8 <= a.xs && a.vec;
+  if (full) {
+    float4 fv[3][2], ov[3][2];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const float4* fp = reinterpret_cast<const float4*>(a.f + c * a.fps + static_cast<size_t>(cgy) * a.frs + cgx);
+      const float4* op = reinterpret_cast<const float4*>(a.orig + c * a.ops + static_cast<size_t>(cgy) * a.ors + cgx);
+      fv[c][0] = fp[0]; fv[c][1] = fp[1];
+      ov[c][0] = __ldg(op); ov[c][1] = __ldg(op + 1);
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      float4* d = reinterpret_cast<float4*>(&S[c][cy_][8 * ck]);
+      d[0] = make_float4(fv[c][0].x - ov[c][0].x, fv[c][0].y - ov[c][0].y, fv[c][0].z - ov[c][0].z,
+                         fv[c][0].w - ov[c][0].w);
+      d[1] = make_float4(fv[c][1].x - ov[c][1].x, fv[c][1].y - ov[c][1].y, fv[c][1].z - ov[c][1].z,
+                         fv[c][1].w - ov[c][1].w);
+    }
+  } else {
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        float r = 0.f;
+        if (cgy < a.ys && cgx + j < a.xs)
+          r = a.f[c * a.fps + static_cast<size_t>(cgy) * a.frs + cgx + j] -
+              a.orig[c * a.ops + static_cast<size_t>(cgy) * a.ors + cgx + j];
+        S[c][cy_][8 * ck + j] = r;
+      }
   }
   __syncthreads();
   {
@@ -1385,12 +1409,28 @@ __global__ void __launch_bounds__(128, 6) k_qco(const __grid_constant__ QcoArgs 
     }
   }
   __syncthreads();
-  for (int i = tid; i < 3 * 32 * 32; i += 128) {
-    const int c = i >> 10, y = (i >> 5) & 31, x = i & 31;
-    const int gy = py0 + y, gx = px0 + x;
-    if (gy < a.ys && gx < a.xs && cs.owner[(y >> 3) * 4 + (x >> 3)] >= 0)
-      a.f[c * a.fps + static_cast<size_t>(gy) * a.frs + gx] =
-          a.orig[c * a.ops + static_cast<size_t>(gy) * a.ors + gx] + S[c][y][x];
+  // constrained samples: the same chunk per thread
+  if (cgy < a.ys && cs.owner[(cy_ >> 3) * 4 + ck] >= 0) {
+    if (full) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const float4* op = reinterpret_cast<const float4*>(a.orig + c * a.ops + static_cast<size_t>(cgy) * a.ors + cgx);
+        float4* fp = reinterpret_cast<float4*>(a.f + c * a.fps + static_cast<size_t>(cgy) * a.frs + cgx);
+        const float4 o0 = __ldg(op), o1 = __ldg(op + 1);
+        const float4* r = reinterpret_cast<const float4*>(&S[c][cy_][8 * ck]);
+        const float4 r0 = r[0], r1 = r[1];
+        fp[0] = make_float4(o0.x + r0.x, o0.y + r0.y, o0.z + r0.z, o0.w + r0.w);
+        fp[1] = make_float4(o1.x + r1.x, o1.y + r1.y, o1.z + r1.z, o1.w + r1.w);
+      }
+    } else {
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+          if (cgx + j < a.xs)
+            a.f[c * a.fps + static_cast<size_t>(cgy) * a.frs + cgx + j] =
+                a.orig[c * a.ops + static_cast<size_t>(cgy) * a.ors + cgx + j] + S[c][cy_][8 * ck + j];
+    }
   }
 }
 
@@ -1423,147 +1463,9 @@ void launch_sigma(const SigmaArgs& a, cudaStream_t s) {
 }
 
 // ---------------------------------------------------------------------------
-// k_filter: EPF (J.2) + Gaborish (J.4) + colour (L.2) on a 32 x 32 tile
+// Tile size of the filter kernel without the EPF (k_filter)
 // ---------------------------------------------------------------------------
 constexpr int kTW = 32, kTH = 32;
-constexpr int kGX = 5, kGY = 5;                 // halo before the tile
-constexpr int kGW = kTW + 12, kGH = kTH + 10;   // guide/sample window
-constexpr int kEW = kTW + 2, kEH = kTH + 2;     // EPF output with a 1-sample ring
-
-__device__ __forceinline__ void filter_tile(const FilterArgs& a, int tbx, int tby) {
-  __shared__ float F[3][kGH][kGW];
-  __shared__ uint32_t G[kGH][kGW];
-  __shared__ float E[3][kEH][kEW];
-  const int tid = threadIdx.x;
-  const int x0 = tbx * kTW, y0 = tby * kTH;
-  const int wx0 = x0 - kGX, wy0 = y0 - kGY;     // window origin (image coords)
-
-  // ---- load the window with mirrored coordinates (6.5) --------------------
-  for (int i = tid; i < kGH * kGW; i += blockDim.x) {
-    const int ly = i / kGW, lx = i % kGW;
-    const int gy = mirror_coord(wy0 + ly, a.ys), gx = mirror_coord(wx0 + lx, a.xs);
-    const size_t off = static_cast<size_t>(gy) * a.rstride + gx;
-    float v[3];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      v[c] = __ldg(a.xyb + c * a.pstride + off);
-      F[c][ly][lx] = v[c];
-    }
-    if (a.epf) {
-      uint32_t g = 0;
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        const float s = fminf(fmaxf(guide_scaled(a.sp, c, v[c]), 0.f), 255.f);
-        g |= static_cast<uint32_t>(s) << (8 * c);
-      }
-      G[ly][lx] = g;
-    }
-  }
-  __syncthreads();
-
-  // ---- J.2 on the tile plus a one-sample ring ------------------------------
-  const int R = a.gab ? 1 : 0;
-  if (a.epf) {
-    const int ew = kTW + 2 * R, eh = kTH + 2 * R;
-    for (int i = tid; i < ew * eh; i += blockDim.x) {
-      const int qy = i / ew - R, qx = i % ew - R;          // tile-relative
-      const int gy = y0 + qy, gx = x0 + qx;
-      if (gy >= a.ys + 1 || gx >= a.xs + 1) continue;      // beyond the ring
-      const int cy = mirror_coord(gy, a.ys), cx = mirror_coord(gx, a.xs);
-      const int ly = cy - wy0, lx = cx - wx0;              // window coords
-      const int sigma = min(max(static_cast<int>(a.sigma[(cy >> 3) * a.bw + (cx >> 3)]), 0), 672);
-      float rx, ry, rb;
-      if (sigma < 16) {
-        rx = F[0][ly][lx]; ry = F[1][ly][lx]; rb = F[2][ly][lx];
-      } else {
-        const int M = 16 * c_mul4[sigma];
-        uint32_t own[3][4];
-#pragma unroll
-        for (int iy = 0; iy < 3; ++iy)
-#pragma unroll
-          for (int ix = 0; ix < 4; ++ix) own[iy][ix] = G[ly + iy - 1][lx + ix - 1];
-        float ax = 0.f, ay = 0.f, ab = 0.f, ws = 0.f;
-#pragma unroll 1
-        for (int oy = -3; oy <= 3; ++oy) {
-          uint32_t sad[8];
-#pragma unroll
-          for (int o = 0; o < 8; ++o) sad[o] = 0;
-#pragma unroll
-          for (int iy = 0; iy < 3; ++iy) {
-            const uint32_t* row = &G[ly + oy + iy - 1][lx - 4];
-            uint32_t r[11];
-#pragma unroll
-            for (int j = 0; j < 11; ++j) r[j] = row[j];
-#pragma unroll
-            for (int o = 0; o < 8; ++o)
-#pragma unroll
-              for (int ix = 0; ix < 4; ++ix)
-                sad[o] = __dp4a(__vabsdiffu4(own[iy][ix], r[o + ix]), 0x01010101u, sad[o]);
-          }
-#pragma unroll
-          for (int o = 0; o < 8; ++o) {
-            const int s = min(static_cast<int>(sad[o]), 507);
-            uint32_t bits = (0x3F800000u + static_cast<uint32_t>(s * M)) & 0xFFFF0000u;
-            if (bits < a.wmin_bits) bits = 0;
-            const float w = __uint_as_float(bits);
-            const int sy = ly + oy, sx = lx + o - 3;
-            ax = fmaf(w, F[0][sy][sx], ax);
-            ay = fmaf(w, F[1][sy][sx], ay);
-            ab = fmaf(w, F[2][sy][sx], ab);
-            ws += w;
-          }
-        }
-        const float inv = 1.f / ws;
-        rx = ax * inv; ry = ay * inv; rb = ab * inv;
-      }
-      E[0][qy + R][qx + R] = rx;
-      E[1][qy + R][qx + R] = ry;
-      E[2][qy + R][qx + R] = rb;
-    }
-    __syncthreads();
-  }
-
-  // ---- J.4 Gaborish + L.2 + store: 4 pixels per item ----------------------
-  for (int i = tid; i < kTH * (kTW / 4); i += blockDim.x) {
-    const int ty = i / (kTW / 4), tx = 4 * (i % (kTW / 4));
-    const int gy = y0 + ty, gx = x0 + tx;
-    if (gy >= a.ys || gx >= a.xs) continue;
-    const int n = min(4, a.xs - gx);
-    float X[4], Y[4], B[4];
-    float* dst[3] = {X, Y, B};
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        float v;
-        if (a.gab) {
-          // source sample (dy, dx) around the pixel, mirrored at the image
-          // border (J.4); E holds the ring, F the unfiltered window
-          float acc = 0.f;
-#pragma unroll
-          for (int dy = -1; dy <= 1; ++dy) {
-#pragma unroll
-            for (int dx = -1; dx <= 1; ++dx) {
-              const int wgt = (dx != 0) + (dy != 0);
-              float sv;
-              // F already holds mirrored samples at window coordinates
-              sv = a.epf ? E[c][ty + dy + 1][tx + j + dx + 1]
-                         : F[c][ty + dy + kGY][tx + j + dx + kGX];
-              acc = fmaf(a.gw[c][wgt], sv, acc);
-            }
-          }
-          v = acc;
-        } else if (a.epf) {
-          v = E[c][ty][tx + j];
-        } else {
-          v = F[c][ty + kGY][tx + j + kGX];
-        }
-        dst[c][j] = v;
-      }
-    }
-    emit4(a.cp, a.out, gx, gy, n, X, Y, B);
-  }
-}
 
 // ---------------------------------------------------------------------------
 // k_epf: J.2 with shared per-offset patch sums, then J.4 + L.2 (30x30 tile)
@@ -1830,6 +1732,74 @@ __device__ __forceinline__ void epf_tile(const FilterArgs& a, int tbx, int tby) 
   }
 }
 
+// ---------------------------------------------------------------------------
+// J.4 Gaborish (optional) + L.2 + store without the EPF: 32x32 tile, 256
+// threads.  The tile and a one-sample ring (mirrored at the image bounds,
+// 6.5) are loaded with all of a thread's loads in flight; each thread then
+// walks 4 rows of one column, 3 shared loads per pixel and channel.
+// ---------------------------------------------------------------------------
+constexpr int kGT = 32, kGR = kGT + 2, kGS2 = kGR + 1;
+
+__device__ __forceinline__ void gab_tile(const FilterArgs& a, int tbx, int tby) {
+  __shared__ float Wn[3][kGR][kGS2];
+  const int tid = threadIdx.x;
+  const int x0 = tbx * kGT, y0 = tby * kGT;
+  const bool inner = x0 >= 1 && y0 >= 1 && x0 + kGT + 1 <= a.xs && y0 + kGT + 1 <= a.ys;
+  constexpr int kN = kGR * kGR, kPer = (kN + 255) / 256;
+  float v[kPer][3];
+#pragma unroll
+  for (int j = 0; j < kPer; ++j) {
+    const int i = tid + 256 * j;
+    if (i < kN) {
+      const int ly = i / kGR, lx = i - ly * kGR;
+      const int gy = inner ? y0 - 1 + ly : mirror_coord(y0 - 1 + ly, a.ys);
+      const int gx = inner ? x0 - 1 + lx : mirror_coord(x0 - 1 + lx, a.xs);
+      const size_t off = static_cast<size_t>(gy) * a.rstride + gx;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) v[j][c] = __ldg(a.xyb + c * a.pstride + off);
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < kPer; ++j) {
+    const int i = tid + 256 * j;
+    if (i < kN) {
+      const int ly = i / kGR, lx = i - ly * kGR;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) Wn[c][ly][lx] = v[j][c];
+    }
+  }
+  __syncthreads();
+  const int tx = tid & 31, ty0 = (tid >> 5) * 4;
+  const int gx = x0 + tx;
+  if (gx >= a.xs) return;
+  float bp[3], sp[3], bc[3], sc[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    bp[c] = Wn[c][ty0][tx + 1];
+    sp[c] = Wn[c][ty0][tx] + Wn[c][ty0][tx + 2];
+    bc[c] = Wn[c][ty0 + 1][tx + 1];
+    sc[c] = Wn[c][ty0 + 1][tx] + Wn[c][ty0 + 1][tx + 2];
+  }
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const int ty = ty0 + r, gy = y0 + ty;
+    if (gy >= a.ys) break;
+    float o[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const float bn = Wn[c][ty + 2][tx + 1];
+      const float sn = Wn[c][ty + 2][tx] + Wn[c][ty + 2][tx + 2];
+      o[c] = a.gab ? fmaf(a.gw[c][0], bc[c],
+                          fmaf(a.gw[c][1], bp[c] + bn + sc[c], a.gw[c][2] * (sp[c] + sn)))
+                   : bc[c];
+      bp[c] = bc[c]; sp[c] = sc[c];
+      bc[c] = bn; sc[c] = sn;
+    }
+    float X[4] = {o[0], 0.f, 0.f, 0.f}, Y[4] = {o[1], 0.f, 0.f, 0.f}, B[4] = {o[2], 0.f, 0.f, 0.f};
+    emit4(a.cp, a.out, gx, gy, 1, X, Y, B);
+  }
+}
+
 // True when Weight()'s clamp of sad at 507 can change a weight that survives
 // the cut-off, for some sigma the request can produce.
 static bool epf_needs_clamp(const FilterArgs& a, const int32_t* mul4) {
@@ -1845,7 +1815,7 @@ static bool epf_needs_clamp(const FilterArgs& a, const int32_t* mul4) {
 }
 
 __global__ void __launch_bounds__(256) k_filter(const __grid_constant__ FilterArgs a) {
-  filter_tile(a, blockIdx.x, blockIdx.y);
+  gab_tile(a, blockIdx.x, blockIdx.y);
 }
 
 template <bool kClamp>
@@ -1880,7 +1850,7 @@ __global__ void __launch_bounds__(kEpf ? 128 : 256, kEpf ? 4 : 1)
     const int local = w - prefix[img];
     const int tw = kEpf ? (sa.xs + kET - 1) / kET : (sa.xs + kTW - 1) / kTW;
     if (kEpf) epf_tile<kClamp>(sa, local % tw, local / tw);
-    else filter_tile(sa, local % tw, local / tw);
+    else gab_tile(sa, local % tw, local / tw);
   }
 }
 

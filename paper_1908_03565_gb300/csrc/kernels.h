@@ -91,6 +91,7 @@ struct QcoArgs {
   int xs, ys, bw, bh;
   float m_dc[3];
   float mul;                  // qco_interval_mul
+  int vec;                    // 1: both images allow 16-byte accesses of 8-sample chunks
 };
 
 void launch_validate(const uint8_t* vmap, int bw, int bh, unsigned* status, cudaStream_t s);
