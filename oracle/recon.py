@@ -60,6 +60,8 @@ class Params:
         self.lf_predict = False       # Annex H AC prediction
         self.qco = False              # J.3 quantization constraint (with EPF)
         self.qco_interval_mul = T.QCO_INTERVAL_MUL
+        self.noise = False            # K.5 noise synthesis
+        self.noise_lut = (0.0,) * 16  # C.4.8 LUT (u(10) / 1024 each)
         for k, v in kw.items():
             if not hasattr(self, k):
                 raise KeyError(k)
@@ -669,4 +671,7 @@ def reconstruct(inp, params, diag=None):
             img = qco(img, xyb, inp['vmap'], inp['acmul'], params)
     if params.gab:
         img = gaborish(img, params)
+    if params.noise:                  # K.5, after Gaborish (9.12 ordering)
+        from . import noise as NZ
+        img = NZ.add_noise(img, params.noise_lut)
     return {'xyb_padded': xyb, 'xyb': img, 'rgb01': xyb_to_linear01(img, params)}
