@@ -268,8 +268,8 @@ def precision_leg(binding, torch, steps, sample=1024):
 def extra_steps_leg(binding, torch, steps):
     """Cost of the optional steps on a 4096x4096 image with a smooth DC
     field: the same step (EPF + Gaborish, f32 out) plain, with F.2 adaptive
-    DC smoothing, with F.2 + Annex H AC prediction, and with the J.3
-    quantization constraint.  CUDA events over the timed steps; the recon
+    DC smoothing, with F.2 + Annex H AC prediction, with the J.3
+    quantization constraint, and with K.5 noise (constant LUT 0.5).  CUDA events over the timed steps; the recon
     stage includes the DC-domain kernels, the filter stage the J.3 chain."""
     from paper_1908_03565_gb300 import synth
     img = synth.make_image(XS, YS, SEED + 5, dc='smooth')
@@ -279,9 +279,11 @@ def extra_steps_leg(binding, torch, steps):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     res = {}
     with binding.Context(stream=stream.cuda_stream, timing=True) as ctx:
-        for name, sm, lf, qc in (("plain", 0, 0, 0), ("dc_smooth", 1, 0, 0),
-                                 ("dc_smooth+lf_predict", 1, 1, 0), ("qco", 0, 0, 1)):
-            p = binding.filter_defaults(epf=1, gab=1, dc_smooth=sm, lf_predict=lf, qco=qc)
+        for name, sm, lf, qc, nz in (("plain", 0, 0, 0, 0), ("dc_smooth", 1, 0, 0, 0),
+                                     ("dc_smooth+lf_predict", 1, 1, 0, 0), ("qco", 0, 0, 1, 0),
+                                     ("noise", 0, 0, 0, 1)):
+            p = binding.filter_defaults(epf=1, gab=1, dc_smooth=sm, lf_predict=lf, qco=qc,
+                                        noise=nz, noise_lut=[0.5] * 16)
             for _ in range(3):
                 ctx.poll(ctx.submit(dimg, p, out, binding.OUT_F32_LINEAR, on_device=True))
             stream.synchronize()
@@ -301,6 +303,38 @@ def extra_steps_leg(binding, torch, steps):
                          "mpx_s": round(XS * YS / ms / 1e3, 1),
                          "launches_per_step": (ctx.launch_count() - l0) / steps}
     res["input"] = f"{XS}x{YS} mixed varblocks, smooth DC field (synth dc='smooth')"
+    return res
+
+
+def epf_off_leg(binding, torch, steps, peak_gbs):
+    """The same 4096x4096 image without the EPF: no loop filter (the
+    reconstruction kernel writes linear RGB directly) and Gaborish only
+    (reconstruction to XYB, then Gaborish + colour), f32 and u8 out;
+    algorithmic bytes per pixel 6.0957 in + 12 (f32) or 3 (u8) out."""
+    from paper_1908_03565_gb300 import synth
+    img = synth.make_image(XS, YS, SEED)
+    dimg = binding.to_device(img, torch)
+    stream = torch.cuda.Stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    res = {}
+    with binding.Context(stream=stream.cuda_stream, timing=True) as ctx:
+        for name, gab, dt, tdt, ob in (("no_filter_f32", 0, binding.OUT_F32_LINEAR, torch.float32, 12),
+                                       ("no_filter_u8", 0, binding.OUT_U8_SRGB, torch.uint8, 3),
+                                       ("gaborish_f32", 1, binding.OUT_F32_LINEAR, torch.float32, 12)):
+            out = torch.empty((YS, XS, 3), dtype=tdt, device="cuda")
+            p = binding.filter_defaults(gab=gab)
+            for _ in range(3):
+                ctx.poll(ctx.submit(dimg, p, out, dt, on_device=True))
+            stream.synchronize()
+            e0.record(stream)
+            for _ in range(steps):
+                ctx.poll(ctx.submit(dimg, p, out, dt, on_device=True))
+            e1.record(stream)
+            stream.synchronize()
+            ms = e0.elapsed_time(e1) / steps
+            gbs = XS * YS * (IN_BPP + ob) / (ms * 1e-3) / 1e9
+            res[name] = {"ms_per_step": round(ms, 4), "mpx_s": round(XS * YS / ms / 1e3, 1),
+                         "algorithmic_gbs": round(gbs, 1), "hbm_frac": round(gbs / peak_gbs, 4)}
     return res
 
 
@@ -512,6 +546,9 @@ def main():
     dclf = None
     if rank == 0 and args.extra_steps > 0:
         dclf = extra_steps_leg(binding, torch, args.extra_steps)
+    epf_off = None
+    if rank == 0 and args.extra_steps > 0:
+        epf_off = epf_off_leg(binding, torch, args.extra_steps, hbm_peak)
     jpeg = None
     if rank == 0 and args.jpeg_steps > 0:
         jpeg = jpeg1_leg(binding, torch, args.jpeg_steps, hbm_peak)
@@ -544,7 +581,7 @@ def main():
                          "recon_gbs": round(recon_gbs, 1)},
             "peaks": peak_kind,
             "clocks": clocks, "e2e": e2e, "gpu_launches": int(launches),
-            "cpu_baseline": cb, "precision": precision, "extra_steps": dclf, "jpeg1": jpeg, "batched": batched, "served": served,
+            "cpu_baseline": cb, "precision": precision, "extra_steps": dclf, "epf_off": epf_off, "jpeg1": jpeg, "batched": batched, "served": served,
         }
         print(json.dumps(line), flush=True)
     ctx.close()

@@ -147,6 +147,11 @@ typedef struct {
    * +-qco_interval_mul times its interval (C.10: default 0.5). */
   int qco;
   float qco_interval_mul;
+  /* K.5 noise synthesis after Gaborish (kNoise): 1 adds the noise of each
+   * 256 x 256 group with the strength LUT of C.4.8 (16 entries, the decoded
+   * u(10) / 1024 values). */
+  int noise;
+  float noise_lut[16];
 } jxl_recon_filter_params;
 
 /* Caller-owned output buffer of ysize rows, row_stride_bytes apart. */
@@ -160,7 +165,7 @@ typedef struct {
 
 /* Fills *p with the defaults of C.10, C.4.1 (m_DC of the synthetic
  * workloads: (0.02, 0.2, 0.2) / (64 sqrt 2)) and L.2; both filters, DC
- * smoothing, AC prediction and the quantization constraint off. */
+ * smoothing, AC prediction, the quantization constraint and noise off. */
 void jxl_recon_filter_defaults(jxl_recon_filter_params* p);
 
 /* Creates a context on config->device: builds the constant tables (C.6.1

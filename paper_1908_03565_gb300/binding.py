@@ -55,7 +55,8 @@ class FilterParams(ctypes.Structure):
                 ("opsin_bias", ctypes.c_float * 3), ("target_nits_div50", ctypes.c_uint32),
                 ("dequant", ctypes.c_void_p), ("dc_smooth", ctypes.c_int),
                 ("lf_predict", ctypes.c_int), ("qco", ctypes.c_int),
-                ("qco_interval_mul", ctypes.c_float)]
+                ("qco_interval_mul", ctypes.c_float), ("noise", ctypes.c_int),
+                ("noise_lut", ctypes.c_float * 16)]
 
 
 class JpegComponent(ctypes.Structure):

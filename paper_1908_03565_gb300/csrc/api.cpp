@@ -19,6 +19,7 @@
 #include "kernels.h"
 #include "jpeg1.h"
 #include "lf.h"
+#include "noise.h"
 
 using namespace jxlr;
 
@@ -176,6 +177,12 @@ jxlr_status jxl_recon_create(const jxl_recon_config* cfg, jxl_recon_ctx** out) {
       for (int j = 0; j < 2; ++j)
         odd4[n * 2 + j] = static_cast<float>(std::cos((2 * n + 1) * (2 * j + 1) * pi / 8.0));
     if (!upload_jpeg_constants(odd8, odd4, static_cast<float>(std::cos(pi / 4.0))))
+      return fail(JXLR_ECUDA, "create: constant upload failed");
+  }
+  {
+    std::vector<uint64_t> jump(kNoiseJumpLevels * 256);
+    noise_jump_tables(jump.data());
+    if (!upload_noise_constants(jump.data()))
       return fail(JXLR_ECUDA, "create: constant upload failed");
   }
 
@@ -341,6 +348,22 @@ jxlr_status finish_submit(jxl_recon_ctx* ctx, Slot* slot, unsigned* d_status, ui
 
 }  // namespace
 
+// K.5.2 channels of every group into r ([3][ys][xs]); fa reads them.
+static int setup_noise(FilterArgs& fa, float* r, cudaStream_t s) {
+  NoiseGenArgs na;
+  na.r = r;
+  na.rs = fa.xs;
+  na.ps = static_cast<size_t>(fa.xs) * fa.ys;
+  na.xs = fa.xs;
+  na.ys = fa.ys;
+  na.ngx = (fa.xs + 255) / 256;
+  na.ngy = (fa.ys + 255) / 256;
+  fa.noise_r = r;
+  fa.nrs = na.rs;
+  fa.nps = na.ps;
+  return launch_noise_gen(na, s);
+}
+
 // J.2 into eo, J.3 in place on eo, then J.4 / L.2 from eo (three launches).
 // fa: the filter arguments of the plain path (EPF on); orig = fa.xyb.
 static void launch_qco_chain(const FilterArgs& fa, float* eo, const uint8_t* vmap,
@@ -416,7 +439,7 @@ extern "C" jxlr_status jxl_recon_submit(jxl_recon_ctx* ctx, const jxl_recon_coef
     dq_scaled.resize(kDequantFloats);
     prescale_dequant(fp->dequant, dq_scaled.data());
   }
-  const bool filters = fp->epf || fp->gab;
+  const bool filters = fp->epf || fp->gab || fp->noise;
 
   // ---- scratch layout ----
   const size_t cstride = wp;
@@ -445,6 +468,7 @@ extern "C" jxlr_status jxl_recon_submit(jxl_recon_ctx* ctx, const jxl_recon_coef
   }
   const bool qco = fp->epf && fp->qco;
   if (qco) add(sizeof(float) * 3 * wp * hp);         // EPF output for J.3
+  if (fp->noise) add(sizeof(float) * 3 * static_cast<size_t>(xs) * ys);   // K.5.2 channels
   const size_t out_bytes = out->row_stride_bytes * (ys - 1) + px_bytes * xs;
   if (!out->on_device) add(out_bytes);
   need = align_up(need, 256);
@@ -578,6 +602,7 @@ extern "C" jxlr_status jxl_recon_submit(jxl_recon_ctx* ctx, const jxl_recon_coef
     fa.xs = xs; fa.ys = ys; fa.bw = bw;
     fa.sigma = sig;
     fa.out = op;
+    if (fp->noise) ctx->launches += setup_noise(fa, cv.take<float>(3 * static_cast<size_t>(xs) * ys), s);
     if (qco) {
       float* eo = cv.take<float>(static_cast<size_t>(3) * wp * hp);
       launch_qco_chain(fa, eo, ra.vmap, ra.acmul, ra.dequant, bh, *fp, s);
@@ -622,6 +647,7 @@ extern "C" jxlr_status jxl_recon_submit_xyb(jxl_recon_ctx* ctx, const float* xyb
     return fail(JXLR_EINVAL, "submit_xyb: the quantization constraint uses the default matrices here");
   size_t need = 256 + (fp->epf ? align_up(sizeof(int16_t) * bw * bh, 256) : 0);
   if (qco) need += align_up(sizeof(float) * 3 * 64 * static_cast<size_t>(bw) * bh, 256);
+  if (fp->noise) need += align_up(sizeof(float) * 3 * static_cast<size_t>(xs) * ys, 256);
   std::lock_guard<std::mutex> lock(ctx->mu);
   CK(cudaSetDevice(ctx->device));
   Slot* slot = nullptr;
@@ -666,6 +692,7 @@ extern "C" jxlr_status jxl_recon_submit_xyb(jxl_recon_ctx* ctx, const float* xyb
   fa.out.data = out->data;
   fa.out.stride = out->row_stride_bytes;
   fa.out.dtype = out->dtype;
+  if (fp->noise) ctx->launches += setup_noise(fa, cv.take<float>(3 * static_cast<size_t>(xs) * ys), s);
   if (qco) {
     float* eo = cv.take<float>(static_cast<size_t>(3) * 64 * bw * bh);
     launch_qco_chain(fa, eo, vmap, qf, ctx->d_dequant, bh, *fp, s);

@@ -199,8 +199,8 @@ extern "C" jxlr_status jxl_recon_batch_create(jxl_recon_ctx* ctx, const jxl_reco
     if (o->dtype < 0 || o->dtype > 3 || !o->data || o->row_stride_bytes < px_bytes * xs)
       return bfail(JXLR_EINVAL, "batch_create: bad output");
     if (fp->epf && !fp->sharpness) return bfail(JXLR_EINVAL, "batch_create: EPF needs sharpness");
-    if (fp->dc_smooth || fp->lf_predict || (fp->epf && fp->qco))
-      return bfail(JXLR_EINVAL, "batch_create: DC smoothing, AC prediction and the quantization constraint run on the submit path only");
+    if (fp->dc_smooth || fp->lf_predict || (fp->epf && fp->qco) || fp->noise)
+      return bfail(JXLR_EINVAL, "batch_create: DC smoothing, AC prediction and the quantization constraint run on the submit path only (so does noise)");
     pixels += uint64_t(xs) * ys;
     ReconArgs& a = ra[i];
     std::memset(&a, 0, sizeof(a));

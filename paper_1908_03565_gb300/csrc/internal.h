@@ -66,6 +66,12 @@ constexpr int kLfUpFloats = 42;
 constexpr int kLfInvFloats = 84;
 void lf_tables(float* up, float* inv, float* half);
 
+// K.5 generator jumps: for level b in [0, kNoiseJumpLevels), the 128 x 128
+// GF(2) matrix of 2^b steps of one generator's state (s0 bits 0..63, then
+// s1 bits 0..63), as 128 columns of (s0, s1) words.
+constexpr int kNoiseJumpLevels = 14;
+void noise_jump_tables(uint64_t* out /* kNoiseJumpLevels * 256 */);
+
 // 4 * mul_table[sigma] of J.2.4 for sigma in [0, 672]; entries below 16 are 0.
 void mul_table4(int32_t* out /* 673 */);
 

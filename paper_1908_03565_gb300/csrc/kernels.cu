@@ -1468,6 +1468,43 @@ void launch_sigma(const SigmaArgs& a, cudaStream_t s) {
 constexpr int kTW = 32, kTH = 32;
 
 // ---------------------------------------------------------------------------
+// K.5.3 additive noise at image pixel (x, y): the K.5.2 channels convolved
+// with the 5x5 Laplacian-like kernel (mirrored at the bounds of the pixel's
+// 256 x 256 group), scaled by 0.22, modulated by the LUT strength of
+// Y + X and Y - X.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float noise_strength(const float* lut, float v) {
+  const float sc = v * 14.f;
+  const float fi = floorf(sc);
+  const float fr = sc - fi;
+  const int i = static_cast<int>(fminf(fmaxf(fi, 0.f), 14.f));
+  return fminf(fmaxf(fmaf(lut[i + 1], fr, lut[i] * (1.f - fr)), 0.f), 1.f);
+}
+
+__device__ void apply_noise(const FilterArgs& a, int x, int y, float& X, float& Y, float& B) {
+  const int gx0 = x & ~255, gy0 = y & ~255;
+  const int gw = min(256, a.xs - gx0), gh = min(256, a.ys - gy0);
+  const int lx = x - gx0, ly = y - gy0;
+  const int xm = gx0 + mirror_coord(lx - 2, gw), xp = gx0 + mirror_coord(lx + 2, gw);
+  const int ym = gy0 + mirror_coord(ly - 2, gh), yp = gy0 + mirror_coord(ly + 2, gh);
+  float A[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const float* r = a.noise_r + c * a.nps;
+    const float* row = r + static_cast<size_t>(y) * a.nrs;
+    const float lap = (row[xm] + row[xp]) + (r[static_cast<size_t>(ym) * a.nrs + x] +
+                                             r[static_cast<size_t>(yp) * a.nrs + x]) - 4.f * row[x];
+    A[c] = 0.22f * lap;
+  }
+  const float sr = noise_strength(a.noise_lut, Y + X), sg = noise_strength(a.noise_lut, Y - X);
+  const float nr = fmaf(0.01f * A[0], sr, 0.99f * A[2] * sr);
+  const float ng = fmaf(0.01f * A[1], sg, 0.99f * A[2] * sg);
+  X += nr - ng;
+  Y += nr + ng;
+  B = fmaf(0.935669f, nr + ng, B);
+}
+
+// ---------------------------------------------------------------------------
 // k_epf: J.2 with shared per-offset patch sums, then J.4 + L.2 (30x30 tile)
 //
 // The 3x4 patch SAD of J.2.3 is a box sum of the per-offset distance image
@@ -1726,6 +1763,7 @@ __device__ __forceinline__ void epf_tile(const FilterArgs& a, int tbx, int tby) 
         }
         float X[4] = {v[0], 0.f, 0.f, 0.f}, Y[4] = {v[1], 0.f, 0.f, 0.f};
         float B[4] = {v[2], 0.f, 0.f, 0.f};
+        if (a.noise) apply_noise(a, gx, gy, X[0], Y[0], B[0]);
         emit4(a.cp, a.out, gx, gy, 1, X, Y, B);
       }
     }
@@ -1796,6 +1834,7 @@ __device__ __forceinline__ void gab_tile(const FilterArgs& a, int tbx, int tby) 
       bc[c] = bn; sc[c] = sn;
     }
     float X[4] = {o[0], 0.f, 0.f, 0.f}, Y[4] = {o[1], 0.f, 0.f, 0.f}, B[4] = {o[2], 0.f, 0.f, 0.f};
+    if (a.noise) apply_noise(a, gx, gy, X[0], Y[0], B[0]);
     emit4(a.cp, a.out, gx, gy, 1, X, Y, B);
   }
 }

@@ -77,6 +77,10 @@ struct FilterArgs {
   OutParams out;
   float* epf_out;             // non-null: write the EPF result here (planar XYB,
   size_t ors, ops;            // row / plane stride in elements) and stop before J.4
+  int noise;                  // K.5 after J.4: channels noise_r [3][ys][nrs]
+  const float* noise_r;
+  size_t nrs, nps;
+  float noise_lut[16];
 };
 
 // J.3 on the EPF output f, in place, with the EPF input orig (planar XYB).

@@ -128,7 +128,7 @@ extern "C" jxlr_status jxl_recon_run_noalloc(const jxl_recon_coeffs* co, const u
     return noalloc_fail(JXLR_EINVAL, "run_noalloc: output stride too small");
   if (fp->epf && !fp->sharpness)
     return noalloc_fail(JXLR_EINVAL, "run_noalloc: EPF needs the sharpness map");
-  if (fp->dc_smooth || fp->lf_predict || (fp->epf && fp->qco))
+  if (fp->dc_smooth || fp->lf_predict || (fp->epf && fp->qco) || fp->noise)
     return noalloc_fail(JXLR_EINVAL, "run_noalloc: DC smoothing, AC prediction and the quantization constraint run on the submit path only");
 
   int dev = 0;

@@ -55,6 +55,8 @@ FilterArgs filter_args(const jxl_recon_filter_params& p) {
   f.wmin_bits = weight_min_bits(p.epf_weight_min);
   f.sp = sigma_params(p);
   f.cp = color_params(p);
+  f.noise = p.noise != 0;
+  for (int k = 0; k < 16; ++k) f.noise_lut[k] = p.noise_lut[k];
   return f;
 }
 

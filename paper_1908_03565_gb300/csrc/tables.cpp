@@ -462,6 +462,44 @@ void lf_tables(float* up, float* inv, float* half) {
   *half = static_cast<float>(1.0 / cos_mean(8, 1, 0, 4));
 }
 
+namespace {
+// One step of the K.5 generator's state (the two words exchanged, then the
+// printed xorshift update); linear over GF(2).
+void noise_state_step(uint64_t& s0, uint64_t& s1) {
+  const uint64_t a = s1;
+  uint64_t b = s0;
+  b ^= b << 23;
+  b ^= a ^ (b >> 18) ^ (a >> 5);
+  s0 = a;
+  s1 = b;
+}
+}  // namespace
+
+void noise_jump_tables(uint64_t* out) {
+  // level 0: the images of the 128 basis vectors under one step
+  std::vector<uint64_t> cur(256), nxt(256);
+  for (int j = 0; j < 128; ++j) {
+    uint64_t s0 = j < 64 ? (1ULL << j) : 0, s1 = j < 64 ? 0 : (1ULL << (j - 64));
+    noise_state_step(s0, s1);
+    cur[2 * j] = s0;
+    cur[2 * j + 1] = s1;
+  }
+  for (int lv = 0; lv < kNoiseJumpLevels; ++lv) {
+    std::memcpy(out + lv * 256, cur.data(), sizeof(uint64_t) * 256);
+    // square: column j of M^2 is M applied to column j of M
+    for (int j = 0; j < 128; ++j) {
+      uint64_t r0 = 0, r1 = 0;
+      for (int k = 0; k < 128; ++k) {
+        const uint64_t bit = k < 64 ? (cur[2 * j] >> k) & 1 : (cur[2 * j + 1] >> (k - 64)) & 1;
+        if (bit) { r0 ^= cur[2 * k]; r1 ^= cur[2 * k + 1]; }
+      }
+      nxt[2 * j] = r0;
+      nxt[2 * j + 1] = r1;
+    }
+    cur.swap(nxt);
+  }
+}
+
 int llf_map_index(int cx, int cy) {
   // (cx, cy) in {1,2,4}^2 minus (1,1) and (1,... ) combinations that occur
   if (cx == 2 && cy == 2) return 0;
