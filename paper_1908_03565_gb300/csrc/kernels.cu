@@ -180,7 +180,10 @@ __device__ __forceinline__ void xyb_to_rgb01(const ColorParams& cp, float X, flo
 
 __device__ __forceinline__ uint32_t srgb8(float v) {
   float x = fminf(fmaxf(v, 0.f), 1.f);
-  float e = x <= 0.0031308f ? 12.92f * x : fmaf(1.055f, powf(x, 1.f / 2.4f), -0.055f);
+  // x^(1/2.4) as exp2(log2(x) / 2.4) with the hardware approximations: a
+  // few ulps, far inside the 8-bit step
+  float e = x <= 0.0031308f ? 12.92f * x
+                            : fmaf(1.055f, exp2f(__log2f(x) * (1.f / 2.4f)), -0.055f);
   return static_cast<uint32_t>(floorf(fmaf(e, 255.f, 0.5f)));
 }
 
@@ -1532,7 +1535,7 @@ constexpr int kWW = 42, kWH = 40;        // sample / guide window, origin (x0-5,
 constexpr int kGS = 49;                  // guide row stride (words), = 17 mod 32: the
                                          // 8 rows x 4 runs a warp reads hit 32 banks
 
-template <bool kClamp>
+template <bool kClamp, bool kNoise = false>
 __device__ __forceinline__ void epf_tile(const FilterArgs& a, int tbx, int tby) {
   __shared__ float F[3][kWH][kWW];
   __shared__ uint32_t G[kWH][kGS];
@@ -1763,7 +1766,7 @@ __device__ __forceinline__ void epf_tile(const FilterArgs& a, int tbx, int tby) 
         }
         float X[4] = {v[0], 0.f, 0.f, 0.f}, Y[4] = {v[1], 0.f, 0.f, 0.f};
         float B[4] = {v[2], 0.f, 0.f, 0.f};
-        if (a.noise) apply_noise(a, gx, gy, X[0], Y[0], B[0]);
+        if (kNoise) apply_noise(a, gx, gy, X[0], Y[0], B[0]);
         emit4(a.cp, a.out, gx, gy, 1, X, Y, B);
       }
     }
@@ -1857,9 +1860,9 @@ __global__ void __launch_bounds__(256) k_filter(const __grid_constant__ FilterAr
   gab_tile(a, blockIdx.x, blockIdx.y);
 }
 
-template <bool kClamp>
+template <bool kClamp, bool kNoise>
 __global__ void __launch_bounds__(128, 4) k_epf(const __grid_constant__ FilterArgs a) {
-  epf_tile<kClamp>(a, blockIdx.x, blockIdx.y);
+  epf_tile<kClamp, kNoise>(a, blockIdx.x, blockIdx.y);
 }
 
 // Multi-image forms of the two filter kernels (tiles in raster order per
@@ -1918,8 +1921,10 @@ static void prefer_shared_carveout() {
   cudaFuncSetAttribute(k_recon_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        static_cast<int>(sizeof(TcShared) + 1024));
   cudaFuncSetAttribute(k_recon_batch, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
-  cudaFuncSetAttribute(k_epf<false>, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
-  cudaFuncSetAttribute(k_epf<true>, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+  cudaFuncSetAttribute(k_epf<false, false>, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+  cudaFuncSetAttribute(k_epf<true, false>, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+  cudaFuncSetAttribute(k_epf<false, true>, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+  cudaFuncSetAttribute(k_epf<true, true>, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
   cudaFuncSetAttribute(k_filter_batch<true, false>, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
   cudaFuncSetAttribute(k_filter_batch<true, true>, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
   cudaFuncSetAttribute(k_filter, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
@@ -1952,8 +1957,14 @@ void launch_filter(const FilterArgs& a, cudaStream_t s) {
       return t;
     }();
     dim3 grid((a.xs + kET - 1) / kET, (a.ys + kET - 1) / kET);
-    if (epf_needs_clamp(a, mul4.data())) k_epf<true><<<grid, 128, 0, s>>>(a);
-    else k_epf<false><<<grid, 128, 0, s>>>(a);
+    const bool clamp = epf_needs_clamp(a, mul4.data());
+    if (a.noise) {
+      if (clamp) k_epf<true, true><<<grid, 128, 0, s>>>(a);
+      else k_epf<false, true><<<grid, 128, 0, s>>>(a);
+    } else {
+      if (clamp) k_epf<true, false><<<grid, 128, 0, s>>>(a);
+      else k_epf<false, false><<<grid, 128, 0, s>>>(a);
+    }
     return;
   }
   dim3 grid((a.xs + kTW - 1) / kTW, (a.ys + kTH - 1) / kTH);
