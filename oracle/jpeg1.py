@@ -13,9 +13,19 @@ Steps, per component, then per pixel:
 
 Coefficients are given per component as ``coeffs[by][bx][64]`` in the
 natural order of M.6.1 (index 8u + v: u the vertical, v the horizontal
-frequency).  The DC/AC conditioning of M.6.1.1 is optional in the draft
-("the decoder can choose") and is not performed.  The HDR colour-space
-transform of M.6.5.1 is outside this path.
+frequency).  The DC/AC conditioning of M.6.1.1 runs when a component
+carries ``cond = (max_gap, min_step)``.  The HDR colour-space transform of
+M.6.5.1 is outside this path.
+
+READINGS (M.6.1.1): the garbled indices dc(y, start), ac_h(x, start - 1) and
+has_v[v, u] are dc(start, y), ac_h(start - 1, y) and has_v[x, y]; the bullet
+"abs(to - from) > min_step" is a third condition of is_sane;
+dc_multiplier is Q[0] I(8, 0) I(8, 0) for the three replaced coefficients
+(it is defined once, before the loop; with it a slope of -delta/2 per block
+makes the block's samples change by about delta across its width).  The
+plateau arithmetic (from, to, the sanity tests, the interpolation) is done
+in binary32, operation by operation, as in the kernels, because its
+comparisons decide which coefficients are replaced.
 """
 import numpy as np
 
@@ -33,14 +43,82 @@ def dequantize_block(src, quant):
     return out
 
 
-def component_pixels(coeffs, quant):
-    """M.6.1 + M.6.2: the component's sample plane (8 bh, 8 bw); values are
-    level-shifted (about -128..127)."""
+def _plateaus(dc, ac, q_ratio, max_gap, min_step):
+    """M.6.1.1 along the rows of dc / ac ((n, m) int arrays; rows are
+    independent): approximations, slopes and the flags, binary32."""
+    f32 = np.float32
+    n, m = dc.shape
+    approx = np.zeros((n, m), f32)
+    slope = np.zeros((n, m), f32)
+    has = np.zeros((n, m), bool)
+    q = f32(q_ratio)
+    for y in range(n):
+        x = 0
+        while x < m:
+            end = x
+            while end + 1 < m and dc[y, end + 1] == dc[y, x]:
+                end += 1
+            start = x
+            x = end + 1
+            if start == 0 and end == m - 1:
+                continue
+            if np.any(ac[y, start:end + 1] != 0):
+                continue
+            cur = f32(dc[y, start])
+            if start == 0:
+                frm = cur
+            else:
+                frm = f32(0.5) * f32(f32(cur + f32(dc[y, start - 1])) + f32(q * f32(ac[y, start - 1])))
+            if end == m - 1:
+                to = cur
+            else:
+                to = f32(0.5) * f32(f32(cur + f32(dc[y, end + 1])) + f32(q * f32(ac[y, end + 1])))
+            sane = (abs(f32(to - cur)) <= f32(max_gap) and abs(f32(cur - frm)) <= f32(max_gap)
+                    and abs(f32(to - frm)) > f32(min_step))
+            if not sane:
+                continue
+            span = f32(end - start + 1)
+            ratio = f32(f32(to - frm) / span)
+            for xx in range(start, end + 1):
+                i = f32(xx - start)
+                approx[y, xx] = f32(frm + f32(f32(f32(0.5) + i) * ratio))
+                slope[y, xx] = f32(f32(-0.5) * ratio)
+                has[y, xx] = True
+    return approx, slope, has
+
+
+def conditioning(coeffs, quant, max_gap, min_step):
+    """M.6.1.1: per block the DC to use (in DC quantisation steps) and the
+    replacements of coefficients 1 and 8 (in the same units), or None."""
+    dc = coeffs[:, :, 0].astype(np.int64)
+    hq = float(np.float32(quant[1]) / np.float32(quant[0]))
+    vq = float(np.float32(quant[8]) / np.float32(quant[0]))
+    ha, hs, hh = _plateaus(dc, coeffs[:, :, 1].astype(np.int64), hq, max_gap, min_step)
+    va, vs, vh = _plateaus(dc.T, coeffs[:, :, 8].astype(np.int64).T, vq, max_gap, min_step)
+    va, vs, vh = va.T, vs.T, vh.T
+    f32 = np.float32
+    approx = np.where(hh & vh, f32(0.5) * (ha + va), np.where(hh, ha, np.where(vh, va, dc.astype(f32))))
+    return approx.astype(np.float64), hs.astype(np.float64), hh, vs.astype(np.float64), vh
+
+
+def component_pixels(coeffs, quant, cond=None):
+    """M.6.1 (+ M.6.1.1 when cond = (max_gap, min_step)) + M.6.2: the
+    component's sample plane (8 bh, 8 bw); values are level-shifted (about
+    -128..127)."""
     bh, bw = coeffs.shape[:2]
     plane = np.zeros((8 * bh, 8 * bw))
+    if cond is not None:
+        approx, hs, hh, vs, vh = conditioning(coeffs, quant, *cond)
+        mult = float(quant[0]) * T.I(8, 0) * T.I(8, 0)
     for by in range(bh):
         for bx in range(bw):
             blk = dequantize_block(coeffs[by, bx], quant)
+            if cond is not None:
+                blk[0, 0] = approx[by, bx] * mult
+                if hh[by, bx]:
+                    blk[0, 1] = hs[by, bx] * mult
+                if vh[by, bx]:
+                    blk[1, 0] = vs[by, bx] * mult
             plane[8 * by:8 * by + 8, 8 * bx:8 * bx + 8] = TR.idct_2d(blk)
     return plane
 
@@ -113,17 +191,18 @@ def ycbcr_to_rgb(y, cb, cr):
 
 
 def rasterize(stream):
-    """The whole of M.6 (without the optional conditioning): (ysize, xsize,
+    """The whole of M.6: (ysize, xsize,
     3) RGB samples on the nominal 0..255 scale, unclamped.  ``stream``:
     xsize, ysize and a list of components, each a dict with coeffs
-    (bh, bw, 64), quant (64,), h_samp, v_samp and an optional 'gab' tuple
-    (w1, w2, threshold, limit)."""
+    (bh, bw, 64), quant (64,), h_samp, v_samp, an optional 'gab' tuple
+    (w1, w2, threshold, limit) and an optional 'cond' tuple (max_gap,
+    min_step)."""
     comps = stream['components']
     hmax = max(c['h_samp'] for c in comps)
     vmax = max(c['v_samp'] for c in comps)
     planes = []
     for c in comps:
-        p = component_pixels(c['coeffs'], c['quant'])
+        p = component_pixels(c['coeffs'], c['quant'], c.get('cond'))
         if c.get('gab') is not None:
             p = conditional_gaborish(p, *c['gab'])
         if c['h_samp'] != hmax:

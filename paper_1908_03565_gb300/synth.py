@@ -218,7 +218,8 @@ def shape_area_fractions(vmap):
     return {c: a / area for c, a in sorted(tot.items())}
 
 
-def make_jpeg(xsize, ysize, seed, sampling='420', gab=False, ac_scale=6.0):
+def make_jpeg(xsize, ysize, seed, sampling='420', gab=False, ac_scale=6.0, plateaus=False,
+              cond=None):
     """A synthetic JPEG1 coefficient stream (the input of direct
     rasterisation).  ``sampling``: '420' (Y 2x2, Cb and Cr 1x1), '444' or
     'grey'.  Quantisation tables: 3 + 2 (u + v) for Y and 4 + 3 (u + v) for
@@ -226,9 +227,13 @@ def make_jpeg(xsize, ysize, seed, sampling='420', gab=False, ac_scale=6.0):
     amplitude 200 steps (period 40 blocks) plus Gaussian noise of 2 steps;
     AC: Laplace(0, ac_scale / (1 + u + v)) rounded.  ``gab`` adds the block-
     conditional Gaborish side channel (w1 118/1024, w2 63/1024, threshold
-    2.5, limit 20) to every component.  Returns a dict with xsize, ysize and
+    2.5, limit 20) to every component.  ``plateaus`` makes the quantised DC
+    a coarse staircase (the field / 20, rounded: long runs of equal values)
+    and zeroes coefficients 1 and 8 in 80% of the blocks, the inputs the DC
+    / AC conditioning of M.6.1.1 acts on; ``cond`` = (max_gap, min_step)
+    requests that conditioning.  Returns a dict with xsize, ysize and
     components (coeffs int16 (bh, bw, 64), quant uint16 (64,), h_samp,
-    v_samp, gab)."""
+    v_samp, gab, cond)."""
     rng = np.random.default_rng(seed)
     if sampling == '420':
         samp = [(2, 2), (1, 1), (1, 1)]
@@ -254,8 +259,15 @@ def make_jpeg(xsize, ysize, seed, sampling='420', gab=False, ac_scale=6.0):
         by, bx = np.mgrid[0:bh, 0:bw]
         ph = rng.uniform(0, 2 * math.pi, size=2)
         dc = 200.0 * np.sin(2 * math.pi * bx / 40.0 + ph[0]) * np.cos(2 * math.pi * by / 40.0 + ph[1])
-        q[:, :, 0] = np.rint(dc + rng.normal(0.0, 2.0, size=(bh, bw)))
+        if plateaus:
+            q[:, :, 0] = np.rint(dc / 20.0)
+            zero = rng.random(size=(bh, bw)) < 0.8
+            q[:, :, 1] = np.where(zero, 0, q[:, :, 1])
+            q[:, :, 8] = np.where(zero, 0, q[:, :, 8])
+        else:
+            q[:, :, 0] = np.rint(dc + rng.normal(0.0, 2.0, size=(bh, bw)))
         comps.append({'coeffs': np.clip(q, -32768, 32767).astype(np.int16), 'quant': quant,
                       'h_samp': h, 'v_samp': v,
-                      'gab': (118 / 1024, 63 / 1024, 40 / 16, 20) if gab else None})
+                      'gab': (118 / 1024, 63 / 1024, 40 / 16, 20) if gab else None,
+                      'cond': cond})
     return {'xsize': xsize, 'ysize': ysize, 'components': comps}

@@ -109,3 +109,44 @@ def test_rasterize_shapes_and_grey():
     g = J.rasterize(grey)
     np.testing.assert_array_equal(g[..., 0], g[..., 1])
     assert J.to_u8(np.array([-3.0, 0.5, 254.5, 300.0])).tolist() == [0, 1, 255, 255]
+
+
+def test_conditioning_staircase_by_hand():
+    """M.6.1.1 on one row of DC 0 0 0 1 1 1 2 2 2 with zero AC: the first run
+    has |to - from| = 0.5, not above min_step 0.5; the middle run from 0.5 to
+    1.5 over 3 blocks gives 0.5 + (0.5 + i) / 3 and slopes -1/6; the last run
+    is symmetric to the first."""
+    dc = np.array([[0, 0, 0, 1, 1, 1, 2, 2, 2]])
+    ac = np.zeros_like(dc)
+    a, s, h = J._plateaus(dc, ac, 5 / 3, 0.5, 0.5)
+    assert h.tolist() == [[False] * 3 + [True] * 3 + [False] * 3]
+    np.testing.assert_allclose(a[0, 3:6], [0.5 + 0.5 / 3, 1.0, 1.5 - 0.5 / 3], rtol=1e-6)
+    np.testing.assert_allclose(s[0, 3:6], -1 / 6, rtol=1e-6)
+    # a whole-row run is never a range; a nonzero AC in the run disables it
+    assert not J._plateaus(np.zeros((1, 5), int), np.zeros((1, 5), int), 1.0, 0.5, 0.5)[2].any()
+    ac2 = ac.copy()
+    ac2[0, 4] = 1
+    assert not J._plateaus(dc, ac2, 5 / 3, 0.5, 0.5)[2][0, 3:6].any()
+
+
+def test_conditioning_makes_a_ramp():
+    """With the replaced DC and slope the middle run's samples rise
+    monotonically from about 0.5 to 1.5 DC steps (the reading of
+    dc_multiplier): no step larger than a third of a DC step."""
+    q = np.zeros((1, 9, 64), np.int16)
+    q[0, :, 0] = [0, 0, 0, 1, 1, 1, 2, 2, 2]
+    quant = np.full(64, 8, np.uint16)
+    plain = J.component_pixels(q, quant)
+    cond = J.component_pixels(q, quant, (0.5, 0.5))
+    row = cond[3, 24:48] / (8 / 8.0)                    # in DC steps (Q0 / 8 per step)
+    assert np.all(np.diff(row) >= -1e-6)
+    assert np.abs(np.diff(row)).max() < 1 / 3
+    assert row[0] == pytest.approx(0.5, abs=0.1) and row[-1] == pytest.approx(1.5, abs=0.1)
+    np.testing.assert_allclose(cond[:, :24], plain[:, :24], atol=1e-12)   # first run untouched
+
+
+def test_conditioning_stream_statistics():
+    st = synth.make_jpeg(200, 136, 8, sampling='420', plateaus=True, cond=(0.5, 0.5))
+    c = st['components'][0]
+    approx, hs, hh, vs, vh = J.conditioning(c['coeffs'], c['quant'], 0.5, 0.5)
+    assert 0.05 < hh.mean() < 0.95 and 0.05 < vh.mean() < 0.95
