@@ -210,7 +210,8 @@ jxlr_status jxl_recon_submit_xyb(jxl_recon_ctx* ctx, const float* xyb,
  * v_samp: sampling factors (1 or 2); a component whose factor is below the
  * largest one is upsampled 2x along that axis (M.6.4).  gab: 1 when the
  * block-conditional Gaborish side channel of M.6.3 is present, with its
- * decoded weights (u(8) / 1024), threshold (u(8) / 16) and limit. */
+ * decoded weights (u(8) / 1024), threshold (u(8) / 16) and limit; cond: 1
+ * when the coefficients are to be conditioned (M.6.1.1). */
 typedef struct {
   uint32_t width_in_blocks, height_in_blocks;
   uint32_t h_samp, v_samp;
@@ -219,6 +220,10 @@ typedef struct {
   int gab;
   float gab_w1, gab_w2, gab_threshold;
   int gab_limit;
+  /* 1: the DC / AC conditioning of M.6.1.1 with its max_gap and min_step
+   * (u(8) / 64 from the side channel, or 0.5 / 0.5 by the decoder's choice). */
+  int cond;
+  float cond_max_gap, cond_min_step;
 } jxl_jpeg_component;
 
 /* num_components: 1 (grey) or 3 (Y, Cb, Cr).  The block grids must cover
@@ -232,10 +237,10 @@ typedef struct {
   int on_device;
 } jxl_jpeg_stream;
 
-/* Enqueues M.6.1 (dequantisation), M.6.2 (IDCT_2D), M.6.3, M.6.4, M.6.5
- * (YCbCr -> RGB) and M.6.6 (cropping) for one stream.  The optional DC/AC
- * conditioning of M.6.1.1 and the HDR transform of M.6.5.1 are not
- * performed.  Output: JXLR_OUT_U8_SRGB gives the rasterised samples
+/* Enqueues M.6.1 (dequantisation, with the M.6.1.1 conditioning of the
+ * components that ask for it), M.6.2 (IDCT_2D), M.6.3, M.6.4, M.6.5 (YCbCr
+ * -> RGB) and M.6.6 (cropping) for one stream.  The HDR transform of
+ * M.6.5.1 is not performed.  Output: JXLR_OUT_U8_SRGB gives the rasterised samples
  * clamped to [0, 255] and rounded half up (no transfer function is applied:
  * the samples are already in the JPEG's colour encoding); F32_LINEAR and
  * F16_LINEAR give sample / 255 unclamped; F32_XYB is rejected.  Same ticket

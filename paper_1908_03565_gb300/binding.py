@@ -64,7 +64,9 @@ class JpegComponent(ctypes.Structure):
                 ("h_samp", ctypes.c_uint32), ("v_samp", ctypes.c_uint32),
                 ("coeffs", ctypes.c_void_p), ("quant", ctypes.c_void_p), ("gab", ctypes.c_int),
                 ("gab_w1", ctypes.c_float), ("gab_w2", ctypes.c_float),
-                ("gab_threshold", ctypes.c_float), ("gab_limit", ctypes.c_int)]
+                ("gab_threshold", ctypes.c_float), ("gab_limit", ctypes.c_int),
+                ("cond", ctypes.c_int), ("cond_max_gap", ctypes.c_float),
+                ("cond_min_step", ctypes.c_float)]
 
 
 class JpegStream(ctypes.Structure):
@@ -284,6 +286,9 @@ class Context:
             if c.get('gab') is not None:
                 k.gab = 1
                 k.gab_w1, k.gab_w2, k.gab_threshold, k.gab_limit = c['gab']
+            if c.get('cond') is not None:
+                k.cond = 1
+                k.cond_max_gap, k.cond_min_step = c['cond']
         st.on_device = 1 if on_device else 0
         if out_stride is None:
             out_stride = OUT_BYTES[out_dtype] * xs

@@ -804,6 +804,8 @@ extern "C" jxlr_status jxl_recon_submit_jpeg(jxl_recon_ctx* ctx, const jxl_jpeg_
     if (cw < xs || ch < ys) return fail(JXLR_EINVAL, "submit_jpeg: block grid does not cover the image");
     if (st->on_device && (reinterpret_cast<uintptr_t>(k.coeffs) & 15))
       return fail(JXLR_EINVAL, "submit_jpeg: device coefficients must be 16-byte aligned");
+    if (k.cond && (k.quant[0] == 0 || !std::isfinite(k.cond_max_gap) || !std::isfinite(k.cond_min_step)))
+      return fail(JXLR_EINVAL, "submit_jpeg: bad conditioning parameters");
     if (k.gab && !(k.gab_limit >= 0 && std::isfinite(k.gab_w1) && std::isfinite(k.gab_w2) &&
                    std::isfinite(k.gab_threshold) && 1.0 + 4.0 * k.gab_w1 + 4.0 * k.gab_w2 != 0.0))
       return fail(JXLR_EINVAL, "submit_jpeg: bad Gaborish side channel");
@@ -817,6 +819,11 @@ extern "C" jxlr_status jxl_recon_submit_jpeg(jxl_recon_ctx* ctx, const jxl_jpeg_
     if (!st->on_device) add(nb * 128);
     add(nb * 256);                                    // sample plane
     if (st->comp[c].gab) add(nb * 256);               // after M.6.3
+    if (st->comp[c].cond) {                           // M.6.1.1 results
+      for (int k = 0; k < 4; ++k) add(nb * 4);
+      add(nb);
+      add(nb);
+    }
   }
   const size_t out_bytes = out->row_stride_bytes * (ys - 1) + px_bytes * xs;
   if (!out->on_device) add(out_bytes);
@@ -864,6 +871,30 @@ extern "C" jxlr_status jxl_recon_submit_jpeg(jxl_recon_ctx* ctx, const jxl_jpeg_
         ia.dq[8 * u + v] = static_cast<float>(k.quant[8 * u + v] * eu * ev / 4.0);
       }
     ia.plane = cv.take<float>(static_cast<size_t>(bw) * bh * 64);
+    ia.cond = 0;
+    std::memset(&ia.c, 0, sizeof(ia.c));
+    if (k.cond) {
+      const size_t nb = static_cast<size_t>(bw) * bh;
+      JpegCondArgs ja;
+      ja.coef = coef[c];
+      ja.bw = bw;
+      ja.bh = bh;
+      ja.q_h = static_cast<float>(k.quant[1]) / static_cast<float>(k.quant[0]);
+      ja.q_v = static_cast<float>(k.quant[8]) / static_cast<float>(k.quant[0]);
+      ja.max_gap = k.cond_max_gap;
+      ja.min_step = k.cond_min_step;
+      ja.out.h_approx = cv.take<float>(nb);
+      ja.out.h_slope = cv.take<float>(nb);
+      ja.out.v_approx = cv.take<float>(nb);
+      ja.out.v_slope = cv.take<float>(nb);
+      ja.out.has_h = cv.take<uint8_t>(nb);
+      ja.out.has_v = cv.take<uint8_t>(nb);
+      ctx->launches += launch_jpeg_cond(ja, s);
+      ia.cond = 1;
+      ia.c = ja.out;
+      ia.m0 = static_cast<float>(k.quant[0] / 8.0);
+      ia.m1 = static_cast<float>(k.quant[0] / 8.0 / std::cos(3.14159265358979323846 / 16.0));
+    }
     launch_jpeg_idct(ia, s);
     ctx->launches++;
     const float* plane = ia.plane;

@@ -1,6 +1,8 @@
 // JPEG1 direct rasterisation (M.6): dequantisation and IDCT per 8x8 block,
 // block-conditional Gaborish, 2x linear chroma upsampling and YCbCr -> RGB.
 //
+//  k_jpeg_cond_rows / k_jpeg_cond_cols  M.6.1.1 plateau scans, one thread
+//               per block row / column.
 //  k_jpeg_idct  128 threads = 16 blocks x 8 rows.  A thread loads one
 //               coefficient row (8 x int16, one 128-bit load), dequantises
 //               it with the prescaled table and transforms it; the block's
@@ -50,6 +52,63 @@ __device__ __forceinline__ void idct8(float (&x)[8]) {
   }
 }
 
+// M.6.1.1 along one line of n blocks (rows: step 1 block; columns: step bw
+// blocks), in binary32, operation by operation (the comparisons decide which
+// coefficients are replaced).  acx: index of the AC coefficient of the scan
+// direction (1 horizontal, 8 vertical).
+__device__ void cond_line(const int16_t* coef, int first, int stride, int n, int acx, float q,
+                          float max_gap, float min_step, float* approx, float* slope,
+                          uint8_t* has) {
+  auto dc = [&](int i) { return static_cast<int>(coef[static_cast<size_t>(first + i * stride) * 64]); };
+  auto ac = [&](int i) { return static_cast<int>(coef[static_cast<size_t>(first + i * stride) * 64 + acx]); };
+  int x = 0;
+  while (x < n) {
+    const int d = dc(x);
+    int end = x;
+    bool zero = ac(x) == 0;
+    while (end + 1 < n && dc(end + 1) == d) {
+      ++end;
+      zero = zero && ac(end) == 0;
+    }
+    const int start = x;
+    x = end + 1;
+    bool sane = false;
+    float frm = 0.f, to = 0.f;
+    if (zero && !(start == 0 && end == n - 1)) {
+      const float cur = static_cast<float>(d);
+      frm = start == 0 ? cur
+                       : 0.5f * __fadd_rn(__fadd_rn(cur, static_cast<float>(dc(start - 1))),
+                                          __fmul_rn(q, static_cast<float>(ac(start - 1))));
+      to = end == n - 1 ? cur
+                        : 0.5f * __fadd_rn(__fadd_rn(cur, static_cast<float>(dc(end + 1))),
+                                           __fmul_rn(q, static_cast<float>(ac(end + 1))));
+      sane = fabsf(__fsub_rn(to, cur)) <= max_gap && fabsf(__fsub_rn(cur, frm)) <= max_gap &&
+             fabsf(__fsub_rn(to, frm)) > min_step;
+    }
+    const float ratio = sane ? __fdiv_rn(__fsub_rn(to, frm), static_cast<float>(end - start + 1)) : 0.f;
+    for (int i = start; i <= end; ++i) {
+      const size_t o = static_cast<size_t>(first + i * stride);
+      has[o] = sane ? 1 : 0;
+      approx[o] = sane ? __fadd_rn(frm, __fmul_rn(__fadd_rn(0.5f, static_cast<float>(i - start)), ratio)) : 0.f;
+      slope[o] = sane ? -0.5f * ratio : 0.f;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(128) k_jpeg_cond_rows(const __grid_constant__ JpegCondArgs a) {
+  const int y = blockIdx.x * blockDim.x + threadIdx.x;
+  if (y >= a.bh) return;
+  cond_line(a.coef, y * a.bw, 1, a.bw, 1, a.q_h, a.max_gap, a.min_step, a.out.h_approx,
+            a.out.h_slope, a.out.has_h);
+}
+
+__global__ void __launch_bounds__(128) k_jpeg_cond_cols(const __grid_constant__ JpegCondArgs a) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= a.bw) return;
+  cond_line(a.coef, x, a.bw, a.bh, 8, a.q_v, a.max_gap, a.min_step, a.out.v_approx,
+            a.out.v_slope, a.out.has_v);
+}
+
 __global__ void __launch_bounds__(128) k_jpeg_idct(const __grid_constant__ JpegIdctArgs a) {
   __shared__ float sT[16][8][9];
   const int tid = threadIdx.x;
@@ -62,6 +121,19 @@ __global__ void __launch_bounds__(128) k_jpeg_idct(const __grid_constant__ JpegI
     const int16_t* h = reinterpret_cast<const int16_t*>(&raw);
 #pragma unroll
     for (int j = 0; j < 8; ++j) x[j] = static_cast<float>(h[j]) * a.dq[8 * r + j];
+    if (a.cond && r < 2) {   // M.6.1.1: coefficients 0 and 1 (row 0), 8 (row 1)
+      const bool hh = a.c.has_h[blk] != 0, vh = a.c.has_v[blk] != 0;
+      if (r == 0) {
+        float dcv = static_cast<float>(h[0]);
+        if (hh && vh) dcv = 0.5f * __fadd_rn(a.c.h_approx[blk], a.c.v_approx[blk]);
+        else if (hh) dcv = a.c.h_approx[blk];
+        else if (vh) dcv = a.c.v_approx[blk];
+        x[0] = dcv * a.m0;
+        if (hh) x[1] = a.c.h_slope[blk] * a.m1;
+      } else if (vh) {
+        x[0] = a.c.v_slope[blk] * a.m1;
+      }
+    }
   } else {
 #pragma unroll
     for (int j = 0; j < 8; ++j) x[j] = 0.f;
@@ -187,6 +259,12 @@ bool upload_jpeg_constants(const float* odd8, const float* odd4, float odd2) {
 void launch_jpeg_idct(const JpegIdctArgs& a, cudaStream_t s) {
   const int nblk = a.bw * a.bh;
   k_jpeg_idct<<<(nblk + 15) / 16, 128, 0, s>>>(a);
+}
+
+int launch_jpeg_cond(const JpegCondArgs& a, cudaStream_t s) {
+  k_jpeg_cond_rows<<<(a.bh + 127) / 128, 128, 0, s>>>(a);
+  k_jpeg_cond_cols<<<(a.bw + 127) / 128, 128, 0, s>>>(a);
+  return 2;
 }
 
 void launch_jpeg_gab(const JpegGabArgs& a, cudaStream_t s) {

@@ -131,3 +131,18 @@ def test_jpeg1_rejects_ill_formed_streams(B, ctx):
                         torch.empty((64, 64, 3), dtype=torch.float32, device="cuda"), XYB)
     # the context still works
     assert _run(B, ctx, st, U8).shape == (64, 64, 3)
+
+
+@pytest.mark.parametrize("sampling,xs,ys", [('420', 200, 136), ('444', 72, 56), ('grey', 131, 77)])
+def test_jpeg1_conditioning(B, ctx, sampling, xs, ys):
+    """M.6.1.1 on staircase DC with mostly zero first AC coefficients: the
+    plateau decisions are binary32 on both sides, so the outputs agree
+    within float rounding everywhere."""
+    st = synth.make_jpeg(xs, ys, 3000 + xs, sampling=sampling, plateaus=True, cond=(0.5, 0.5))
+    want = J.rasterize(st)
+    plain = dict(st)
+    plain['components'] = [dict(c, cond=None) for c in st['components']]
+    assert np.abs(want - J.rasterize(plain)).max() > 0.1       # conditioning changed samples
+    got = _run(B, ctx, st, F32)
+    np.testing.assert_allclose(got, want / 255.0, atol=1e-5, rtol=0)
+    np.testing.assert_array_equal(_run(B, ctx, st, U8), _run(B, ctx, st, U8, device_io=False))
