@@ -516,6 +516,11 @@ def main():
     step_hbm_frac = (px * (IN_BPP + OUT_BPP) / (ms * 1e-3) / 1e9) / hbm_peak
 
     # ---- end to end through the public API with host buffers -------------
+    # A context with its own stream per slot (3 slots), so that the
+    # host-to-device copy of one step, the kernels of the next and the
+    # device-to-host copy of the one before overlap; at most 3 steps in
+    # flight, each with its own pinned output.  Timed on the host clock with
+    # the device idle on both sides (events cannot span the slots' streams).
     e2e = None
     if rank == 0 or world > 1:
         himg = dict(img)
@@ -524,21 +529,35 @@ def main():
             t = torch.from_numpy(np.ascontiguousarray(img[k])).pin_memory()
             pinned[k] = t
             himg[k] = t.numpy()
-        hout_t = torch.empty((YS, XS, 3), dtype=torch.float32).pin_memory()
-        hout = hout_t.numpy()
-        run_steps(3, dev=False, host=(himg, hout))
+        nslot = 3
+        houts_t = [torch.empty((YS, XS, 3), dtype=torch.float32).pin_memory() for _ in range(nslot)]
+        houts = [t.numpy() for t in houts_t]
+        ectx = binding.Context(device=local, max_slots=nslot)
+
+        def e2e_steps(n):
+            q = []
+            for i in range(n):
+                if len(q) == nslot:
+                    ectx.poll(q.pop(0))
+                q.append(ectx.submit(himg, params, houts[i % nslot], binding.OUT_F32_LINEAR,
+                                     on_device=False, out_on_device=False))
+            for t in q:
+                ectx.poll(t)
+
+        e2e_steps(3)
         barrier()
-        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        f0.record(stream)
-        n_e2e = max(3, min(args.steps, 10))
-        run_steps(n_e2e, dev=False, host=(himg, hout))
-        f1.record(stream)
+        n_e2e = max(6, min(args.steps, 30))
+        w0 = time.perf_counter()
+        e2e_steps(n_e2e)
         barrier()
-        ems = max_over_ranks(f0.elapsed_time(f1)) / n_e2e
+        ems = max_over_ranks((time.perf_counter() - w0) * 1e3) / n_e2e
+        ectx.close()
         h2d = sum(img[k].nbytes for k in ("coeffs", "vmap", "acmul", "cfl", "sharpness"))
         e2e = {"value": round(world * px / (ems * 1e-3) / 1e6, 1), "unit": "Mpx/s",
                "ms_per_step": round(ems, 4), "h2d_bytes_per_step": int(h2d),
-               "d2h_bytes_per_step": int(hout.nbytes)}
+               "d2h_bytes_per_step": int(houts[0].nbytes),
+               "method": f"{nslot} slots with their own streams, pipelined; host clock over "
+                         f"{n_e2e} steps between device synchronisations"}
 
     precision = None
     if rank == 0 and args.precision_steps > 0:
