@@ -264,6 +264,15 @@ jxlr_status jxl_recon_poll(jxl_recon_ctx* ctx, uint64_t ticket, int64_t timeout_
  * the values stay until the next completed request of that slot. */
 jxlr_status jxl_recon_stage_ms(jxl_recon_ctx* ctx, uint64_t ticket, float ms[4]);
 
+/* The edge-preserving filter of a finished request (J.2; context created
+ * with timing = 1): *epf_ms is the device time of its kernel alone (part of
+ * ms[2] of jxl_recon_stage_ms()), *epf_blocks the number of 8x8 blocks it
+ * filtered, i.e. those with sigma >= 16 (J.2.4); the samples of the other
+ * blocks pass through unchanged.  Both 0 when the request had no EPF or was
+ * a batch / JPEG1 request.  Call after jxl_recon_poll() returned JXLR_OK. */
+jxlr_status jxl_recon_epf_stats(jxl_recon_ctx* ctx, uint64_t ticket, float* epf_ms,
+                                uint32_t* epf_blocks);
+
 /* One request of a serving schedule: the arguments of jxl_recon_submit(). */
 typedef struct {
   const jxl_recon_coeffs* coeffs;

@@ -25,7 +25,7 @@ EXPORTS = ("jxl_recon_filter_defaults", "jxl_recon_create", "jxl_recon_submit",
            "jxl_recon_launch_count", "jxl_recon_device_bytes", "jxl_recon_destroy",
            "jxl_recon_last_error", "jxl_recon_run_noalloc", "jxl_recon_serve",
            "jxl_recon_batch_create", "jxl_recon_batch_launch", "jxl_recon_batch_query",
-           "jxl_recon_batch_destroy", "jxl_recon_submit_jpeg")
+           "jxl_recon_batch_destroy", "jxl_recon_submit_jpeg", "jxl_recon_epf_stats")
 
 
 class Config(ctypes.Structure):
@@ -133,6 +133,9 @@ def load(path=LIB_PATH):
     lib.jxl_recon_poll.restype = ctypes.c_int
     lib.jxl_recon_stage_ms.argtypes = [ctypes.c_void_p, ctypes.c_uint64, P(ctypes.c_float)]
     lib.jxl_recon_stage_ms.restype = ctypes.c_int
+    lib.jxl_recon_epf_stats.argtypes = [ctypes.c_void_p, ctypes.c_uint64, P(ctypes.c_float),
+                                        P(ctypes.c_uint32)]
+    lib.jxl_recon_epf_stats.restype = ctypes.c_int
     lib.jxl_recon_launch_count.argtypes = [ctypes.c_void_p]
     lib.jxl_recon_launch_count.restype = ctypes.c_uint64
     lib.jxl_recon_device_bytes.argtypes = [ctypes.c_void_p]
@@ -340,6 +343,15 @@ class Context:
         if st != JXLR_OK:
             raise JxlrError(st, self.last_error())
         return list(ms)
+
+    def epf_stats(self, ticket):
+        """(device ms of the J.2 kernel, 8x8 blocks it filtered) of a finished
+        request of a timing context."""
+        ms, n = ctypes.c_float(), ctypes.c_uint32()
+        st = self.lib.jxl_recon_epf_stats(self.h, ticket, ctypes.byref(ms), ctypes.byref(n))
+        if st != JXLR_OK:
+            raise JxlrError(st, self.last_error())
+        return float(ms.value), int(n.value)
 
     def launch_count(self):
         return self.lib.jxl_recon_launch_count(self.h)

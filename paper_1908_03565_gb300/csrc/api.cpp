@@ -56,7 +56,9 @@ struct Slot {
   cudaStream_t stream = nullptr;
   bool own_stream = true;
   cudaEvent_t done = nullptr;
-  cudaEvent_t ev[5] = {};     // timing marks: start, validated, recon, filter, end
+  // timing marks: start, staged, validated, recon, end, before J.2, after J.2
+  cudaEvent_t ev[7] = {};
+  bool epf_marked = false;    // marks 5 and 6 were recorded for this request
   char* arena = nullptr;
   size_t arena_bytes = 0;
   unsigned* h_status = nullptr;   // pinned: device status copied back here
@@ -69,7 +71,14 @@ struct Slot {
 
 struct Timing {
   float ms[4];
+  float epf_ms = 0.f;
+  unsigned epf_blocks = 0;
 };
+
+// Words of the per-request device status block: [0] validation flags,
+// [1] [2] validation counters, [3] tensor-core wait expired, [4] blocks the
+// J.2 kernel filtered.
+constexpr int kStatusWords = 8;
 
 }  // namespace
 
@@ -213,7 +222,7 @@ jxlr_status jxl_recon_create(const jxl_recon_config* cfg, jxl_recon_ctx** out) {
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming);
     for (auto& ev : s.ev)
       if (e == cudaSuccess) e = cudaEventCreate(&ev);
-    if (e == cudaSuccess) e = cudaMallocHost(&s.h_status, 4 * sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMallocHost(&s.h_status, kStatusWords * sizeof(unsigned));
   }
   if (e != cudaSuccess) {
     jxl_recon_destroy(ctx);
@@ -336,7 +345,7 @@ void mark(Slot* s, int i) {
 }
 
 jxlr_status finish_submit(jxl_recon_ctx* ctx, Slot* slot, unsigned* d_status, uint64_t* ticket) {
-  CK(cudaMemcpyAsync(slot->h_status, d_status, 4 * sizeof(unsigned), cudaMemcpyDeviceToHost,
+  CK(cudaMemcpyAsync(slot->h_status, d_status, kStatusWords * sizeof(unsigned), cudaMemcpyDeviceToHost,
                      slot->stream));
   CK(cudaEventRecord(slot->done, slot->stream));
   CK(cudaGetLastError());
@@ -364,35 +373,43 @@ static int setup_noise(FilterArgs& fa, float* r, cudaStream_t s) {
   return launch_noise_gen(na, s);
 }
 
-// J.2 into eo, J.3 in place on eo, then J.4 / L.2 from eo (three launches).
-// fa: the filter arguments of the plain path (EPF on); orig = fa.xyb.
-static void launch_qco_chain(const FilterArgs& fa, float* eo, const uint8_t* vmap,
-                             const float* acmul, const float* dequant, int bh,
-                             const jxl_recon_filter_params& fp, cudaStream_t s) {
+// J.2 into eo (the blocks the sigma pass listed; it copied the others
+// there), J.3 in place on eo when asked, then J.4 / L.2 (and K.5) from eo.
+// fa: the filter arguments of the request (EPF on); orig = fa.xyb.  Returns
+// the number of launches.
+static int launch_epf_chain(Slot* slot, const FilterArgs& fa, float* eo, const EpfSink& sink,
+                            bool qco, const uint8_t* vmap, const float* acmul,
+                            const float* dequant, int bh, const jxl_recon_filter_params& fp,
+                            cudaStream_t s) {
   const size_t wp = static_cast<size_t>(fa.bw) * 8, hp = static_cast<size_t>(bh) * 8;
   FilterArgs e = fa;
   e.epf_out = eo;
   e.ors = wp;
   e.ops = wp * hp;
-  launch_filter(e, s);
-  QcoArgs q;
-  std::memset(&q, 0, sizeof(q));
-  q.orig = fa.xyb;
-  q.ors = fa.rstride;
-  q.ops = fa.pstride;
-  q.f = eo;
-  q.frs = wp;
-  q.fps = wp * hp;
-  q.vmap = vmap;
-  q.acmul = acmul;
-  q.dequant = dequant;
-  q.xs = fa.xs; q.ys = fa.ys; q.bw = fa.bw; q.bh = bh;
-  for (int c = 0; c < 3; ++c) q.m_dc[c] = fp.m_dc[c];
-  q.mul = fp.qco_interval_mul;
-  q.vec = (q.ors % 4 == 0 && q.ops % 4 == 0 && q.frs % 4 == 0 && q.fps % 4 == 0 &&
-           (reinterpret_cast<uintptr_t>(q.orig) & 15) == 0 &&
-           (reinterpret_cast<uintptr_t>(q.f) & 15) == 0) ? 1 : 0;
-  launch_qco(q, s);
+  mark(slot, 5);
+  launch_epf_work(e, sink.list, sink.count, s);
+  mark(slot, 6);
+  slot->epf_marked = slot->timed;
+  if (qco) {
+    QcoArgs q;
+    std::memset(&q, 0, sizeof(q));
+    q.orig = fa.xyb;
+    q.ors = fa.rstride;
+    q.ops = fa.pstride;
+    q.f = eo;
+    q.frs = wp;
+    q.fps = wp * hp;
+    q.vmap = vmap;
+    q.acmul = acmul;
+    q.dequant = dequant;
+    q.xs = fa.xs; q.ys = fa.ys; q.bw = fa.bw; q.bh = bh;
+    for (int c = 0; c < 3; ++c) q.m_dc[c] = fp.m_dc[c];
+    q.mul = fp.qco_interval_mul;
+    q.vec = (q.ors % 4 == 0 && q.ops % 4 == 0 && q.frs % 4 == 0 && q.fps % 4 == 0 &&
+             (reinterpret_cast<uintptr_t>(q.orig) & 15) == 0 &&
+             (reinterpret_cast<uintptr_t>(q.f) & 15) == 0) ? 1 : 0;
+    launch_qco(q, s);
+  }
   FilterArgs g = fa;
   g.epf = 0;
   g.sigma = nullptr;
@@ -400,6 +417,7 @@ static void launch_qco_chain(const FilterArgs& fa, float* eo, const uint8_t* vma
   g.rstride = wp;
   g.pstride = wp * hp;
   launch_filter(g, s);
+  return qco ? 3 : 2;
 }
 
 extern "C" jxlr_status jxl_recon_submit(jxl_recon_ctx* ctx, const jxl_recon_coeffs* co,
@@ -445,7 +463,7 @@ extern "C" jxlr_status jxl_recon_submit(jxl_recon_ctx* ctx, const jxl_recon_coef
   const size_t cstride = wp;
   size_t need = 0;
   auto add = [&](size_t bytes) { need = align_up(need, 256) + bytes; };
-  add(16);                                            // status
+  add(sizeof(unsigned) * kStatusWords);               // status
   if (!dev_in) {
     for (int c = 0; c < 3; ++c) add(sizeof(int16_t) * cstride * hp);
     add(static_cast<size_t>(bw) * bh);                // map
@@ -467,7 +485,10 @@ extern "C" jxlr_status jxl_recon_submit(jxl_recon_ctx* ctx, const jxl_recon_coef
     add(sizeof(float) * 12 * nblk);                   // predicted coefficients
   }
   const bool qco = fp->epf && fp->qco;
-  if (qco) add(sizeof(float) * 3 * wp * hp);         // EPF output for J.3
+  if (fp->epf) {
+    add(sizeof(float) * 3 * wp * hp);                 // J.2 output
+    add(sizeof(int) * nblk);                          // blocks J.2 filters
+  }
   if (fp->noise) add(sizeof(float) * 3 * static_cast<size_t>(xs) * ys);   // K.5.2 channels
   const size_t out_bytes = out->row_stride_bytes * (ys - 1) + px_bytes * xs;
   if (!out->on_device) add(out_bytes);
@@ -479,11 +500,12 @@ extern "C" jxlr_status jxl_recon_submit(jxl_recon_ctx* ctx, const jxl_recon_coef
   jxlr_status st = acquire_slot(ctx, need, &slot);
   if (st != JXLR_OK) return st;
   slot->timed = ctx->timing;
+  slot->epf_marked = false;
   slot->t_submit = Clock::now();
   cudaStream_t s = slot->stream;
   Carve cv(slot->arena);
-  unsigned* d_status = cv.take<unsigned>(4);
-  CK(cudaMemsetAsync(d_status, 0, 16, s));
+  unsigned* d_status = cv.take<unsigned>(kStatusWords);
+  CK(cudaMemsetAsync(d_status, 0, kStatusWords * sizeof(unsigned), s));
   mark(slot, 0);
 
   ReconArgs ra;
@@ -588,9 +610,21 @@ extern "C" jxlr_status jxl_recon_submit(jxl_recon_ctx* ctx, const jxl_recon_coef
   if (filters) {
     float* xyb = cv.take<float>(static_cast<size_t>(3) * wp * hp);
     int16_t* sig = fp->epf ? cv.take<int16_t>(static_cast<size_t>(bw) * bh) : nullptr;
+    EpfSink sink;
+    std::memset(&sink, 0, sizeof(sink));
+    float* eo = nullptr;
+    if (fp->epf) {
+      eo = cv.take<float>(static_cast<size_t>(3) * wp * hp);
+      sink.list = cv.take<int>(nblk);
+      sink.count = d_status + 4;
+      sink.pass = eo;
+      sink.prs = wp;
+      sink.pps = static_cast<size_t>(wp) * hp;
+    }
     ra.write_xyb = 1;
     ra.xyb = xyb;
     ra.sigma = sig;
+    ra.epf = sink;
     if (tc) launch_recon_tc(ra, s);
     else launch_recon(ra, s);
     ctx->launches++;
@@ -603,10 +637,9 @@ extern "C" jxlr_status jxl_recon_submit(jxl_recon_ctx* ctx, const jxl_recon_coef
     fa.sigma = sig;
     fa.out = op;
     if (fp->noise) ctx->launches += setup_noise(fa, cv.take<float>(3 * static_cast<size_t>(xs) * ys), s);
-    if (qco) {
-      float* eo = cv.take<float>(static_cast<size_t>(3) * wp * hp);
-      launch_qco_chain(fa, eo, ra.vmap, ra.acmul, ra.dequant, bh, *fp, s);
-      ctx->launches += 3;
+    if (fp->epf) {
+      ctx->launches += launch_epf_chain(slot, fa, eo, sink, qco, ra.vmap, ra.acmul, ra.dequant,
+                                        bh, *fp, s);
     } else {
       launch_filter(fa, s);
       ctx->launches++;
@@ -646,7 +679,10 @@ extern "C" jxlr_status jxl_recon_submit_xyb(jxl_recon_ctx* ctx, const float* xyb
   if (qco && fp->dequant)
     return fail(JXLR_EINVAL, "submit_xyb: the quantization constraint uses the default matrices here");
   size_t need = 256 + (fp->epf ? align_up(sizeof(int16_t) * bw * bh, 256) : 0);
-  if (qco) need += align_up(sizeof(float) * 3 * 64 * static_cast<size_t>(bw) * bh, 256);
+  if (fp->epf) {
+    need += align_up(sizeof(float) * 3 * 64 * static_cast<size_t>(bw) * bh, 256);
+    need += align_up(sizeof(int) * static_cast<size_t>(bw) * bh, 256);
+  }
   if (fp->noise) need += align_up(sizeof(float) * 3 * static_cast<size_t>(xs) * ys, 256);
   std::lock_guard<std::mutex> lock(ctx->mu);
   CK(cudaSetDevice(ctx->device));
@@ -654,14 +690,18 @@ extern "C" jxlr_status jxl_recon_submit_xyb(jxl_recon_ctx* ctx, const float* xyb
   jxlr_status st = acquire_slot(ctx, need, &slot);
   if (st != JXLR_OK) return st;
   slot->timed = ctx->timing;
+  slot->epf_marked = false;
   slot->t_submit = Clock::now();
   cudaStream_t s = slot->stream;
   Carve cv(slot->arena);
-  unsigned* d_status = cv.take<unsigned>(4);
-  CK(cudaMemsetAsync(d_status, 0, 16, s));
+  unsigned* d_status = cv.take<unsigned>(kStatusWords);
+  CK(cudaMemsetAsync(d_status, 0, kStatusWords * sizeof(unsigned), s));
   mark(slot, 0);
   mark(slot, 1);   // no input staging on this path
   int16_t* sig = nullptr;
+  EpfSink sink;
+  std::memset(&sink, 0, sizeof(sink));
+  float* eo = nullptr;
   if (fp->epf) {
     launch_validate(vmap, bw, bh, d_status, s);
     ctx->launches++;
@@ -669,7 +709,14 @@ extern "C" jxlr_status jxl_recon_submit_xyb(jxl_recon_ctx* ctx, const float* xyb
   mark(slot, 2);
   if (fp->epf) {
     sig = cv.take<int16_t>(static_cast<size_t>(bw) * bh);
+    eo = cv.take<float>(static_cast<size_t>(3) * 64 * bw * bh);
+    sink.list = cv.take<int>(static_cast<size_t>(bw) * bh);
+    sink.count = d_status + 4;
+    sink.pass = eo;
+    sink.prs = static_cast<size_t>(8) * bw;
+    sink.pps = static_cast<size_t>(64) * bw * bh;
     SigmaArgs sa;
+    std::memset(&sa, 0, sizeof(sa));
     sa.xyb = xyb;
     sa.rstride = row_stride_elems;
     sa.pstride = row_stride_elems * ys;
@@ -679,6 +726,7 @@ extern "C" jxlr_status jxl_recon_submit_xyb(jxl_recon_ctx* ctx, const float* xyb
     sa.xs = xs; sa.ys = ys; sa.bw = bw; sa.bh = bh;
     sa.sigma = sig;
     sa.sp = sigma_params(*fp);
+    sa.epf = sink;
     launch_sigma(sa, s);
     ctx->launches++;
   }
@@ -693,10 +741,9 @@ extern "C" jxlr_status jxl_recon_submit_xyb(jxl_recon_ctx* ctx, const float* xyb
   fa.out.stride = out->row_stride_bytes;
   fa.out.dtype = out->dtype;
   if (fp->noise) ctx->launches += setup_noise(fa, cv.take<float>(3 * static_cast<size_t>(xs) * ys), s);
-  if (qco) {
-    float* eo = cv.take<float>(static_cast<size_t>(3) * 64 * bw * bh);
-    launch_qco_chain(fa, eo, vmap, qf, ctx->d_dequant, bh, *fp, s);
-    ctx->launches += 3;
+  if (fp->epf) {
+    ctx->launches += launch_epf_chain(slot, fa, eo, sink, qco, vmap, qf, ctx->d_dequant, bh, *fp,
+                                      s);
   } else {
     launch_filter(fa, s);
     ctx->launches++;
@@ -747,6 +794,10 @@ extern "C" jxlr_status jxl_recon_poll(jxl_recon_ctx* ctx, uint64_t ticket, int64
     t.ms[1] = c;   // dequantisation + transforms (+ colour when unfiltered)
     t.ms[2] = d;   // filters + colour
     t.ms[3] = a;   // input staging copies
+    if (slot->epf_marked) {
+      cudaEventElapsedTime(&t.epf_ms, slot->ev[5], slot->ev[6]);
+      t.epf_blocks = slot->h_status[4];
+    }
     if (ctx->timings.size() > 4096) ctx->timings.clear();
     ctx->timings[ticket] = t;
   }
@@ -767,6 +818,17 @@ extern "C" jxlr_status jxl_recon_stage_ms(jxl_recon_ctx* ctx, uint64_t ticket, f
   auto it = ctx->timings.find(ticket);
   if (it == ctx->timings.end()) return fail(JXLR_EINVAL, "stage_ms: no timing for this ticket");
   std::memcpy(ms, it->second.ms, sizeof(float) * 4);
+  return JXLR_OK;
+}
+
+extern "C" jxlr_status jxl_recon_epf_stats(jxl_recon_ctx* ctx, uint64_t ticket, float* epf_ms,
+                                           uint32_t* epf_blocks) {
+  if (!ctx || !epf_ms || !epf_blocks) return fail(JXLR_EINVAL, "epf_stats: null argument");
+  std::lock_guard<std::mutex> lock(ctx->mu);
+  auto it = ctx->timings.find(ticket);
+  if (it == ctx->timings.end()) return fail(JXLR_EINVAL, "epf_stats: no timing for this ticket");
+  *epf_ms = it->second.epf_ms;
+  *epf_blocks = it->second.epf_blocks;
   return JXLR_OK;
 }
 
@@ -813,7 +875,7 @@ extern "C" jxlr_status jxl_recon_submit_jpeg(jxl_recon_ctx* ctx, const jxl_jpeg_
 
   size_t need = 0;
   auto add = [&](size_t bytes) { need = align_up(need, 256) + bytes; };
-  add(16);
+  add(sizeof(unsigned) * kStatusWords);
   for (int c = 0; c < nc; ++c) {
     const size_t nb = static_cast<size_t>(st->comp[c].width_in_blocks) * st->comp[c].height_in_blocks;
     if (!st->on_device) add(nb * 128);
@@ -835,11 +897,12 @@ extern "C" jxlr_status jxl_recon_submit_jpeg(jxl_recon_ctx* ctx, const jxl_jpeg_
   jxlr_status status = acquire_slot(ctx, need, &slot);
   if (status != JXLR_OK) return status;
   slot->timed = ctx->timing;
+  slot->epf_marked = false;
   slot->t_submit = Clock::now();
   cudaStream_t s = slot->stream;
   Carve cv(slot->arena);
-  unsigned* d_status = cv.take<unsigned>(4);
-  CK(cudaMemsetAsync(d_status, 0, 16, s));
+  unsigned* d_status = cv.take<unsigned>(kStatusWords);
+  CK(cudaMemsetAsync(d_status, 0, kStatusWords * sizeof(unsigned), s));
   mark(slot, 0);
   const int16_t* coef[3] = {nullptr, nullptr, nullptr};
   for (int c = 0; c < nc; ++c) {

@@ -8,10 +8,15 @@
 //               from luma, I.2.7 LLF from DC, I.2.4 inverse transforms of
 //               all 15 shapes in shared memory (row pass, column pass), then
 //               either L.2 colour + store, or planar XYB + the J.2.4 sigma
-//               of every 8x8 block.
+//               of every 8x8 block (+ the EPF's block list).
 //   k_sigma     the J.2.4 sigma pass alone, for XYB supplied by the caller.
-//   k_filter    one output tile per CTA: J.2 edge-preserving filter on the
-//               tile plus a one-sample ring, J.4 Gaborish, L.2 colour, store.
+//   k_epf_work  J.2 on the 8x8 blocks with sigma >= 16, which the sigma
+//               pass lists (it copies the others, which J.2 leaves
+//               unchanged), into a planar XYB buffer.
+//   k_filter    J.4 Gaborish, K.5 noise, L.2 colour and store of a 32x32
+//               tile (after k_epf_work, or on the reconstruction).
+//   k_epf       single-launch form for the batch and no-allocation entry
+//               points: J.2 on a tile plus a one-sample ring, J.4, L.2.
 //
 // The inverse transforms run as unscaled cosine sums
 // x[n] = sum_k c[k] cos((2n+1) k pi / 2N); the per-frequency scale of the
@@ -654,8 +659,9 @@ __device__ void fwd_col_item(float (*S)[kPR][kRS], float (*T)[kPR][kRS], const C
 __device__ void cell_sigma(float (*S)[kPR][kRS], CellState& cs, const SigmaParams& sp,
                            int gbx0, int gby0, int xs, int ys, int bw, int bh,
                            const float* __restrict__ acmul, const uint8_t* __restrict__ sharp,
-                           int16_t* __restrict__ sigma) {
+                           int16_t* __restrict__ sigma, const EpfSink& epf) {
   const int tid = threadIdx.x;
+  int sv = -1;                                  // sigma of block tid (tid < 16, in the image)
   {
     const int b = tid >> 3, r = tid & 7;        // block b (0..15), row r
     const int lx0 = 8 * (b & 3), ly = 8 * (b >> 2) + r;
@@ -701,6 +707,7 @@ __device__ void cell_sigma(float (*S)[kPR][kRS], CellState& cs, const SigmaParam
     const int o = cs.owner[b];
     if (o < 0 && gbx < bw && gby < bh) {
       sigma[gby * bw + gbx] = 0;   // not covered (ill-formed map): unfiltered
+      sv = 0;
     } else if (o >= 0 && gbx < bw && gby < bh && gbx * 8 < xs && gby * 8 < ys) {
       const CellVB& v = cs.vb[o];
       const int w8 = 1 << (v.lw - 3), h8 = 1 << (v.lh - 3);
@@ -717,7 +724,36 @@ __device__ void cell_sigma(float (*S)[kPR][kRS], CellState& cs, const SigmaParam
       if (si > 672) si = 672;
       if (si < 0) si = 0;
       sigma[bi] = static_cast<int16_t>(si);
+      sv = si;
     }
+  }
+  if (!epf.list) return;
+  // the EPF's work: the blocks it filters, cell by cell; the others (which
+  // it leaves unchanged) copied to its output
+  __shared__ unsigned s_pass;
+  if (tid < 32) {
+    const bool filt = sv >= 16;
+    const unsigned fm = __ballot_sync(0xFFFFFFFFu, filt);
+    const unsigned pm = __ballot_sync(0xFFFFFFFFu, sv >= 0 && !filt);
+    unsigned base = 0;
+    if (tid == 0) {
+      s_pass = pm;
+      if (fm) base = atomicAdd(epf.count, static_cast<unsigned>(__popc(fm)));
+    }
+    base = __shfl_sync(0xFFFFFFFFu, base, 0);
+    if (filt) epf.list[base + __popc(fm & ((1u << tid) - 1u))] = (gby0 + (tid >> 2)) * bw + gbx0 + (tid & 3);
+  }
+  __syncthreads();
+  const unsigned pm = s_pass;
+  if (!pm) return;
+  const int hp = 8 * bh, wp = 8 * bw;
+  for (int i = tid; i < 3 * 32 * 8; i += blockDim.x) {
+    const int c = i / 256, y = (i >> 3) & 31, k4 = i & 7;
+    if (!((pm >> ((y >> 3) * 4 + (k4 >> 1))) & 1u)) continue;
+    const int gy = gby0 * 8 + y, gx = gbx0 * 8 + 4 * k4;
+    if (gy < hp && gx < wp)
+      *reinterpret_cast<float4*>(epf.pass + c * epf.pps + static_cast<size_t>(gy) * epf.prs + gx) =
+          *reinterpret_cast<const float4*>(&S[c][y][4 * k4]);
   }
 }
 
@@ -1151,7 +1187,8 @@ __device__ __forceinline__ void recon_cell(const ReconArgs& a, int cxi, int cyi)
       }
     }
     if (a.sigma)
-      cell_sigma(S, cs, a.sp, gbx0, gby0, a.xs, a.ys, a.bw, a.bh, a.acmul, a.sharp, a.sigma);
+      cell_sigma(S, cs, a.sp, gbx0, gby0, a.xs, a.ys, a.bw, a.bh, a.acmul, a.sharp, a.sigma,
+                 a.epf);
   } else {
     for (int i = tid; i < 32 * 8; i += blockDim.x) {
       const int y = i >> 3, k4 = i & 7;
@@ -1457,7 +1494,7 @@ __global__ void __launch_bounds__(128) k_sigma(const SigmaArgs a) {
     S[c][y][x] = (gy < a.ys && gx < a.xs) ? a.xyb[c * a.pstride + gy * a.rstride + gx] : 0.f;
   }
   __syncthreads();
-  cell_sigma(S, cs, a.sp, gbx0, gby0, a.xs, a.ys, a.bw, a.bh, a.acmul, a.sharp, a.sigma);
+  cell_sigma(S, cs, a.sp, gbx0, gby0, a.xs, a.ys, a.bw, a.bh, a.acmul, a.sharp, a.sigma, a.epf);
 }
 
 void launch_sigma(const SigmaArgs& a, cudaStream_t s) {
@@ -1508,7 +1545,9 @@ __device__ void apply_noise(const FilterArgs& a, int x, int y, float& X, float& 
 }
 
 // ---------------------------------------------------------------------------
-// k_epf: J.2 with shared per-offset patch sums, then J.4 + L.2 (30x30 tile)
+// k_epf: J.2 with shared per-offset patch sums, then J.4 + L.2 (30x30 tile),
+// in one launch (the batch and no-allocation entry points, which have no
+// buffer for an intermediate image).
 //
 // The 3x4 patch SAD of J.2.3 is a box sum of the per-offset distance image
 // D_o(q) = sum_c |g_c(q) - g_c(q + o)|.  For each horizontal offset ox the
@@ -1535,7 +1574,7 @@ constexpr int kWW = 42, kWH = 40;        // sample / guide window, origin (x0-5,
 constexpr int kGS = 49;                  // guide row stride (words), = 17 mod 32: the
                                          // 8 rows x 4 runs a warp reads hit 32 banks
 
-template <bool kClamp, bool kNoise = false>
+template <bool kClamp>
 __device__ __forceinline__ void epf_tile(const FilterArgs& a, int tbx, int tby) {
   __shared__ float F[3][kWH][kWW];
   __shared__ uint32_t G[kWH][kGS];
@@ -1721,19 +1760,6 @@ __device__ __forceinline__ void epf_tile(const FilterArgs& a, int tbx, int tby) 
   }
   __syncthreads();
 
-  if (a.epf_out) {   // EPF result only (the quantization constraint follows)
-    for (int i = tid; i < kET * kET; i += 128) {
-      const int ty = i / kET, tx = i - ty * kET;
-      const int gy = y0 + ty, gx = x0 + tx;
-      if (gy < a.ys && gx < a.xs) {
-        float* o = a.epf_out + static_cast<size_t>(gy) * a.ors + gx;
-#pragma unroll
-        for (int c = 0; c < 3; ++c) o[c * a.ops] = E[c][ty + 1][tx + 1];
-      }
-    }
-    return;
-  }
-
   // ---- J.4 Gaborish + L.2 + store: each thread walks a column of up to 8
   // pixels keeping the centre and the left+right sum of the previous, current
   // and next rows (3 shared loads per pixel and channel) ------------------
@@ -1766,7 +1792,6 @@ __device__ __forceinline__ void epf_tile(const FilterArgs& a, int tbx, int tby) 
         }
         float X[4] = {v[0], 0.f, 0.f, 0.f}, Y[4] = {v[1], 0.f, 0.f, 0.f};
         float B[4] = {v[2], 0.f, 0.f, 0.f};
-        if (kNoise) apply_noise(a, gx, gy, X[0], Y[0], B[0]);
         emit4(a.cp, a.out, gx, gy, 1, X, Y, B);
       }
     }
@@ -1860,9 +1885,192 @@ __global__ void __launch_bounds__(256) k_filter(const __grid_constant__ FilterAr
   gab_tile(a, blockIdx.x, blockIdx.y);
 }
 
-template <bool kClamp, bool kNoise>
+template <bool kClamp>
 __global__ void __launch_bounds__(128, 4) k_epf(const __grid_constant__ FilterArgs a) {
-  epf_tile<kClamp, kNoise>(a, blockIdx.x, blockIdx.y);
+  epf_tile<kClamp>(a, blockIdx.x, blockIdx.y);
+}
+
+// ---------------------------------------------------------------------------
+// J.2 on the 8x8 blocks that the filter changes (the submit entry points).
+//
+// A block whose sigma is below 16 passes its samples through unchanged, so
+// its pixels need no patch sums.  The sigma pass (k_recon / k_sigma) lists
+// the others, 32x32 cell by cell, so that consecutive entries are
+// neighbours (their windows share cache lines), and copies the others to
+// the J.2 output; k_epf_work filters the listed blocks into that output.
+//   k_epf_work  persistent one-warp CTAs taking 2 listed blocks at a time:
+//               per block a window of mirrored samples and packed guide
+//               bytes (6.5, J.2.2), then per horizontal offset ox
+//               step 1  the horizontal 4-sums H_o of the 10 rows the block's
+//                       3x4 patches touch (block rows -1..8) for the 7
+//                       vertical offsets, as 16-bit values, one lane per
+//                       (block, row, oy) unit;
+//               step 2  one lane per half column (4 rows) of a block,
+//                       walking its rows with the sliding vertical 3-sum,
+//                       the J.2.4 weight and the J.2.5 sums.
+//               Weights, cut-off and summation order are those of k_epf, so
+//               the two kernels give the same bits.  Warps synchronise only
+//               within themselves: a CTA never waits on another warp.
+// ---------------------------------------------------------------------------
+constexpr int kLG = 2;                            // blocks per warp and round (the lane
+                                                  // layout of step 2 assumes 2)
+constexpr int kLGH = 16, kLGW = 18, kLGS = 19;    // guide window, origin (-4, -4) of the block
+constexpr int kLFH = 14, kLFW = 15, kLFS = 18;    // sample window, origin (-3, -3); row stride
+constexpr int kLFC = kLFH * kLFS;                 // floats per channel
+constexpr int kLFB = 784;                         // floats per block (>= 3 kLFC, = 16 mod 32:
+                                                  // the lane groups of step 2 hit different banks)
+constexpr int kLHR = 10;                          // rows of horizontal sums per block
+
+template <bool kClamp>
+__global__ void __launch_bounds__(32, 20) k_epf_work(const __grid_constant__ FilterArgs a,
+                                                     const int* __restrict__ list,
+                                                     const unsigned* __restrict__ count) {
+  __shared__ uint32_t G[kLG][kLGH][kLGS];
+  __shared__ float F[kLG][kLFB];
+  __shared__ __align__(16) uint16_t Hb[kLG][7][kLHR][8];
+  const int lane = threadIdx.x;
+  const int total = static_cast<int>(*count);
+  const int C = 0x3F800000;
+  const int T16 = static_cast<int>((a.wmin_bits + 0xFFFFu) & 0xFFFF0000u);
+  // step 2: lane = (block sk, rows 4 hh .. 4 hh + 3, column cx)
+  const int sk = lane >> 4, hh = (lane >> 3) & 1, cx = lane & 7, r0 = 4 * hh;
+  for (int grp = blockIdx.x; kLG * grp < total; grp += gridDim.x) {
+    const int nb = min(kLG, total - kLG * grp);
+    // ---- windows of mirrored samples and packed guide bytes (6.5, J.2.2) --
+#pragma unroll
+    for (int k = 0; k < kLG; ++k) {
+      if (k >= nb) break;
+      const int b = __ldg(list + kLG * grp + k);
+      const int by = b / a.bw;
+      const int wx0 = 8 * (b - by * a.bw) - 4, wy0 = 8 * by - 4;
+      const bool inner = wx0 >= 0 && wy0 >= 0 && wx0 + kLGW <= a.xs && wy0 + kLGH <= a.ys;
+      constexpr int kPer = (kLGH * kLGW + 31) / 32;   // 9
+      float wv[kPer][3];
+#pragma unroll
+      for (int q = 0; q < kPer; ++q) {
+        const int p = lane + 32 * q;
+        const int ly = p / kLGW, lx = p - ly * kLGW;
+        const int gy = inner ? wy0 + ly : mirror_coord(wy0 + ly, a.ys);
+        const int gx = inner ? wx0 + lx : mirror_coord(wx0 + lx, a.xs);
+        const size_t off = static_cast<size_t>(gy) * a.rstride + gx;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) wv[q][c] = __ldg(a.xyb + c * a.pstride + off);
+      }
+#pragma unroll
+      for (int q = 0; q < kPer; ++q) {
+        const int p = lane + 32 * q;
+        const int ly = p / kLGW, lx = p - ly * kLGW;
+        uint32_t g = 0;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const float sc = fminf(fmaxf(guide_scaled(a.sp, c, wv[q][c]), 0.f), 255.f);
+          g |= static_cast<uint32_t>(sc) << (8 * c);
+        }
+        G[k][ly][lx] = g;
+        if (ly >= 1 && ly <= kLFH && lx >= 1 && lx <= kLFW) {
+#pragma unroll
+          for (int c = 0; c < 3; ++c) F[k][c * kLFC + (ly - 1) * kLFS + (lx - 1)] = wv[q][c];
+        }
+      }
+    }
+
+    // ---- this lane's half column (step 2) --------------------------------
+    const bool strip = sk < nb;
+    const int sb0 = strip ? __ldg(list + kLG * grp + sk) : 0;
+    const int sby = sb0 / a.bw, sbx = sb0 - sby * a.bw;
+    int Mneg = 0, vmax = -1;
+    if (strip) {
+      const int sg = min(max(static_cast<int>(a.sigma[sb0]), 16), 672);
+      const int M = 16 * c_mul4[sg];
+      Mneg = -M;
+      vmax = (M < 0 && C >= T16) ? (C - T16) / (-M) : -1;
+    }
+    float ax[4], ay[4], ab[4], ws[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) { ax[r] = ay[r] = ab[r] = ws[r] = 0.f; }
+    const int nunits = 7 * kLHR * nb;   // step-1 units (block, row, oy)
+    __syncwarp();
+
+#pragma unroll 1
+    for (int g = 0; g < 8; ++g) {
+      const int ox = g - 3;
+      // ---- step 1 ----------------------------------------------------------
+#pragma unroll 1
+      for (int u = lane; u < nunits; u += 32) {
+        const int kj = u / 7, oi = u - 7 * kj;
+        const int k = kj / kLHR, j = kj - kLHR * k;
+        const uint32_t* own = &G[k][j + 3][3];
+        const uint32_t* nbp = &G[k][j + oi][3 + ox];
+        uint32_t d[11];   // sum over the 3 channel bytes of |own - neighbour|
+#pragma unroll
+        for (int i = 0; i < 11; ++i) d[i] = __vsadu4(own[i], nbp[i]);
+        uint32_t h[8];
+        h[0] = d[0] + d[1] + d[2] + d[3];
+#pragma unroll
+        for (int i = 1; i < 8; ++i) h[i] = h[i - 1] + d[i + 3] - d[i - 1];
+        *reinterpret_cast<uint4*>(&Hb[k][oi][j][0]) =
+            make_uint4(h[0] | (h[1] << 16), h[2] | (h[3] << 16), h[4] | (h[5] << 16),
+                       h[6] | (h[7] << 16));
+      }
+      __syncwarp();
+
+      // ---- step 2 ----------------------------------------------------------
+      if (strip) {
+        const float* Fk = &F[sk][0];
+        const int col = cx + ox + 3;
+        float sx[10], sy[10], sb[10];
+#pragma unroll
+        for (int m = 0; m < 10; ++m) {
+          sx[m] = Fk[(r0 + m) * kLFS + col];
+          sy[m] = Fk[kLFC + (r0 + m) * kLFS + col];
+          sb[m] = Fk[2 * kLFC + (r0 + m) * kLFS + col];
+        }
+#pragma unroll
+        for (int oi = 0; oi < 7; ++oi) {
+          int hv[6];
+#pragma unroll
+          for (int jj = 0; jj < 6; ++jj) hv[jj] = Hb[sk][oi][r0 + jj][cx];
+          int v = hv[0] + hv[1] + hv[2];
+#pragma unroll
+          for (int r = 0; r < 4; ++r) {
+            if (r > 0) v += hv[r + 2] - hv[r - 1];
+            uint32_t bits;
+            if (kClamp) {
+              const int s = min(v, 507);
+              bits = static_cast<uint32_t>(0x3F800000 - s * Mneg) & 0xFFFF0000u;
+              if (bits < a.wmin_bits) bits = 0;
+            } else {
+              bits = (0x3F800000u - static_cast<uint32_t>(v) * static_cast<uint32_t>(Mneg)) &
+                     0xFFFF0000u & ~static_cast<uint32_t>((vmax - v) >> 31);
+            }
+            const float w = __uint_as_float(bits);
+            ax[r] = fmaf(w, sx[r + oi], ax[r]);
+            ay[r] = fmaf(w, sy[r + oi], ay[r]);
+            ab[r] = fmaf(w, sb[r + oi], ab[r]);
+            ws[r] += w;
+          }
+        }
+      }
+      __syncwarp();
+    }
+
+    if (strip) {
+      const int gx = 8 * sbx + cx;
+      if (gx < a.xs) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          const int gy = 8 * sby + r0 + r;
+          if (gy >= a.ys) break;
+          const float inv = 1.f / ws[r];
+          float* o = a.epf_out + static_cast<size_t>(gy) * a.ors + gx;
+          o[0] = ax[r] * inv;
+          o[a.ops] = ay[r] * inv;
+          o[2 * a.ops] = ab[r] * inv;
+        }
+      }
+    }
+    __syncwarp();   // the next group's windows overwrite G and F
+  }
 }
 
 // Multi-image forms of the two filter kernels (tiles in raster order per
@@ -1921,13 +2129,13 @@ static void prefer_shared_carveout() {
   cudaFuncSetAttribute(k_recon_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        static_cast<int>(sizeof(TcShared) + 1024));
   cudaFuncSetAttribute(k_recon_batch, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
-  cudaFuncSetAttribute(k_epf<false, false>, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
-  cudaFuncSetAttribute(k_epf<true, false>, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
-  cudaFuncSetAttribute(k_epf<false, true>, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
-  cudaFuncSetAttribute(k_epf<true, true>, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+  cudaFuncSetAttribute(k_epf<false>, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+  cudaFuncSetAttribute(k_epf<true>, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
   cudaFuncSetAttribute(k_filter_batch<true, false>, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
   cudaFuncSetAttribute(k_filter_batch<true, true>, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
   cudaFuncSetAttribute(k_filter, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+  cudaFuncSetAttribute(k_epf_work<false>, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+  cudaFuncSetAttribute(k_epf_work<true>, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
   cudaGetLastError();
 }
 
@@ -1949,6 +2157,22 @@ int filter_tiles(const FilterArgs& a) {
                : ((a.xs + kTW - 1) / kTW) * ((a.ys + kTH - 1) / kTH);
 }
 
+void launch_epf_work(const FilterArgs& a, const int* list, const unsigned* count, cudaStream_t s) {
+  // resident one-warp CTAs of k_epf_work on the current device (persistent grid)
+  static int grid_of[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  int& grid = grid_of[dev & 63];
+  if (grid == 0) {
+    int sms = 0, per = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_epf_work<false>, 32, 0);
+    grid = (sms > 0 ? sms : 1) * (per > 0 ? per : 1);
+  }
+  if (filter_needs_clamp(a)) k_epf_work<true><<<grid, 32, 0, s>>>(a, list, count);
+  else k_epf_work<false><<<grid, 32, 0, s>>>(a, list, count);
+}
+
 void launch_filter(const FilterArgs& a, cudaStream_t s) {
   if (a.epf) {
     static const std::vector<int32_t> mul4 = [] {
@@ -1957,14 +2181,8 @@ void launch_filter(const FilterArgs& a, cudaStream_t s) {
       return t;
     }();
     dim3 grid((a.xs + kET - 1) / kET, (a.ys + kET - 1) / kET);
-    const bool clamp = epf_needs_clamp(a, mul4.data());
-    if (a.noise) {
-      if (clamp) k_epf<true, true><<<grid, 128, 0, s>>>(a);
-      else k_epf<false, true><<<grid, 128, 0, s>>>(a);
-    } else {
-      if (clamp) k_epf<true, false><<<grid, 128, 0, s>>>(a);
-      else k_epf<false, false><<<grid, 128, 0, s>>>(a);
-    }
+    if (epf_needs_clamp(a, mul4.data())) k_epf<true><<<grid, 128, 0, s>>>(a);
+    else k_epf<false><<<grid, 128, 0, s>>>(a);
     return;
   }
   dim3 grid((a.xs + kTW - 1) / kTW, (a.ys + kTH - 1) / kTH);

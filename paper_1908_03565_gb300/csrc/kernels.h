@@ -29,6 +29,18 @@ struct OutParams {
   int dtype;            // jxlr_out_dtype
 };
 
+// Work the sigma pass hands to the EPF (list == nullptr: none): the blocks
+// with sigma >= 16 are appended to list (block indices), *count counting
+// them; the others, which J.2 leaves unchanged, are copied to pass (the J.2
+// output: planar XYB of the padded size, row / plane stride prs / pps in
+// elements, 16-byte aligned rows).
+struct EpfSink {
+  int* list;
+  unsigned* count;
+  float* pass;
+  size_t prs, pps;
+};
+
 struct ReconArgs {
   const int16_t* coef[3];
   size_t cstride;             // elements per coefficient row
@@ -51,6 +63,7 @@ struct ReconArgs {
   unsigned* err;              // error flags of the tensor-core variant
   const float* dc1;           // [3][bh][bw] DC after F.2 smoothing and G, or nullptr
   const float* lfp;           // [3][2bh][2bw] Annex H coefficients, or nullptr
+  EpfSink epf;                // with sigma
 };
 
 struct SigmaArgs {
@@ -62,6 +75,7 @@ struct SigmaArgs {
   int xs, ys, bw, bh;
   int16_t* sigma;
   SigmaParams sp;
+  EpfSink epf;
 };
 
 struct FilterArgs {
@@ -75,8 +89,8 @@ struct FilterArgs {
   SigmaParams sp;             // guide parameters
   ColorParams cp;
   OutParams out;
-  float* epf_out;             // non-null: write the EPF result here (planar XYB,
-  size_t ors, ops;            // row / plane stride in elements) and stop before J.4
+  float* epf_out;             // J.2 result (planar XYB) of k_epf_work,
+  size_t ors, ops;            // row / plane stride in elements
   int noise;                  // K.5 after J.4: channels noise_r [3][ys][nrs]
   const float* noise_r;
   size_t nrs, nps;
@@ -107,6 +121,10 @@ constexpr int kTcBasisBytes = 6144;
 void launch_sigma(const SigmaArgs& a, cudaStream_t s);
 void launch_qco(const QcoArgs& a, cudaStream_t s);
 void launch_filter(const FilterArgs& a, cudaStream_t s);
+// J.2 on the blocks the sigma pass listed (EpfSink), into a.epf_out, where
+// that pass copied the other blocks; J.4 / L.2 then run as launch_filter()
+// on that output.
+void launch_epf_work(const FilterArgs& a, const int* list, const unsigned* count, cudaStream_t s);
 
 // Multi-image launches: args[i] per image (device array), prefix[i] = first
 // work item of image i (prefix[nimg] = total), grid CTAs striding over items.

@@ -1,0 +1,97 @@
+"""The block-sparse J.2 kernel of the submit paths against the single-launch
+EPF kernel of the batch entry point, and its block count.
+
+Both kernels form every weight and every weighted sum in the same order, so
+their results must agree bit for bit; the block-sparse one only skips the
+patch sums of the 8x8 blocks whose sigma is below 16 (J.2.4: their samples
+pass through) and copies those blocks instead.
+"""
+import numpy as np
+import pytest
+
+from oracle import recon as R
+from paper_1908_03565_gb300 import synth
+from test_gpu_parity import B, XYB, F32, U8, params_pair, run  # noqa: F401
+
+pytestmark = pytest.mark.gpu
+
+# Statistics under which the EPF changes most blocks (small AC, smooth DC,
+# AcMul 0.5) and those of the throughput workload (most weights cut off).
+ACTIVE = dict(coef_scale=2.0, acmul=0.5, dc='smooth')
+
+
+@pytest.fixture(scope="module")
+def tctx(B):
+    c = B.Context(max_slots=2, timing=True)
+    yield c
+    c.close()
+
+
+def _fused(B, ctx, img, lp, dtype):
+    """The same request through a one-image batch (the single-launch EPF)."""
+    import torch
+    dimg = B.to_device(img, torch)
+    shape, npd = B.out_shape(img, dtype)
+    tdt = {np.float32: torch.float32, np.float16: torch.float16, np.uint8: torch.uint8}[npd]
+    out = torch.full(shape, 7, dtype=tdt, device="cuda")
+    b = ctx.batch([(dimg, lp, out, dtype)], autotune=False)
+    stream = torch.cuda.Stream()
+    b.launch(stream.cuda_stream)
+    stream.synchronize()
+    b.close()
+    return out.cpu().numpy()
+
+
+@pytest.mark.parametrize("xs,ys,stats", [(9, 13, 'active'), (33, 17, 'active'),
+                                         (97, 61, 'active'), (300, 264, 'active'),
+                                         (520, 264, 'workload'), (131, 77, 'workload')])
+@pytest.mark.parametrize("gab", [False, True])
+def test_block_kernel_equals_single_launch(B, tctx, xs, ys, stats, gab):
+    kw = ACTIVE if stats == 'active' else {}
+    img = synth.make_image(xs, ys, 5 * xs + ys, **kw)
+    _, lp = params_pair(B, epf=True, gab=gab)
+    for dtype in (XYB, F32, U8):
+        np.testing.assert_array_equal(run(B, tctx, img, lp, dtype), _fused(B, tctx, img, lp, dtype))
+
+
+def _count_and_sigma(B, ctx, img, lp):
+    import torch
+    dimg = B.to_device(img, torch)
+    shape, _ = B.out_shape(img, F32)
+    out = torch.empty(shape, dtype=torch.float32, device="cuda")
+    t = ctx.submit(dimg, lp, out, F32, on_device=True)
+    ctx.poll(t)
+    return ctx.epf_stats(t)
+
+
+@pytest.mark.parametrize("xs,ys,stats", [(300, 264, 'active'), (520, 264, 'workload'),
+                                         (33, 17, 'active')])
+def test_block_count(B, tctx, xs, ys, stats):
+    """The filtered blocks are those with sigma >= 16: the oracle's binary32
+    sigma of the GPU's own XYB samples gives the same count."""
+    kw = ACTIVE if stats == 'active' else {}
+    img = synth.make_image(xs, ys, 7 * xs + ys, **kw)
+    p, lp = params_pair(B, epf=True, gab=True)
+    xyb = run(B, tctx, img, params_pair(B)[1], XYB).transpose(2, 0, 1).astype(np.float64)
+    sig = R.epf_sigma(xyb, img['vmap'], img['acmul'], img['sharpness'], p)
+    ms, n = _count_and_sigma(B, tctx, img, lp)
+    assert n == int(np.sum(sig >= 16))
+    assert 0 < n < sig.size
+    assert ms > 0
+
+
+def test_all_blocks_pass(B, tctx):
+    """sigma_max below 16: no block is filtered, and the output is that of
+    Gaborish alone."""
+    img = synth.make_image(200, 136, 91, **ACTIVE)
+    lp = B.filter_defaults(epf=1, gab=1, epf_sigma_max=15)
+    ms, n = _count_and_sigma(B, tctx, img, lp)
+    assert n == 0
+    np.testing.assert_array_equal(run(B, tctx, img, lp, F32),
+                                  run(B, tctx, img, B.filter_defaults(gab=1), F32))
+    np.testing.assert_array_equal(run(B, tctx, img, lp, F32), _fused(B, tctx, img, lp, F32))
+
+
+def test_no_epf_stats_without_the_filter(B, tctx):
+    ms, n = _count_and_sigma(B, tctx, synth.make_image(64, 64, 3), B.filter_defaults(gab=1))
+    assert (ms, n) == (0.0, 0)
