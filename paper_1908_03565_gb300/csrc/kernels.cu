@@ -1904,7 +1904,8 @@ __global__ void __launch_bounds__(128, 4) k_epf(const __grid_constant__ FilterAr
 //               step 1  the horizontal 4-sums H_o of the 10 rows the block's
 //                       3x4 patches touch (block rows -1..8) for the 7
 //                       vertical offsets, as 16-bit values, one lane per
-//                       (block, row, oy) unit;
+//                       (block, row) walking the 7 offsets with its own
+//                       guide bytes in registers;
 //               step 2  one lane per half column (4 rows) of a block,
 //                       walking its rows with the sliding vertical 3-sum,
 //                       the J.2.4 weight and the J.2.5 sums.
@@ -1988,29 +1989,33 @@ __global__ void __launch_bounds__(32, 20) k_epf_work(const __grid_constant__ Fil
     float ax[4], ay[4], ab[4], ws[4];
 #pragma unroll
     for (int r = 0; r < 4; ++r) { ax[r] = ay[r] = ab[r] = ws[r] = 0.f; }
-    const int nunits = 7 * kLHR * nb;   // step-1 units (block, row, oy)
+    // step 1: lane = (block k1, row j1) for the first 10 nb lanes
+    const int k1 = lane >= kLHR ? 1 : 0, j1 = lane - kLHR * k1;
+    const bool row1 = lane < kLHR * nb;
     __syncwarp();
 
 #pragma unroll 1
     for (int g = 0; g < 8; ++g) {
       const int ox = g - 3;
-      // ---- step 1 ----------------------------------------------------------
-#pragma unroll 1
-      for (int u = lane; u < nunits; u += 32) {
-        const int kj = u / 7, oi = u - 7 * kj;
-        const int k = kj / kLHR, j = kj - kLHR * k;
-        const uint32_t* own = &G[k][j + 3][3];
-        const uint32_t* nbp = &G[k][j + oi][3 + ox];
-        uint32_t d[11];   // sum over the 3 channel bytes of |own - neighbour|
+      // ---- step 1: lane (block k1, row j1) walks the 7 offsets oy ----------
+      if (row1) {
+        uint32_t own[11];
 #pragma unroll
-        for (int i = 0; i < 11; ++i) d[i] = __vsadu4(own[i], nbp[i]);
-        uint32_t h[8];
-        h[0] = d[0] + d[1] + d[2] + d[3];
+        for (int i = 0; i < 11; ++i) own[i] = G[k1][j1 + 3][3 + i];
 #pragma unroll
-        for (int i = 1; i < 8; ++i) h[i] = h[i - 1] + d[i + 3] - d[i - 1];
-        *reinterpret_cast<uint4*>(&Hb[k][oi][j][0]) =
-            make_uint4(h[0] | (h[1] << 16), h[2] | (h[3] << 16), h[4] | (h[5] << 16),
-                       h[6] | (h[7] << 16));
+        for (int oi = 0; oi < 7; ++oi) {
+          const uint32_t* nbp = &G[k1][j1 + oi][3 + ox];
+          uint32_t d[11];   // sum over the 3 channel bytes of |own - neighbour|
+#pragma unroll
+          for (int i = 0; i < 11; ++i) d[i] = __vsadu4(own[i], nbp[i]);
+          uint32_t h[8];
+          h[0] = d[0] + d[1] + d[2] + d[3];
+#pragma unroll
+          for (int i = 1; i < 8; ++i) h[i] = h[i - 1] + d[i + 3] - d[i - 1];
+          *reinterpret_cast<uint4*>(&Hb[k1][oi][j1][0]) =
+              make_uint4(h[0] | (h[1] << 16), h[2] | (h[3] << 16), h[4] | (h[5] << 16),
+                         h[6] | (h[7] << 16));
+        }
       }
       __syncwarp();
 
