@@ -593,7 +593,7 @@ def main():
             for t in q:
                 ectx.poll(t)
 
-        e2e_steps(3)
+        e2e_steps(max(10, args.warmup))
         barrier()
         n_e2e = max(6, min(args.steps, 30))
         reps = []

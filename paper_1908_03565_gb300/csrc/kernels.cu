@@ -1207,7 +1207,7 @@ __device__ __forceinline__ void recon_cell(const ReconArgs& a, int cxi, int cyi)
   }
 }
 
-__global__ void __launch_bounds__(128, 6) k_recon(const __grid_constant__ ReconArgs a) {
+__global__ void __launch_bounds__(128, 7) k_recon(const __grid_constant__ ReconArgs a) {
   recon_cell(a, blockIdx.x, blockIdx.y);
 }
 

@@ -54,6 +54,14 @@ def test_block_kernel_equals_single_launch(B, tctx, xs, ys, stats, gab):
         np.testing.assert_array_equal(run(B, tctx, img, lp, dtype), _fused(B, tctx, img, lp, dtype))
 
 
+def test_block_kernel_many_groups_per_warp(B, tctx):
+    """A size where every persistent warp of k_epf_work takes several groups
+    of listed blocks (about 21,000 blocks filtered, 2 per group)."""
+    img = synth.make_image(2048, 1088, 77, **ACTIVE)
+    _, lp = params_pair(B, epf=True, gab=True)
+    np.testing.assert_array_equal(run(B, tctx, img, lp, F32), _fused(B, tctx, img, lp, F32))
+
+
 def _count_and_sigma(B, ctx, img, lp):
     import torch
     dimg = B.to_device(img, torch)
