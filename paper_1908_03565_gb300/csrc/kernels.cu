@@ -1799,15 +1799,16 @@ __device__ __forceinline__ void epf_tile(const FilterArgs& a, int tbx, int tby) 
 }
 
 // ---------------------------------------------------------------------------
-// J.4 Gaborish (optional) + L.2 + store without the EPF: 32x32 tile, 256
-// threads.  The tile and a one-sample ring (mirrored at the image bounds,
-// 6.5) are loaded with all of a thread's loads in flight; each thread then
-// walks 4 rows of one column, 3 shared loads per pixel and channel.
+// J.4 Gaborish (optional) + K.5 + L.2 + store: 32x32 tile, 256 threads.  The
+// tile and a one-sample ring (mirrored at the image bounds, 6.5) are loaded
+// with all of a thread's loads in flight; each thread then takes 4
+// neighbouring pixels of one row (6 x 3 samples per channel as one 16-byte
+// and one 8-byte shared load per row) and stores them as 16-byte words.
 // ---------------------------------------------------------------------------
-constexpr int kGT = 32, kGR = kGT + 2, kGS2 = kGR + 1;
+constexpr int kGT = 32, kGR = kGT + 2, kGS2 = 36;   // rows of 16-byte aligned 144 bytes
 
 __device__ __forceinline__ void gab_tile(const FilterArgs& a, int tbx, int tby) {
-  __shared__ float Wn[3][kGR][kGS2];
+  __shared__ __align__(16) float Wn[3][kGR][kGS2];
   const int tid = threadIdx.x;
   const int x0 = tbx * kGT, y0 = tby * kGT;
   const bool inner = x0 >= 1 && y0 >= 1 && x0 + kGT + 1 <= a.xs && y0 + kGT + 1 <= a.ys;
@@ -1835,36 +1836,34 @@ __device__ __forceinline__ void gab_tile(const FilterArgs& a, int tbx, int tby) 
     }
   }
   __syncthreads();
-  const int tx = tid & 31, ty0 = (tid >> 5) * 4;
-  const int gx = x0 + tx;
-  if (gx >= a.xs) return;
-  float bp[3], sp[3], bc[3], sc[3];
+  const int tx4 = tid & 7, ty = tid >> 3;   // pixels 4 tx4 .. 4 tx4 + 3 of row ty
+  const int gx = x0 + 4 * tx4, gy = y0 + ty;
+  if (gx >= a.xs || gy >= a.ys) return;
+  const int n = min(4, a.xs - gx);
+  float o[3][4];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    bp[c] = Wn[c][ty0][tx + 1];
-    sp[c] = Wn[c][ty0][tx] + Wn[c][ty0][tx + 2];
-    bc[c] = Wn[c][ty0 + 1][tx + 1];
-    sc[c] = Wn[c][ty0 + 1][tx] + Wn[c][ty0 + 1][tx + 2];
-  }
+    float w[3][6];   // window rows ty .. ty + 2 (image rows gy - 1 .. gy + 1), columns 4 tx4 ..
 #pragma unroll
-  for (int r = 0; r < 4; ++r) {
-    const int ty = ty0 + r, gy = y0 + ty;
-    if (gy >= a.ys) break;
-    float o[3];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      const float bn = Wn[c][ty + 2][tx + 1];
-      const float sn = Wn[c][ty + 2][tx] + Wn[c][ty + 2][tx + 2];
-      o[c] = a.gab ? fmaf(a.gw[c][0], bc[c],
-                          fmaf(a.gw[c][1], bp[c] + bn + sc[c], a.gw[c][2] * (sp[c] + sn)))
-                   : bc[c];
-      bp[c] = bc[c]; sp[c] = sc[c];
-      bc[c] = bn; sc[c] = sn;
+    for (int r = 0; r < 3; ++r) {
+      const float4 q = *reinterpret_cast<const float4*>(&Wn[c][ty + r][4 * tx4]);
+      const float2 e = *reinterpret_cast<const float2*>(&Wn[c][ty + r][4 * tx4 + 4]);
+      w[r][0] = q.x; w[r][1] = q.y; w[r][2] = q.z; w[r][3] = q.w; w[r][4] = e.x; w[r][5] = e.y;
     }
-    float X[4] = {o[0], 0.f, 0.f, 0.f}, Y[4] = {o[1], 0.f, 0.f, 0.f}, B[4] = {o[2], 0.f, 0.f, 0.f};
-    if (a.noise) apply_noise(a, gx, gy, X[0], Y[0], B[0]);
-    emit4(a.cp, a.out, gx, gy, 1, X, Y, B);
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+      const float edge = (w[0][p + 1] + w[2][p + 1]) + (w[1][p] + w[1][p + 2]);
+      const float corner = (w[0][p] + w[0][p + 2]) + (w[2][p] + w[2][p + 2]);
+      o[c][p] = a.gab ? fmaf(a.gw[c][0], w[1][p + 1], fmaf(a.gw[c][1], edge, a.gw[c][2] * corner))
+                      : w[1][p + 1];
+    }
   }
+  if (a.noise) {
+#pragma unroll
+    for (int p = 0; p < 4; ++p)
+      if (p < n) apply_noise(a, gx + p, gy, o[0][p], o[1][p], o[2][p]);
+  }
+  emit4(a.cp, a.out, gx, gy, n, o[0], o[1], o[2]);
 }
 
 // True when Weight()'s clamp of sad at 507 can change a weight that survives
