@@ -4,10 +4,15 @@
 // Every image keeps its own parameter block (sizes, pointers, filters,
 // output encoding) in device memory; the multi-image kernels map their work
 // items (32x32 cells for the transforms, filter tiles) to (image, cell) by a
-// prefix array.  The grid of each kernel (one CTA per item, or a persistent
-// multiple of the resident CTAs) is chosen by timing on the batch itself
-// when JXLR_BATCH_AUTOTUNE is set, and remembered per batch shape (in this
-// process, and in the file named by $JXLR_AUTOTUNE_CACHE if set).
+// prefix array.  With the EPF, the transform kernel lists each image's 8x8
+// blocks with sigma >= 16 (and copies the others to its J.2 buffer), the
+// J.2 kernel's persistent warps take the images' listed blocks round robin,
+// and Gaborish + colour run on the J.2 buffers with the other images'
+// filter tiles.  The grids of the transform and filter kernels (one CTA per
+// item, or a persistent multiple of the resident CTAs) are chosen by timing
+// on the batch itself when JXLR_BATCH_AUTOTUNE is set, and remembered per
+// batch shape (in this process, and in the file named by
+// $JXLR_AUTOTUNE_CACHE if set); the J.2 kernel keeps its resident grid.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -37,11 +42,11 @@ struct jxl_recon_batch {
   ReconArgs* d_rargs = nullptr;
   int* d_rprefix = nullptr;
   int rtotal = 0;
-  FilterArgs* d_eargs = nullptr;   // images with the EPF
-  int* d_eprefix = nullptr;
+  FilterArgs* d_eargs = nullptr;   // J.2 of the images with the EPF
+  unsigned* d_counts = nullptr;    // their listed-block counts (zeroed per launch)
   int ne = 0, etotal = 0;
   bool clamp = false;
-  FilterArgs* d_fargs = nullptr;   // images with Gaborish only
+  FilterArgs* d_fargs = nullptr;   // Gaborish / colour of every filtered image
   int* d_fprefix = nullptr;
   int nf = 0, ftotal = 0;
   int grid[3] = {0, 0, 0};         // recon, epf, filter
@@ -62,12 +67,11 @@ jxlr_status bfail(jxlr_status s, const std::string& m) {
 }
 
 void enqueue(const jxl_recon_batch* b, const int* grid, cudaStream_t s) {
+  if (b->ne) cudaMemsetAsync(b->d_counts, 0, sizeof(unsigned) * b->ne, s);
   if (b->rtotal) launch_recon_batch(b->d_rargs, b->d_rprefix, static_cast<int>(b->n), b->rtotal,
                                     grid[0], s);
-  if (b->etotal) launch_filter_batch(b->d_eargs, b->d_eprefix, b->ne, b->etotal, true, b->clamp,
-                                     grid[1], s);
-  if (b->ftotal) launch_filter_batch(b->d_fargs, b->d_fprefix, b->nf, b->ftotal, false, false,
-                                     grid[2], s);
+  if (b->ne) launch_epf_work_batch(b->d_eargs, b->ne, b->clamp, grid[1], s);
+  if (b->ftotal) launch_filter_batch(b->d_fargs, b->d_fprefix, b->nf, b->ftotal, grid[2], s);
 }
 
 using Key = std::tuple<uint32_t, int, int, int>;
@@ -107,8 +111,8 @@ void tuned_store(const Key& k, const int* grid) {
 jxlr_status autotune(jxl_recon_batch* b) {
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
-  const int kinds[3] = {0, b->clamp ? 2 : 1, 3};
-  const int totals[3] = {b->rtotal, b->etotal, b->ftotal};
+  const int kinds[3] = {0, 1, 2};
+  const int totals[3] = {b->rtotal, 0, b->ftotal};   // the J.2 kernel keeps its resident grid
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
@@ -126,10 +130,12 @@ jxlr_status autotune(jxl_recon_batch* b) {
       std::vector<float> t;
       for (int rep = 0; rep < 4; ++rep) {
         cudaEventRecord(e0, b->cap);
-        if (k == 0) launch_recon_batch(b->d_rargs, b->d_rprefix, b->n, b->rtotal, g, b->cap);
-        else if (k == 1)
-          launch_filter_batch(b->d_eargs, b->d_eprefix, b->ne, b->etotal, true, b->clamp, g, b->cap);
-        else launch_filter_batch(b->d_fargs, b->d_fprefix, b->nf, b->ftotal, false, false, g, b->cap);
+        if (k == 0) {
+          // the transform kernel appends to the J.2 lists: they restart empty
+          if (b->ne) cudaMemsetAsync(b->d_counts, 0, sizeof(unsigned) * b->ne, b->cap);
+          launch_recon_batch(b->d_rargs, b->d_rprefix, b->n, b->rtotal, g, b->cap);
+        }
+        else launch_filter_batch(b->d_fargs, b->d_fprefix, b->nf, b->ftotal, g, b->cap);
         cudaEventRecord(e1, b->cap);
         cudaEventSynchronize(e1);
         float ms = 0;
@@ -172,8 +178,8 @@ extern "C" jxlr_status jxl_recon_batch_create(jxl_recon_ctx* ctx, const jxl_reco
   if (cudaSetDevice(dev) != cudaSuccess) return bfail(JXLR_ECUDA, "batch_create: set device");
   std::vector<ReconArgs> ra(n);
   std::vector<FilterArgs> ea, fa;
-  std::vector<int> rpre(1, 0), epre(1, 0), fpre(1, 0);
-  std::vector<size_t> scratch_off(n, 0), sig_off(n, 0);
+  std::vector<int> rpre(1, 0), fpre(1, 0);
+  std::vector<size_t> scratch_off(n, 0), sig_off(n, 0), eo_off(n, 0), list_off(n, 0);
   std::vector<int> eimg, fimg;
   size_t scratch = 0;
   uint64_t pixels = 0;
@@ -235,6 +241,12 @@ extern "C" jxlr_status jxl_recon_batch_create(jxl_recon_ctx* ctx, const jxl_reco
         scratch = up(scratch, 256);
         sig_off[i] = scratch;
         scratch += sizeof(int16_t) * size_t(bw) * bh;
+        scratch = up(scratch, 256);
+        eo_off[i] = scratch;                              // J.2 output
+        scratch += sizeof(float) * 3 * size_t(wp) * hp;
+        scratch = up(scratch, 256);
+        list_off[i] = scratch;                            // listed blocks
+        scratch += sizeof(int) * size_t(bw) * bh;
       }
       FilterArgs f = filter_args(*fp);
       f.rstride = wp;
@@ -242,14 +254,16 @@ extern "C" jxlr_status jxl_recon_batch_create(jxl_recon_ctx* ctx, const jxl_reco
       f.xs = xs; f.ys = ys; f.bw = bw;
       f.out = op;
       if (fp->epf) {
+        f.ors = wp;
+        f.ops = size_t(wp) * hp;
         ea.push_back(f);
         eimg.push_back(static_cast<int>(i));
-        epre.push_back(epre.back() + filter_tiles(f));
-      } else {
-        fa.push_back(f);
-        fimg.push_back(static_cast<int>(i));
-        fpre.push_back(fpre.back() + filter_tiles(f));
       }
+      FilterArgs g = f;   // J.4 / L.2 (on the J.2 output with the EPF)
+      g.epf = 0;
+      fa.push_back(g);
+      fimg.push_back(static_cast<int>(i));
+      fpre.push_back(fpre.back() + filter_tiles(g));
     } else {
       a.write_xyb = 0;
       a.out = op;
@@ -263,13 +277,13 @@ extern "C" jxlr_status jxl_recon_batch_create(jxl_recon_ctx* ctx, const jxl_reco
   b->ne = static_cast<int>(ea.size());
   b->nf = static_cast<int>(fa.size());
   b->rtotal = rpre.back();
-  b->etotal = epre.back();
+  b->etotal = b->ne;
   b->ftotal = fpre.back();
   // one device allocation: parameter blocks, prefixes, statuses, scratch
   size_t off = 0;
   auto take = [&](size_t bytes) { off = up(off, 256); size_t o = off; off += bytes; return o; };
   const size_t o_r = take(sizeof(ReconArgs) * n), o_rp = take(sizeof(int) * rpre.size());
-  const size_t o_e = take(sizeof(FilterArgs) * ea.size()), o_ep = take(sizeof(int) * epre.size());
+  const size_t o_e = take(sizeof(FilterArgs) * ea.size()), o_ec = take(sizeof(unsigned) * ea.size());
   const size_t o_f = take(sizeof(FilterArgs) * fa.size()), o_fp = take(sizeof(int) * fpre.size());
   const size_t o_st = take(sizeof(unsigned) * 4 * n);
   const size_t o_sc = take(scratch);
@@ -280,6 +294,8 @@ extern "C" jxlr_status jxl_recon_batch_create(jxl_recon_ctx* ctx, const jxl_reco
     return bfail(JXLR_ENOMEM, "batch_create: device allocation failed");
   }
   char* base = b->dmem;
+  b->d_counts = reinterpret_cast<unsigned*>(base + o_ec);
+  std::vector<float*> eo(n, nullptr);
   for (size_t i = 0; i < n; ++i) {
     if (ra[i].write_xyb) {
       ra[i].xyb = reinterpret_cast<float*>(base + o_sc + scratch_off[i]);
@@ -288,15 +304,28 @@ extern "C" jxlr_status jxl_recon_batch_create(jxl_recon_ctx* ctx, const jxl_reco
     }
   }
   for (size_t j = 0; j < ea.size(); ++j) {
-    ea[j].xyb = ra[eimg[j]].xyb;
-    ea[j].sigma = ra[eimg[j]].sigma;
+    ReconArgs& r = ra[eimg[j]];
+    eo[eimg[j]] = reinterpret_cast<float*>(base + o_sc + eo_off[eimg[j]]);
+    r.epf.list = reinterpret_cast<int*>(base + o_sc + list_off[eimg[j]]);
+    r.epf.count = b->d_counts + j;
+    r.epf.pass = eo[eimg[j]];
+    r.epf.prs = size_t(r.wp);
+    r.epf.pps = size_t(r.wp) * r.hp;
+    ea[j].xyb = r.xyb;
+    ea[j].sigma = r.sigma;
+    ea[j].epf_out = eo[eimg[j]];
+    ea[j].epf_list = r.epf.list;
+    ea[j].epf_count = r.epf.count;
     b->clamp = b->clamp || filter_needs_clamp(ea[j]);
   }
-  for (size_t j = 0; j < fa.size(); ++j) fa[j].xyb = ra[fimg[j]].xyb;
+  for (size_t j = 0; j < fa.size(); ++j) {
+    const int i = fimg[j];
+    fa[j].xyb = eo[i] ? eo[i] : ra[i].xyb;
+    fa[j].sigma = nullptr;
+  }
   b->d_rargs = reinterpret_cast<ReconArgs*>(base + o_r);
   b->d_rprefix = reinterpret_cast<int*>(base + o_rp);
   b->d_eargs = reinterpret_cast<FilterArgs*>(base + o_e);
-  b->d_eprefix = reinterpret_cast<int*>(base + o_ep);
   b->d_fargs = reinterpret_cast<FilterArgs*>(base + o_f);
   b->d_fprefix = reinterpret_cast<int*>(base + o_fp);
   unsigned* d_status = reinterpret_cast<unsigned*>(base + o_st);
@@ -307,7 +336,6 @@ extern "C" jxlr_status jxl_recon_batch_create(jxl_recon_ctx* ctx, const jxl_reco
   h2d(b->d_rargs, ra.data(), sizeof(ReconArgs) * n);
   h2d(b->d_rprefix, rpre.data(), sizeof(int) * rpre.size());
   h2d(b->d_eargs, ea.data(), sizeof(FilterArgs) * ea.size());
-  h2d(b->d_eprefix, epre.data(), sizeof(int) * epre.size());
   h2d(b->d_fargs, fa.data(), sizeof(FilterArgs) * fa.size());
   h2d(b->d_fprefix, fpre.data(), sizeof(int) * fpre.size());
   // C.5.4 validation of every map, once, at creation
@@ -330,8 +358,10 @@ extern "C" jxlr_status jxl_recon_batch_create(jxl_recon_ctx* ctx, const jxl_reco
     }
   ctx_count_launches(ctx, static_cast<int>(n));
   // grids: cached tuning, fresh tuning, or one CTA per work item
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   b->grid[0] = b->rtotal;
-  b->grid[1] = b->etotal;
+  b->grid[1] = b->ne ? sms * batch_blocks_per_sm(1) : 0;   // persistent J.2 grid
   b->grid[2] = b->ftotal;
   const Key key(b->n, b->rtotal, b->etotal, b->ftotal);
   if (tuned_lookup(key, b->grid)) {
@@ -357,7 +387,7 @@ extern "C" jxlr_status jxl_recon_batch_create(jxl_recon_ctx* ctx, const jxl_reco
     jxl_recon_batch_destroy(b);
     return bfail(JXLR_ECUDA, std::string("batch graph: ") + cudaGetErrorString(e));
   }
-  b->kernels = (b->rtotal > 0) + (b->etotal > 0) + (b->ftotal > 0);
+  b->kernels = (b->rtotal > 0) + (b->ne > 0) + (b->ftotal > 0);
   *out = b;
   return JXLR_OK;
 }

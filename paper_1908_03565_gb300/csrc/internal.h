@@ -98,7 +98,7 @@ int ctx_device(const jxl_recon_ctx* c);
 void ctx_count_launches(jxl_recon_ctx* c, int n);
 
 // Resident CTAs per SM of the multi-image kernels (kernels.cu):
-// kind 0 recon, 1 EPF, 2 EPF exact-clamp, 3 Gaborish/colour only.
+// kind 0 recon, 1 EPF (J.2 on the listed blocks), 2 Gaborish/colour.
 int batch_blocks_per_sm(int kind);
 
 // Sets the message jxl_recon_last_error() returns on this thread (api.cpp).

@@ -1921,20 +1921,19 @@ constexpr int kLFB = 784;                         // floats per block (>= 3 kLFC
                                                   // the lane groups of step 2 hit different banks)
 constexpr int kLHR = 10;                          // rows of horizontal sums per block
 
+// The groups g0, g0 + gs, ... of one image's list (total listed blocks).
 template <bool kClamp>
-__global__ void __launch_bounds__(32, 20) k_epf_work(const __grid_constant__ FilterArgs a,
-                                                     const int* __restrict__ list,
-                                                     const unsigned* __restrict__ count) {
+__device__ __forceinline__ void epf_work_groups(const FilterArgs& a, const int* __restrict__ list,
+                                                int total, int g0, int gs) {
   __shared__ uint32_t G[kLG][kLGH][kLGS];
   __shared__ float F[kLG][kLFB];
   __shared__ __align__(16) uint16_t Hb[kLG][7][kLHR][8];
   const int lane = threadIdx.x;
-  const int total = static_cast<int>(*count);
   const int C = 0x3F800000;
   const int T16 = static_cast<int>((a.wmin_bits + 0xFFFFu) & 0xFFFF0000u);
   // step 2: lane = (block sk, rows 4 hh .. 4 hh + 3, column cx)
   const int sk = lane >> 4, hh = (lane >> 3) & 1, cx = lane & 7, r0 = 4 * hh;
-  for (int grp = blockIdx.x; kLG * grp < total; grp += gridDim.x) {
+  for (int grp = g0; kLG * grp < total; grp += gs) {
     const int nb = min(kLG, total - kLG * grp);
     // ---- windows of mirrored samples and packed guide bytes (6.5, J.2.2) --
 #pragma unroll
@@ -2077,10 +2076,38 @@ __global__ void __launch_bounds__(32, 20) k_epf_work(const __grid_constant__ Fil
   }
 }
 
-// Multi-image forms of the two filter kernels (tiles in raster order per
-// image, CTAs striding over work items).
-template <bool kEpf, bool kClamp>
-__global__ void __launch_bounds__(kEpf ? 128 : 256, kEpf ? 4 : 1)
+template <bool kClamp>
+__global__ void __launch_bounds__(32, 20) k_epf_work(const __grid_constant__ FilterArgs a,
+                                                     const int* __restrict__ list,
+                                                     const unsigned* __restrict__ count) {
+  epf_work_groups<kClamp>(a, list, static_cast<int>(*count), blockIdx.x, gridDim.x);
+}
+
+// Multi-image form: the warps take the images' groups round robin, the first
+// group of each image going to the warp after the one that took the previous
+// image's last group.
+template <bool kClamp>
+__global__ void __launch_bounds__(32, 18) k_epf_work_batch(const FilterArgs* __restrict__ args,
+                                                           int nimg) {
+  __shared__ FilterArgs sa;
+  static_assert(sizeof(FilterArgs) % 4 == 0, "word copy");
+  int rot = 0;
+  for (int j = 0; j < nimg; ++j) {
+    __syncwarp();
+    for (int k = threadIdx.x; k < int(sizeof(FilterArgs) / 4); k += 32)
+      reinterpret_cast<int*>(&sa)[k] = reinterpret_cast<const int*>(&args[j])[k];
+    __syncwarp();
+    const int total = static_cast<int>(*sa.epf_count);
+    int g0 = static_cast<int>(blockIdx.x) - rot;
+    if (g0 < 0) g0 += gridDim.x;
+    epf_work_groups<kClamp>(sa, sa.epf_list, total, g0, gridDim.x);
+    rot = (rot + (total + kLG - 1) / kLG) % static_cast<int>(gridDim.x);
+  }
+}
+
+// Multi-image form of k_filter (tiles in raster order per image, CTAs
+// striding over work items).
+__global__ void __launch_bounds__(256)
     k_filter_batch(const FilterArgs* __restrict__ args, const int* __restrict__ prefix, int nimg,
                    int total) {
   __shared__ FilterArgs sa;
@@ -2102,9 +2129,8 @@ __global__ void __launch_bounds__(kEpf ? 128 : 256, kEpf ? 4 : 1)
       reinterpret_cast<int*>(&sa)[k] = reinterpret_cast<const int*>(&args[img])[k];
     __syncthreads();
     const int local = w - prefix[img];
-    const int tw = kEpf ? (sa.xs + kET - 1) / kET : (sa.xs + kTW - 1) / kTW;
-    if (kEpf) epf_tile<kClamp>(sa, local % tw, local / tw);
-    else gab_tile(sa, local % tw, local / tw);
+    const int tw = (sa.xs + kTW - 1) / kTW;
+    gab_tile(sa, local % tw, local / tw);
   }
 }
 
@@ -2117,11 +2143,15 @@ bool filter_needs_clamp(const FilterArgs& a) {
   return epf_needs_clamp(a, mul4.data());
 }
 
-void launch_filter_batch(const FilterArgs* args, const int* prefix, int nimg, int total,
-                         bool epf, bool clamp, int grid, cudaStream_t s) {
-  if (!epf) k_filter_batch<false, false><<<grid, 256, 0, s>>>(args, prefix, nimg, total);
-  else if (clamp) k_filter_batch<true, true><<<grid, 128, 0, s>>>(args, prefix, nimg, total);
-  else k_filter_batch<true, false><<<grid, 128, 0, s>>>(args, prefix, nimg, total);
+void launch_filter_batch(const FilterArgs* args, const int* prefix, int nimg, int total, int grid,
+                         cudaStream_t s) {
+  k_filter_batch<<<grid, 256, 0, s>>>(args, prefix, nimg, total);
+}
+
+void launch_epf_work_batch(const FilterArgs* args, int nimg, bool clamp, int grid,
+                           cudaStream_t s) {
+  if (clamp) k_epf_work_batch<true><<<grid, 32, 0, s>>>(args, nimg);
+  else k_epf_work_batch<false><<<grid, 32, 0, s>>>(args, nimg);
 }
 
 // The kernels use static shared memory; ask for the largest carveout so the
@@ -2135,8 +2165,8 @@ static void prefer_shared_carveout() {
   cudaFuncSetAttribute(k_recon_batch, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
   cudaFuncSetAttribute(k_epf<false>, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
   cudaFuncSetAttribute(k_epf<true>, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
-  cudaFuncSetAttribute(k_filter_batch<true, false>, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
-  cudaFuncSetAttribute(k_filter_batch<true, true>, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+  cudaFuncSetAttribute(k_epf_work_batch<false>, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+  cudaFuncSetAttribute(k_epf_work_batch<true>, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
   cudaFuncSetAttribute(k_filter, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
   cudaFuncSetAttribute(k_epf_work<false>, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
   cudaFuncSetAttribute(k_epf_work<true>, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
@@ -2148,11 +2178,9 @@ int batch_blocks_per_sm(int kind) {
   cudaError_t e = cudaSuccess;
   if (kind == 0) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_recon_batch, 128, 0);
   else if (kind == 1)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_filter_batch<true, false>, 128, 0);
-  else if (kind == 2)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_filter_batch<true, true>, 128, 0);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_epf_work_batch<false>, 32, 0);
   else
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_filter_batch<false, false>, 256, 0);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_filter_batch, 256, 0);
   return e == cudaSuccess && n > 0 ? n : 1;
 }
 

@@ -91,6 +91,8 @@ struct FilterArgs {
   OutParams out;
   float* epf_out;             // J.2 result (planar XYB) of k_epf_work,
   size_t ors, ops;            // row / plane stride in elements
+  const int* epf_list;        // multi-image J.2: the image's listed blocks and their
+  const unsigned* epf_count;  // number (EpfSink of its sigma pass)
   int noise;                  // K.5 after J.4: channels noise_r [3][ys][nrs]
   const float* noise_r;
   size_t nrs, nps;
@@ -130,8 +132,12 @@ void launch_epf_work(const FilterArgs& a, const int* list, const unsigned* count
 // work item of image i (prefix[nimg] = total), grid CTAs striding over items.
 void launch_recon_batch(const ReconArgs* args, const int* prefix, int nimg, int total, int grid,
                         cudaStream_t s);
-void launch_filter_batch(const FilterArgs* args, const int* prefix, int nimg, int total,
-                         bool epf, bool clamp, int grid, cudaStream_t s);
+void launch_filter_batch(const FilterArgs* args, const int* prefix, int nimg, int total, int grid,
+                         cudaStream_t s);
+// J.2 of many images (args[i].epf_list / epf_count / epf_out set; the sigma
+// pass copied the unchanged blocks), persistent grid of one-warp CTAs.
+void launch_epf_work_batch(const FilterArgs* args, int nimg, bool clamp, int grid,
+                           cudaStream_t s);
 // Work items (tiles) of the filter kernel that handles a, and whether the
 // EPF needs its exact-clamp variant for a's parameters.
 int filter_tiles(const FilterArgs& a);

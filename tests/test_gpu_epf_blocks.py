@@ -1,5 +1,6 @@
-"""The block-sparse J.2 kernel of the submit paths against the single-launch
-EPF kernel of the batch entry point, and its block count.
+"""The block-list J.2 kernel of the submit and batch paths against the
+single-launch EPF kernel of the no-allocation entry point, and its block
+count.
 
 Both kernels form every weight and every weighted sum in the same order, so
 their results must agree bit for bit; the block-sparse one only skips the
@@ -28,7 +29,21 @@ def tctx(B):
 
 
 def _fused(B, ctx, img, lp, dtype):
-    """The same request through a one-image batch (the single-launch EPF)."""
+    """The same request through the no-allocation entry point (the
+    single-launch EPF)."""
+    import torch
+    dimg = B.to_device(img, torch)
+    shape, npd = B.out_shape(img, dtype)
+    tdt = {np.float32: torch.float32, np.float16: torch.float16, np.uint8: torch.uint8}[npd]
+    out = torch.full(shape, 7, dtype=tdt, device="cuda")
+    torch.cuda.synchronize()
+    B.run_noalloc(dimg, lp, out, dtype)
+    torch.cuda.synchronize()
+    return out.cpu().numpy()
+
+
+def _batch(B, ctx, img, lp, dtype):
+    """The same request through a one-image batch."""
     import torch
     dimg = B.to_device(img, torch)
     shape, npd = B.out_shape(img, dtype)
@@ -36,7 +51,8 @@ def _fused(B, ctx, img, lp, dtype):
     out = torch.full(shape, 7, dtype=tdt, device="cuda")
     b = ctx.batch([(dimg, lp, out, dtype)], autotune=False)
     stream = torch.cuda.Stream()
-    b.launch(stream.cuda_stream)
+    for _ in range(2):   # replays restart the block lists
+        b.launch(stream.cuda_stream)
     stream.synchronize()
     b.close()
     return out.cpu().numpy()
@@ -51,7 +67,9 @@ def test_block_kernel_equals_single_launch(B, tctx, xs, ys, stats, gab):
     img = synth.make_image(xs, ys, 5 * xs + ys, **kw)
     _, lp = params_pair(B, epf=True, gab=gab)
     for dtype in (XYB, F32, U8):
-        np.testing.assert_array_equal(run(B, tctx, img, lp, dtype), _fused(B, tctx, img, lp, dtype))
+        want = _fused(B, tctx, img, lp, dtype)
+        np.testing.assert_array_equal(run(B, tctx, img, lp, dtype), want)
+        np.testing.assert_array_equal(_batch(B, tctx, img, lp, dtype), want)
 
 
 def test_block_kernel_many_groups_per_warp(B, tctx):
@@ -59,7 +77,9 @@ def test_block_kernel_many_groups_per_warp(B, tctx):
     of listed blocks (about 21,000 blocks filtered, 2 per group)."""
     img = synth.make_image(2048, 1088, 77, **ACTIVE)
     _, lp = params_pair(B, epf=True, gab=True)
-    np.testing.assert_array_equal(run(B, tctx, img, lp, F32), _fused(B, tctx, img, lp, F32))
+    want = _fused(B, tctx, img, lp, F32)
+    np.testing.assert_array_equal(run(B, tctx, img, lp, F32), want)
+    np.testing.assert_array_equal(_batch(B, tctx, img, lp, F32), want)
 
 
 def _count_and_sigma(B, ctx, img, lp):
