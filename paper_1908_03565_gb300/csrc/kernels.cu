@@ -659,7 +659,8 @@ __device__ void fwd_col_item(float (*S)[kPR][kRS], float (*T)[kPR][kRS], const C
 __device__ void cell_sigma(float (*S)[kPR][kRS], CellState& cs, const SigmaParams& sp,
                            int gbx0, int gby0, int xs, int ys, int bw, int bh,
                            const float* __restrict__ acmul, const uint8_t* __restrict__ sharp,
-                           int16_t* __restrict__ sigma, const EpfSink& epf) {
+                           int16_t* __restrict__ sigma, const EpfSink& epf,
+                           float* __restrict__ xyb_out) {
   const int tid = threadIdx.x;
   int sv = -1;                                  // sigma of block tid (tid < 16, in the image)
   {
@@ -727,10 +728,11 @@ __device__ void cell_sigma(float (*S)[kPR][kRS], CellState& cs, const SigmaParam
       sv = si;
     }
   }
-  if (!epf.list) return;
   // the EPF's work: the blocks it filters, cell by cell; the others (which
   // it leaves unchanged) copied to its output
   __shared__ unsigned s_pass;
+  unsigned pm = 0;
+  if (epf.list) {
   if (tid < 32) {
     const bool filt = sv >= 16;
     const unsigned fm = __ballot_sync(0xFFFFFFFFu, filt);
@@ -744,16 +746,23 @@ __device__ void cell_sigma(float (*S)[kPR][kRS], CellState& cs, const SigmaParam
     if (filt) epf.list[base + __popc(fm & ((1u << tid) - 1u))] = (gby0 + (tid >> 2)) * bw + gbx0 + (tid & 3);
   }
   __syncthreads();
-  const unsigned pm = s_pass;
-  if (!pm) return;
+  pm = s_pass;
+  }
+  if (!pm && !xyb_out) return;
+  // planar XYB [3][hp][wp] (xyb_out) and the unchanged blocks' copy, float4
+  // per thread step
   const int hp = 8 * bh, wp = 8 * bw;
   for (int i = tid; i < 3 * 32 * 8; i += blockDim.x) {
     const int c = i / 256, y = (i >> 3) & 31, k4 = i & 7;
-    if (!((pm >> ((y >> 3) * 4 + (k4 >> 1))) & 1u)) continue;
+    const bool pass = (pm >> ((y >> 3) * 4 + (k4 >> 1))) & 1u;
+    if (!pass && !xyb_out) continue;
     const int gy = gby0 * 8 + y, gx = gbx0 * 8 + 4 * k4;
-    if (gy < hp && gx < wp)
-      *reinterpret_cast<float4*>(epf.pass + c * epf.pps + static_cast<size_t>(gy) * epf.prs + gx) =
-          *reinterpret_cast<const float4*>(&S[c][y][4 * k4]);
+    if (gy < hp && gx < wp) {
+      const float4 v4 = *reinterpret_cast<const float4*>(&S[c][y][4 * k4]);
+      if (xyb_out) *reinterpret_cast<float4*>(xyb_out + (static_cast<size_t>(c) * hp + gy) * wp + gx) = v4;
+      if (pass)
+        *reinterpret_cast<float4*>(epf.pass + c * epf.pps + static_cast<size_t>(gy) * epf.prs + gx) = v4;
+    }
   }
 }
 
@@ -1176,7 +1185,12 @@ __device__ __forceinline__ void recon_cell(const ReconArgs& a, int cxi, int cyi)
   __syncthreads();
 
   // ---- output ---------------------------------------------------------------
-  if (a.write_xyb) {
+  if (a.write_xyb && a.sigma) {
+    // sigma, the EPF's block list, then the XYB store (and the copy of the
+    // blocks the EPF leaves unchanged)
+    cell_sigma(S, cs, a.sp, gbx0, gby0, a.xs, a.ys, a.bw, a.bh, a.acmul, a.sharp, a.sigma, a.epf,
+               a.xyb);
+  } else if (a.write_xyb) {
     // planar XYB [3][hp][wp], float4 per thread step
     for (int i = tid; i < 3 * 32 * 8; i += blockDim.x) {
       const int c = i / 256, y = (i >> 3) & 31, k4 = i & 7;
@@ -1186,9 +1200,6 @@ __device__ __forceinline__ void recon_cell(const ReconArgs& a, int cxi, int cyi)
         *reinterpret_cast<float4*>(a.xyb + (static_cast<size_t>(c) * a.hp + gy) * a.wp + gx) = v4;
       }
     }
-    if (a.sigma)
-      cell_sigma(S, cs, a.sp, gbx0, gby0, a.xs, a.ys, a.bw, a.bh, a.acmul, a.sharp, a.sigma,
-                 a.epf);
   } else {
     for (int i = tid; i < 32 * 8; i += blockDim.x) {
       const int y = i >> 3, k4 = i & 7;
@@ -1494,7 +1505,8 @@ __global__ void __launch_bounds__(128) k_sigma(const SigmaArgs a) {
     S[c][y][x] = (gy < a.ys && gx < a.xs) ? a.xyb[c * a.pstride + gy * a.rstride + gx] : 0.f;
   }
   __syncthreads();
-  cell_sigma(S, cs, a.sp, gbx0, gby0, a.xs, a.ys, a.bw, a.bh, a.acmul, a.sharp, a.sigma, a.epf);
+  cell_sigma(S, cs, a.sp, gbx0, gby0, a.xs, a.ys, a.bw, a.bh, a.acmul, a.sharp, a.sigma, a.epf,
+             nullptr);
 }
 
 void launch_sigma(const SigmaArgs& a, cudaStream_t s) {
