@@ -308,20 +308,22 @@ jxlr_status jxl_recon_serve(jxl_recon_ctx* ctx, const jxl_recon_request* reqs, s
  * images): many uneven images reconstructed by one launch per kernel kind,
  * captured once in a CUDA graph and replayed by jxl_recon_batch_launch().
  * Every request must be device-resident (inputs and output) with the
- * default dequantisation matrices; the batch owns the XYB/sigma scratch of
- * all its images (allocated at creation).  Maps are validated at creation
- * (JXLR_EINVAL).  With JXLR_BATCH_AUTOTUNE the grid of each kernel is
- * chosen by timing candidates on this batch (remembered per batch shape in
- * the process and in $JXLR_AUTOTUNE_CACHE if set); otherwise a remembered
- * choice is used, else one CTA per work item.  The inputs and outputs of
- * the requests must stay valid for the batch's lifetime. */
+ * default dequantisation matrices; the batch owns the scratch of all its
+ * images (XYB, sigma, and with the EPF its output and block list;
+ * allocated at creation).  Maps are validated at creation (JXLR_EINVAL).
+ * With JXLR_BATCH_AUTOTUNE the grids of the transform and filter kernels
+ * are chosen by timing candidates on this batch (remembered per batch shape
+ * in the process and in $JXLR_AUTOTUNE_CACHE if set); otherwise a
+ * remembered choice is used, else one CTA per work item; the EPF kernel
+ * runs on a persistent grid of its resident CTAs.  The inputs and outputs
+ * of the requests must stay valid for the batch's lifetime. */
 typedef struct jxl_recon_batch jxl_recon_batch;
 #define JXLR_BATCH_AUTOTUNE 1
 
 typedef struct {
   uint32_t images;
   uint64_t pixels;
-  uint32_t recon_items, epf_items, filter_items;   /* cells / tiles */
+  uint32_t recon_items, epf_items, filter_items;   /* cells / images with the EPF / tiles */
   int recon_grid, epf_grid, filter_grid;           /* CTAs per launch */
   int kernels_per_launch;
   int autotuned;                                   /* 0 no, 1 tuned now, 2 cached */

@@ -2197,8 +2197,7 @@ int batch_blocks_per_sm(int kind) {
 }
 
 int filter_tiles(const FilterArgs& a) {
-  return a.epf ? ((a.xs + kET - 1) / kET) * ((a.ys + kET - 1) / kET)
-               : ((a.xs + kTW - 1) / kTW) * ((a.ys + kTH - 1) / kTH);
+  return ((a.xs + kTW - 1) / kTW) * ((a.ys + kTH - 1) / kTH);
 }
 
 void launch_epf_work(const FilterArgs& a, const int* list, const unsigned* count, cudaStream_t s) {

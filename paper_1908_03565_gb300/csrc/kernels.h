@@ -138,8 +138,8 @@ void launch_filter_batch(const FilterArgs* args, const int* prefix, int nimg, in
 // pass copied the unchanged blocks), persistent grid of one-warp CTAs.
 void launch_epf_work_batch(const FilterArgs* args, int nimg, bool clamp, int grid,
                            cudaStream_t s);
-// Work items (tiles) of the filter kernel that handles a, and whether the
-// EPF needs its exact-clamp variant for a's parameters.
+// Work items (32x32 tiles) of k_filter for a, and whether the EPF needs its
+// exact-clamp variant for a's parameters.
 int filter_tiles(const FilterArgs& a);
 bool filter_needs_clamp(const FilterArgs& a);
 
