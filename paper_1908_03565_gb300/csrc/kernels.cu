@@ -1902,13 +1902,15 @@ __global__ void __launch_bounds__(128, 4) k_epf(const __grid_constant__ FilterAr
 }
 
 // ---------------------------------------------------------------------------
-// J.2 on the 8x8 blocks that the filter changes (the submit entry points).
+// J.2 on the 8x8 blocks that the filter changes (the submit and batch entry
+// points).
 //
 // A block whose sigma is below 16 passes its samples through unchanged, so
 // its pixels need no patch sums.  The sigma pass (k_recon / k_sigma) lists
-// the others, 32x32 cell by cell, so that consecutive entries are
-// neighbours (their windows share cache lines), and copies the others to
-// the J.2 output; k_epf_work filters the listed blocks into that output.
+// the other blocks, 32x32 cell by cell, so that consecutive entries are
+// neighbours (their windows share cache lines), and copies the unchanged
+// ones to the J.2 output; k_epf_work filters the listed blocks into that
+// output (k_epf_work_batch: the same for many images).
 //   k_epf_work  persistent one-warp CTAs taking 2 listed blocks at a time:
 //               per block a window of mirrored samples and packed guide
 //               bytes (6.5, J.2.2), then per horizontal offset ox
