@@ -101,10 +101,10 @@ def clocks_stop(p):
 
 
 def serve_leg(binding, torch, n_req, loads, pool_n=24, seed=4000, slots=8):
-    """Config-4 style serving: a pool of images with sides log-uniform in
-    [32, 8192] (config-1 statistics, EPF + Gaborish, u8 sRGB out) resident on
-    the device, requests drawn from it, Poisson arrivals at a fraction of the
-    measured capacity; the native request loop with `slots` concurrent
+    """Serving: a pool of images with sides log-uniform in [32, 8192] (the
+    main workload's mixed-varblock statistics, EPF + Gaborish, u8 sRGB out)
+    resident on the device, requests drawn from it, Poisson arrivals at a
+    fraction of the measured capacity; the native request loop with `slots` concurrent
     requests (continuous batching) against the plain path (one request at a
     time), both under a 40 GB HBM cap."""
     import math
@@ -149,10 +149,10 @@ def serve_leg(binding, torch, n_req, loads, pool_n=24, seed=4000, slots=8):
 
 
 def batch_leg(binding, torch, n_img=512, pool_n=64, seed=3000, reps=10):
-    """Config-3 style batching: 512 images with sides log-uniform in
+    """Multi-image batching: 512 images with sides log-uniform in
     [64, 2048] (multiples of 8; drawn from a pool of 64 distinct images with
-    config-1 statistics), EPF + Gaborish, half u8 sRGB and half f16 linear
-    outputs; one multi-image launch per kernel kind, autotuned grids, replayed
+    the main workload's statistics), EPF + Gaborish, half u8 sRGB and half
+    f16 linear outputs; one multi-image launch per kernel kind, autotuned grids, replayed
     as a CUDA graph; against the plain path (one submit + poll per image)."""
     import math
     from paper_1908_03565_gb300 import synth
@@ -206,7 +206,7 @@ def batch_leg(binding, torch, n_img=512, pool_n=64, seed=3000, reps=10):
 
 
 def precision_leg(binding, torch, steps, sample=1024):
-    """Config-2 style precision study: the FP32 CUDA-core path against the
+    """Precision study: the FP32 CUDA-core path against the
     tensor-core FP16 hi/lo path.  Time: 4096x4096 with both filters (f32 out),
     CUDA events.  Error: max |XYB - oracle| relative to the local magnitude,
     max |RGB01 - oracle| and the share of u8 samples within +-1 of the
@@ -643,7 +643,8 @@ def main():
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"{XS}x{YS} mixed varblocks (config-1 statistics), "
+            "config": {"workload": f"{XS}x{YS} mixed varblocks (log-uniform AcMul, Laplace "
+                                   "coefficients), "
                                    "EPF+Gaborish, f32 linear RGB out",
                        "global_batch": world, "image": f"{XS}x{YS}",
                        "l2": f"inputs larger than L2 ({6 * px / 1e6:.1f} MB coefficients, "
