@@ -106,7 +106,7 @@ def check_u8(got, want01):
 # ---------------------------------------------------------------------------
 # linear path: dequantisation, CfL, LLF, transforms, colour
 # ---------------------------------------------------------------------------
-def test_config0_dct8_256(B, ctx):
+def test_dct8_256_no_filters(B, ctx):
     """256x256, all DCT8, AcMul 1, no CfL, no filters, f32 output."""
     img = synth.make_image(256, 256, 0, mix='dct8', acmul=1.0, cfl=False)
     p, lp = params_pair(B)
@@ -266,7 +266,7 @@ def rgb_tolerance(x, m, p):
     return tol
 
 
-def test_config1_statistics_from_scratch(B, ctx):
+def test_mixed_statistics_from_scratch(B, ctx):
     """Mixed tiling, quant field, CfL, EPF + Gaborish, f32 and u8 outputs,
     against the oracle run from the coefficients."""
     img = synth.make_image(320, 200, 1001, y_dc_offset_q=200)
@@ -298,7 +298,7 @@ def test_config1_statistics_from_scratch(B, ctx):
           f"{plain.mean():.4f}, max err there {err[plain].max():.2e}")
 
 
-def test_config1_full_size_sampled(B, ctx):
+def test_mixed_1920x1088_sampled(B, ctx):
     """1920x1088 at the mixed statistics with both filters: the linear part
     everywhere; the filters on windows (corners, edges, interior) computed
     by the oracle from the GPU's XYB."""
