@@ -12,7 +12,8 @@ import pytest
 
 from oracle import recon as R
 from paper_1908_03565_gb300 import synth
-from test_gpu_parity import B, XYB, F32, U8, params_pair, run  # noqa: F401
+from test_gpu_parity import (B, XYB, F32, U8, assert_xyb_close, params_pair, run,  # noqa: F401
+                             _filters_on_gpu_xyb, _oracle_filters)
 
 pytestmark = pytest.mark.gpu
 
@@ -123,3 +124,24 @@ def test_all_blocks_pass(B, tctx):
 def test_no_epf_stats_without_the_filter(B, tctx):
     ms, n = _count_and_sigma(B, tctx, synth.make_image(64, 64, 3), B.filter_defaults(gab=1))
     assert (ms, n) == (0.0, 0)
+
+
+def test_exact_clamp_variant(B, tctx):
+    """Parameters under which Weight()'s clamp of sad at 507 can keep a weight
+    above the cut-off (cut-off 0.001, sigma up to 672): the kernels' exact-clamp
+    variant, block-list == single launch == batch, and the filter stage
+    against the oracle on the same binary32 XYB."""
+    kw = dict(epf_weight_min=0.001, epf_sigma_max=672, epf_quant_mul=1000.0)
+    img = synth.make_image(264, 200, 95, **ACTIVE)
+    lp = B.filter_defaults(epf=1, gab=1, **kw)
+    for dtype in (XYB, F32):
+        want = _fused(B, tctx, img, lp, dtype)
+        np.testing.assert_array_equal(run(B, tctx, img, lp, dtype), want)
+        np.testing.assert_array_equal(_batch(B, tctx, img, lp, dtype), want)
+    p = R.Params(epf=True, **kw)
+    lp1 = B.filter_defaults(epf=1, **kw)
+    xyb, got = _filters_on_gpu_xyb(B, tctx, img, lp1, True, False, XYB)
+    sig = R.epf_sigma(xyb.astype(np.float64), img['vmap'], img['acmul'], img['sharpness'], p)
+    assert (sig >= 202).any()          # the clamp variant's sigma range is reached
+    want = _oracle_filters(img, xyb, p)
+    assert_xyb_close(got.transpose(2, 0, 1), want, abs_tol=5e-6, radius=8)
