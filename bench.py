@@ -40,6 +40,11 @@ OUT_BPP = 12.0
 # the guide 17
 EPF_OPS_PER_FILTERED_PX = 56 * 14 + 4
 GUIDE_OPS_PER_PX = 17
+# DRAM bytes (read + write) of one k_epf_work launch, from an ncu capture of
+# the current kernel on the same statistics at 4096x2048 (50,730 listed
+# blocks): 100,004,352 + 23,243,776; scaled to a launch by its pixels.  Set to
+# None whenever the kernel changes until it is captured again.
+EPF_WORK_DRAM_BYTES_4096x2048 = 100004352 + 23243776
 CPU_SAMPLE = 1024         # oracle sample: one 1024x1024 image, same statistics
 
 
@@ -551,9 +556,14 @@ def main():
     achieved_alu = (EPF_OPS_PER_FILTERED_PX * 64 * epf_blocks + GUIDE_OPS_PER_PX * px) / \
         (epf_ms * 1e-3) / 1e12
     recon_gbs = px * (IN_BPP + 12.0 + 4 / 64) / (recon_ms * 1e-3) / 1e9  # reads coefs, writes XYB
+    epf_traffic = (None if EPF_WORK_DRAM_BYTES_4096x2048 is None else
+                   int(round(EPF_WORK_DRAM_BYTES_4096x2048 * px / (4096 * 2048))))
     roof_epf = {"kernel": "k_epf_work (J.2 on the 8x8 blocks with sigma >= 16)", "bound": "alu",
                 "achieved": round(achieved_alu, 3), "peak": round(alu_peak, 3),
-                "unit": "Tops/s", "frac": round(achieved_alu / alu_peak, 4), "traffic": None,
+                "unit": "Tops/s", "frac": round(achieved_alu / alu_peak, 4),
+                "traffic": epf_traffic,
+                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one "
+                                  "launch at 4096x2048, scaled by pixels",
                 "peak_source": f"{sm_count} SMs x 128 lanes x {sm_mhz:.0f} MHz",
                 "ms_per_launch": round(epf_ms, 4), "filtered_blocks": epf_blocks,
                 "filtered_frac": round(epf_blocks / nblk, 4)}
