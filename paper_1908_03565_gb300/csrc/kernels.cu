@@ -1929,10 +1929,13 @@ __global__ void __launch_bounds__(128, 4) k_epf(const __grid_constant__ FilterAr
 constexpr int kLG = 2;                            // blocks per warp and round (the lane
                                                   // layout of step 2 assumes 2)
 constexpr int kLGH = 16, kLGW = 18, kLGS = 19;    // guide window, origin (-4, -4) of the block
-constexpr int kLFH = 14, kLFW = 15, kLFS = 18;    // sample window, origin (-3, -3); row stride
+constexpr int kLFH = 14, kLFW = 15, kLFS = 16;    // sample window, origin (-3, -3); row stride
 constexpr int kLFC = kLFH * kLFS;                 // floats per channel
-constexpr int kLFB = 784;                         // floats per block (>= 3 kLFC, = 16 mod 32:
-                                                  // the lane groups of step 2 hit different banks)
+constexpr int kLFB = 688;                         // floats per block (>= 3 kLFC, = 16 mod 32)
+// Column of sample (row fr, column fc) in its row: rows 4 apart (the two
+// half-column lane groups of step 2) swap their 8-column halves, so that the
+// groups read different banks.
+__device__ __forceinline__ int lf_col(int fr, int fc) { return fc ^ (((fr >> 2) & 1) << 3); }
 constexpr int kLHR = 10;                          // rows of horizontal sums per block
 
 // The groups g0, g0 + gs, ... of one image's list (total listed blocks).
@@ -1982,7 +1985,8 @@ __device__ __forceinline__ void epf_work_groups(const FilterArgs& a, const int* 
         G[k][ly][lx] = g;
         if (ly >= 1 && ly <= kLFH && lx >= 1 && lx <= kLFW) {
 #pragma unroll
-          for (int c = 0; c < 3; ++c) F[k][c * kLFC + (ly - 1) * kLFS + (lx - 1)] = wv[q][c];
+          for (int c = 0; c < 3; ++c)
+            F[k][c * kLFC + (ly - 1) * kLFS + lf_col(ly - 1, lx - 1)] = wv[q][c];
         }
       }
     }
@@ -2038,9 +2042,10 @@ __device__ __forceinline__ void epf_work_groups(const FilterArgs& a, const int* 
         float sx[10], sy[10], sb[10];
 #pragma unroll
         for (int m = 0; m < 10; ++m) {
-          sx[m] = Fk[(r0 + m) * kLFS + col];
-          sy[m] = Fk[kLFC + (r0 + m) * kLFS + col];
-          sb[m] = Fk[2 * kLFC + (r0 + m) * kLFS + col];
+          const int o = (r0 + m) * kLFS + lf_col(r0 + m, col);
+          sx[m] = Fk[o];
+          sy[m] = Fk[kLFC + o];
+          sb[m] = Fk[2 * kLFC + o];
         }
 #pragma unroll
         for (int oi = 0; oi < 7; ++oi) {
