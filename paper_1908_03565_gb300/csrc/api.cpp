@@ -76,8 +76,9 @@ struct Timing {
 };
 
 // Words of the per-request device status block: [0] validation flags,
-// [1] [2] validation counters, [3] tensor-core wait expired, [4] blocks the
-// J.2 kernel filtered.
+// [1] [2] validation counters, [3] a bounded device wait expired (4: the
+// tensor-core completion, 8: a filter tile load), [4] blocks the J.2 kernel
+// filtered.
 constexpr int kStatusWords = 8;
 
 }  // namespace
@@ -630,6 +631,7 @@ extern "C" jxlr_status jxl_recon_submit(jxl_recon_ctx* ctx, const jxl_recon_coef
     ctx->launches++;
     mark(slot, 3);
     FilterArgs fa = filter_args(*fp);
+    fa.err = d_status + 3;
     fa.xyb = xyb;
     fa.rstride = wp;
     fa.pstride = static_cast<size_t>(wp) * hp;
@@ -732,6 +734,7 @@ extern "C" jxlr_status jxl_recon_submit_xyb(jxl_recon_ctx* ctx, const float* xyb
   }
   mark(slot, 3);
   FilterArgs fa = filter_args(*fp);
+  fa.err = d_status + 3;
   fa.xyb = xyb;
   fa.rstride = row_stride_elems;
   fa.pstride = row_stride_elems * ys;
@@ -802,7 +805,9 @@ extern "C" jxlr_status jxl_recon_poll(jxl_recon_ctx* ctx, uint64_t ticket, int64
     ctx->timings[ticket] = t;
   }
   if (slot->h_status[3] != 0)
-    return fail(JXLR_ETIMEDOUT, "tensor-core completion wait expired in the transform kernel");
+    return fail(JXLR_ETIMEDOUT, (slot->h_status[3] & 8u)
+                                    ? "tile-load wait expired in the filter kernel"
+                                    : "tensor-core completion wait expired in the transform kernel");
   if (slot->check_status && slot->h_status[0] != 0) {
     char buf[96];
     std::snprintf(buf, sizeof(buf), "device validation: DctSelect map ill-formed (flags 0x%x)",

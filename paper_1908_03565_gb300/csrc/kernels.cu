@@ -24,6 +24,8 @@
 // maps on the host.  The 1-D sums use the even/odd split
 // x[n] = E[n] + O[n], x[N-1-n] = E[n] - O[n] recursively, with the odd-part
 // cosine matrices in constant memory.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
@@ -1819,6 +1821,30 @@ __device__ __forceinline__ void epf_tile(const FilterArgs& a, int tbx, int tby) 
 // ---------------------------------------------------------------------------
 constexpr int kGT = 32, kGR = kGT + 2, kGS2 = 36;   // rows of 16-byte aligned 144 bytes
 
+// J.4 (optional), K.5 and L.2 of the pixels gx .. gx + n - 1 (n <= 4) of row
+// gy from their neighbourhood w[c][r][i] (image row gy - 1 + r, column
+// gx - 1 + i), then the store.
+__device__ __forceinline__ void gab4_finish(const FilterArgs& a, int gx, int gy, int n,
+                                            const float (&w)[3][3][6]) {
+  float o[3][4];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+      const float edge = (w[c][0][p + 1] + w[c][2][p + 1]) + (w[c][1][p] + w[c][1][p + 2]);
+      const float corner = (w[c][0][p] + w[c][0][p + 2]) + (w[c][2][p] + w[c][2][p + 2]);
+      o[c][p] = a.gab ? fmaf(a.gw[c][0], w[c][1][p + 1], fmaf(a.gw[c][1], edge, a.gw[c][2] * corner))
+                      : w[c][1][p + 1];
+    }
+  }
+  if (a.noise) {
+#pragma unroll
+    for (int p = 0; p < 4; ++p)
+      if (p < n) apply_noise(a, gx + p, gy, o[0][p], o[1][p], o[2][p]);
+  }
+  emit4(a.cp, a.out, gx, gy, n, o[0], o[1], o[2]);
+}
+
 __device__ __forceinline__ void gab_tile(const FilterArgs& a, int tbx, int tby) {
   __shared__ __align__(16) float Wn[3][kGR][kGS2];
   const int tid = threadIdx.x;
@@ -1851,31 +1877,18 @@ __device__ __forceinline__ void gab_tile(const FilterArgs& a, int tbx, int tby) 
   const int tx4 = tid & 7, ty = tid >> 3;   // pixels 4 tx4 .. 4 tx4 + 3 of row ty
   const int gx = x0 + 4 * tx4, gy = y0 + ty;
   if (gx >= a.xs || gy >= a.ys) return;
-  const int n = min(4, a.xs - gx);
-  float o[3][4];
+  float w[3][3][6];   // window rows ty .. ty + 2 (image rows gy - 1 .. gy + 1), columns 4 tx4 ..
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    float w[3][6];   // window rows ty .. ty + 2 (image rows gy - 1 .. gy + 1), columns 4 tx4 ..
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
       const float4 q = *reinterpret_cast<const float4*>(&Wn[c][ty + r][4 * tx4]);
       const float2 e = *reinterpret_cast<const float2*>(&Wn[c][ty + r][4 * tx4 + 4]);
-      w[r][0] = q.x; w[r][1] = q.y; w[r][2] = q.z; w[r][3] = q.w; w[r][4] = e.x; w[r][5] = e.y;
-    }
-#pragma unroll
-    for (int p = 0; p < 4; ++p) {
-      const float edge = (w[0][p + 1] + w[2][p + 1]) + (w[1][p] + w[1][p + 2]);
-      const float corner = (w[0][p] + w[0][p + 2]) + (w[2][p] + w[2][p + 2]);
-      o[c][p] = a.gab ? fmaf(a.gw[c][0], w[1][p + 1], fmaf(a.gw[c][1], edge, a.gw[c][2] * corner))
-                      : w[1][p + 1];
+      w[c][r][0] = q.x; w[c][r][1] = q.y; w[c][r][2] = q.z; w[c][r][3] = q.w;
+      w[c][r][4] = e.x; w[c][r][5] = e.y;
     }
   }
-  if (a.noise) {
-#pragma unroll
-    for (int p = 0; p < 4; ++p)
-      if (p < n) apply_noise(a, gx + p, gy, o[0][p], o[1][p], o[2][p]);
-  }
-  emit4(a.cp, a.out, gx, gy, n, o[0], o[1], o[2]);
+  gab4_finish(a, gx, gy, min(4, a.xs - gx), w);
 }
 
 // True when Weight()'s clamp of sad at 507 can change a weight that survives
@@ -1894,6 +1907,148 @@ static bool epf_needs_clamp(const FilterArgs& a, const int32_t* mul4) {
 
 __global__ void __launch_bounds__(256) k_filter(const __grid_constant__ FilterArgs a) {
   gab_tile(a, blockIdx.x, blockIdx.y);
+}
+
+// ---------------------------------------------------------------------------
+// k_filter_tma: k_filter's work on a persistent grid, the tiles brought in by
+// the tensor memory accelerator.  One 3-D TMA load per tile (columns
+// x0 - 4 .. x0 + 35, rows y0 - 1 .. y0 + 32, the 3 channel planes) lands in
+// one of two shared buffers and completes on that buffer's mbarrier; the
+// load of the tile after next is issued as soon as the CTA is done with a
+// buffer, so it overlaps the arithmetic of the next tile.  Outside the image
+// the TMA fills zeros; the one-sample ring there takes the mirrored sample
+// (6.5) before the arithmetic.  The waits are bounded: on expiry the kernel
+// sets bit 8 of *err and stops.
+// ---------------------------------------------------------------------------
+constexpr int kQW = 40, kQH = 34;                          // tile box (columns, rows)
+constexpr uint32_t kQBytes = 3u * kQH * kQW * 4u;          // one buffer, 16,320 bytes
+constexpr int kQWaitLimit = 1 << 22;
+
+struct __align__(128) QTile {
+  float s[3][kQH][kQW];
+};
+
+__device__ __forceinline__ bool q_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t done = 0;
+  for (int it = 0; it < kQWaitLimit && !done; ++it) {
+    asm volatile("{\n.reg .pred q;\nmbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\n"
+                 "selp.u32 %0, 1, 0, q;\n}\n"
+                 : "=r"(done) : "r"(smem_addr(bar)), "r"(parity) : "memory");
+  }
+  return done != 0;
+}
+
+__global__ void __launch_bounds__(256) k_filter_tma(const __grid_constant__ FilterArgs a,
+                                                    const __grid_constant__ CUtensorMap tm,
+                                                    int ntx, int ntiles, unsigned* err) {
+  extern __shared__ __align__(128) unsigned char q_dyn[];
+  QTile* buf = reinterpret_cast<QTile*>(q_dyn);      // 2 buffers
+  __shared__ __align__(8) uint64_t bar[2];
+  __shared__ int s_fail;
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_addr(&bar[0])));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_addr(&bar[1])));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    s_fail = 0;
+  }
+  __syncthreads();
+  auto issue = [&](int t, int b) {   // one thread
+    const int x = (t % ntx) * kGT - 4, y = (t / ntx) * kGT - 1;
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                 :: "r"(smem_addr(&bar[b])), "r"(kQBytes) : "memory");
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];"
+        :: "r"(smem_addr(&buf[b])), "l"(reinterpret_cast<uint64_t>(&tm)), "r"(x), "r"(y), "r"(0),
+           "r"(smem_addr(&bar[b]))
+        : "memory");
+  };
+  int t = blockIdx.x;
+  if (tid == 0) {
+    if (t < ntiles) issue(t, 0);
+    if (t + static_cast<int>(gridDim.x) < ntiles) issue(t + gridDim.x, 1);
+  }
+  const int tx4 = tid & 7, ty = tid >> 3;   // pixels 4 tx4 .. 4 tx4 + 3 of row ty
+  for (int i = 0; t < ntiles; ++i, t += gridDim.x) {
+    const int b = i & 1;
+    QTile& q = buf[b];
+    if (!q_wait(&bar[b], (i >> 1) & 1)) {
+      if (tid == 0 && err) atomicOr(err, 8u);
+      s_fail = 1;
+    }
+    __syncthreads();
+    if (s_fail) {
+      // the other buffer's load, if one was issued, must land before exit
+      if (t + static_cast<int>(gridDim.x) < ntiles) q_wait(&bar[b ^ 1], ((i + 1) >> 1) & 1);
+      return;
+    }
+    const int x0 = (t % ntx) * kGT, y0 = (t / ntx) * kGT;
+    // ring outside the image: rows first, then columns (corners mirror twice)
+    const bool top = y0 == 0, bottom = y0 + kGT + 1 > a.ys;
+    const bool left = x0 == 0, right = x0 + kGT + 1 > a.xs;
+    if (top || bottom) {
+      for (int k = tid; k < 2 * 3 * kQW; k += 256) {
+        const int side = k / (3 * kQW), c = (k / kQW) % 3, lx = k % kQW;
+        if (side == 0 && top) q.s[c][0][lx] = q.s[c][1][lx];
+        if (side == 1 && bottom && a.ys - y0 + 1 < kQH)
+          q.s[c][a.ys - y0 + 1][lx] = q.s[c][a.ys - y0][lx];
+      }
+      __syncthreads();
+    }
+    if (left || right) {
+      for (int k = tid; k < 2 * 3 * kQH; k += 256) {
+        const int side = k / (3 * kQH), c = (k / kQH) % 3, ly = k % kQH;
+        if (side == 0 && left) q.s[c][ly][3] = q.s[c][ly][4];
+        if (side == 1 && right && a.xs - x0 + 4 < kQW)
+          q.s[c][ly][a.xs - x0 + 4] = q.s[c][ly][a.xs - x0 + 3];
+      }
+      __syncthreads();
+    }
+    const int gx = x0 + 4 * tx4, gy = y0 + ty;
+    if (gx < a.xs && gy < a.ys) {
+      float w[3][3][6];   // image rows gy - 1 .. gy + 1, columns gx - 1 .. gx + 4
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+          const float* row = &q.s[c][ty + r][4 * tx4 + 3];
+          const float4 m = *reinterpret_cast<const float4*>(row + 1);
+          w[c][r][0] = row[0];
+          w[c][r][1] = m.x; w[c][r][2] = m.y; w[c][r][3] = m.z; w[c][r][4] = m.w;
+          w[c][r][5] = row[5];
+        }
+      }
+      gab4_finish(a, gx, gy, min(4, a.xs - gx), w);
+    }
+    __syncthreads();   // every thread is done with buffer b
+    if (tid == 0 && t + 2 * static_cast<int>(gridDim.x) < ntiles) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      issue(t + 2 * gridDim.x, b);
+    }
+  }
+}
+
+// The tensor map of a's planar XYB for k_filter_tma, when its layout allows
+// TMA (16-byte aligned base and strides); false otherwise.
+static bool filter_tensor_map(const FilterArgs& a, CUtensorMap* tm) {
+  if ((reinterpret_cast<uintptr_t>(a.xyb) & 15) || (a.rstride & 3) || (a.pstride & 3)) return false;
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = [] {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
+                                         &q) != cudaSuccess || q != cudaDriverEntryPointSuccess)
+      fn = nullptr;
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }();
+  if (!encode) return false;
+  const cuuint64_t dims[3] = {static_cast<cuuint64_t>(a.xs), static_cast<cuuint64_t>(a.ys), 3};
+  const cuuint64_t strides[2] = {a.rstride * 4, a.pstride * 4};
+  const cuuint32_t box[3] = {kQW, kQH, 3};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  return encode(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(a.xyb), dims, strides,
+                box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 template <bool kClamp>
@@ -2233,6 +2388,24 @@ void launch_filter(const FilterArgs& a, cudaStream_t s) {
     dim3 grid((a.xs + kET - 1) / kET, (a.ys + kET - 1) / kET);
     if (epf_needs_clamp(a, mul4.data())) k_epf<true><<<grid, 128, 0, s>>>(a);
     else k_epf<false><<<grid, 128, 0, s>>>(a);
+    return;
+  }
+  CUtensorMap tm;
+  if (filter_tensor_map(a, &tm)) {
+    // persistent grid of resident CTAs
+    static int grid_of[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    int& grid = grid_of[dev & 63];
+    if (grid == 0) {
+      int sms = 0, per = 0;
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_filter_tma, 256, 2 * sizeof(QTile));
+      grid = (sms > 0 ? sms : 1) * (per > 0 ? per : 1);
+    }
+    const int ntx = (a.xs + kGT - 1) / kGT, ntiles = ntx * ((a.ys + kGT - 1) / kGT);
+    k_filter_tma<<<grid < ntiles ? grid : ntiles, 256, 2 * sizeof(QTile), s>>>(a, tm, ntx, ntiles,
+                                                                            a.err);
     return;
   }
   dim3 grid((a.xs + kTW - 1) / kTW, (a.ys + kTH - 1) / kTH);

@@ -93,6 +93,7 @@ struct FilterArgs {
   size_t ors, ops;            // row / plane stride in elements
   const int* epf_list;        // multi-image J.2: the image's listed blocks and their
   const unsigned* epf_count;  // number (EpfSink of its sigma pass)
+  unsigned* err;              // bounded device waits set bit 8 here on expiry (or nullptr)
   int noise;                  // K.5 after J.4: channels noise_r [3][ys][nrs]
   const float* noise_r;
   size_t nrs, nps;
