@@ -44,7 +44,7 @@ GUIDE_OPS_PER_PX = 17
 # the current kernel on the same statistics at 4096x2048 (50,730 listed
 # blocks): 100,004,352 + 23,243,776; scaled to a launch by its pixels.  Set to
 # None whenever the kernel changes until it is captured again.
-EPF_WORK_DRAM_BYTES_4096x2048 = None
+EPF_WORK_DRAM_BYTES_4096x2048 = 100054528 + 22760192
 CPU_SAMPLE = 1024         # oracle sample: one 1024x1024 image, same statistics
 
 
