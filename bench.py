@@ -32,19 +32,22 @@ SEED = 2000
 # 3 float32)
 IN_BPP = 6.0 + 1 / 64 + 4 / 64 + 1 / 64 + 8 / 4096
 OUT_BPP = 12.0
-# algorithmic lane operations of the J.2 kernel (separable 3x4 patch sums on
-# packed guide bytes, J.2.4 weight, J.2.5 accumulation): per pixel it filters
-# (those of the 8x8 blocks with sigma >= 16; the others pass through), per
-# offset absdiff 1, channel sum 1, horizontal and vertical sliding sums 4,
-# weight 4, accumulation 4 (x 56), normalisation 4; per pixel of the image,
-# the guide 17
-EPF_OPS_PER_FILTERED_PX = 56 * 14 + 4
+# algorithmic lane operations of the J.2 kernel, a lower bound that holds on
+# any data: per pixel it filters (those of the 8x8 blocks with sigma >= 16;
+# the others pass through), per offset the patch SAD on packed guide bytes
+# with separable 3x4 sums (absdiff 1, channel sum 1, horizontal and vertical
+# sliding sums 4) and the J.2.4 cut-off test (multiply-add 1, compare 1)
+# (x 56), the J.2.5 accumulation of the centre sample, whose weight is always
+# 1 (4), normalisation 4; per pixel of the image, the guide 17.  The
+# accumulation of the other samples whose weights pass the cut-off (4 per
+# such pixel and offset) depends on the data and is not counted.
+EPF_OPS_PER_FILTERED_PX = 56 * 8 + 4 + 4
 GUIDE_OPS_PER_PX = 17
 # DRAM bytes (read + write) of one k_epf_work launch, from an ncu capture of
 # the current kernel on the same statistics at 4096x2048 (50,730 listed
 # blocks): 100,004,352 + 23,243,776; scaled to a launch by its pixels.  Set to
 # None whenever the kernel changes until it is captured again.
-EPF_WORK_DRAM_BYTES_4096x2048 = 100054528 + 22760192
+EPF_WORK_DRAM_BYTES_4096x2048 = None
 CPU_SAMPLE = 1024         # oracle sample: one 1024x1024 image, same statistics
 
 

@@ -2163,6 +2163,7 @@ __device__ __forceinline__ void epf_work_groups(const FilterArgs& a, const int* 
     // step 1: lane = (block k1, row j1) for the first 10 nb lanes
     const int k1 = lane >= kLHR ? 1 : 0, j1 = lane - kLHR * k1;
     const bool row1 = lane < kLHR * nb;
+    bool dense = false;     // step 2: every offset of the last ox was live
     __syncwarp();
 
 #pragma unroll 1
@@ -2191,7 +2192,39 @@ __device__ __forceinline__ void epf_work_groups(const FilterArgs& a, const int* 
       __syncwarp();
 
       // ---- step 2 ----------------------------------------------------------
-      if (strip) {
+      // the patch SADs of the lane's 4 pixels for the 7 offsets, and which
+      // offsets give some pixel of the warp a weight above the cut-off
+      int sad[7][4];
+#pragma unroll
+      for (int oi = 0; oi < 7; ++oi) {
+        int hv[6];
+#pragma unroll
+        for (int jj = 0; jj < 6; ++jj) hv[jj] = strip ? Hb[sk][oi][r0 + jj][cx] : 0;
+        int v = hv[0] + hv[1] + hv[2];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          if (r > 0) v += hv[r + 2] - hv[r - 1];
+          sad[oi][r] = v;
+        }
+      }
+      // An offset none of whose weights passes the cut-off adds exactly zero
+      // to the J.2.5 sums (partial sums start at +0 and never become -0), so
+      // skipping it leaves every result bit unchanged.  Once a horizontal
+      // offset has all 7 offsets live, the group stops testing (computing a
+      // zero weight is as exact as skipping it).
+      unsigned live = 0x7Fu;
+      if (!dense) {
+        live = 0;
+#pragma unroll
+        for (int oi = 0; oi < 7; ++oi) {
+          const int smin = min(min(sad[oi][0], sad[oi][1]), min(sad[oi][2], sad[oi][3]));
+          // Weight() clamps sad at 507, which matters only in the kClamp variant
+          live |= static_cast<unsigned>((kClamp ? min(smin, 507) : smin) <= vmax) << oi;
+        }
+        live = __reduce_or_sync(0xFFFFFFFFu, live);
+        dense = live == 0x7Fu;
+      }
+      if (live && strip) {
         const float* Fk = &F[sk][0];
         const int col = cx + ox + 3;
         float sx[10], sy[10], sb[10];
@@ -2204,13 +2237,10 @@ __device__ __forceinline__ void epf_work_groups(const FilterArgs& a, const int* 
         }
 #pragma unroll
         for (int oi = 0; oi < 7; ++oi) {
-          int hv[6];
-#pragma unroll
-          for (int jj = 0; jj < 6; ++jj) hv[jj] = Hb[sk][oi][r0 + jj][cx];
-          int v = hv[0] + hv[1] + hv[2];
+          if (!((live >> oi) & 1u)) continue;
 #pragma unroll
           for (int r = 0; r < 4; ++r) {
-            if (r > 0) v += hv[r + 2] - hv[r - 1];
+            const int v = sad[oi][r];
             uint32_t bits;
             if (kClamp) {
               const int s = min(v, 507);
