@@ -38,6 +38,7 @@
 namespace jxlr {
 
 __constant__ float c_llf[kLlfMaps * 256];
+__device__ float g_llf[kLlfMaps * 256];   // the same maps, read with per-lane addresses
 __constant__ float c_box[kLlfMaps * 256];
 __constant__ float c_odd[kOddFloats];
 __constant__ int32_t c_mul4[673];
@@ -69,6 +70,7 @@ bool upload_constants(const float* llf, const float* box, const float* odd,
   int offs[kNumCodes];
   for (int c = 0; c < kNumCodes; ++c) offs[c] = dequant_offset(c, 0);
   return cudaMemcpyToSymbol(c_llf, llf, sizeof(float) * kLlfMaps * 256) == cudaSuccess &&
+         cudaMemcpyToSymbol(g_llf, llf, sizeof(float) * kLlfMaps * 256) == cudaSuccess &&
          cudaMemcpyToSymbol(c_box, box, sizeof(float) * kLlfMaps * 256) == cudaSuccess &&
          cudaMemcpyToSymbol(c_odd, odd, sizeof(float) * kOddFloats) == cudaSuccess &&
          cudaMemcpyToSymbol(c_mul4, mul4, sizeof(int32_t) * 673) == cudaSuccess &&
@@ -330,6 +332,14 @@ struct CellState {
   int owner[16];         // per in-cell block: index into vb, or -1
   int row_pre[17];       // prefix sums of row-phase items
   int col_pre[17];       // prefix sums of column-phase items
+  int frow_pre[17];      // prefix sums of the forward row-phase items (J.3)
+  // LLF phase (I.2.7 and the DC pre-steps of DCT4 / 8x4 / 4x8): the
+  // varblocks with such work in order of decreasing LLF size n, each with
+  // 3 n items (one per channel and LLF slot; 3 for a pre-step), so that the
+  // n items of a channel start at a multiple of n and share a warp
+  int nllf;
+  int llf_vb[16];        // index into vb
+  int llf_pre[17];       // prefix sums of LLF-phase items
   float brange[16];      // per block: max over channels of the scaled range
 };
 
@@ -341,68 +351,106 @@ __device__ __forceinline__ bool separable(int code) {
 __device__ __forceinline__ bool tc_shape(int code) { return code >= kDCT16 && code <= kDCT16x32; }
 
 __device__ __forceinline__ int row_items(int code) {
+  if (code == kIdentity || code == kAFV) return 12;    // 4 quadrants x 3 channels
+  return 3 * (8 << lg_h8(code));                       // DCT2: one item per row too
+}
+
+// Items of the forward row pass (fwd_row_item).
+__device__ __forceinline__ int fwd_row_items(int code) {
   if (code == kIdentity || code == kDCT2) return 3;   // whole block per channel
-  if (code == kAFV) return 12;                          // 4 quadrants x 3 channels
+  if (code == kAFV) return 12;
   return 3 * (8 << lg_h8(code));
 }
 
+// Items of the LLF phase of a varblock: 3 channels x n LLF slots for the
+// shapes larger than 8x8, 3 for the DC pre-steps of DCT4 / 8x4 / 4x8.
+__device__ __forceinline__ int llf_items(int code) {
+  const int ln = lg_w8(code) + lg_h8(code);
+  if (ln > 0) return 3 << ln;
+  return code == kDCT4 || code == kDCT8x4 || code == kDCT4x8 ? 3 : 0;
+}
+
 __device__ __forceinline__ int col_items(int code) { return 3 * (8 << lg_w8(code)); }
+
+// One AuxIDCT2x2 level of I.2.4.2 on the top-left 2h x 2h of q, in place:
+// the 2x2 groups at (y, x), (y, h + x), (h + y, x), (h + y, h + x) become
+// the 2x2 output blocks at (2y, 2x).
+template <int H>
+__device__ __forceinline__ void aux_idct2x2_level(float (&q)[4][4]) {
+  float o[2 * H][2 * H];
+#pragma unroll
+  for (int y = 0; y < H; ++y)
+#pragma unroll
+    for (int x = 0; x < H; ++x) {
+      const float c00 = q[y][x], c01 = q[y][H + x];
+      const float c10 = q[y + H][x], c11 = q[y + H][H + x];
+      o[2 * y][2 * x] = c00 + c01 + c10 + c11;
+      o[2 * y][2 * x + 1] = c00 + c01 - c10 - c11;
+      o[2 * y + 1][2 * x] = c00 - c01 + c10 - c11;
+      o[2 * y + 1][2 * x + 1] = c00 - c01 - c10 + c11;
+    }
+#pragma unroll
+  for (int y = 0; y < 2 * H; ++y)
+#pragma unroll
+    for (int x = 0; x < 2 * H; ++x) q[y][x] = o[y][x];
+}
 
 // Row pass of one item.  S: coefficients, T: output of the pass.
 __device__ void row_item(float (*S)[kPR][kRS], float (*T)[kPR][kRS], const CellVB& v, int k) {
   const int code = v.code;
   const int x0 = 8 * v.bx, y0 = 8 * v.by;
   if (code == kDCT2) {
-    // I.2.4.2: AuxIDCT2x2 at S = 2, 4, 8; ping-pong between S and T.
-    const int c = k;
-    float* s = &S[c][y0][x0];
+    // I.2.4.2: AuxIDCT2x2 at S = 2, 4, 8.  Item (channel c, row r) copies
+    // the coefficients of row r outside the top-left 4x4 to T; item r = 0
+    // also takes the first two levels on the top-left 4x4 (into T).  The
+    // column pass applies the level S = 8 (col_item).
+    const int c = k >> 3, r = k & 7;
+    const float* s = &S[c][y0][x0];
     float* t = &T[c][y0][x0];
-    for (int y = 0; y < 8; ++y)
-      for (int x = 0; x < 8; ++x) t[y * kRS + x] = s[y * kRS + x];
-    float* src = s;
-    float* dst = t;
-    for (int lv = 2; lv <= 8; lv *= 2) {
-      const int h = lv / 2;
-      for (int y = 0; y < h; ++y) {
-        for (int x = 0; x < h; ++x) {
-          const float c00 = src[y * kRS + x], c01 = src[y * kRS + h + x];
-          const float c10 = src[(y + h) * kRS + x], c11 = src[(y + h) * kRS + h + x];
-          dst[(2 * y) * kRS + 2 * x] = c00 + c01 + c10 + c11;
-          dst[(2 * y) * kRS + 2 * x + 1] = c00 + c01 - c10 - c11;
-          dst[(2 * y + 1) * kRS + 2 * x] = c00 - c01 + c10 - c11;
-          dst[(2 * y + 1) * kRS + 2 * x + 1] = c00 - c01 - c10 + c11;
-        }
-      }
-      float* tmp = src; src = dst; dst = tmp;
+#pragma unroll
+    for (int x = 0; x < 8; ++x)
+      if (r >= 4 || x >= 4) t[r * kRS + x] = s[r * kRS + x];
+    if (r == 0) {
+      float q[4][4];
+#pragma unroll
+      for (int y = 0; y < 4; ++y)
+#pragma unroll
+        for (int x = 0; x < 4; ++x) q[y][x] = s[y * kRS + x];
+      aux_idct2x2_level<1>(q);
+      aux_idct2x2_level<2>(q);
+#pragma unroll
+      for (int y = 0; y < 4; ++y)
+#pragma unroll
+        for (int x = 0; x < 4; ++x) t[y * kRS + x] = q[y][x];
     }
-    // after three levels the result is in T (levels write T, S, T)
     return;
   }
   if (code == kIdentity) {
-    // I.2.4.4
-    const int c = k;
+    // I.2.4.4, item (channel c, quadrant (x, y))
+    const int c = k >> 2, x = k & 1, y = (k >> 1) & 1;
     const float* s = &S[c][y0][x0];
     float* t = &T[c][y0][x0];
     const float c00 = s[0], c01 = s[1], c10 = s[kRS], c11 = s[kRS + 1];
-    const float dcs[2][2] = {{c00 + c01 + c10 + c11, c00 + c01 - c10 - c11},
-                             {c00 - c01 + c10 - c11, c00 - c01 - c10 + c11}};
-    for (int y = 0; y < 2; ++y) {
-      for (int x = 0; x < 2; ++x) {
-        float rs = 0.f;
-        for (int iy = 0; iy < 4; ++iy)
-          for (int ix = 0; ix < 4; ++ix)
-            if (ix | iy) rs += s[(y + 2 * iy) * kRS + x + 2 * ix];
-        const float s11 = dcs[y][x] - rs * (1.f / 16.f);
-        for (int iy = 0; iy < 4; ++iy)
-          for (int ix = 0; ix < 4; ++ix) {
-            float v2;
-            if (ix == 1 && iy == 1) v2 = s11;
-            else if (ix == 0 && iy == 0) v2 = s[(y + 2) * kRS + x + 2] + s11;
-            else v2 = s[(y + 2 * iy) * kRS + x + 2 * ix] + s11;
-            t[(4 * y + iy) * kRS + 4 * x + ix] = v2;
-          }
+    // the quadrant's DC: the 2x2 Hadamard entry (y, x) of the corner
+    const float dq = y == 0 ? (x == 0 ? c00 + c01 + c10 + c11 : c00 + c01 - c10 - c11)
+                            : (x == 0 ? c00 - c01 + c10 - c11 : c00 - c01 - c10 + c11);
+    float rs = 0.f;
+#pragma unroll
+    for (int iy = 0; iy < 4; ++iy)
+#pragma unroll
+      for (int ix = 0; ix < 4; ++ix)
+        if (ix | iy) rs += s[(y + 2 * iy) * kRS + x + 2 * ix];
+    const float s11 = dq - rs * (1.f / 16.f);
+#pragma unroll
+    for (int iy = 0; iy < 4; ++iy)
+#pragma unroll
+      for (int ix = 0; ix < 4; ++ix) {
+        float v2;
+        if (ix == 1 && iy == 1) v2 = s11;
+        else if (ix == 0 && iy == 0) v2 = s[(y + 2) * kRS + x + 2] + s11;
+        else v2 = s[(y + 2 * iy) * kRS + x + 2 * ix] + s11;
+        t[(4 * y + iy) * kRS + 4 * x + ix] = v2;
       }
-    }
     return;
   }
   if (code == kAFV) {
@@ -458,7 +506,26 @@ __device__ void col_item(float (*S)[kPR][kRS], float (*T)[kPR][kRS], const CellV
     case kDCT16: case kDCT16x8: case kDCT16x32: col_idct<16>(src, dst, kRS); break;
     case kDCT32: case kDCT32x8: case kDCT32x16: col_idct<32>(src, dst, kRS); break;
     case kDCT4: case kDCT4x8: pair4(src, kRS, dst, kRS); break;
-    default:  // Identity, DCT2, AFV: the row pass already produced samples
+    case kDCT2: {
+      // level S = 8 of I.2.4.2 for output column col = 2 x + odd, from the
+      // row pass's T (top-left 4x4 after the levels S = 2, 4)
+      const int x = col >> 1;
+      const float* t = &T[c][y0][x0];
+#pragma unroll
+      for (int y = 0; y < 4; ++y) {
+        const float c00 = t[y * kRS + x], c01 = t[y * kRS + 4 + x];
+        const float c10 = t[(y + 4) * kRS + x], c11 = t[(y + 4) * kRS + 4 + x];
+        if (col & 1) {
+          dst[(2 * y) * kRS] = c00 + c01 - c10 - c11;
+          dst[(2 * y + 1) * kRS] = c00 - c01 - c10 + c11;
+        } else {
+          dst[(2 * y) * kRS] = c00 + c01 + c10 + c11;
+          dst[(2 * y + 1) * kRS] = c00 - c01 + c10 - c11;
+        }
+      }
+      break;
+    }
+    default:  // Identity, AFV: the row pass already produced samples
 #pragma unroll
       for (int i = 0; i < 8; ++i) dst[i * kRS] = src[i * kRS];
       break;
@@ -787,7 +854,7 @@ __device__ void cell_setup(CellState& cs, const uint8_t* __restrict__ vmap,
       am = acmul[gby * bw + gbx];
     }
     bool valid = false;
-    int ri = 0, ci = 0, w8 = 1, h8 = 1;
+    int ri = 0, ci = 0, fi = 0, li = 0, w8 = 1, h8 = 1;
     if (tid < 16 && code < kNumCodes) {
       w8 = 1 << lg_w8(code);
       h8 = 1 << lg_h8(code);
@@ -796,21 +863,31 @@ __device__ void cell_setup(CellState& cs, const uint8_t* __restrict__ vmap,
                 gby0 + by + h8 > bh);
       ri = tc && tc_shape(code) ? 0 : row_items(code);
       ci = tc && tc_shape(code) ? 0 : col_items(code);
+      fi = fwd_row_items(code);
+      li = llf_items(code);
     }
     const int key = valid ? code * 16 + b : 0x7fffffff;
-    int rank = 0, pr = 0, pc = 0;
+    const bool lwork = valid && li > 0;
+    const int lkey = lwork ? (4 - lg_w8(code) - lg_h8(code)) * 16 + b : 0x7fffffff;
+    int rank = 0, pr = 0, pc = 0, pf = 0, lrank = 0, pl = 0;
 #pragma unroll
     for (int j = 0; j < 16; ++j) {
       const int kj = __shfl_sync(full, key, j);
       const int rj = __shfl_sync(full, ri, j);
       const int cj = __shfl_sync(full, ci, j);
-      if (kj < key) { ++rank; pr += rj; pc += cj; }
+      const int fj = __shfl_sync(full, fi, j);
+      const int lkj = __shfl_sync(full, lkey, j);
+      const int lj = __shfl_sync(full, li, j);
+      if (kj < key) { ++rank; pr += rj; pc += cj; pf += fj; }
+      if (lkj < lkey) { ++lrank; pl += lj; }
     }
     const int n = __popc(__ballot_sync(full, valid));
+    const int nl = __popc(__ballot_sync(full, lwork));
     if (tid < 16) cs.owner[tid] = -1;
     if (tid == 0) {
       cs.nvb = n;
-      cs.row_pre[0] = cs.col_pre[0] = 0;
+      cs.nllf = nl;
+      cs.row_pre[0] = cs.col_pre[0] = cs.frow_pre[0] = cs.llf_pre[0] = 0;
     }
     __syncwarp();
     if (valid) {
@@ -822,6 +899,11 @@ __device__ void cell_setup(CellState& cs, const uint8_t* __restrict__ vmap,
       cs.vb[rank] = v;
       cs.row_pre[rank + 1] = pr + ri;
       cs.col_pre[rank + 1] = pc + ci;
+      cs.frow_pre[rank + 1] = pf + fi;
+      if (lwork) {
+        cs.llf_vb[lrank] = rank;
+        cs.llf_pre[lrank + 1] = pl + li;
+      }
       for (int yy = 0; yy < h8; ++yy)
         for (int xx = 0; xx < w8; ++xx) cs.owner[(by + yy) * 4 + bx + xx] = rank;
     }
@@ -1110,41 +1192,49 @@ __device__ __forceinline__ void recon_cell(const ReconArgs& a, int cxi, int cyi)
   __syncthreads();
 
   // ---- I.2.7 LLF from DC, and the DC pre-steps of DCT4 / 8x4 / 4x8 -------
-  if (tid < 3 * cs.nvb) {
-    const CellVB v = cs.vb[tid / 3];
-    const int c = tid % 3;
-    float* s = &S[c][8 * v.by][8 * v.bx];
-    const int cxl = 1 << (v.lw - 3), cyl = 1 << (v.lh - 3);
-    const int n = cxl * cyl;
-    if (n > 1) {
-      const float* mp = c_llf + llf_map_index_dev(cxl, cyl) * 256;
-      const int lcx = v.lw - 3;
-      // dc is indexed statically (guarded) so that it stays in registers; it
-      // is read in full before the first output overwrites the LLF slots
-      float dc[16];
+  // item = (varblock, channel, LLF slot j): llf[j] = sum_i M[j][i] dc[i]; the
+  // items of one channel share a warp, read all DC samples, then write
+  {
+    float* dst = nullptr;
+    float val = 0.f;
+    if (tid < cs.llf_pre[cs.nllf]) {
+      int lr = 0;
+      while (tid >= cs.llf_pre[lr + 1]) ++lr;
+      const CellVB v = cs.vb[cs.llf_vb[lr]];
+      const int o = tid - cs.llf_pre[lr];
+      const int lcx = v.lw - 3, ln = v.lw + v.lh - 6;
+      const int c = o >> ln, j = o & ((1 << ln) - 1);
+      float* s = &S[c][8 * v.by][8 * v.bx];
+      if (ln > 0) {
+        const int n = 1 << ln, cxl = 1 << lcx;
+        const float* mp = g_llf + llf_map_index_dev(cxl, 1 << (v.lh - 3)) * 256 + j * 16;
+        // dc is indexed statically (guarded) so that it stays in registers
+        float dc[16];
 #pragma unroll
-      for (int i = 0; i < 16; ++i) dc[i] = i < n ? s[(i >> lcx) * kRS + (i & (cxl - 1))] : 0.f;
-      for (int j = 0; j < n; ++j) {
+        for (int i = 0; i < 16; ++i) dc[i] = i < n ? s[(i >> lcx) * kRS + (i & (cxl - 1))] : 0.f;
         float acc = 0.f;
 #pragma unroll
-        for (int i = 0; i < 16; ++i) acc = fmaf(mp[j * 16 + i], dc[i], acc);
-        s[(j >> lcx) * kRS + (j & (cxl - 1))] = acc;
+        for (int i = 0; i < 16; ++i) acc = fmaf(__ldg(mp + i), dc[i], acc);
+        dst = s + (j >> lcx) * kRS + (j & (cxl - 1));
+        val = acc;
+      } else if (v.code == kDCT4) {
+        const float c00 = s[0], c01 = s[1], c10 = s[kRS], c11 = s[kRS + 1];
+        s[0] = c00 + c01 + c10 + c11;
+        s[1] = c00 + c01 - c10 - c11;
+        s[kRS] = c00 - c01 + c10 - c11;
+        s[kRS + 1] = c00 - c01 - c10 + c11;
+      } else if (v.code == kDCT8x4) {
+        const float c0 = s[0], c1 = s[1];
+        s[0] = c0 + c1;
+        s[1] = c0 - c1;
+      } else {   // kDCT4x8
+        const float c0 = s[0], c1 = s[kRS];
+        s[0] = c0 + c1;
+        s[kRS] = c0 - c1;
       }
-    } else if (v.code == kDCT4) {
-      const float c00 = s[0], c01 = s[1], c10 = s[kRS], c11 = s[kRS + 1];
-      s[0] = c00 + c01 + c10 + c11;
-      s[1] = c00 + c01 - c10 - c11;
-      s[kRS] = c00 - c01 + c10 - c11;
-      s[kRS + 1] = c00 - c01 - c10 + c11;
-    } else if (v.code == kDCT8x4) {
-      const float c0 = s[0], c1 = s[1];
-      s[0] = c0 + c1;
-      s[1] = c0 - c1;
-    } else if (v.code == kDCT4x8) {
-      const float c0 = s[0], c1 = s[kRS];
-      s[0] = c0 + c1;
-      s[kRS] = c0 - c1;
     }
+    __syncwarp();   // every DC sample of a channel is read before its LLF slots change
+    if (dst) *dst = val;
   }
   __syncthreads();
 
@@ -1326,11 +1416,11 @@ __global__ void __launch_bounds__(128, 6) k_qco(const __grid_constant__ QcoArgs 
   }
   __syncthreads();
   {
-    const int total = cs.row_pre[cs.nvb];
+    const int total = cs.frow_pre[cs.nvb];
     int vi = 0;
     for (int it = tid; it < total; it += blockDim.x) {
-      while (it >= cs.row_pre[vi + 1]) ++vi;
-      fwd_row_item(S, T, cs.vb[vi], it - cs.row_pre[vi]);
+      while (it >= cs.frow_pre[vi + 1]) ++vi;
+      fwd_row_item(S, T, cs.vb[vi], it - cs.frow_pre[vi]);
     }
   }
   __syncthreads();
