@@ -341,6 +341,8 @@ struct CellState {
   int llf_vb[16];        // index into vb
   int llf_pre[17];       // prefix sums of LLF-phase items
   float brange[16];      // per block: max over channels of the scaled range
+  float bacmul[16];      // per block: AcMul (1 outside the image)
+  int bsharp[16];        // per block: sharpness (when cell_setup is given the map)
 };
 
 __device__ __forceinline__ bool separable(int code) {
@@ -724,10 +726,10 @@ __device__ void fwd_col_item(float (*S)[kPR][kRS], float (*T)[kPR][kRS], const C
 }
 
 // J.2.4 per-block sigma for the 16 blocks of the cell held in S (channel
-// planes, 32 x 32).  Requires cs.owner and cs.vb; 128 threads.
+// planes, 32 x 32).  Requires cs.owner, cs.vb and the blocks' AcMul and
+// sharpness (cell_setup with the sharpness map); 128 threads.
 __device__ void cell_sigma(float (*S)[kPR][kRS], CellState& cs, const SigmaParams& sp,
                            int gbx0, int gby0, int xs, int ys, int bw, int bh,
-                           const float* __restrict__ acmul, const uint8_t* __restrict__ sharp,
                            int16_t* __restrict__ sigma, const EpfSink& epf,
                            float* __restrict__ xyb_out) {
   const int tid = threadIdx.x;
@@ -786,8 +788,8 @@ __device__ void cell_sigma(float (*S)[kPR][kRS], CellState& cs, const SigmaParam
         for (int xx = 0; xx < w8; ++xx) rng = fmaxf(rng, cs.brange[(v.by + yy) * 4 + v.bx + xx]);
       const int bi = gby * bw + gbx;
       float sg = __fmul_rn(fminf(rng, sp.range_max), sp.range_mul);
-      sg = __fmul_rn(sg, sp.lut[sharp[bi] & 7]);
-      const float quant = __frcp_rn(acmul[bi]);
+      sg = __fmul_rn(sg, sp.lut[cs.bsharp[b] & 7]);
+      const float quant = __frcp_rn(cs.bacmul[b]);
       sg = fminf(sg, __fmul_rn(quant, sp.quant_mul));
       sg = fminf(sg, sp.sigma_max);
       int si = static_cast<int>(truncf(sg));
@@ -799,39 +801,43 @@ __device__ void cell_sigma(float (*S)[kPR][kRS], CellState& cs, const SigmaParam
   }
   // the EPF's work: the blocks it filters, cell by cell; the others (which
   // it leaves unchanged) copied to its output
+  // (the list entries are written after the stores, so that the atomic's
+  // round trip overlaps them)
   __shared__ unsigned s_pass;
-  unsigned pm = 0;
+  unsigned pm = 0, fm = 0, base = 0;
   if (epf.list) {
-  if (tid < 32) {
-    const bool filt = sv >= 16;
-    const unsigned fm = __ballot_sync(0xFFFFFFFFu, filt);
-    const unsigned pm = __ballot_sync(0xFFFFFFFFu, sv >= 0 && !filt);
-    unsigned base = 0;
-    if (tid == 0) {
-      s_pass = pm;
-      if (fm) base = atomicAdd(epf.count, static_cast<unsigned>(__popc(fm)));
+    if (tid < 32) {
+      fm = __ballot_sync(0xFFFFFFFFu, sv >= 16);
+      const unsigned pmw = __ballot_sync(0xFFFFFFFFu, sv >= 0 && sv < 16);
+      if (tid == 0) {
+        s_pass = pmw;
+        if (fm) base = atomicAdd(epf.count, static_cast<unsigned>(__popc(fm)));
+      }
     }
-    base = __shfl_sync(0xFFFFFFFFu, base, 0);
-    if (filt) epf.list[base + __popc(fm & ((1u << tid) - 1u))] = (gby0 + (tid >> 2)) * bw + gbx0 + (tid & 3);
+    __syncthreads();
+    pm = s_pass;
   }
-  __syncthreads();
-  pm = s_pass;
-  }
-  if (!pm && !xyb_out) return;
   // planar XYB [3][hp][wp] (xyb_out) and the unchanged blocks' copy, float4
   // per thread step
-  const int hp = 8 * bh, wp = 8 * bw;
-  for (int i = tid; i < 3 * 32 * 8; i += blockDim.x) {
-    const int c = i / 256, y = (i >> 3) & 31, k4 = i & 7;
-    const bool pass = (pm >> ((y >> 3) * 4 + (k4 >> 1))) & 1u;
-    if (!pass && !xyb_out) continue;
-    const int gy = gby0 * 8 + y, gx = gbx0 * 8 + 4 * k4;
-    if (gy < hp && gx < wp) {
-      const float4 v4 = *reinterpret_cast<const float4*>(&S[c][y][4 * k4]);
-      if (xyb_out) *reinterpret_cast<float4*>(xyb_out + (static_cast<size_t>(c) * hp + gy) * wp + gx) = v4;
-      if (pass)
-        *reinterpret_cast<float4*>(epf.pass + c * epf.pps + static_cast<size_t>(gy) * epf.prs + gx) = v4;
+  if (pm || xyb_out) {
+    const int hp = 8 * bh, wp = 8 * bw;
+    for (int i = tid; i < 3 * 32 * 8; i += blockDim.x) {
+      const int c = i / 256, y = (i >> 3) & 31, k4 = i & 7;
+      const bool pass = (pm >> ((y >> 3) * 4 + (k4 >> 1))) & 1u;
+      if (!pass && !xyb_out) continue;
+      const int gy = gby0 * 8 + y, gx = gbx0 * 8 + 4 * k4;
+      if (gy < hp && gx < wp) {
+        const float4 v4 = *reinterpret_cast<const float4*>(&S[c][y][4 * k4]);
+        if (xyb_out) *reinterpret_cast<float4*>(xyb_out + (static_cast<size_t>(c) * hp + gy) * wp + gx) = v4;
+        if (pass)
+          *reinterpret_cast<float4*>(epf.pass + c * epf.pps + static_cast<size_t>(gy) * epf.prs + gx) = v4;
+      }
     }
+  }
+  if (epf.list && tid < 32) {
+    base = __shfl_sync(0xFFFFFFFFu, base, 0);
+    if (sv >= 16)
+      epf.list[base + __popc(fm & ((1u << tid) - 1u))] = (gby0 + (tid >> 2)) * bw + gbx0 + (tid & 3);
   }
 }
 
@@ -841,17 +847,18 @@ __device__ void cell_sigma(float (*S)[kPR][kRS], CellState& cs, const SigmaParam
 // sorted list and its item prefix sums come from shuffles.
 __device__ void cell_setup(CellState& cs, const uint8_t* __restrict__ vmap,
                            const float* __restrict__ acmul, int gbx0, int gby0, int bw,
-                           int bh, bool tc = false) {
+                           int bh, bool tc = false, const uint8_t* __restrict__ sharp = nullptr) {
   const int tid = threadIdx.x;
   if (tid < 32) {
     const unsigned full = 0xffffffffu;
     const int b = tid & 15, bx = b & 3, by = b >> 2;
     const int gbx = gbx0 + bx, gby = gby0 + by;
-    int code = kCovered;
+    int code = kCovered, sh = 0;
     float am = 1.f;
     if (tid < 16 && gbx < bw && gby < bh) {
       code = vmap[gby * bw + gbx];
       am = acmul[gby * bw + gbx];
+      if (sharp) sh = sharp[gby * bw + gbx];
     }
     bool valid = false;
     int ri = 0, ci = 0, fi = 0, li = 0, w8 = 1, h8 = 1;
@@ -883,7 +890,11 @@ __device__ void cell_setup(CellState& cs, const uint8_t* __restrict__ vmap,
     }
     const int n = __popc(__ballot_sync(full, valid));
     const int nl = __popc(__ballot_sync(full, lwork));
-    if (tid < 16) cs.owner[tid] = -1;
+    if (tid < 16) {
+      cs.owner[tid] = -1;
+      cs.bacmul[tid] = am;
+      cs.bsharp[tid] = sh;
+    }
     if (tid == 0) {
       cs.nvb = n;
       cs.nllf = nl;
@@ -1117,7 +1128,7 @@ __device__ __forceinline__ void recon_cell(const ReconArgs& a, int cxi, int cyi)
       v = *reinterpret_cast<const float2*>(a.lfp + 4 * c * bpl + static_cast<size_t>(y) * (2 * a.bw) + x);
     *reinterpret_cast<float2*>(&slp[c][r][2 * q]) = v;
   }
-  cell_setup(cs, a.vmap, a.acmul, gbx0, gby0, a.bw, a.bh, kTC);
+  cell_setup(cs, a.vmap, a.acmul, gbx0, gby0, a.bw, a.bh, kTC, a.sigma ? a.sharp : nullptr);
   if (kTC) tc_fence_after();
 
   // ---- F.2 / F.3 / G: one 8-sample row chunk of all three channels -------
@@ -1280,7 +1291,7 @@ __device__ __forceinline__ void recon_cell(const ReconArgs& a, int cxi, int cyi)
   if (a.write_xyb && a.sigma) {
     // sigma, the EPF's block list, then the XYB store (and the copy of the
     // blocks the EPF leaves unchanged)
-    cell_sigma(S, cs, a.sp, gbx0, gby0, a.xs, a.ys, a.bw, a.bh, a.acmul, a.sharp, a.sigma, a.epf,
+    cell_sigma(S, cs, a.sp, gbx0, gby0, a.xs, a.ys, a.bw, a.bh, a.sigma, a.epf,
                a.xyb);
   } else if (a.write_xyb) {
     // planar XYB [3][hp][wp], float4 per thread step
@@ -1590,14 +1601,14 @@ __global__ void __launch_bounds__(128) k_sigma(const SigmaArgs a) {
   __shared__ CellState cs;
   const int tid = threadIdx.x;
   const int gbx0 = blockIdx.x * 4, gby0 = blockIdx.y * 4;
-  cell_setup(cs, a.vmap, a.acmul, gbx0, gby0, a.bw, a.bh);
+  cell_setup(cs, a.vmap, a.acmul, gbx0, gby0, a.bw, a.bh, false, a.sharp);
   for (int i = tid; i < 3 * 32 * 32; i += blockDim.x) {
     const int c = i >> 10, y = (i >> 5) & 31, x = i & 31;
     const int gy = gby0 * 8 + y, gx = gbx0 * 8 + x;
     S[c][y][x] = (gy < a.ys && gx < a.xs) ? a.xyb[c * a.pstride + gy * a.rstride + gx] : 0.f;
   }
   __syncthreads();
-  cell_sigma(S, cs, a.sp, gbx0, gby0, a.xs, a.ys, a.bw, a.bh, a.acmul, a.sharp, a.sigma, a.epf,
+  cell_sigma(S, cs, a.sp, gbx0, gby0, a.xs, a.ys, a.bw, a.bh, a.sigma, a.epf,
              nullptr);
 }
 
