@@ -2016,10 +2016,12 @@ __global__ void __launch_bounds__(256) k_filter(const __grid_constant__ FilterAr
 // x0 - 4 .. x0 + 35, rows y0 - 1 .. y0 + 32, the 3 channel planes) lands in
 // one of two shared buffers and completes on that buffer's mbarrier; the
 // load of the tile after next is issued as soon as the CTA is done with a
-// buffer, so it overlaps the arithmetic of the next tile.  Outside the image
+// buffer, so it overlaps the arithmetic of the next tile.  Warps release a
+// buffer on its "empty" mbarrier; only the issuing thread waits for all of
+// them, so no CTA-wide barrier separates interior tiles.  Outside the image
 // the TMA fills zeros; the one-sample ring there takes the mirrored sample
 // (6.5) before the arithmetic.  The waits are bounded: on expiry the kernel
-// sets bit 8 of *err and stops.
+// sets bit 8 of *err and stops waiting.
 // ---------------------------------------------------------------------------
 constexpr int kQW = 40, kQH = 34;                          // tile box (columns, rows)
 constexpr uint32_t kQBytes = 3u * kQH * kQW * 4u;          // one buffer, 16,320 bytes
@@ -2044,48 +2046,58 @@ __global__ void __launch_bounds__(256) k_filter_tma(const __grid_constant__ Filt
                                                     int ntx, int ntiles, unsigned* err) {
   extern __shared__ __align__(128) unsigned char q_dyn[];
   QTile* buf = reinterpret_cast<QTile*>(q_dyn);      // 2 buffers
-  __shared__ __align__(8) uint64_t bar[2];
-  __shared__ int s_fail;
+  // full[b]: buffer b's tile has landed (TMA transaction count); empty[b]:
+  // all 8 warps are done reading it (one arrival per warp)
+  __shared__ __align__(8) uint64_t full[2], empty[2];
   const int tid = threadIdx.x;
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_addr(&bar[0])));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_addr(&bar[1])));
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_addr(&full[b])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;"
+                   :: "r"(smem_addr(&empty[b])), "r"(static_cast<int>(blockDim.x >> 5)));
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    s_fail = 0;
   }
   __syncthreads();
   auto issue = [&](int t, int b) {   // one thread
     const int x = (t % ntx) * kGT - 4, y = (t / ntx) * kGT - 1;
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
-                 :: "r"(smem_addr(&bar[b])), "r"(kQBytes) : "memory");
+                 :: "r"(smem_addr(&full[b])), "r"(kQBytes) : "memory");
     asm volatile(
         "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
         " [%0], [%1, {%2, %3, %4}], [%5];"
         :: "r"(smem_addr(&buf[b])), "l"(reinterpret_cast<uint64_t>(&tm)), "r"(x), "r"(y), "r"(0),
-           "r"(smem_addr(&bar[b]))
+           "r"(smem_addr(&full[b]))
         : "memory");
   };
   int t = blockIdx.x;
+  const int G = static_cast<int>(gridDim.x);
+  // thread 0: the use of buffer 0 / 1 whose load it has not seen land (-1: none)
+  int pend0 = -1, pend1 = -1;
   if (tid == 0) {
-    if (t < ntiles) issue(t, 0);
-    if (t + static_cast<int>(gridDim.x) < ntiles) issue(t + gridDim.x, 1);
+    if (t < ntiles) { issue(t, 0); pend0 = 0; }
+    if (t + G < ntiles) { issue(t + G, 1); pend1 = 0; }
   }
+  // A thread whose bounded wait expires sets bit 8 of *err and skips every
+  // later wait (and thread 0 every later load), following the same barriers
+  // as the others, so the launch ends promptly.
+  bool dead = false;
   const int tx4 = tid & 7, ty = tid >> 3;   // pixels 4 tx4 .. 4 tx4 + 3 of row ty
-  for (int i = 0; t < ntiles; ++i, t += gridDim.x) {
-    const int b = i & 1;
+  for (int i = 0; t < ntiles; ++i, t += G) {
+    const int b = i & 1, u = i >> 1;
     QTile& q = buf[b];
-    if (!q_wait(&bar[b], (i >> 1) & 1)) {
-      if (tid == 0 && err) atomicOr(err, 8u);
-      s_fail = 1;
-    }
-    __syncthreads();
-    if (s_fail) {
-      // the other buffer's load, if one was issued, must land before exit
-      if (t + static_cast<int>(gridDim.x) < ntiles) q_wait(&bar[b ^ 1], ((i + 1) >> 1) & 1);
-      return;
+    if (!dead) {
+      if (q_wait(&full[b], u & 1)) {
+        if (b) pend1 = -1; else pend0 = -1;
+      } else {
+        dead = true;
+        if (err) atomicOr(err, 8u);
+      }
     }
     const int x0 = (t % ntx) * kGT, y0 = (t / ntx) * kGT;
-    // ring outside the image: rows first, then columns (corners mirror twice)
+    // ring outside the image: rows first, then columns (corners mirror twice);
+    // edge tiles are the same for the whole CTA
     const bool top = y0 == 0, bottom = y0 + kGT + 1 > a.ys;
     const bool left = x0 == 0, right = x0 + kGT + 1 > a.xs;
     if (top || bottom) {
@@ -2122,11 +2134,26 @@ __global__ void __launch_bounds__(256) k_filter_tma(const __grid_constant__ Filt
       }
       gab4_finish(a, gx, gy, min(4, a.xs - gx), w);
     }
-    __syncthreads();   // every thread is done with buffer b
-    if (tid == 0 && t + 2 * static_cast<int>(gridDim.x) < ntiles) {
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      issue(t + 2 * gridDim.x, b);
+    // this warp is done with buffer b (and, for edge tiles, before the next
+    // tile's ring writes: those follow the next full wait)
+    __syncwarp();
+    if ((tid & 31) == 0)
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(smem_addr(&empty[b])) : "memory");
+    if (tid == 0 && !dead && t + 2 * G < ntiles) {
+      if (q_wait(&empty[b], u & 1)) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        issue(t + 2 * G, b);
+        if (b) pend1 = u + 1; else pend0 = u + 1;
+      } else {
+        dead = true;
+        if (err) atomicOr(err, 8u);
+      }
     }
+  }
+  // a load still in flight lands before the CTA's shared memory is released
+  if (tid == 0) {
+    if (pend0 >= 0) q_wait(&full[0], pend0 & 1);
+    if (pend1 >= 0) q_wait(&full[1], pend1 & 1);
   }
 }
 
