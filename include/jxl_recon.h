@@ -327,6 +327,9 @@ typedef struct {
   int recon_grid, epf_grid, filter_grid;           /* CTAs per launch */
   int kernels_per_launch;
   int autotuned;                                   /* 0 no, 1 tuned now, 2 cached */
+  int filter_tma;                                  /* 1: the Gaborish / colour kernel loads
+                                                      its tiles by TMA (every filtered
+                                                      image's scratch allows it) */
 } jxl_recon_batch_info;
 
 jxlr_status jxl_recon_batch_create(jxl_recon_ctx* ctx, const jxl_recon_request* reqs, size_t n,
@@ -335,6 +338,11 @@ jxlr_status jxl_recon_batch_create(jxl_recon_ctx* ctx, const jxl_recon_request* 
  * default stream) and returns; completion is the stream's. */
 jxlr_status jxl_recon_batch_launch(jxl_recon_batch* batch, void* cuda_stream);
 jxlr_status jxl_recon_batch_query(const jxl_recon_batch* batch, jxl_recon_batch_info* info);
+/* Error flags of the batch's launches so far (call once the launch's stream
+ * has completed; a blocking device read): bit 8 = a bounded tile-load wait
+ * of the Gaborish / colour kernel expired (its output is then not valid);
+ * 0 = none.  JXLR_EINVAL on a null argument, JXLR_ECUDA if the read fails. */
+jxlr_status jxl_recon_batch_status(const jxl_recon_batch* batch, uint32_t* flags);
 jxlr_status jxl_recon_batch_destroy(jxl_recon_batch* batch);
 
 /* Number of kernels the context has launched so far. */

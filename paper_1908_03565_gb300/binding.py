@@ -25,6 +25,7 @@ EXPORTS = ("jxl_recon_filter_defaults", "jxl_recon_create", "jxl_recon_submit",
            "jxl_recon_launch_count", "jxl_recon_device_bytes", "jxl_recon_destroy",
            "jxl_recon_last_error", "jxl_recon_run_noalloc", "jxl_recon_serve",
            "jxl_recon_batch_create", "jxl_recon_batch_launch", "jxl_recon_batch_query",
+           "jxl_recon_batch_status",
            "jxl_recon_batch_destroy", "jxl_recon_submit_jpeg", "jxl_recon_epf_stats")
 
 
@@ -96,7 +97,8 @@ class BatchInfo(ctypes.Structure):
                 ("recon_items", ctypes.c_uint32), ("epf_items", ctypes.c_uint32),
                 ("filter_items", ctypes.c_uint32), ("recon_grid", ctypes.c_int),
                 ("epf_grid", ctypes.c_int), ("filter_grid", ctypes.c_int),
-                ("kernels_per_launch", ctypes.c_int), ("autotuned", ctypes.c_int)]
+                ("kernels_per_launch", ctypes.c_int), ("autotuned", ctypes.c_int),
+                ("filter_tma", ctypes.c_int)]
 
 
 BATCH_AUTOTUNE = 1
@@ -154,6 +156,8 @@ def load(path=LIB_PATH):
     lib.jxl_recon_batch_launch.restype = ctypes.c_int
     lib.jxl_recon_batch_query.argtypes = [ctypes.c_void_p, P(BatchInfo)]
     lib.jxl_recon_batch_query.restype = ctypes.c_int
+    lib.jxl_recon_batch_status.argtypes = [ctypes.c_void_p, P(ctypes.c_uint32)]
+    lib.jxl_recon_batch_status.restype = ctypes.c_int
     lib.jxl_recon_batch_destroy.argtypes = [ctypes.c_void_p]
     lib.jxl_recon_batch_destroy.restype = ctypes.c_int
     _lib = lib
@@ -405,6 +409,15 @@ class Batch:
         i = BatchInfo()
         self.lib.jxl_recon_batch_query(self.h, ctypes.byref(i))
         return {k: getattr(i, k) for k, _ in BatchInfo._fields_}
+
+    def status(self):
+        """Error flags of the launches so far (bit 8: a filter tile-load wait
+        expired); call after the launch's stream completed."""
+        f = ctypes.c_uint32()
+        st = self.lib.jxl_recon_batch_status(self.h, ctypes.byref(f))
+        if st != JXLR_OK:
+            raise JxlrError(st, self.ctx.last_error())
+        return f.value
 
     def close(self):
         if self.h:

@@ -49,6 +49,8 @@ struct jxl_recon_batch {
   FilterArgs* d_fargs = nullptr;   // Gaborish / colour of every filtered image
   int* d_fprefix = nullptr;
   int nf = 0, ftotal = 0;
+  void* d_maps = nullptr;          // their tensor maps (TMA form of the filter), or null
+  unsigned* d_err = nullptr;       // bit 8: a bounded tile-load wait of the filter expired
   int grid[3] = {0, 0, 0};         // recon, epf, filter
   int autotuned = 0;
   cudaStream_t cap = nullptr;
@@ -71,7 +73,13 @@ void enqueue(const jxl_recon_batch* b, const int* grid, cudaStream_t s) {
   if (b->rtotal) launch_recon_batch(b->d_rargs, b->d_rprefix, static_cast<int>(b->n), b->rtotal,
                                     grid[0], s);
   if (b->ne) launch_epf_work_batch(b->d_eargs, b->ne, b->clamp, grid[1], s);
-  if (b->ftotal) launch_filter_batch(b->d_fargs, b->d_fprefix, b->nf, b->ftotal, grid[2], s);
+  if (b->ftotal) {
+    if (b->d_maps)
+      launch_filter_batch_tma(b->d_fargs, b->d_fprefix, b->d_maps, b->nf, b->ftotal, grid[2],
+                              b->d_err, s);
+    else
+      launch_filter_batch(b->d_fargs, b->d_fprefix, b->nf, b->ftotal, grid[2], s);
+  }
 }
 
 using Key = std::tuple<uint32_t, int, int, int>;
@@ -112,7 +120,8 @@ jxlr_status autotune(jxl_recon_batch* b) {
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
   const int kinds[3] = {0, 1, 2};
-  const int totals[3] = {b->rtotal, 0, b->ftotal};   // the J.2 kernel keeps its resident grid
+  // the J.2 kernel and the TMA form of the filter keep their resident grids
+  const int totals[3] = {b->rtotal, 0, b->d_maps ? 0 : b->ftotal};
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
@@ -286,6 +295,11 @@ extern "C" jxlr_status jxl_recon_batch_create(jxl_recon_ctx* ctx, const jxl_reco
   const size_t o_e = take(sizeof(FilterArgs) * ea.size()), o_ec = take(sizeof(unsigned) * ea.size());
   const size_t o_f = take(sizeof(FilterArgs) * fa.size()), o_fp = take(sizeof(int) * fpre.size());
   const size_t o_st = take(sizeof(unsigned) * 4 * n);
+  // one tensor map per filtered image when every one of them allows TMA
+  struct alignas(64) Map { unsigned char b[kTensorMapBytes]; };
+  std::vector<Map> maps(fa.size());
+  bool tma = !fa.empty();
+  const size_t o_tm = take(sizeof(Map) * fa.size()), o_er = take(sizeof(unsigned));
   const size_t o_sc = take(scratch);
   cudaError_t e = cudaMalloc(&b->dmem, up(off, 256));
   if (e != cudaSuccess) {
@@ -322,6 +336,11 @@ extern "C" jxlr_status jxl_recon_batch_create(jxl_recon_ctx* ctx, const jxl_reco
     const int i = fimg[j];
     fa[j].xyb = eo[i] ? eo[i] : ra[i].xyb;
     fa[j].sigma = nullptr;
+    tma = tma && make_filter_tensor_map(fa[j], &maps[j]);
+  }
+  if (tma) {
+    b->d_maps = base + o_tm;
+    b->d_err = reinterpret_cast<unsigned*>(base + o_er);
   }
   b->d_rargs = reinterpret_cast<ReconArgs*>(base + o_r);
   b->d_rprefix = reinterpret_cast<int*>(base + o_rp);
@@ -338,6 +357,8 @@ extern "C" jxlr_status jxl_recon_batch_create(jxl_recon_ctx* ctx, const jxl_reco
   h2d(b->d_eargs, ea.data(), sizeof(FilterArgs) * ea.size());
   h2d(b->d_fargs, fa.data(), sizeof(FilterArgs) * fa.size());
   h2d(b->d_fprefix, fpre.data(), sizeof(int) * fpre.size());
+  if (b->d_maps) h2d(b->d_maps, maps.data(), sizeof(Map) * maps.size());
+  if (b->d_err && e == cudaSuccess) e = cudaMemsetAsync(b->d_err, 0, sizeof(unsigned), b->cap);
   // C.5.4 validation of every map, once, at creation
   if (e == cudaSuccess) e = cudaMemsetAsync(d_status, 0, sizeof(unsigned) * 4 * n, b->cap);
   for (size_t i = 0; i < n && e == cudaSuccess; ++i)
@@ -362,9 +383,11 @@ extern "C" jxlr_status jxl_recon_batch_create(jxl_recon_ctx* ctx, const jxl_reco
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   b->grid[0] = b->rtotal;
   b->grid[1] = b->ne ? sms * batch_blocks_per_sm(1) : 0;   // persistent J.2 grid
-  b->grid[2] = b->ftotal;
+  b->grid[2] = b->d_maps ? sms * batch_blocks_per_sm(3) : b->ftotal;   // TMA form: persistent
   const Key key(b->n, b->rtotal, b->etotal, b->ftotal);
+  const int grid_tma = b->grid[2];
   if (tuned_lookup(key, b->grid)) {
+    if (b->d_maps) b->grid[2] = grid_tma;
     b->autotuned = 2;
   } else if (flags & JXLR_BATCH_AUTOTUNE) {
     jxlr_status ts = autotune(b);
@@ -413,5 +436,16 @@ extern "C" jxlr_status jxl_recon_batch_query(const jxl_recon_batch* b, jxl_recon
   info->filter_grid = b->grid[2];
   info->kernels_per_launch = b->kernels;
   info->autotuned = b->autotuned;
+  info->filter_tma = b->d_maps != nullptr;
+  return JXLR_OK;
+}
+
+extern "C" jxlr_status jxl_recon_batch_status(const jxl_recon_batch* b, uint32_t* flags) {
+  if (!b || !flags) return bfail(JXLR_EINVAL, "batch_status: null argument");
+  *flags = 0;
+  if (!b->d_err) return JXLR_OK;
+  if (cudaSetDevice(b->device) != cudaSuccess ||
+      cudaMemcpy(flags, b->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return bfail(JXLR_ECUDA, "batch_status: read failed");
   return JXLR_OK;
 }

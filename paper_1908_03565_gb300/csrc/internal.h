@@ -98,7 +98,8 @@ int ctx_device(const jxl_recon_ctx* c);
 void ctx_count_launches(jxl_recon_ctx* c, int n);
 
 // Resident CTAs per SM of the multi-image kernels (kernels.cu):
-// kind 0 recon, 1 EPF (J.2 on the listed blocks), 2 Gaborish/colour.
+// kind 0 recon, 1 EPF (J.2 on the listed blocks), 2 Gaborish/colour, 3 its
+// TMA form.
 int batch_blocks_per_sm(int kind);
 
 // Sets the message jxl_recon_last_error() returns on this thread (api.cpp).

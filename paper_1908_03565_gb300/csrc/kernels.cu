@@ -2018,7 +2018,9 @@ __global__ void __launch_bounds__(256) k_filter(const __grid_constant__ FilterAr
 // load of the tile after next is issued as soon as the CTA is done with a
 // buffer, so it overlaps the arithmetic of the next tile.  Warps release a
 // buffer on its "empty" mbarrier; only the issuing thread waits for all of
-// them, so no CTA-wide barrier separates interior tiles.  Outside the image
+// them, so no CTA-wide barrier separates interior tiles.  k_filter_batch_tma
+// runs the same pipeline over the tiles of many images, one tensor map per
+// image in global memory.  Outside the image
 // the TMA fills zeros; the one-sample ring there takes the mirrored sample
 // (6.5) before the arithmetic.  The waits are bounded: on expiry the kernel
 // sets bit 8 of *err and stops waiting.
@@ -2041,13 +2043,76 @@ __device__ __forceinline__ bool q_wait(uint64_t* bar, uint32_t parity) {
   return done != 0;
 }
 
-__global__ void __launch_bounds__(256) k_filter_tma(const __grid_constant__ FilterArgs a,
-                                                    const __grid_constant__ CUtensorMap tm,
-                                                    int ntx, int ntiles, unsigned* err) {
+// One landed tile of the TMA filter kernels: the mirrored ring outside the
+// image (rows first, then columns, so corners mirror twice; edge tiles are
+// the same for the whole CTA, which takes the barriers they need), then J.4
+// / K.5 / L.2 for 4 neighbouring pixels of a row per thread.
+__device__ __forceinline__ void filter_tma_tile(const FilterArgs& a, QTile& q, int x0, int y0) {
+  const int tid = threadIdx.x;
+  const int tx4 = tid & 7, ty = tid >> 3;   // pixels 4 tx4 .. 4 tx4 + 3 of row ty
+  const bool top = y0 == 0, bottom = y0 + kGT + 1 > a.ys;
+  const bool left = x0 == 0, right = x0 + kGT + 1 > a.xs;
+  if (top || bottom) {
+    for (int k = tid; k < 2 * 3 * kQW; k += 256) {
+      const int side = k / (3 * kQW), c = (k / kQW) % 3, lx = k % kQW;
+      if (side == 0 && top) q.s[c][0][lx] = q.s[c][1][lx];
+      if (side == 1 && bottom && a.ys - y0 + 1 < kQH)
+        q.s[c][a.ys - y0 + 1][lx] = q.s[c][a.ys - y0][lx];
+    }
+    __syncthreads();
+  }
+  if (left || right) {
+    for (int k = tid; k < 2 * 3 * kQH; k += 256) {
+      const int side = k / (3 * kQH), c = (k / kQH) % 3, ly = k % kQH;
+      if (side == 0 && left) q.s[c][ly][3] = q.s[c][ly][4];
+      if (side == 1 && right && a.xs - x0 + 4 < kQW)
+        q.s[c][ly][a.xs - x0 + 4] = q.s[c][ly][a.xs - x0 + 3];
+    }
+    __syncthreads();
+  }
+  const int gx = x0 + 4 * tx4, gy = y0 + ty;
+  if (gx < a.xs && gy < a.ys) {
+    float w[3][3][6];   // image rows gy - 1 .. gy + 1, columns gx - 1 .. gx + 4
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        const float* row = &q.s[c][ty + r][4 * tx4 + 3];
+        const float4 m = *reinterpret_cast<const float4*>(row + 1);
+        w[c][r][0] = row[0];
+        w[c][r][1] = m.x; w[c][r][2] = m.y; w[c][r][3] = m.z; w[c][r][4] = m.w;
+        w[c][r][5] = row[5];
+      }
+    }
+    gab4_finish(a, gx, gy, min(4, a.xs - gx), w);
+  }
+}
+
+// One 3-D TMA load of tile box {kQW, kQH, 3} at (x, y, 0) of tensor map tm into
+// dst, completing on the mbarrier at bar (one thread).
+__device__ __forceinline__ void tma_tile_load(const void* tm, int x, int y, uint32_t dst,
+                                              uint32_t bar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+               :: "r"(bar), "r"(kQBytes) : "memory");
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];"
+      :: "r"(dst), "l"(reinterpret_cast<uint64_t>(tm)), "r"(x), "r"(y), "r"(0), "r"(bar)
+      : "memory");
+}
+
+// The pipeline of the TMA filter kernels over tiles blockIdx.x, + gridDim.x,
+// ... < ntiles: two buffers, "full" mbarriers (TMA transaction counts) and
+// "empty" ones (one arrival per warp); thread 0 loads the tile after next
+// into a buffer once the 8 warps released it.  src.issue(t, dst, bar) loads
+// tile t (thread 0); src.consume(t, q) filters it (all threads).  A thread
+// whose bounded wait expires sets bit 8 of *err and skips every later wait
+// (and thread 0 every later load), following the same barriers as the
+// others, so the launch ends promptly.
+template <class Src>
+__device__ __forceinline__ void filter_tma_pipeline(Src& src, int ntiles, unsigned* err) {
   extern __shared__ __align__(128) unsigned char q_dyn[];
   QTile* buf = reinterpret_cast<QTile*>(q_dyn);      // 2 buffers
-  // full[b]: buffer b's tile has landed (TMA transaction count); empty[b]:
-  // all 8 warps are done reading it (one arrival per warp)
   __shared__ __align__(8) uint64_t full[2], empty[2];
   const int tid = threadIdx.x;
   if (tid == 0) {
@@ -2060,33 +2125,17 @@ __global__ void __launch_bounds__(256) k_filter_tma(const __grid_constant__ Filt
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
-  auto issue = [&](int t, int b) {   // one thread
-    const int x = (t % ntx) * kGT - 4, y = (t / ntx) * kGT - 1;
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
-                 :: "r"(smem_addr(&full[b])), "r"(kQBytes) : "memory");
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%2, %3, %4}], [%5];"
-        :: "r"(smem_addr(&buf[b])), "l"(reinterpret_cast<uint64_t>(&tm)), "r"(x), "r"(y), "r"(0),
-           "r"(smem_addr(&full[b]))
-        : "memory");
-  };
   int t = blockIdx.x;
   const int G = static_cast<int>(gridDim.x);
   // thread 0: the use of buffer 0 / 1 whose load it has not seen land (-1: none)
   int pend0 = -1, pend1 = -1;
   if (tid == 0) {
-    if (t < ntiles) { issue(t, 0); pend0 = 0; }
-    if (t + G < ntiles) { issue(t + G, 1); pend1 = 0; }
+    if (t < ntiles) { src.issue(t, smem_addr(&buf[0]), smem_addr(&full[0])); pend0 = 0; }
+    if (t + G < ntiles) { src.issue(t + G, smem_addr(&buf[1]), smem_addr(&full[1])); pend1 = 0; }
   }
-  // A thread whose bounded wait expires sets bit 8 of *err and skips every
-  // later wait (and thread 0 every later load), following the same barriers
-  // as the others, so the launch ends promptly.
   bool dead = false;
-  const int tx4 = tid & 7, ty = tid >> 3;   // pixels 4 tx4 .. 4 tx4 + 3 of row ty
   for (int i = 0; t < ntiles; ++i, t += G) {
     const int b = i & 1, u = i >> 1;
-    QTile& q = buf[b];
     if (!dead) {
       if (q_wait(&full[b], u & 1)) {
         if (b) pend1 = -1; else pend0 = -1;
@@ -2095,45 +2144,7 @@ __global__ void __launch_bounds__(256) k_filter_tma(const __grid_constant__ Filt
         if (err) atomicOr(err, 8u);
       }
     }
-    const int x0 = (t % ntx) * kGT, y0 = (t / ntx) * kGT;
-    // ring outside the image: rows first, then columns (corners mirror twice);
-    // edge tiles are the same for the whole CTA
-    const bool top = y0 == 0, bottom = y0 + kGT + 1 > a.ys;
-    const bool left = x0 == 0, right = x0 + kGT + 1 > a.xs;
-    if (top || bottom) {
-      for (int k = tid; k < 2 * 3 * kQW; k += 256) {
-        const int side = k / (3 * kQW), c = (k / kQW) % 3, lx = k % kQW;
-        if (side == 0 && top) q.s[c][0][lx] = q.s[c][1][lx];
-        if (side == 1 && bottom && a.ys - y0 + 1 < kQH)
-          q.s[c][a.ys - y0 + 1][lx] = q.s[c][a.ys - y0][lx];
-      }
-      __syncthreads();
-    }
-    if (left || right) {
-      for (int k = tid; k < 2 * 3 * kQH; k += 256) {
-        const int side = k / (3 * kQH), c = (k / kQH) % 3, ly = k % kQH;
-        if (side == 0 && left) q.s[c][ly][3] = q.s[c][ly][4];
-        if (side == 1 && right && a.xs - x0 + 4 < kQW)
-          q.s[c][ly][a.xs - x0 + 4] = q.s[c][ly][a.xs - x0 + 3];
-      }
-      __syncthreads();
-    }
-    const int gx = x0 + 4 * tx4, gy = y0 + ty;
-    if (gx < a.xs && gy < a.ys) {
-      float w[3][3][6];   // image rows gy - 1 .. gy + 1, columns gx - 1 .. gx + 4
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-#pragma unroll
-        for (int r = 0; r < 3; ++r) {
-          const float* row = &q.s[c][ty + r][4 * tx4 + 3];
-          const float4 m = *reinterpret_cast<const float4*>(row + 1);
-          w[c][r][0] = row[0];
-          w[c][r][1] = m.x; w[c][r][2] = m.y; w[c][r][3] = m.z; w[c][r][4] = m.w;
-          w[c][r][5] = row[5];
-        }
-      }
-      gab4_finish(a, gx, gy, min(4, a.xs - gx), w);
-    }
+    src.consume(t, buf[b]);
     // this warp is done with buffer b (and, for edge tiles, before the next
     // tile's ring writes: those follow the next full wait)
     __syncwarp();
@@ -2142,7 +2153,7 @@ __global__ void __launch_bounds__(256) k_filter_tma(const __grid_constant__ Filt
     if (tid == 0 && !dead && t + 2 * G < ntiles) {
       if (q_wait(&empty[b], u & 1)) {
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        issue(t + 2 * G, b);
+        src.issue(t + 2 * G, smem_addr(&buf[b]), smem_addr(&full[b]));
         if (b) pend1 = u + 1; else pend0 = u + 1;
       } else {
         dead = true;
@@ -2155,6 +2166,70 @@ __global__ void __launch_bounds__(256) k_filter_tma(const __grid_constant__ Filt
     if (pend0 >= 0) q_wait(&full[0], pend0 & 1);
     if (pend1 >= 0) q_wait(&full[1], pend1 & 1);
   }
+}
+
+// Tiles of one image (ntx per row), its tensor map passed as a kernel parameter.
+struct OneImageTiles {
+  const FilterArgs& a;
+  const CUtensorMap& tm;
+  int ntx;
+  __device__ void issue(int t, uint32_t dst, uint32_t bar) const {
+    tma_tile_load(&tm, (t % ntx) * kGT - 4, (t / ntx) * kGT - 1, dst, bar);
+  }
+  __device__ void consume(int t, QTile& q) const {
+    filter_tma_tile(a, q, (t % ntx) * kGT, (t / ntx) * kGT);
+  }
+};
+
+__global__ void __launch_bounds__(256) k_filter_tma(const __grid_constant__ FilterArgs a,
+                                                    const __grid_constant__ CUtensorMap tm,
+                                                    int ntx, int ntiles, unsigned* err) {
+  OneImageTiles src{a, tm, ntx};
+  filter_tma_pipeline(src, ntiles, err);
+}
+
+// Tiles of many images: tile t is tile t - prefix[i] of image i (row-major,
+// 32x32), loaded through image i's tensor map maps[i] in global memory.
+// The tiles a CTA visits only increase, so each of the two streams (loads
+// issued by thread 0, tiles consumed) keeps its own image cursor.
+struct BatchTiles {
+  const FilterArgs* args;
+  const int* prefix;
+  const CUtensorMap* maps;
+  int nimg;
+  int ii = 0, ci = 0;      // image cursors: issue (thread 0), consume
+  int fenced = -1;         // thread 0: last map made visible to the tensor proxy
+  __device__ int advance(int& cur, int t) const {
+    while (cur + 1 < nimg && __ldg(prefix + cur + 1) <= t) ++cur;
+    return cur;
+  }
+  __device__ void issue(int t, uint32_t dst, uint32_t bar) {
+    const int im = advance(ii, t);
+    if (im != fenced) {
+      // the maps were written to global memory by copies from the host
+      asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;"
+                   :: "l"(reinterpret_cast<uint64_t>(maps + im)) : "memory");
+      fenced = im;
+    }
+    const int local = t - __ldg(prefix + im);
+    const int tw = (args[im].xs + kGT - 1) / kGT;
+    tma_tile_load(maps + im, (local % tw) * kGT - 4, (local / tw) * kGT - 1, dst, bar);
+  }
+  __device__ void consume(int t, QTile& q) {
+    const int im = advance(ci, t);
+    const FilterArgs& a = args[im];
+    const int local = t - __ldg(prefix + im);
+    const int tw = (a.xs + kGT - 1) / kGT;
+    filter_tma_tile(a, q, (local % tw) * kGT, (local / tw) * kGT);
+  }
+};
+
+__global__ void __launch_bounds__(256) k_filter_batch_tma(const FilterArgs* __restrict__ args,
+                                                          const int* __restrict__ prefix,
+                                                          const CUtensorMap* __restrict__ maps,
+                                                          int nimg, int total, unsigned* err) {
+  BatchTiles src{args, prefix, maps, nimg};
+  filter_tma_pipeline(src, total, err);
 }
 
 // The tensor map of a's planar XYB for k_filter_tma, when its layout allows
@@ -2480,6 +2555,17 @@ void launch_filter_batch(const FilterArgs* args, const int* prefix, int nimg, in
   k_filter_batch<<<grid, 256, 0, s>>>(args, prefix, nimg, total);
 }
 
+bool make_filter_tensor_map(const FilterArgs& a, void* tm) {
+  static_assert(sizeof(CUtensorMap) == kTensorMapBytes, "tensor map size");
+  return filter_tensor_map(a, static_cast<CUtensorMap*>(tm));
+}
+
+void launch_filter_batch_tma(const FilterArgs* args, const int* prefix, const void* maps,
+                             int nimg, int total, int grid, unsigned* err, cudaStream_t s) {
+  k_filter_batch_tma<<<grid < total ? grid : total, 256, 2 * sizeof(QTile), s>>>(
+      args, prefix, static_cast<const CUtensorMap*>(maps), nimg, total, err);
+}
+
 void launch_epf_work_batch(const FilterArgs* args, int nimg, bool clamp, int grid,
                            cudaStream_t s) {
   if (clamp) k_epf_work_batch<true><<<grid, 32, 0, s>>>(args, nimg);
@@ -2511,8 +2597,11 @@ int batch_blocks_per_sm(int kind) {
   if (kind == 0) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_recon_batch, 128, 0);
   else if (kind == 1)
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_epf_work_batch<false>, 32, 0);
-  else
+  else if (kind == 2)
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_filter_batch, 256, 0);
+  else
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_filter_batch_tma, 256,
+                                                      2 * sizeof(QTile));
   return e == cudaSuccess && n > 0 ? n : 1;
 }
 

@@ -135,6 +135,14 @@ void launch_recon_batch(const ReconArgs* args, const int* prefix, int nimg, int 
                         cudaStream_t s);
 void launch_filter_batch(const FilterArgs* args, const int* prefix, int nimg, int total, int grid,
                          cudaStream_t s);
+// The TMA form of the multi-image Gaborish / colour launch: maps[i] is the
+// tensor map of args[i].xyb made by make_filter_tensor_map() (kTensorMapBytes
+// each, 64-byte aligned, in device memory); grid CTAs take the tiles
+// round robin; bounded waits set bit 8 of *err on expiry.
+constexpr size_t kTensorMapBytes = 128;
+bool make_filter_tensor_map(const FilterArgs& a, void* tm);
+void launch_filter_batch_tma(const FilterArgs* args, const int* prefix, const void* maps,
+                             int nimg, int total, int grid, unsigned* err, cudaStream_t s);
 // J.2 of many images (args[i].epf_list / epf_count / epf_out set; the sigma
 // pass copied the unchanged blocks), persistent grid of one-warp CTAs.
 void launch_epf_work_batch(const FilterArgs* args, int nimg, bool clamp, int grid,

@@ -38,6 +38,7 @@ def test_batch_equals_per_image(autotune):
         b = ctx.batch(jobs, autotune=autotune)
         info = b.info()
         assert info["images"] == len(jobs) and info["kernels_per_launch"] == 3
+        assert info["filter_tma"] == 1             # every scratch allows TMA tile loads
         stream = torch.cuda.Stream()
         for rep in range(2):                       # graph replayed twice
             b.launch(stream.cuda_stream)
@@ -45,6 +46,39 @@ def test_batch_equals_per_image(autotune):
             for (img, params, out, dtype), w in zip(jobs, want):
                 np.testing.assert_array_equal(out.cpu().numpy(), w)
                 out.zero_()
+        assert b.status() == 0
+        b.close()
+
+
+def test_batch_of_thin_images():
+    """Images one pixel wide or high (every tile an edge tile, the ring
+    mirrored on all sides) next to ordinary ones, with and without the EPF
+    and Gaborish: the TMA tile loads of the batch equal the per-image results."""
+    import torch
+    from paper_1908_03565_gb300 import binding as B
+    sizes = [(1, 1), (1, 37), (37, 1), (33, 2), (2, 45), (9, 13), (64, 40), (131, 77)]
+    jobs = []
+    for i, (xs, ys) in enumerate(sizes * 2):
+        img = B.to_device(synth.make_image(xs, ys, 7300 + i), torch)
+        dtype = (B.OUT_U8_SRGB, B.OUT_F32_LINEAR, B.OUT_F16_LINEAR)[i % 3]
+        params = B.filter_defaults(epf=int(i < len(sizes)), gab=int(i % 4 != 1))
+        shape, npd = B.out_shape(img, dtype)
+        tdt = {np.float32: torch.float32, np.float16: torch.float16, np.uint8: torch.uint8}[npd]
+        jobs.append((img, params, torch.zeros(shape, dtype=tdt, device="cuda"), dtype))
+    with B.Context(max_slots=1) as ctx:
+        want = []
+        for img, params, out, dtype in jobs:
+            ctx.poll(ctx.submit(img, params, out, dtype, on_device=True))
+            want.append(out.cpu().numpy().copy())
+            out.zero_()
+        b = ctx.batch(jobs, autotune=False)
+        assert b.info()["filter_tma"] == 1
+        stream = torch.cuda.Stream()
+        b.launch(stream.cuda_stream)
+        stream.synchronize()
+        for (img, params, out, dtype), w in zip(jobs, want):
+            np.testing.assert_array_equal(out.cpu().numpy(), w)
+        assert b.status() == 0
         b.close()
 
 
