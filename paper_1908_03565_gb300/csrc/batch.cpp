@@ -72,7 +72,7 @@ void enqueue(const jxl_recon_batch* b, const int* grid, cudaStream_t s) {
   if (b->ne) cudaMemsetAsync(b->d_counts, 0, sizeof(unsigned) * b->ne, s);
   if (b->rtotal) launch_recon_batch(b->d_rargs, b->d_rprefix, static_cast<int>(b->n), b->rtotal,
                                     grid[0], s);
-  if (b->ne) launch_epf_work_batch(b->d_eargs, b->ne, b->clamp, grid[1], s);
+  if (b->ne) launch_epf_work_batch(b->d_eargs, b->d_counts, b->ne, b->clamp, grid[1], s);
   if (b->ftotal) {
     if (b->d_maps)
       launch_filter_batch_tma(b->d_fargs, b->d_fprefix, b->d_maps, b->nf, b->ftotal, grid[2],

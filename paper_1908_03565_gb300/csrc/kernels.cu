@@ -2492,23 +2492,40 @@ __global__ void __launch_bounds__(32, 20) k_epf_work(const __grid_constant__ Fil
 
 // Multi-image form: the warps take the images' groups round robin, the first
 // group of each image going to the warp after the one that took the previous
-// image's last group.
+// image's last group.  counts[j] is image j's number of listed blocks
+// (args[j].epf_count points there); they are read 128 images at a time in one
+// coalesced load, and a warp reads an image's parameter block only when it
+// has a group in that image.
+constexpr int kEpfCountChunk = 128;
+
 template <bool kClamp>
 __global__ void __launch_bounds__(32, 18) k_epf_work_batch(const FilterArgs* __restrict__ args,
+                                                           const unsigned* __restrict__ counts,
                                                            int nimg) {
   __shared__ FilterArgs sa;
+  __shared__ unsigned scount[kEpfCountChunk];
   static_assert(sizeof(FilterArgs) % 4 == 0, "word copy");
+  const int G = static_cast<int>(gridDim.x);
   int rot = 0;
-  for (int j = 0; j < nimg; ++j) {
+  for (int c0 = 0; c0 < nimg; c0 += kEpfCountChunk) {
+    const int nc = min(kEpfCountChunk, nimg - c0);
     __syncwarp();
-    for (int k = threadIdx.x; k < int(sizeof(FilterArgs) / 4); k += 32)
-      reinterpret_cast<int*>(&sa)[k] = reinterpret_cast<const int*>(&args[j])[k];
+    for (int k = threadIdx.x; k < nc; k += 32) scount[k] = counts[c0 + k];
     __syncwarp();
-    const int total = static_cast<int>(*sa.epf_count);
-    int g0 = static_cast<int>(blockIdx.x) - rot;
-    if (g0 < 0) g0 += gridDim.x;
-    epf_work_groups<kClamp>(sa, sa.epf_list, total, g0, gridDim.x);
-    rot = (rot + (total + kLG - 1) / kLG) % static_cast<int>(gridDim.x);
+    for (int jj = 0; jj < nc; ++jj) {
+      const int total = static_cast<int>(scount[jj]);
+      const int groups = (total + kLG - 1) / kLG;
+      int g0 = static_cast<int>(blockIdx.x) - rot;
+      if (g0 < 0) g0 += G;
+      rot = (rot + groups) % G;
+      if (g0 >= groups) continue;          // no group of this image for this warp
+      __syncwarp();
+      const int* src = reinterpret_cast<const int*>(&args[c0 + jj]);
+      for (int k = threadIdx.x; k < int(sizeof(FilterArgs) / 4); k += 32)
+        reinterpret_cast<int*>(&sa)[k] = src[k];
+      __syncwarp();
+      epf_work_groups<kClamp>(sa, sa.epf_list, total, g0, G);
+    }
   }
 }
 
@@ -2566,10 +2583,10 @@ void launch_filter_batch_tma(const FilterArgs* args, const int* prefix, const vo
       args, prefix, static_cast<const CUtensorMap*>(maps), nimg, total, err);
 }
 
-void launch_epf_work_batch(const FilterArgs* args, int nimg, bool clamp, int grid,
-                           cudaStream_t s) {
-  if (clamp) k_epf_work_batch<true><<<grid, 32, 0, s>>>(args, nimg);
-  else k_epf_work_batch<false><<<grid, 32, 0, s>>>(args, nimg);
+void launch_epf_work_batch(const FilterArgs* args, const unsigned* counts, int nimg, bool clamp,
+                           int grid, cudaStream_t s) {
+  if (clamp) k_epf_work_batch<true><<<grid, 32, 0, s>>>(args, counts, nimg);
+  else k_epf_work_batch<false><<<grid, 32, 0, s>>>(args, counts, nimg);
 }
 
 // The kernels use static shared memory; ask for the largest carveout so the
