@@ -40,7 +40,7 @@ struct jxl_recon_batch {
   uint64_t pixels = 0;
   char* dmem = nullptr;
   ReconArgs* d_rargs = nullptr;
-  int* d_rprefix = nullptr;
+  int* d_ritem = nullptr;          // per transform work item: (image, cell in it)
   int rtotal = 0;
   FilterArgs* d_eargs = nullptr;   // J.2 of the images with the EPF
   unsigned* d_counts = nullptr;    // their listed-block counts (zeroed per launch)
@@ -70,8 +70,7 @@ jxlr_status bfail(jxlr_status s, const std::string& m) {
 
 void enqueue(const jxl_recon_batch* b, const int* grid, cudaStream_t s) {
   if (b->ne) cudaMemsetAsync(b->d_counts, 0, sizeof(unsigned) * b->ne, s);
-  if (b->rtotal) launch_recon_batch(b->d_rargs, b->d_rprefix, static_cast<int>(b->n), b->rtotal,
-                                    grid[0], s);
+  if (b->rtotal) launch_recon_batch(b->d_rargs, b->d_ritem, b->rtotal, grid[0], s);
   if (b->ne) launch_epf_work_batch(b->d_eargs, b->d_counts, b->ne, b->clamp, grid[1], s);
   if (b->ftotal) {
     if (b->d_maps)
@@ -142,7 +141,7 @@ jxlr_status autotune(jxl_recon_batch* b) {
         if (k == 0) {
           // the transform kernel appends to the J.2 lists: they restart empty
           if (b->ne) cudaMemsetAsync(b->d_counts, 0, sizeof(unsigned) * b->ne, b->cap);
-          launch_recon_batch(b->d_rargs, b->d_rprefix, b->n, b->rtotal, g, b->cap);
+          launch_recon_batch(b->d_rargs, b->d_ritem, b->rtotal, g, b->cap);
         }
         else launch_filter_batch(b->d_fargs, b->d_fprefix, b->nf, b->ftotal, g, b->cap);
         cudaEventRecord(e1, b->cap);
@@ -291,7 +290,14 @@ extern "C" jxlr_status jxl_recon_batch_create(jxl_recon_ctx* ctx, const jxl_reco
   // one device allocation: parameter blocks, prefixes, statuses, scratch
   size_t off = 0;
   auto take = [&](size_t bytes) { off = up(off, 256); size_t o = off; off += bytes; return o; };
-  const size_t o_r = take(sizeof(ReconArgs) * n), o_rp = take(sizeof(int) * rpre.size());
+  // per transform work item: its image and its cell within the image
+  std::vector<int> ritem(2 * static_cast<size_t>(rpre.back()));
+  for (size_t i = 0; i < n; ++i)
+    for (int w = rpre[i]; w < rpre[i + 1]; ++w) {
+      ritem[2 * static_cast<size_t>(w)] = static_cast<int>(i);
+      ritem[2 * static_cast<size_t>(w) + 1] = w - rpre[i];
+    }
+  const size_t o_r = take(sizeof(ReconArgs) * n), o_rp = take(sizeof(int) * ritem.size());
   const size_t o_e = take(sizeof(FilterArgs) * ea.size()), o_ec = take(sizeof(unsigned) * ea.size());
   const size_t o_f = take(sizeof(FilterArgs) * fa.size()), o_fp = take(sizeof(int) * fpre.size());
   const size_t o_st = take(sizeof(unsigned) * 4 * n);
@@ -343,7 +349,7 @@ extern "C" jxlr_status jxl_recon_batch_create(jxl_recon_ctx* ctx, const jxl_reco
     b->d_err = reinterpret_cast<unsigned*>(base + o_er);
   }
   b->d_rargs = reinterpret_cast<ReconArgs*>(base + o_r);
-  b->d_rprefix = reinterpret_cast<int*>(base + o_rp);
+  b->d_ritem = reinterpret_cast<int*>(base + o_rp);
   b->d_eargs = reinterpret_cast<FilterArgs*>(base + o_e);
   b->d_fargs = reinterpret_cast<FilterArgs*>(base + o_f);
   b->d_fprefix = reinterpret_cast<int*>(base + o_fp);
@@ -353,7 +359,7 @@ extern "C" jxlr_status jxl_recon_batch_create(jxl_recon_ctx* ctx, const jxl_reco
     if (e == cudaSuccess && bytes) e = cudaMemcpyAsync(d, h, bytes, cudaMemcpyHostToDevice, b->cap);
   };
   h2d(b->d_rargs, ra.data(), sizeof(ReconArgs) * n);
-  h2d(b->d_rprefix, rpre.data(), sizeof(int) * rpre.size());
+  h2d(b->d_ritem, ritem.data(), sizeof(int) * ritem.size());
   h2d(b->d_eargs, ea.data(), sizeof(FilterArgs) * ea.size());
   h2d(b->d_fargs, fa.data(), sizeof(FilterArgs) * fa.size());
   h2d(b->d_fprefix, fpre.data(), sizeof(int) * fpre.size());

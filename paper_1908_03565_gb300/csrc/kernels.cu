@@ -1325,30 +1325,23 @@ __global__ void __launch_bounds__(128, 7) k_recon(const __grid_constant__ ReconA
   recon_cell(a, blockIdx.x, blockIdx.y);
 }
 
-// Multi-image form: work item w is cell (w - prefix[i]) of image i, cells in
-// raster order; CTAs stride over the items.
+// Multi-image form: work item w is cell item_cell[w].y (raster order) of
+// image item_cell[w].x, a table made at batch creation (one load per item);
+// CTAs stride over the items.
 __global__ void __launch_bounds__(128, 6) k_recon_batch(const ReconArgs* __restrict__ args,
-                                                     const int* __restrict__ prefix, int nimg,
+                                                     const int2* __restrict__ item_cell,
                                                      int total) {
   __shared__ ReconArgs sa;
-  __shared__ int s_img;
+  __shared__ int2 s_ic;
   for (int w = blockIdx.x; w < total; w += gridDim.x) {
     __syncthreads();
-    if (threadIdx.x == 0) {
-      int lo = 0, hi = nimg;            // largest i with prefix[i] <= w
-      while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (prefix[mid] <= w) lo = mid; else hi = mid;
-      }
-      s_img = lo;
-    }
+    if (threadIdx.x == 0) s_ic = __ldg(item_cell + w);   // (image, its cell index)
     __syncthreads();
-    const int img = s_img;
+    const int img = s_ic.x, local = s_ic.y;
     static_assert(sizeof(ReconArgs) % 4 == 0, "word copy");
     for (int k = threadIdx.x; k < int(sizeof(ReconArgs) / 4); k += blockDim.x)
       reinterpret_cast<int*>(&sa)[k] = reinterpret_cast<const int*>(&args[img])[k];
     __syncthreads();
-    const int local = w - prefix[img];
     const int cells_x = (sa.wp + 31) / 32;
     recon_cell<false, false>(sa, local % cells_x, local / cells_x);
   }
@@ -1368,9 +1361,9 @@ void launch_recon(const ReconArgs& a, cudaStream_t s) {
   k_recon<<<grid, 128, 0, s>>>(a);
 }
 
-void launch_recon_batch(const ReconArgs* args, const int* prefix, int nimg, int total, int grid,
+void launch_recon_batch(const ReconArgs* args, const int* item_cell, int total, int grid,
                         cudaStream_t s) {
-  k_recon_batch<<<grid, 128, 0, s>>>(args, prefix, nimg, total);
+  k_recon_batch<<<grid, 128, 0, s>>>(args, reinterpret_cast<const int2*>(item_cell), total);
 }
 
 // ---------------------------------------------------------------------------

@@ -131,7 +131,9 @@ void launch_epf_work(const FilterArgs& a, const int* list, const unsigned* count
 
 // Multi-image launches: args[i] per image (device array), prefix[i] = first
 // work item of image i (prefix[nimg] = total), grid CTAs striding over items.
-void launch_recon_batch(const ReconArgs* args, const int* prefix, int nimg, int total, int grid,
+// The transform launch takes instead item_cell[2 w], item_cell[2 w + 1] =
+// (image, cell index within it) of work item w.
+void launch_recon_batch(const ReconArgs* args, const int* item_cell, int total, int grid,
                         cudaStream_t s);
 void launch_filter_batch(const FilterArgs* args, const int* prefix, int nimg, int total, int grid,
                          cudaStream_t s);
