@@ -47,7 +47,7 @@ GUIDE_OPS_PER_PX = 17
 # the current kernel on the same statistics at 4096x2048 (50,730 listed
 # blocks): 99,456,512 + 23,432,960; scaled to a launch by its pixels.  Set to
 # None whenever the kernel changes until it is captured again.
-EPF_WORK_DRAM_BYTES_4096x2048 = 99456512 + 23432960
+EPF_WORK_DRAM_BYTES_4096x2048 = None
 CPU_SAMPLE = 1024         # oracle sample: one 1024x1024 image, same statistics
 
 

@@ -78,7 +78,7 @@ struct Timing {
 // Words of the per-request device status block: [0] validation flags,
 // [1] [2] validation counters, [3] a bounded device wait expired (4: the
 // tensor-core completion, 8: a filter tile load), [4] blocks the J.2 kernel
-// filtered.
+// filtered, [5] the J.2 kernel's group counter (its warps claim work there).
 constexpr int kStatusWords = 8;
 
 }  // namespace
@@ -388,7 +388,7 @@ static int launch_epf_chain(Slot* slot, const FilterArgs& fa, float* eo, const E
   e.ors = wp;
   e.ops = wp * hp;
   mark(slot, 5);
-  launch_epf_work(e, sink.list, sink.count, s);
+  launch_epf_work(e, sink.list, sink.count, sink.count + 1, s);   // status words 4, 5
   mark(slot, 6);
   slot->epf_marked = slot->timed;
   if (qco) {

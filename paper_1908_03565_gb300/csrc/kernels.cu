@@ -2289,10 +2289,13 @@ constexpr int kLFB = 688;                         // floats per block (>= 3 kLFC
 __device__ __forceinline__ int lf_col(int fr, int fc) { return fc ^ (((fr >> 2) & 1) << 3); }
 constexpr int kLHR = 10;                          // rows of horizontal sums per block
 
-// The groups g0, g0 + gs, ... of one image's list (total listed blocks).
+// The groups of one image's list (total listed blocks) a warp takes: g0,
+// g0 + gs, ... or, with next (a zeroed counter), the ones it claims there one
+// at a time, the next claim issued before the current group's work.
 template <bool kClamp>
 __device__ __forceinline__ void epf_work_groups(const FilterArgs& a, const int* __restrict__ list,
-                                                int total, int g0, int gs) {
+                                                int total, int g0, int gs,
+                                                unsigned* next = nullptr) {
   __shared__ uint32_t G[kLG][kLGH][kLGS];
   __shared__ float F[kLG][kLFB];
   __shared__ __align__(16) uint16_t Hb[kLG][7][kLHR][8];
@@ -2301,7 +2304,15 @@ __device__ __forceinline__ void epf_work_groups(const FilterArgs& a, const int* 
   const int T16 = static_cast<int>((a.wmin_bits + 0xFFFFu) & 0xFFFF0000u);
   // step 2: lane = (block sk, rows 4 hh .. 4 hh + 3, column cx)
   const int sk = lane >> 4, hh = (lane >> 3) & 1, cx = lane & 7, r0 = 4 * hh;
-  for (int grp = g0; kLG * grp < total; grp += gs) {
+  int grp = g0;
+  if (next) {
+    unsigned v = 0;
+    if (lane == 0) v = atomicAdd(next, 1u);
+    grp = static_cast<int>(__shfl_sync(0xFFFFFFFFu, v, 0));
+  }
+  while (kLG * grp < total) {
+    unsigned claim = 0;
+    if (next && lane == 0) claim = atomicAdd(next, 1u);   // used after this group
     const int nb = min(kLG, total - kLG * grp);
     // ---- windows of mirrored samples and packed guide bytes (6.5, J.2.2) --
 #pragma unroll
@@ -2473,14 +2484,16 @@ __device__ __forceinline__ void epf_work_groups(const FilterArgs& a, const int* 
       }
     }
     __syncwarp();   // the next group's windows overwrite G and F
+    grp = next ? static_cast<int>(__shfl_sync(0xFFFFFFFFu, claim, 0)) : grp + gs;
   }
 }
 
 template <bool kClamp>
 __global__ void __launch_bounds__(32, 20) k_epf_work(const __grid_constant__ FilterArgs a,
                                                      const int* __restrict__ list,
-                                                     const unsigned* __restrict__ count) {
-  epf_work_groups<kClamp>(a, list, static_cast<int>(*count), blockIdx.x, gridDim.x);
+                                                     const unsigned* __restrict__ count,
+                                                     unsigned* next) {
+  epf_work_groups<kClamp>(a, list, static_cast<int>(*count), blockIdx.x, gridDim.x, next);
 }
 
 // Multi-image form: the warps take the images' groups round robin, the first
@@ -2619,7 +2632,8 @@ int filter_tiles(const FilterArgs& a) {
   return ((a.xs + kTW - 1) / kTW) * ((a.ys + kTH - 1) / kTH);
 }
 
-void launch_epf_work(const FilterArgs& a, const int* list, const unsigned* count, cudaStream_t s) {
+void launch_epf_work(const FilterArgs& a, const int* list, const unsigned* count, unsigned* next,
+                     cudaStream_t s) {
   // resident one-warp CTAs of k_epf_work on the current device (persistent grid)
   static int grid_of[64] = {};
   int dev = 0;
@@ -2631,8 +2645,8 @@ void launch_epf_work(const FilterArgs& a, const int* list, const unsigned* count
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_epf_work<false>, 32, 0);
     grid = (sms > 0 ? sms : 1) * (per > 0 ? per : 1);
   }
-  if (filter_needs_clamp(a)) k_epf_work<true><<<grid, 32, 0, s>>>(a, list, count);
-  else k_epf_work<false><<<grid, 32, 0, s>>>(a, list, count);
+  if (filter_needs_clamp(a)) k_epf_work<true><<<grid, 32, 0, s>>>(a, list, count, next);
+  else k_epf_work<false><<<grid, 32, 0, s>>>(a, list, count, next);
 }
 
 void launch_filter(const FilterArgs& a, cudaStream_t s) {

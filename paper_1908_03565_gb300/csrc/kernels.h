@@ -126,8 +126,10 @@ void launch_qco(const QcoArgs& a, cudaStream_t s);
 void launch_filter(const FilterArgs& a, cudaStream_t s);
 // J.2 on the blocks the sigma pass listed (EpfSink), into a.epf_out, where
 // that pass copied the other blocks; J.4 / L.2 then run as launch_filter()
-// on that output.
-void launch_epf_work(const FilterArgs& a, const int* list, const unsigned* count, cudaStream_t s);
+// on that output.  next: a zeroed counter the warps claim groups of 2 listed
+// blocks from (or nullptr: a fixed round robin).
+void launch_epf_work(const FilterArgs& a, const int* list, const unsigned* count, unsigned* next,
+                     cudaStream_t s);
 
 // Multi-image launches: args[i] per image (device array), prefix[i] = first
 // work item of image i (prefix[nimg] = total), grid CTAs striding over items.
