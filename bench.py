@@ -45,9 +45,9 @@ EPF_OPS_PER_FILTERED_PX = 56 * 8 + 4 + 4
 GUIDE_OPS_PER_PX = 17
 # DRAM bytes (read + write) of one k_epf_work launch, from an ncu capture of
 # the current kernel on the same statistics at 4096x2048 (50,730 listed
-# blocks): 99,456,512 + 23,432,960; scaled to a launch by its pixels.  Set to
+# blocks): 99,083,520 + 22,990,336; scaled to a launch by its pixels.  Set to
 # None whenever the kernel changes until it is captured again.
-EPF_WORK_DRAM_BYTES_4096x2048 = None
+EPF_WORK_DRAM_BYTES_4096x2048 = 99083520 + 22990336
 CPU_SAMPLE = 1024         # oracle sample: one 1024x1024 image, same statistics
 
 
