@@ -2262,7 +2262,8 @@ __global__ void __launch_bounds__(128, 4) k_epf(const __grid_constant__ FilterAr
 // neighbours (their windows share cache lines), and copies the unchanged
 // ones to the J.2 output; k_epf_work filters the listed blocks into that
 // output (k_epf_work_batch: the same for many images).
-//   k_epf_work  persistent one-warp CTAs taking 2 listed blocks at a time:
+//   k_epf_work  persistent one-warp CTAs taking 2 listed blocks at a time
+//               (a group; the warps claim groups from a per-request counter):
 //               per block a window of mirrored samples and packed guide
 //               bytes (6.5, J.2.2), then per horizontal offset ox
 //               step 1  the horizontal 4-sums H_o of the 10 rows the block's
@@ -2270,11 +2271,14 @@ __global__ void __launch_bounds__(128, 4) k_epf(const __grid_constant__ FilterAr
 //                       vertical offsets, as 16-bit values, one lane per
 //                       (block, row) walking the 7 offsets with its own
 //                       guide bytes in registers;
-//               step 2  one lane per half column (4 rows) of a block,
-//                       walking its rows with the sliding vertical 3-sum,
-//                       the J.2.4 weight and the J.2.5 sums.
+//               step 2  one lane per half column (4 rows) of a block: the
+//                       sliding vertical 3-sums (the patch SADs) of the 7
+//                       vertical offsets, a warp vote on which offsets give
+//                       some pixel a weight above the J.2.4 cut-off, and for
+//                       those only the weights and the J.2.5 sums.
 //               Weights, cut-off and summation order are those of k_epf, so
-//               the two kernels give the same bits.  Warps synchronise only
+//               the two kernels give the same bits (an offset skipped by
+//               the vote would add exactly zero).  Warps synchronise only
 //               within themselves: a CTA never waits on another warp.
 // ---------------------------------------------------------------------------
 constexpr int kLG = 2;                            // blocks per warp and round (the lane
