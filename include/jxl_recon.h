@@ -319,6 +319,10 @@ jxlr_status jxl_recon_serve(jxl_recon_ctx* ctx, const jxl_recon_request* reqs, s
  * of the requests must stay valid for the batch's lifetime. */
 typedef struct jxl_recon_batch jxl_recon_batch;
 #define JXLR_BATCH_AUTOTUNE 1
+/* The Gaborish / colour kernel of the batch loads its tiles with ordinary
+ * loads instead of TMA (the same results; without it the TMA form is used
+ * whenever every filtered image's scratch allows it). */
+#define JXLR_BATCH_PLAIN_LOADS 2
 
 typedef struct {
   uint32_t images;

@@ -102,6 +102,7 @@ class BatchInfo(ctypes.Structure):
 
 
 BATCH_AUTOTUNE = 1
+BATCH_PLAIN_LOADS = 2
 _lib = None
 
 
@@ -337,9 +338,10 @@ class Context:
                                   "completed": stats.completed,
                                   "max_in_flight": stats.max_in_flight}
 
-    def batch(self, jobs, autotune=True):
-        """A multi-image batch (CUDA graph) over device-resident jobs."""
-        return Batch(self, jobs, autotune)
+    def batch(self, jobs, autotune=True, plain_loads=False):
+        """A multi-image batch (CUDA graph) over device-resident jobs;
+        plain_loads: the filter's tiles by ordinary loads instead of TMA."""
+        return Batch(self, jobs, autotune, plain_loads)
 
     def stage_ms(self, ticket):
         ms = (ctypes.c_float * 4)()
@@ -389,13 +391,15 @@ def requests(jobs):
 class Batch:
     """jxl_recon_batch: create once, launch (graph replay) many times."""
 
-    def __init__(self, ctx, jobs, autotune=True):
+    def __init__(self, ctx, jobs, autotune=True, plain_loads=False):
         self.ctx = ctx
         self.lib = ctx.lib
         self.reqs, self.keep = requests(jobs)
         h = ctypes.c_void_p()
         st = self.lib.jxl_recon_batch_create(ctx.h, self.reqs, len(jobs),
-                                             BATCH_AUTOTUNE if autotune else 0, ctypes.byref(h))
+                                             (BATCH_AUTOTUNE if autotune else 0) |
+                                             (BATCH_PLAIN_LOADS if plain_loads else 0),
+                                             ctypes.byref(h))
         if st != JXLR_OK:
             raise JxlrError(st, ctx.last_error())
         self.h = h

@@ -304,7 +304,7 @@ extern "C" jxlr_status jxl_recon_batch_create(jxl_recon_ctx* ctx, const jxl_reco
   // one tensor map per filtered image when every one of them allows TMA
   struct alignas(64) Map { unsigned char b[kTensorMapBytes]; };
   std::vector<Map> maps(fa.size());
-  bool tma = !fa.empty();
+  bool tma = !fa.empty() && !(flags & JXLR_BATCH_PLAIN_LOADS);
   const size_t o_tm = take(sizeof(Map) * fa.size()), o_er = take(sizeof(unsigned));
   const size_t o_sc = take(scratch);
   cudaError_t e = cudaMalloc(&b->dmem, up(off, 256));

@@ -82,6 +82,29 @@ def test_batch_of_thin_images():
         b.close()
 
 
+def test_batch_plain_loads_equal_per_image():
+    """JXLR_BATCH_PLAIN_LOADS: the Gaborish / colour kernel of the batch
+    with ordinary tile loads gives the per-image results too."""
+    import torch
+    from paper_1908_03565_gb300 import binding as B
+    jobs = _jobs(B, torch, n=12, seed=7200)
+    with B.Context(max_slots=1) as ctx:
+        want = []
+        for img, params, out, dtype in jobs:
+            ctx.poll(ctx.submit(img, params, out, dtype, on_device=True))
+            want.append(out.cpu().numpy().copy())
+            out.zero_()
+        b = ctx.batch(jobs, autotune=False, plain_loads=True)
+        assert b.info()["filter_tma"] == 0
+        stream = torch.cuda.Stream()
+        b.launch(stream.cuda_stream)
+        stream.synchronize()
+        for (img, params, out, dtype), w in zip(jobs, want):
+            np.testing.assert_array_equal(out.cpu().numpy(), w)
+        assert b.status() == 0
+        b.close()
+
+
 def test_batch_rejects_bad_map():
     import torch
     from paper_1908_03565_gb300 import binding as B
