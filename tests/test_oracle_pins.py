@@ -332,6 +332,52 @@ def test_epf_zero_sad_is_56_tap_mean():
     np.testing.assert_allclose(out, want / 56.0, atol=1e-14)
 
 
+def test_epf_brute_force_per_pixel():
+    """J.2.3 - J.2.5 pixel by pixel on a 16x16 image of EPF-active
+    statistics: for every reference pixel, 56 offsets (cx -3..4, cy -3..3),
+    each distance the sum over the 3 channels of the 3x4 patch (iy -1..1,
+    ix -1..2) of guide differences, samples and guide mirrored at the image
+    edge (6.5); weights by Weight() with the J.2.4 cut-off; the weighted mean
+    of J.2.5.  Pixels of blocks with sigma < 16 pass through.  Only the
+    guide, sigma and Weight() (pinned above) are shared with the oracle."""
+    img = synth.make_image(16, 16, 4242, coef_scale=2.0, acmul=0.5, dc='smooth')
+    p = R.Params(epf=True)
+    xyb = R.reconstruct_xyb(img['coeffs'], img['vmap'], img['acmul'], img['cfl'], p)[:, :16, :16]
+    ys, xs = 16, 16
+    g = R.guide(xyb, p)
+    sig = R.epf_sigma(xyb, img['vmap'], img['acmul'], img['sharpness'], p)
+    mt4 = R.mul_table4()
+    want = np.array(xyb, dtype=np.float64)
+    live = 0
+    for y in range(ys):
+        for x in range(xs):
+            sg = int(sig[y // 8, x // 8])
+            if sg < 16:
+                continue
+            num = np.zeros(3)
+            den = 0.0
+            for cy in range(-3, 4):
+                for cx in range(-3, 5):
+                    sad = 0
+                    for c in range(3):
+                        for iy in (-1, 0, 1):
+                            for ix in (-1, 0, 1, 2):
+                                a = g[c, R.mirror(y + iy, ys), R.mirror(x + ix, xs)]
+                                b = g[c, R.mirror(y + cy + iy, ys), R.mirror(x + cx + ix, xs)]
+                                sad += abs(int(a) - int(b))
+                    w = float(R.weight(sad, mt4[sg]))
+                    if w < p.epf_weight_min:
+                        w = 0.0
+                    if w > 0 and (cx, cy) != (0, 0):
+                        live += 1
+                    num += w * xyb[:, R.mirror(y + cy, ys), R.mirror(x + cx, xs)]
+                    den += w
+            want[:, y, x] = num / den
+    assert live > 1000        # many offsets besides the reference's own keep a weight
+    np.testing.assert_allclose(R.epf(xyb.astype(np.float64), img['vmap'], img['acmul'],
+                                     img['sharpness'], p), want, rtol=0, atol=1e-12)
+
+
 def test_epf_sigma_rule():
     """J.2.4: sigma = trunc(min(min(range,70)*12.6*lut, 20/AcMul, 170)),
     range = max over the varblock of the per-block channel-max range."""
