@@ -307,6 +307,26 @@ def test_epf_preserves_constant_and_gaborish_sums_to_one():
     assert g[0, 3, 3] == pytest.approx(w2 / n)
 
 
+@pytest.mark.parametrize("ys,xs", [(13, 17), (1, 5), (2, 1), (1, 1)])
+def test_gaborish_is_a_mirrored_3x3_correlation(ys, xs):
+    """J.4: per channel, the 3x3 kernel (centre 1, edges w1, corners w2,
+    scaled to sum 1) applied with the 6.5 mirroring, which at a distance of
+    one sample is the edge-duplicating reflection of scipy.ndimage
+    ('reflect'); distinct weights per channel."""
+    ndi = pytest.importorskip("scipy.ndimage")
+    rng = np.random.default_rng(99)
+    img = rng.normal(0.0, 1.0, (3, ys, xs))
+    p = R.Params(gab=True)
+    p.gab_w1 = [0.11, 0.09, 0.13]
+    p.gab_w2 = [0.05, 0.07, 0.02]
+    got = R.gaborish(img, p)
+    for c in range(3):
+        w1, w2 = p.gab_w1[c], p.gab_w2[c]
+        k = np.array([[w2, w1, w2], [w1, 1.0, w1], [w2, w1, w2]]) / (1.0 + 4 * w1 + 4 * w2)
+        np.testing.assert_allclose(got[c], ndi.correlate(img[c], k, mode="reflect"),
+                                   rtol=0, atol=1e-14)
+
+
 def test_epf_zero_sad_is_56_tap_mean():
     """With a guide that is constant (every scaled value clamps to 0) all
     SADs are 0, all weights 1, and J.2.5 is the plain mean of the 7x8
