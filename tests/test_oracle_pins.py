@@ -352,6 +352,28 @@ def test_epf_zero_sad_is_56_tap_mean():
     np.testing.assert_allclose(out, want / 56.0, atol=1e-14)
 
 
+def test_guide_closed_form():
+    """J.2.2: g[c] = clamp(trunc((in[c] - min[c]) * epf_scale[c]), 0, 255)
+    with min = -0.03 * intensity_multiplier3 for X and 0 for Y and B.  The
+    inputs sit at scaled values away from integers, so binary32 rounding
+    cannot move the result."""
+    p = R.Params(epf=True)
+    im3 = (p.target_nits_div50 * 50.0 / 250.0) ** (1.0 / 3.0)
+    ks = np.array([-7.3, -0.4, 0.5, 1.75, 100.25, 254.4, 255.6, 1.0e4])
+    want = np.array([0, 0, 0, 1, 100, 254, 255, 255])
+    img = np.zeros((3, 2, len(ks)))
+    for c in range(3):
+        mn = (-0.03 if c == 0 else 0.0) * im3
+        img[c, :, :] = mn + ks / float(p.epf_scale[c])
+    g = R.guide(img, p)
+    assert g.dtype.kind in "iu"
+    assert (g == want[None, None, :]).all()
+    # the X offset matters: X = 0 is above X's minimum, so its guide is positive
+    zero = R.guide(np.zeros((3, 1, 1)), p)
+    assert zero[0, 0, 0] == int(0.03 * im3 * float(p.epf_scale[0])) > 0
+    assert zero[1, 0, 0] == 0 and zero[2, 0, 0] == 0
+
+
 def test_epf_brute_force_per_pixel():
     """J.2.3 - J.2.5 pixel by pixel on a 16x16 image of EPF-active
     statistics: for every reference pixel, 56 offsets (cx -3..4, cy -3..3),
@@ -359,7 +381,8 @@ def test_epf_brute_force_per_pixel():
     ix -1..2) of guide differences, samples and guide mirrored at the image
     edge (6.5); weights by Weight() with the J.2.4 cut-off; the weighted mean
     of J.2.5.  Pixels of blocks with sigma < 16 pass through.  Only the
-    guide, sigma and Weight() (pinned above) are shared with the oracle."""
+    guide, sigma and Weight() (each pinned in this file) are shared with the
+    oracle."""
     img = synth.make_image(16, 16, 4242, coef_scale=2.0, acmul=0.5, dc='smooth')
     p = R.Params(epf=True)
     xyb = R.reconstruct_xyb(img['coeffs'], img['vmap'], img['acmul'], img['cfl'], p)[:, :16, :16]
