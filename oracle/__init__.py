@@ -9,7 +9,9 @@ never imports it. Only ``tests/``, ``__graft_entry__.smoke()`` and the
 CPU-baseline leg of ``bench.py`` may import it; the product never does.
 
 Pinning status: every function is pinned by ``tests/test_oracle_pins.py``
-against closed forms, round trips and invariants the draft fixes, except the
+against closed forms, round trips and invariants the draft fixes (the C.6.1
+weight synthesis of every shape also against entries derived by hand from
+the printed bands, ``tests/golden/c61_weights.txt``), except the
 reading of the garbled numerator formula of C.6.1 (its 4-point and
 rectangular cases), which no independent value in the draft pins, and the
 bit stream of the K.5 generator read from a garbled listing ("parity

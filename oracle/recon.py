@@ -254,7 +254,8 @@ _LF4_INV = {}
 def half_mean_scale():
     """The coefficient of frequency 1 of the 8-point IDCT whose two 4-sample
     halves average to +1 and -1 (the factor I.2.7.3 writes ScaleF(2, 8, 1);
-    READING: the exact inverse of the half means, like R11 at N = 8)."""
+    READING: the exact inverse of the half means, as the LLF-from-DC step
+    at N = 8 takes the exact inverse of the 8x8 box mean)."""
     return 1.0 / TR.idct_matrix(8)[:4, 1].mean()
 
 

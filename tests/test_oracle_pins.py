@@ -7,6 +7,7 @@ the draft's forward procedures (I.2.3), invariants the draft states
 draft's independent I.2.6 downsampling formula, and brute force.
 """
 import math
+import os
 
 import numpy as np
 import pytest
@@ -182,6 +183,78 @@ def test_dct8_weight_closed_forms():
     assert T.dequant_matrix(0, 0)[0, 1] == pytest.approx(num / 5.0, rel=1e-14)
     assert T.dequant_matrix(0, 0)[1, 1] == pytest.approx(T.I(8, 1) ** 2 / 64.0 / 5.0,
                                                          rel=1e-14)
+
+
+def _c61_golden():
+    """Entries of tests/golden/c61_weights.txt: (code, channel, x, y, value),
+    each value a hand-specialised expression of C.6.1.1's printed numbers."""
+    path = os.path.join(os.path.dirname(__file__), "golden", "c61_weights.txt")
+    rows = []
+    with open(path) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            code, c, x, y, expr = line.split(None, 4)
+            val = eval(expr, {"__builtins__": {}}, {"sqrt": math.sqrt})
+            rows.append((int(code), int(c), int(x), int(y), float(val), expr))
+    return rows
+
+
+def test_c61_weights_hand_derived_entries():
+    """C.6.1 weight synthesis against entries derived by hand from the
+    printed band arrays (distance on a band or at a known fraction between
+    two, eccentricity 0 on the diagonal, 1 on the axes, or in between for
+    the 32x8 shapes), covering every DCT-mode shape, the DCT4 and 4x8
+    up-sampling with their multipliers, and the AFV cells."""
+    rows = _c61_golden()
+    codes = {r[0] for r in rows}
+    assert codes == {0, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14}
+    for code, c, x, y, want, expr in rows:
+        got = T._weights(code, c)[y, x]
+        assert got == pytest.approx(want, rel=1e-12), (code, c, x, y, expr)
+
+
+def test_c61_golden_catches_band_slips():
+    """The hand-derived entries fail for plausible misreadings: bands shifted
+    by one index, the eccentricity bands dropped, DCT32x8 and DCT8x32
+    exchanged, the 4x8 up-sampling on the wrong axis, and the AFV frequency
+    table read transposed."""
+    rows = _c61_golden()
+
+    def fails(weights_fn):
+        return any(abs(weights_fn(code, c)[y, x] - want) > 1e-9 * abs(want)
+                   for code, c, x, y, want, _ in rows
+                   if weights_fn(code, c).shape[0] > y and weights_fn(code, c).shape[1] > x)
+
+    orig_db, orig_ecc = T.distance_bands, T.eccentricity_bands
+    orig_freqs = T._AFV_FREQS
+    try:
+        T.distance_bands = lambda db: [db[0]] + [T._band_factor(db[i + 1 if i + 1 < len(db) else i])
+                                                 * db[0] for i in range(1, len(db))]
+        assert fails(T._weights)
+        T.distance_bands = orig_db
+        T.eccentricity_bands = lambda eb: [1.0] * (len(eb) + 1)
+        assert fails(T._weights)
+        T.eccentricity_bands = orig_ecc
+        T._AFV_FREQS = tuple(orig_freqs[4 * (i % 4) + i // 4] for i in range(16))
+        assert fails(T._weights)
+        T._AFV_FREQS = orig_freqs
+    finally:
+        T.distance_bands, T.eccentricity_bands, T._AFV_FREQS = orig_db, orig_ecc, orig_freqs
+
+    def swapped(code, c):
+        # the orientation misread: DCT32x8 given DCT8x32's matrix and back
+        return T._weights(17 - code if code in (8, 9) else code, c)
+    assert fails(swapped)
+
+    def up_wrong_axis(code, c):
+        if code in (12, 13):
+            w48 = T.dct_weights(4, 8, T._DB_DCT4X8[c], (0.0, 0.0))
+            w = np.array([[w48[y, x // 2] for x in range(8)] for y in range(8)])
+            return w if code == 12 else w.T
+        return T._weights(code, c)
+    assert fails(up_wrong_axis)
 
 
 def test_dct2_identity_matrices_are_reciprocal_parameters():
