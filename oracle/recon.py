@@ -21,10 +21,12 @@ the quantised DC samples of the 8x8 blocks (x0/8 + u, y0/8 + v).
 0xFF on the other blocks it covers; ``acmul[by][bx]`` is AcMul (C.5.5);
 ``cfl[ty][tx] = (kX, kB)`` per 64x64 tile; ``sharpness[by][bx]`` (C.5.6).
 
-Decisions that turn a real number into an integer inside the EPF (the guide
-quantisation and the sigma truncation of J.2.2/J.2.4) are taken in binary32
-arithmetic, operation by operation, exactly as the CUDA kernels take them,
-so that both sides see the same integers for the same input samples.
+Decisions that turn a real number into an integer (the guide bytes and the
+sigma truncation of J.2.2/J.2.4, the window test of the F.2 smoothing) are
+taken in real (FP64) arithmetic, as the draft writes them (5.4).  For
+comparisons with an implementation in binary32, epf_decision_bounds,
+epf_undetermined and dc_smooth_margin give the decisions that a bounded
+perturbation of the input could change.
 """
 import math
 
@@ -80,6 +82,22 @@ def mirror(coord, size):
             return c
         c = np.where(lo, -c - 1, c)
         c = np.where(hi, 2 * size - 1 - c, c)
+
+
+def mirror_pad(arr, pad):
+    """``arr`` (..., h, w) extended by ``pad`` samples on every side with the
+    6.5 mirroring, so that shifted windows become plain slices."""
+    h, w = arr.shape[-2:]
+    rows = mirror(np.arange(-pad, h + pad), h)
+    cols = mirror(np.arange(-pad, w + pad), w)
+    return arr[..., rows[:, None], cols[None, :]]
+
+
+def shifted(padded, pad, region, dx, dy):
+    """The samples at (x + dx, y + dy) for (x, y) in ``region`` (x0, y0, x1,
+    y1), read from an array made by mirror_pad with the same ``pad``."""
+    x0, y0, x1, y1 = region
+    return padded[..., pad + y0 + dy:pad + y1 + dy, pad + x0 + dx:pad + x1 + dx]
 
 
 # ---------------------------------------------------------------------------
@@ -158,9 +176,9 @@ def dequantize(coeffs, vmap, acmul, cfl, params, diag=None):
     out[2] = out[2] + kb * out[1]
     # F.2 DC dequantisation per 8x8 block (and adaptive smoothing), then G
     if params.dc_smooth:
-        dcf = dc_smooth(dc_image(coeffs, vmap, params), params).astype(np.float64)
+        dcf = dc_smooth(dc_image(coeffs, vmap, params), params)
     else:
-        dcf = dc_image(coeffs, vmap, params, dtype=np.float64)
+        dcf = dc_image(coeffs, vmap, params)
     dcf[0] = dcf[0] + params.kx_dc * dcf[1]
     dcf[2] = dcf[2] + params.kb_dc * dcf[1]
     # I.2.7 LLF from DC, per varblock
@@ -183,11 +201,10 @@ def dequantize(coeffs, vmap, acmul, cfl, params, diag=None):
 DC_SMOOTH_W = (0.05226273532324128, 0.20345139757231578, 0.0334829185968739)
 
 
-def dc_image(coeffs, vmap, params, dtype=np.float32):
+def dc_image(coeffs, vmap, params, dtype=np.float64):
     """Dequantised DC samples per 8x8 block, (3, Hp/8, Wp/8), before chroma
     from luma (F.2 with extra_levels 0): the DC of block (bx0+u, by0+v) of a
-    varblock sits at its LLF slot (u, v).  binary32 when the samples feed
-    the smoothing decision (one rounding of q * m_DC, as in the kernels)."""
+    varblock sits at its LLF slot (u, v)."""
     bh, bw = vmap.shape
     out = np.zeros((3, bh, bw), dtype=dtype)
     for c_, bx, by in varblocks(vmap):
@@ -198,31 +215,45 @@ def dc_image(coeffs, vmap, params, dtype=np.float32):
     return out
 
 
+def _dc_window(dc, params):
+    """The F.2 weighted average wa of the 3x3 neighbourhood of every sample
+    off the border (weights for the centre, the 4 edge and the 4 corner
+    neighbours), the centre s, and the half window dcq/2 per channel."""
+    w0, w1, w2 = DC_SMOOTH_W
+    d = np.asarray(dc, np.float64)
+    s_ = d[:, 1:-1, 1:-1]
+    edges = d[:, :-2, 1:-1] + d[:, 1:-1, :-2] + d[:, 1:-1, 2:] + d[:, 2:, 1:-1]
+    corners = d[:, :-2, :-2] + d[:, :-2, 2:] + d[:, 2:, :-2] + d[:, 2:, 2:]
+    wa = w0 * s_ + w1 * edges + w2 * corners
+    half = 0.5 * np.asarray(params.m_dc, np.float64)[:, None, None]
+    return wa, s_, half
+
+
 def dc_smooth(dc, params):
     """F.2: each DC sample not on the first/last row/column of the DC image
-    becomes the 3x3 weighted average wa of its neighbourhood (weights for
-    the centre, the 4 edge and the 4 corner neighbours) when
-    s - dcq/2 <= wa <= s + dcq/2.  READINGS: the averages read the
-    unsmoothed image; dcq, the DcQuantField of C.5.2, is m_DC of the channel
-    (no extra levels); the average and the comparison are evaluated in
-    binary32 in the order centre, then edges (N, W, E, S), then corners
-    (NW, NE, SW, SE), as the kernels do, so that both take the same
-    decisions."""
-    dc = dc.astype(np.float32)
-    out = dc.copy()
-    _, bh, bw = dc.shape
-    if bh < 3 or bw < 3:
+    becomes the 3x3 weighted average wa of its neighbourhood when
+    s - dcq/2 <= wa <= s + dcq/2 (real arithmetic).  READINGS: the averages
+    read the unsmoothed image; dcq, the DcQuantField of C.5.2, is m_DC of
+    the channel (no extra levels)."""
+    out = np.array(dc, dtype=np.float64, copy=True)
+    if out.shape[1] < 3 or out.shape[2] < 3:
         return out
-    w0, w1, w2 = (np.float32(w) for w in DC_SMOOTH_W)
-    for c in range(3):
-        d = dc[c]
-        s_ = d[1:-1, 1:-1]
-        edges = ((d[:-2, 1:-1] + d[1:-1, :-2]) + d[1:-1, 2:]) + d[2:, 1:-1]
-        corners = ((d[:-2, :-2] + d[:-2, 2:]) + d[2:, :-2]) + d[2:, 2:]
-        wa = (w0 * s_ + w1 * edges) + w2 * corners
-        half = np.float32(0.5) * np.float32(params.m_dc[c])
-        keep = (s_ - half <= wa) & (wa <= s_ + half)
-        out[c, 1:-1, 1:-1] = np.where(keep, wa, s_)
+    wa, s_, half = _dc_window(out, params)
+    keep = (s_ - half <= wa) & (wa <= s_ + half)
+    out[:, 1:-1, 1:-1] = np.where(keep, wa, s_)
+    return out
+
+
+def dc_smooth_margin(dc, params):
+    """Distance of each sample's wa from the nearer end of its F.2 window
+    [s - dcq/2, s + dcq/2] (infinite on the border, where no test is made):
+    an evaluation whose error is below the margin takes the same decision."""
+    d = np.asarray(dc, np.float64)
+    out = np.full(d.shape, np.inf)
+    if d.shape[1] < 3 or d.shape[2] < 3:
+        return out
+    wa, s_, half = _dc_window(d, params)
+    out[:, 1:-1, 1:-1] = np.minimum(np.abs(wa - (s_ - half)), np.abs(s_ + half - wa))
     return out
 
 
@@ -459,94 +490,241 @@ def mul_table4():
     return tab
 
 
-def _f32(x):
-    return np.asarray(x, dtype=np.float32)
-
-
 def guide_scaled(img, params):
-    """J.2.2 `scaled`, binary32 operation by operation: (in - min) * scale."""
+    """J.2.2 `scaled` in real (FP64) arithmetic: (in - min[c]) * epf_scale[c],
+    with min[c] = -0.03 * intensity_multiplier3 for X and 0 otherwise."""
     im3 = (params.target_nits_div50 * 50.0 / 250.0) ** (1.0 / 3.0)
-    out = np.zeros(img.shape, dtype=np.float32)
+    out = np.zeros(img.shape, dtype=np.float64)
     for c in range(3):
         mn = (-0.03 if c == 0 else 0.0) * im3
-        t = _f32(img[c]) - np.float32(mn)
-        out[c] = t * np.float32(params.epf_scale[c])
+        out[c] = (np.asarray(img[c], np.float64) - mn) * params.epf_scale[c]
     return out
 
 
+def guide_from_scaled(s):
+    """J.2.2 guide sample: the scaled value clamped to [0, 255] and stored
+    in 8 bits.  READING: the conversion truncates (C++ semantics, 5.4)."""
+    return np.trunc(np.clip(s, 0.0, 255.0)).astype(np.int64)
+
+
 def guide(img, params):
-    s = guide_scaled(img, params)
-    return np.trunc(np.clip(s, np.float32(0), np.float32(255))).astype(np.int64)
+    return guide_from_scaled(guide_scaled(img, params))
+
+
+def block_ranges(scaled, vmap):
+    """J.2.4 `range` per 8x8 block of the cropped image: r[c] is the largest
+    minus the smallest `scaled` sample of channel c in the block, all_r the
+    largest of the three, and a block's range the largest all_r over the
+    blocks of its varblock.  READING: only in-image samples count toward a
+    block's r.  Accepts a pair (low, high) of scaled images instead of one:
+    r is then taken as max(high) - min(low), the largest range that inputs
+    between the two can have, or max(low) - min(high), the smallest (the
+    pair is returned as (smallest, largest))."""
+    if isinstance(scaled, tuple):
+        lo, hi = scaled
+        return (_block_ranges(lo, hi, vmap, smallest=True),
+                _block_ranges(lo, hi, vmap, smallest=False))
+    return _block_ranges(scaled, scaled, vmap, smallest=False)
+
+
+def _block_ranges(lo, hi, vmap, smallest):
+    _, ys, xs = lo.shape
+    bh, bw = (ys + 7) // 8, (xs + 7) // 8
+    r = np.zeros((bh, bw))
+    for by in range(bh):
+        for bx in range(bw):
+            sl = (slice(None), slice(8 * by, 8 * by + 8), slice(8 * bx, 8 * bx + 8))
+            a, b = lo[sl], hi[sl]
+            if smallest:
+                rc = [max(a[c].max() - b[c].min(), 0.0) for c in range(3)]
+            else:
+                rc = [b[c].max() - a[c].min() for c in range(3)]
+            r[by, bx] = max(rc)
+    rng = np.zeros((bh, bw))
+    for c_, bx0, by0 in varblocks(vmap):
+        W, H = T.SHAPE_WH[c_]
+        if by0 >= bh or bx0 >= bw:
+            continue
+        sl = (slice(by0, min(by0 + H // 8, bh)), slice(bx0, min(bx0 + W // 8, bw)))
+        rng[sl] = r[sl].max()
+    return rng
+
+
+def sigma_terms(rng, acmul, sharpness, params):
+    """The two terms of J.2.4 sigma, per block, in real arithmetic: the
+    range term min(range, range_max) * range_mul * sharp_lut[sharpness] and
+    the quant term quant * quant_mul, quant = 1 / AcMul of the block."""
+    bh, bw = rng.shape
+    a = np.minimum(rng, params.epf_range_max) * params.epf_range_mul
+    lut = np.asarray(params.epf_sharp_lut, np.float64)[sharpness[:bh, :bw].astype(np.int64)]
+    a = a * lut
+    q = (1.0 / np.asarray(acmul[:bh, :bw], np.float64)) * params.epf_quant_mul
+    return a, q
+
+
+def sigma_real(rng, acmul, sharpness, params):
+    """J.2.4 sigma before truncation: min(range term, quant term, sigma_max)."""
+    a, q = sigma_terms(rng, acmul, sharpness, params)
+    return np.minimum(np.minimum(a, q), params.epf_sigma_max)
+
+
+def sigma_from_real(sig):
+    """truncate(), then READING: the mul table ends at 672."""
+    return np.minimum(np.trunc(sig).astype(np.int64), 672)
 
 
 def epf_sigma(img, vmap, acmul, sharpness, params):
-    """Per 8x8 block sigma of J.2.4 (binary32 arithmetic), for the cropped
-    image ``img`` (3, ysize, xsize).  READING: only in-image samples count
-    toward a block's range."""
-    _, ys, xs = img.shape
+    """Per 8x8 block sigma of J.2.4 (real arithmetic) for the cropped image
+    ``img`` (3, ysize, xsize)."""
+    rng = block_ranges(guide_scaled(img, params), vmap)
+    return sigma_from_real(sigma_real(rng, acmul, sharpness, params))
+
+
+# ---------------------------------------------------------------------------
+# Decisions of J.2 under uncertain input (for comparisons with binary32)
+# ---------------------------------------------------------------------------
+def epf_decision_bounds(img, vmap, acmul, sharpness, params, slack, rel=0.0, quant_alt=None):
+    """The J.2 decisions for every input whose scaled guide samples lie
+    within +-slack of those of ``img`` (slack: scalar or per sample, in
+    guide units), whose range term of sigma lies within a relative ``rel``
+    of the value those samples give, and whose quant term lies between the
+    real one and ``quant_alt`` (per block; another evaluation of it, or None).
+    Returns (g_lo, g_hi, s_lo, s_hi): the smallest and largest guide bytes
+    and block sigmas reachable.  A decision is fixed where the two agree;
+    where they differ the input lies within the bound of a threshold and
+    either outcome is correct."""
     s = guide_scaled(img, params)
-    bh, bw = (ys + 7) // 8, (xs + 7) // 8
-    r = np.zeros((bh, bw), dtype=np.float32)
-    for by in range(bh):
-        for bx in range(bw):
-            blk = s[:, 8 * by:8 * by + 8, 8 * bx:8 * bx + 8]
-            rc = [np.float32(blk[c].max() - blk[c].min()) for c in range(3)]
-            r[by, bx] = max(rc)
-    code, ox, oy = owner_map(vmap)
-    rng = np.zeros((bh, bw), dtype=np.float32)
-    for c_, bx0, by0 in varblocks(vmap):
-        W, H = T.SHAPE_WH[c_]
-        sl = (slice(by0, min(by0 + H // 8, bh)), slice(bx0, min(bx0 + W // 8, bw)))
-        if sl[0].start >= bh or sl[1].start >= bw:
-            continue
-        rng[sl] = r[sl].max()
-    sig = np.minimum(rng, np.float32(params.epf_range_max))
-    sig = sig * np.float32(params.epf_range_mul)
-    lut = _f32(params.epf_sharp_lut)[sharpness[:bh, :bw].astype(np.int64)]
-    sig = sig * lut
-    quant = np.float32(1.0) / _f32(acmul[:bh, :bw])
-    sig = np.minimum(sig, quant * np.float32(params.epf_quant_mul))
-    sig = np.minimum(sig, np.float32(params.epf_sigma_max))
-    sigma = np.trunc(sig).astype(np.int64)
-    return np.minimum(sigma, 672)   # READING: table ends at 672
+    lo, hi = s - slack, s + slack
+    r_lo, r_hi = block_ranges((lo, hi), vmap)
+    a_lo, q = sigma_terms(r_lo, acmul, sharpness, params)
+    a_hi, _ = sigma_terms(r_hi, acmul, sharpness, params)
+    q_lo = q if quant_alt is None else np.minimum(q, quant_alt)
+    q_hi = q if quant_alt is None else np.maximum(q, quant_alt)
+    smax = params.epf_sigma_max
+    s_lo = sigma_from_real(np.minimum(np.minimum(a_lo * (1.0 - rel), q_lo), smax))
+    s_hi = sigma_from_real(np.minimum(np.minimum(a_hi * (1.0 + rel), q_hi), smax))
+    return guide_from_scaled(lo), guide_from_scaled(hi), s_lo, s_hi
 
 
-EPF_OFFSETS = [(cx, cy) for cy in range(-3, 4) for cx in range(-3, 5)]
-
-
-def epf(img, vmap, acmul, sharpness, params, region=None):
-    """J.2 on the cropped image img (3, ysize, xsize), FP64.  ``region``
-    (x0, y0, x1, y1) restricts the output to a window (sampled checks of
-    large images); the result covers that window only."""
+def epf_undetermined(img, vmap, acmul, sharpness, params, slack, rel=0.0, region=None,
+                     quant_alt=None):
+    """Pixels of the J.2 output (over ``region``) that the input does not
+    determine when its guide samples and sigmas are known only within the
+    bounds of epf_decision_bounds: a pixel is undetermined if its block's
+    sigma is not fixed and some outcome filters it with a non-centre weight
+    at or above the cut-off, or if its sigma is fixed at >= 16 and for some
+    offset the guide bytes that are not fixed could bring the patch SAD to
+    a weight at or above the cut-off (each byte that is not fixed moves the
+    SAD by at most 1).  Everywhere else every reachable set of decisions
+    gives the same weights, hence the same output."""
     _, ys, xs = img.shape
     if region is None:
         region = (0, 0, xs, ys)
     x0, y0, x1, y1 = region
-    g = guide(img, params)
-    sigma_blk = epf_sigma(img, vmap, acmul, sharpness, params)
+    g_lo, g_hi, s_lo, s_hi = epf_decision_bounds(img, vmap, acmul, sharpness, params,
+                                                 slack, rel, quant_alt)
+    g = guide(img, params).astype(np.int32)
+    loose = (g_lo != g_hi).astype(np.int32)
     mt4 = mul_table4()
     px = np.arange(x0, x1)[None, :]
     py = np.arange(y0, y1)[:, None]
+    P = _EPF_PAD
+    gp, lp = mirror_pad(g, P), mirror_pad(loose, P)
+    blo = s_lo[py // 8, px // 8]
+    bhi = s_hi[py // 8, px // 8]
+    mul_hi = mt4[np.clip(bhi, 16, 672)]       # the largest weights: largest sigma
 
-    def at(arr, dx, dy):
-        return arr[..., mirror(py + dy, ys), mirror(px + dx, xs)]
-
-    sad = np.zeros((56, y1 - y0, x1 - x0), dtype=np.int64)
-    for i, (cx, cy) in enumerate(EPF_OFFSETS):
-        acc = np.zeros((y1 - y0, x1 - x0), dtype=np.int64)
+    def one(i, off):
+        cx, cy = off
+        if cx == 0 and cy == 0:
+            return None                       # the centre's SAD is 0 on any input
+        sad = _patch_sad(gp, P, region, cx, cy)
+        # guide bytes that are not fixed, counted over both patches
+        k = np.zeros_like(sad)
         for c in range(3):
             for iy in (-1, 0, 1):
                 for ix in (-1, 0, 1, 2):
-                    acc += np.abs(at(g[c], ix, iy) - at(g[c], cx + ix, cy + iy))
-        sad[i] = acc
+                    k += (shifted(lp[c], P, region, ix, iy)
+                          + shifted(lp[c], P, region, cx + ix, cy + iy))
+        live = weight(np.maximum(sad - k, 0), mul_hi) >= params.epf_weight_min
+        return (((bhi >= 16) & (blo != bhi) & live)
+                | ((blo >= 16) & (blo == bhi) & (k > 0) & live))
+
+    out = np.zeros((y1 - y0, x1 - x0), dtype=bool)
+    for m in _map_offsets(one):
+        if m is not None:
+            out |= m
+    return out
+
+
+EPF_OFFSETS = [(cx, cy) for cy in range(-3, 4) for cx in range(-3, 5)]
+_EPF_PAD = 8        # reach of a patch at the farthest offset: x - 4 .. x + 6, y +- 4
+
+
+def _patch_sad(gp, P, region, cx, cy):
+    """J.2.3 distance for one offset (cx, cy) at every pixel of ``region``:
+    the sum over the 3 channels and the 3x4 patch (rows -1..1, columns
+    -1..2 around the origin) of |g(p + d) - g(p + (cx, cy) + d)|."""
+    x0, y0, x1, y1 = region
+    acc = np.zeros((y1 - y0, x1 - x0), dtype=np.int32)
+    for c in range(3):
+        for iy in (-1, 0, 1):
+            for ix in (-1, 0, 1, 2):
+                acc += np.abs(shifted(gp[c], P, region, ix, iy)
+                              - shifted(gp[c], P, region, cx + ix, cy + iy))
+    return acc
+
+
+THREADS = None      # worker threads of the J.2 offset loop; None: every host core
+
+
+def _map_offsets(fn):
+    """fn(i, (cx, cy)) for the 56 offsets, evaluated on a thread pool of
+    THREADS workers (the work is numpy array arithmetic); results in offset
+    order."""
+    import concurrent.futures as cf
+    import os
+    n = THREADS or os.cpu_count() or 1
+    if n == 1:
+        return [fn(i, off) for i, off in enumerate(EPF_OFFSETS)]
+    with cf.ThreadPoolExecutor(max_workers=n) as ex:
+        return list(ex.map(lambda a: fn(*a), enumerate(EPF_OFFSETS)))
+
+
+def epf(img, vmap, acmul, sharpness, params, region=None, decide=None):
+    """J.2 on the cropped image img (3, ysize, xsize), FP64.  ``region``
+    (x0, y0, x1, y1) restricts the output to a window (sampled checks of
+    large images); the result covers that window only.  ``decide`` (an image
+    of the same shape, for tests) supplies the guide and the sigmas instead
+    of ``img``; the weighted samples are always those of ``img``."""
+    _, ys, xs = img.shape
+    if region is None:
+        region = (0, 0, xs, ys)
+    x0, y0, x1, y1 = region
+    d = img if decide is None else decide
+    g = guide(d, params).astype(np.int32)
+    sigma_blk = epf_sigma(d, vmap, acmul, sharpness, params)
+    mt4 = mul_table4()
+    px = np.arange(x0, x1)[None, :]
+    py = np.arange(y0, y1)[:, None]
+    P = _EPF_PAD
+    gp, ip = mirror_pad(g, P), mirror_pad(np.asarray(img, np.float64), P)
     sigma = sigma_blk[py // 8, px // 8]
     mul4 = mt4[np.maximum(sigma, 16)]
-    w = weight(sad, mul4[None])
-    w = np.where(w < params.epf_weight_min, 0.0, w)
+
+    def one(i, off):
+        # J.2.4 weight of this offset, zero below the cut-off; J.2.5 terms
+        cx, cy = off
+        w = weight(_patch_sad(gp, P, region, cx, cy), mul4)
+        w = np.where(w < params.epf_weight_min, 0.0, w)
+        return w, shifted(ip, P, region, cx, cy) * w[None]
+
+    parts = _map_offsets(one)
+    den = np.zeros((y1 - y0, x1 - x0))
     num = np.zeros((3, y1 - y0, x1 - x0))
-    den = w.sum(axis=0)
-    for i, (cx, cy) in enumerate(EPF_OFFSETS):
-        num += at(img, cx, cy) * w[i][None]
+    for w, t in parts:                 # J.2.5 sums in offset order
+        den += w
+        num += t
     out = num / den[None]
     # READING: mul_table is undefined below sigma 16; such pixels pass through
     keep = sigma < 16

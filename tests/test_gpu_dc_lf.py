@@ -1,9 +1,12 @@
 """Parity of F.2 adaptive DC smoothing and Annex H AC prediction (through the
 C ABI) with the FP64 oracle.
 
-* F.2 decisions are bit-exact: both sides take them in binary32 on the same
-  binary32 DC samples, so with DC-only DCT8 input the XYB samples equal the
-  oracle's smoothed DC exactly.
+* F.2: the oracle decides in real arithmetic, the kernel in binary32.  A
+  sample whose weighted average lies within the binary32 evaluation bound
+  (F2_REL of the window's largest |sample|) of a window edge may go either
+  way; such samples are counted (at most 1e-3 of them) and excluded.  With
+  DC-only DCT8 input every other XYB sample equals the oracle's smoothed DC
+  within binary32 rounding, so every decision outside that bound agrees.
 * Annex H smooths real-valued DC2x2 samples that the two sides compute in
   different precisions; a sample whose weighted average lies within
   LF_AMBIG of a window edge may go either way, so the varblock holding it is
@@ -48,18 +51,33 @@ def _ambiguous_varblocks(img, diag):
     return mask
 
 
-def test_dc_smoothing_decisions_bit_exact(B, ctx):
-    """DC-only DCT8 input: every XYB sample of a block is its DC after F.2,
-    identical to the oracle's binary32 result; both outcomes occur."""
+F2_REL = 2.0 ** -19   # binary32 DC rounding, 9-term average and window ends
+
+
+def test_dc_smoothing_decisions(B, ctx):
+    """DC-only DCT8 input: every XYB sample of a block is its DC after F.2;
+    the kernel's binary32 decisions agree with the real-number ones
+    wherever the margin exceeds the binary32 bound; both outcomes occur."""
+    from scipy.ndimage import maximum_filter
     img = synth.make_image(200, 136, 21, mix='dct8', dc='smooth', ac=False, cfl=False)
     p, lp = _params(B, True, False)
     raw = R.dc_image(img['coeffs'], img['vmap'], p)
     want = R.dc_smooth(raw, p)
     assert 0.2 < np.mean(want != raw) < 0.8
+    mag = maximum_filter(np.abs(raw), size=(1, 3, 3), mode='nearest')
+    near = R.dc_smooth_margin(raw, p) < F2_REL * (mag + np.asarray(p.m_dc)[:, None, None])
+    assert near.mean() <= 1e-3, near.mean()
     got = run(B, ctx, img, lp, XYB).transpose(2, 0, 1)
-    bh, bw = img['vmap'].shape
-    blocks = np.repeat(np.repeat(want, 8, 1), 8, 2)[:, :img['ysize'], :img['xsize']]
-    np.testing.assert_array_equal(got, blocks)
+    ys, xs = img['ysize'], img['xsize']
+
+    def px(a):
+        return np.repeat(np.repeat(a, 8, 1), 8, 2)[:, :ys, :xs]
+
+    err = np.abs(got - px(want))
+    tol = 2.0 ** -20 * px(mag)
+    bad = (err > tol) & ~px(near)
+    assert not bad.any(), f"{bad.sum()} samples, worst {np.where(bad, err, 0).max():.3g}"
+    print(f"F.2 near-ties excluded: {int(near.sum())} of {near.size} DC samples")
 
 
 @pytest.mark.parametrize("xs,ys,seed", [(72, 56, 1), (33, 17, 2), (200, 136, 3), (300, 264, 4)])

@@ -12,8 +12,9 @@ import pytest
 
 from oracle import recon as R
 from paper_1908_03565_gb300 import synth
-from test_gpu_parity import (B, XYB, F32, U8, assert_xyb_close, params_pair, run,  # noqa: F401
-                             _filters_on_gpu_xyb, _oracle_filters)
+from test_gpu_parity import (B, XYB, F32, U8, params_pair, run,  # noqa: F401
+                             _filters_on_gpu_xyb, assert_filter_stage, guide_slack, SIGMA_REL,
+                             quant_binary32)
 
 pytestmark = pytest.mark.gpu
 
@@ -96,16 +97,21 @@ def _count_and_sigma(B, ctx, img, lp):
 @pytest.mark.parametrize("xs,ys,stats", [(300, 264, 'active'), (520, 264, 'workload'),
                                          (33, 17, 'active')])
 def test_block_count(B, tctx, xs, ys, stats):
-    """The filtered blocks are those with sigma >= 16: the oracle's binary32
-    sigma of the GPU's own XYB samples gives the same count."""
+    """The filtered blocks are those with sigma >= 16: on the GPU's own XYB
+    samples the count lies between those of the smallest and the largest
+    real-number sigmas that the binary32 rounding of J.2.2 and J.2.4 allows
+    (equal unless a block's sigma sits within that rounding of 16)."""
     kw = ACTIVE if stats == 'active' else {}
     img = synth.make_image(xs, ys, 7 * xs + ys, **kw)
     p, lp = params_pair(B, epf=True, gab=True)
     xyb = run(B, tctx, img, params_pair(B)[1], XYB).transpose(2, 0, 1).astype(np.float64)
-    sig = R.epf_sigma(xyb, img['vmap'], img['acmul'], img['sharpness'], p)
+    _, _, s_lo, s_hi = R.epf_decision_bounds(xyb, img['vmap'], img['acmul'], img['sharpness'],
+                                             p, guide_slack(xyb, xyb, p), SIGMA_REL,
+                                             quant_binary32(img, p))
     ms, n = _count_and_sigma(B, tctx, img, lp)
-    assert n == int(np.sum(sig >= 16))
-    assert 0 < n < sig.size
+    assert int(np.sum(s_lo >= 16)) <= n <= int(np.sum(s_hi >= 16))
+    assert int(np.sum(s_hi >= 16)) - int(np.sum(s_lo >= 16)) <= max(1, s_lo.size // 1000)
+    assert 0 < n < s_lo.size
     assert ms > 0
 
 
@@ -143,5 +149,4 @@ def test_exact_clamp_variant(B, tctx):
     xyb, got = _filters_on_gpu_xyb(B, tctx, img, lp1, True, False, XYB)
     sig = R.epf_sigma(xyb.astype(np.float64), img['vmap'], img['acmul'], img['sharpness'], p)
     assert (sig >= 202).any()          # the clamp variant's sigma range is reached
-    want = _oracle_filters(img, xyb, p)
-    assert_xyb_close(got.transpose(2, 0, 1), want, abs_tol=5e-6, radius=8)
+    assert_filter_stage(img, xyb, got, p, False, "exact-clamp variant")

@@ -9,11 +9,16 @@ Tolerances (written here; derived from binary32 arithmetic):
     sums of products err in proportion to the magnitude of their terms; the
     draft's default 32x8 / 8x32 matrices make some samples reach ~1e4, so an
     absolute bound alone does not describe FP32 arithmetic there.
-The EPF decides integers (guide bytes, sigma) from real numbers; the oracle
-takes those decisions in binary32 like the kernels, so the filter stage is
-compared on identical input samples (the GPU's own XYB).  From-scratch
-comparisons exclude, and count, only pixels whose EPF window saw a guide
-byte or sigma that differs between the two XYB images.
+The EPF decides integers (guide bytes, block sigmas) from real numbers.  The
+oracle takes them in real (FP64) arithmetic; the kernels take them in
+binary32 from their own XYB.  A comparison therefore excludes, and counts,
+the pixels whose output the decisions do not fix once the input is known
+only within the bound of the two sides' difference: the guide samples
+within |XYB difference| x epf_scale + the binary32 rounding of J.2.2 of a
+byte boundary, the block sigmas within the rounding of J.2.4 of an integer,
+and only where such a decision can change a weight above the cut-off
+(oracle.recon.epf_undetermined), spread by one sample where Gaborish
+follows.  Every other pixel is held to the bounds above.
 """
 import numpy as np
 import pytest
@@ -189,16 +194,31 @@ def _oracle_filters(img, xyb, p, region=None):
     return x
 
 
+def assert_filter_stage(img, xyb, got, p, gab, name):
+    """The library's filter stage on its own binary32 XYB ``xyb`` against
+    the oracle's J.2 (real decisions) + J.4 on the same samples: only the
+    pixels whose decisions lie within the binary32 rounding of a threshold
+    (and that matter) are excluded; they are counted and must be rare."""
+    want = _oracle_filters(img, xyb, p)
+    amb = (undetermined(img, xyb.astype(np.float64), xyb, p, gab) if p.epf
+           else np.zeros(xyb.shape[1:], bool))
+    assert amb.mean() <= AMBIG_MAX, (name, amb.mean())
+    g = np.where(amb[None], want, got.transpose(2, 0, 1))
+    assert_xyb_close(g, want, abs_tol=5e-6, radius=8)
+    print(f"{name}: undetermined {amb.sum()} of {amb.size} pixels")
+    return amb
+
+
 @pytest.mark.parametrize("epf,gab", [(True, False), (False, True), (True, True)])
 @pytest.mark.parametrize("xs,ys", [(64, 64), (131, 77), (9, 13)])
 def test_filter_stage_on_identical_samples(B, ctx, epf, gab, xs, ys):
-    """J.2 + J.4 + L.2 on the same binary32 XYB on both sides: every integer
-    decision agrees, so the result is within float rounding."""
+    """J.2 + J.4 + L.2 on the same binary32 XYB on both sides: every decision
+    the rounding of binary32 cannot move agrees with the real-number one,
+    and the result is then within float rounding."""
     img = synth.make_image(xs, ys, 31 * xs + ys, y_dc_offset_q=200)
     p, lp = params_pair(B, epf=epf, gab=gab)
     xyb, got = _filters_on_gpu_xyb(B, ctx, img, lp, epf, gab, XYB)
-    want = _oracle_filters(img, xyb, p)
-    assert_xyb_close(got.transpose(2, 0, 1), want, abs_tol=5e-6, radius=8)
+    assert_filter_stage(img, xyb, got, p, gab, f"{xs}x{ys}")
 
 
 @pytest.mark.parametrize("epf,gab", [(True, False), (True, True)])
@@ -210,10 +230,9 @@ def test_filter_stage_where_the_epf_acts(B, ctx, epf, gab, xs, ys, mix):
     img = synth.make_image(xs, ys, 13 * xs + ys, mix=mix, coef_scale=2.0, acmul=0.5, dc='smooth')
     p, lp = params_pair(B, epf=epf, gab=gab)
     xyb, got = _filters_on_gpu_xyb(B, ctx, img, lp, epf, gab, XYB)
-    want = _oracle_filters(img, xyb, p)
     assert np.mean(np.abs(R.epf(xyb.astype(np.float64), img['vmap'], img['acmul'],
                                 img["sharpness"], p) - xyb) > 1e-7) > 0.03
-    assert_xyb_close(got.transpose(2, 0, 1), want, abs_tol=5e-6, radius=8)
+    assert_filter_stage(img, xyb, got, p, gab, f"{xs}x{ys} {mix}")
 
 
 def test_full_path_equals_staged_path(B, ctx):
@@ -225,21 +244,53 @@ def test_full_path_equals_staged_path(B, ctx):
     np.testing.assert_array_equal(full, staged)
 
 
-def _ambiguous_mask(img, xyb_a, xyb_b, p):
-    """Pixels whose EPF+Gaborish window (x -5..+6, y -5..+5) contains a guide
-    byte or a block sigma that differs between two XYB images."""
-    ga, gb = R.guide(xyb_a, p), R.guide(xyb_b, p)
-    diff = np.any(ga != gb, axis=0)
-    sa = R.epf_sigma(xyb_a, img['vmap'], img['acmul'], img['sharpness'], p)
-    sb = R.epf_sigma(xyb_b, img['vmap'], img['acmul'], img['sharpness'], p)
-    sd = np.repeat(np.repeat(sa != sb, 8, 0), 8, 1)[:diff.shape[0], :diff.shape[1]]
-    bad = diff | sd
-    out = np.zeros_like(bad)
-    ys, xs = bad.shape
-    for dy in range(-5, 6):
-        for dx in range(-5, 7):
-            out |= bad[R.mirror(np.arange(ys)[:, None] - dy, ys), R.mirror(np.arange(xs)[None, :] - dx, xs)]
+SIGMA_REL = 2.0 ** -21     # binary32 steps of the J.2.4 range term, relative
+AMBIG_MAX = 1e-3           # largest share of pixels a comparison may exclude
+# Largest share of RGB samples, at the workload's coefficient statistics, held
+# to the relaxed bound: there the draft's default 32x8 / 8x32 matrices give XYB
+# samples of 1e2..1e4, where binary32 cannot carry 1e-4 through L.2's cube
+# (1.5-2.5% by the oracle's own count; at realistic magnitudes <= 1%)
+WORKLOAD_RELAXED = 0.03
+
+
+def guide_slack(x_gpu, x_ref, p):
+    """Per-sample bound, in guide units, on the difference between the
+    kernel's binary32 scaled guide value of its samples x_gpu and the real
+    scaled value of the oracle's samples x_ref: the sample difference times
+    epf_scale, plus the rounding of fl(fl(v - min32) * scale32) with min32
+    and scale32 the binary32 parameters, which is at most
+    2^-24 (3 |scaled| + |min| scale) (one rounding each of the difference,
+    the product and the scale, and that of min carried through the scale)."""
+    im3 = (p.target_nits_div50 * 50.0 / 250.0) ** (1.0 / 3.0)
+    s = R.guide_scaled(x_ref, p)
+    out = np.empty_like(s)
+    for c in range(3):
+        mn = (0.03 if c == 0 else 0.0) * im3
+        out[c] = (np.abs(np.asarray(x_gpu[c], np.float64) - x_ref[c]) * p.epf_scale[c]
+                  + 2.0 ** -24 * (3.0 * np.abs(s[c]) + mn * p.epf_scale[c]) + 1e-12)
     return out
+
+
+def quant_binary32(img, p):
+    """The kernels' quant term of J.2.4 per block: the correctly rounded
+    binary32 reciprocal of AcMul times quant_mul, rounded (numpy's float32
+    division and product round correctly, as the kernels' do)."""
+    one = np.float32(1.0)
+    return (one / img['acmul'].astype(np.float32) * np.float32(p.epf_quant_mul)).astype(np.float64)
+
+
+def undetermined(img, x_ref, x_gpu, p, gab, region=None):
+    """Pixels (over ``region``) whose J.2 output the decisions do not fix
+    for inputs within the bound of x_gpu - x_ref, grown by the Gaborish
+    reach when ``gab``."""
+    from scipy.ndimage import binary_dilation
+    x_ref = np.asarray(x_ref, np.float64)
+    u = R.epf_undetermined(x_ref, img['vmap'], img['acmul'], img['sharpness'], p,
+                           guide_slack(x_gpu, x_ref, p), SIGMA_REL, region=region,
+                           quant_alt=quant_binary32(img, p))
+    if gab:
+        u = binary_dilation(u, structure=np.ones((3, 3), bool))
+    return u
 
 
 def local_mag(*views, radius=8):
@@ -249,15 +300,14 @@ def local_mag(*views, radius=8):
     return maximum_filter(mag, size=(1, 2 * radius + 1, 2 * radius + 1), mode='nearest')
 
 
-def rgb_tolerance(x, m, p):
-    """Per-pixel bound for linear RGB in [0, 1] at XYB samples x (3, h, w):
-    TOL01 plus the XYB bound XYB_TOL + LOCAL_REL * m (m from local_mag)
-    carried through L.2 by its Jacobian (central differences).  Where the
-    XYB samples are O(1) the added term is below 1e-5; it grows only where
-    the synthetic coefficients meet large default matrix entries and samples
-    reach 1e2..1e4, as binary32 arithmetic does."""
-    dx = XYB_TOL + LOCAL_REL * m
-    tol = np.full(x.shape[1:] + (3,), TOL01)
+ERR_REL = 1e-6   # XYB error of the FP32 path relative to the local magnitude: 4x the
+                 # largest measured (2.4e-7); a binary32 sum of products errs in
+                 # proportion to the magnitude of its terms
+
+
+def _through_l2(x, dx, p):
+    """|d linear RGB01 / d XYB| . dx per output sample (central differences)."""
+    tol = np.zeros(x.shape[1:] + (3,))
     for c in range(3):
         d = np.zeros_like(x)
         d[c] = 1e-6 * np.maximum(1.0, np.abs(x[c]))
@@ -266,79 +316,144 @@ def rgb_tolerance(x, m, p):
     return tol
 
 
+def rgb_tolerance(x, m, p):
+    """Per-sample bound for linear RGB in [0, 1] at XYB samples x (3, h, w):
+    TOL01 plus the XYB bound XYB_TOL + LOCAL_REL * m (m from local_mag)
+    carried through L.2 by its Jacobian.  Where the XYB samples are O(1)
+    the added term is small; it grows where the synthetic coefficients meet
+    large default matrix entries and samples reach 1e2..1e4."""
+    return TOL01 + _through_l2(x, XYB_TOL + LOCAL_REL * m, p)
+
+
+def rgb_attainable(x, m, p):
+    """The RGB error that binary32 reconstruction can be held to at XYB
+    samples x: ERR_REL * m (+ 1e-7) carried through L.2.  Where it is within
+    TOL01 the flat 1e-4 bound applies."""
+    return _through_l2(x, ERR_REL * m + 1e-7, p)
+
+
+def assert_from_scratch(img, ref, gpu_xyb, f32, u8, p, name, region=None, relaxed_max=0.01):
+    """The library's output against the oracle's, both from the coefficients.
+
+    ``ref``: oracle.recon.reconstruct of ``img``; ``gpu_xyb``: the library's
+    XYB before the filters (3, h, w); ``f32`` / ``u8``: its outputs over
+    ``region`` (x0, y0, x1, y1; the whole image when None).  Bounds: the XYB
+    bound before the filters everywhere; on every pixel the decisions fix
+    (see the module docstring) u8 within +-1, and linear RGB within 1e-4
+    wherever binary32 can attain it (rgb_attainable <= 1e-4), else within
+    1e-4 plus the XYB bound carried through L.2 (rgb_tolerance).  The RGB
+    samples of the second kind whose oracle value is not clamped away from
+    [0, 1] by more than that bound are counted and must be at most
+    ``relaxed_max`` of them; undetermined pixels at most AMBIG_MAX."""
+    ys, xs = img['ysize'], img['xsize']
+    if region is None:
+        region = (0, 0, xs, ys)
+    x0, y0, x1, y1 = region
+    ref_xyb = ref['xyb_padded'][:, :ys, :xs]
+    assert_xyb_close(gpu_xyb, ref_xyb)
+    amb = (undetermined(img, ref_xyb, gpu_xyb, p, p.gab, region) if p.epf
+           else np.zeros((y1 - y0, x1 - x0), bool))
+    ok = np.broadcast_to(~amb[..., None], (y1 - y0, x1 - x0, 3))
+    rx = ref['xyb'][:, y0:y1, x0:x1]
+    mag = local_mag(ref['xyb'], ref_xyb)[:, y0:y1, x0:x1]
+    tol = rgb_tolerance(rx, mag, p)
+    plain = ok & (rgb_attainable(rx, mag, p) <= TOL01)
+    relaxed = ok & ~plain
+    want01 = ref['rgb01'][y0:y1, x0:x1]
+    err = np.abs(np.clip(f32, 0, 1) - np.clip(want01, 0, 1))
+    bound = np.where(plain, TOL01, tol)
+    bad = (err > bound) & ok
+    if bad.any():
+        i = np.unravel_index(np.where(bad, err - bound, -1).argmax(), err.shape)
+        raise AssertionError(f"{name}: {bad.sum()} RGB samples out of bound ({(bad & plain).sum()} "
+                             f"plain); worst at {i}: err {err[i]:.3g} bound {bound[i]:.3g}")
+    live = relaxed & (want01 >= -tol) & (want01 <= 1 + tol)
+    d = np.abs(u8.astype(np.int64) - R.srgb_u8(want01).astype(np.int64))
+    print(f"{name}: undetermined {amb.mean():.2e} of pixels; RGB samples held to 1e-4: "
+          f"{plain.mean():.4f} (max err {err[plain].max():.2e}); to the relaxed bound and "
+          f"not clamped away: {live.mean():.4f} (max err "
+          f"{err[live].max() if live.any() else 0:.2e}); u8 max diff {d[ok].max()} "
+          f"(over all pixels {d.max()})")
+    assert d[ok].max() <= 1, name
+    assert live.mean() <= relaxed_max, (name, live.mean())
+    assert amb.mean() <= AMBIG_MAX, (name, amb.mean())
+    return amb
+
+
 def test_mixed_statistics_from_scratch(B, ctx):
     """Mixed tiling, quant field, CfL, EPF + Gaborish, f32 and u8 outputs,
     against the oracle run from the coefficients."""
     img = synth.make_image(320, 200, 1001, y_dc_offset_q=200)
     p, lp = params_pair(B, epf=True, gab=True)
     ref = R.reconstruct(img, p)
-    ref_xyb = ref['xyb_padded'][:, :200, :320]
     gpu_xyb = run(B, ctx, img, params_pair(B)[1], XYB).transpose(2, 0, 1)
-    assert_xyb_close(gpu_xyb, ref_xyb)
-    amb = _ambiguous_mask(img, ref_xyb, gpu_xyb.astype(np.float64), p)
-    tol = rgb_tolerance(ref['xyb'], local_mag(ref['xyb'], ref_xyb), p)
-    got = run(B, ctx, img, lp, F32)
-    err = np.abs(np.clip(got, 0, 1) - np.clip(ref['rgb01'], 0, 1))
-    ok = ~amb
-    assert np.all((err <= tol)[ok])
-    plain = ok[..., None] & (tol <= 1.1 * TOL01)
-    assert err[plain].max() <= TOL01
-    assert amb.mean() < 0.25, amb.mean()
-    u8 = run(B, ctx, img, lp, U8).astype(np.int64)
-    d = np.abs(u8 - R.srgb_u8(ref['rgb01']).astype(np.int64))
-    assert d[plain].max() <= 1
-    # the filtered XYB itself, everywhere that no decision differs
+    amb = assert_from_scratch(img, ref, gpu_xyb, run(B, ctx, img, lp, F32),
+                              run(B, ctx, img, lp, U8), p, "320x200", relaxed_max=WORKLOAD_RELAXED)
+    # the filtered XYB itself, everywhere the decisions fix
     gx = run(B, ctx, img, lp, XYB).transpose(2, 0, 1)
-    ok = ~amb
-    from scipy.ndimage import maximum_filter
-    m = maximum_filter(np.abs(ref['xyb']), size=(1, 17, 17), mode='nearest')
-    e = np.abs(gx - ref['xyb'])
-    assert np.all((e <= XYB_TOL + LOCAL_REL * m)[:, ok])
-    print(f"ambiguous {amb.mean():.4f}, pixels at the plain 1e-4 bound "
-          f"{plain.mean():.4f}, max err there {err[plain].max():.2e}")
+    assert_xyb_close(np.where(amb[None], ref['xyb'], gx), ref['xyb'])
 
 
-def test_mixed_1920x1088_sampled(B, ctx):
-    """1920x1088 at the mixed statistics with both filters: the linear part
-    everywhere; the filters on windows (corners, edges, interior) computed
-    by the oracle from the GPU's XYB."""
-    xs, ys = 1920, 1088
-    img = synth.make_image(xs, ys, 1000)
+@pytest.mark.parametrize("stats", ['workload', 'active'])
+def test_1920x1088_from_scratch(B, ctx, stats):
+    """1920x1088 at the mixed statistics with both filters, whole image, f32
+    and u8, against the oracle from the coefficients (and at statistics
+    under which the EPF acts on most blocks)."""
+    kw = {} if stats == 'workload' else dict(coef_scale=2.0, acmul=0.5, dc='smooth')
+    img = synth.make_image(1920, 1088, 1000, **kw)
     p, lp = params_pair(B, epf=True, gab=True)
+    ref = R.reconstruct(img, p)
     gpu_xyb = run(B, ctx, img, params_pair(B)[1], XYB).transpose(2, 0, 1)
-    want = R.reconstruct_xyb(img['coeffs'], img['vmap'], img['acmul'], img['cfl'], p)
-    assert_xyb_close(gpu_xyb, want[:, :ys, :xs])
-    got = run(B, ctx, img, lp, F32)
-    x64 = gpu_xyb.astype(np.float64)
-    mag = local_mag(x64)
-    for (x0, y0) in [(0, 0), (xs - 40, 0), (0, ys - 40), (xs - 40, ys - 40), (960, 544)]:
-        region = (x0, y0, x0 + 40, y0 + 40)
-        e = R.epf(x64, img['vmap'], img['acmul'], img['sharpness'], p,
-                  region=(max(0, x0 - 1), max(0, y0 - 1), min(xs, x0 + 41), min(ys, y0 + 41)))
-        xf = _gab_window(x64, e, region, p, img)
-        ref = R.xyb_to_linear01(xf, p)
-        tol = rgb_tolerance(xf, mag[:, y0:y0 + 40, x0:x0 + 40], p)
-        err = np.abs(np.clip(got[y0:y0 + 40, x0:x0 + 40], 0, 1) - np.clip(ref, 0, 1))
-        assert np.all(err <= tol), (x0, y0, float((err - tol).max()))
+    assert_from_scratch(img, ref, gpu_xyb, run(B, ctx, img, lp, F32),
+                        run(B, ctx, img, lp, U8), p, f"1920x1088 {stats}",
+                        relaxed_max=WORKLOAD_RELAXED if stats == 'workload' else 0.01)
 
 
-def _gab_window(x64, e, region, p, img):
-    """Gaborish of the EPF output on `region`, given the EPF output `e` on the
-    region grown by one sample (clipped to the image)."""
-    xs, ys = x64.shape[2], x64.shape[1]
-    x0, y0, x1, y1 = region
-    ex0, ey0 = max(0, x0 - 1), max(0, y0 - 1)
-    out = np.zeros((3, y1 - y0, x1 - x0))
-    for c in range(3):
-        w1, w2 = p.gab_w1[c], p.gab_w2[c]
-        n = 1 + 4 * w1 + 4 * w2
-        for dy in (-1, 0, 1):
-            for dx in (-1, 0, 1):
-                wt = (1.0, w1, w2)[abs(dx) + abs(dy)] / n
-                yy = R.mirror(np.arange(y0, y1)[:, None] + dy, ys) - ey0
-                xx = R.mirror(np.arange(x0, x1)[None, :] + dx, xs) - ex0
-                out[c] += wt * e[c][yy, xx]
-    return out
+def crop_input(img, x0, y0, x1, y1):
+    """The inputs of the 64-aligned rectangle [x0, x1) x [y0, y1) as an image
+    of its own (every varblock and CfL tile lies wholly inside it); its
+    size reaches the source image's edge where the rectangle does."""
+    assert x0 % 64 == 0 and y0 % 64 == 0
+    Wp, Hp = img['coeffs'].shape[2], img['coeffs'].shape[1]
+    x1, y1 = min(x1, Wp), min(y1, Hp)
+    return {'xsize': min(x1, img['xsize']) - x0, 'ysize': min(y1, img['ysize']) - y0,
+            'coeffs': img['coeffs'][:, y0:y1, x0:x1].copy(),
+            'vmap': img['vmap'][y0 // 8:y1 // 8, x0 // 8:x1 // 8].copy(),
+            'acmul': img['acmul'][y0 // 8:y1 // 8, x0 // 8:x1 // 8].copy(),
+            'sharpness': img['sharpness'][y0 // 8:y1 // 8, x0 // 8:x1 // 8].copy(),
+            'cfl': img['cfl'][y0 // 64:(y1 + 63) // 64, x0 // 64:(x1 + 63) // 64].copy()}
+
+
+def test_4096_windows_from_scratch(B, ctx):
+    """The 4096x4096 image of the throughput measurement (seed 2000, mixed
+    statistics, EPF + Gaborish), one full-size run; the oracle from the
+    coefficients on 64x64 windows (corners, edges, interior, random) of it,
+    each from a 64-aligned crop with a margin of at least 64 samples (the
+    filters reach 7 samples plus the window's varblocks) or the image edge."""
+    import torch
+    xs = ys = 4096
+    img = synth.make_image(xs, ys, 2000)
+    p, lp = params_pair(B, epf=True, gab=True)
+    dimg = B.to_device(img, torch)
+    outs = {}
+    for dt, tdt in ((XYB, torch.float32), (F32, torch.float32), (U8, torch.uint8)):
+        o = torch.empty((ys, xs, 3), dtype=tdt, device="cuda")
+        ctx.poll(ctx.submit(dimg, params_pair(B)[1] if dt == XYB else lp, o, dt, on_device=True))
+        outs[dt] = o.cpu().numpy()
+    del dimg
+    rng = np.random.default_rng(4096)
+    wins = [(0, 0), (xs - 64, 0), (0, ys - 64), (xs - 64, ys - 64), (2048, 0), (0, 1344),
+            (1984, 2048)] + [(int(64 * rng.integers(1, 62)), int(64 * rng.integers(1, 62)))
+                             for _ in range(3)]
+    for wx, wy in wins:
+        cx0, cy0 = max(0, wx - 64), max(0, wy - 64)
+        sub = crop_input(img, cx0, cy0, wx + 128, wy + 128)
+        ref = R.reconstruct(sub, p)
+        region = (wx - cx0, wy - cy0, wx - cx0 + 64, wy - cy0 + 64)
+        gx = outs[XYB][cy0:cy0 + sub['ysize'], cx0:cx0 + sub['xsize']].transpose(2, 0, 1)
+        assert_from_scratch(sub, ref, gx, outs[F32][wy:wy + 64, wx:wx + 64],
+                            outs[U8][wy:wy + 64, wx:wx + 64], p, f"4096^2 window ({wx}, {wy})",
+                            region=region, relaxed_max=WORKLOAD_RELAXED)
 
 
 # ---------------------------------------------------------------------------

@@ -516,6 +516,93 @@ def test_epf_sigma_rule():
 # --------------------------------------------------------------------------
 # L.2 colour and the output encodings
 # --------------------------------------------------------------------------
+def test_decision_bounds_without_slack_are_the_decisions():
+    """With no slack the smallest and largest reachable guide bytes and
+    sigmas are the ones J.2.2 and J.2.4 give."""
+    img = synth.make_image(72, 48, 61, coef_scale=2.0, acmul=0.5, dc='smooth')
+    p = R.Params(epf=True)
+    x = R.reconstruct_xyb(img['coeffs'], img['vmap'], img['acmul'], img['cfl'], p)[:, :48, :72]
+    g_lo, g_hi, s_lo, s_hi = R.epf_decision_bounds(x, img['vmap'], img['acmul'],
+                                                   img['sharpness'], p, 0.0)
+    g = R.guide(x, p)
+    s = R.epf_sigma(x, img['vmap'], img['acmul'], img['sharpness'], p)
+    assert np.array_equal(g_lo, g) and np.array_equal(g_hi, g)
+    assert np.array_equal(s_lo, s) and np.array_equal(s_hi, s)
+    assert not R.epf_undetermined(x, img['vmap'], img['acmul'], img['sharpness'], p, 0.0).any()
+
+
+def test_undetermined_pixels_are_the_only_ones_a_perturbation_changes():
+    """Decisions taken from inputs whose scaled guide samples move by up to
+    +-slack (each sample and channel at random, clamped to the slack) leave
+    every pixel that epf_undetermined does not report bit for bit unchanged;
+    the reported pixels do change under some of the perturbations."""
+    img = synth.make_image(64, 48, 62, coef_scale=2.0, acmul=0.5, dc='smooth')
+    p = R.Params(epf=True)
+    x = R.reconstruct_xyb(img['coeffs'], img['vmap'], img['acmul'], img['cfl'], p)[:, :48, :64]
+    args = (img['vmap'], img['acmul'], img['sharpness'], p)
+    slack = 0.05
+    und = R.epf_undetermined(x, *args, slack)
+    assert 0.01 < und.mean() < 0.9
+    base = R.epf(x, *args)
+    rng = np.random.default_rng(5)
+    changed = np.zeros_like(und)
+    scale = np.asarray(p.epf_scale)[:, None, None]
+    for _ in range(6):
+        d = x + rng.uniform(-slack, slack, size=x.shape) / scale
+        got = R.epf(x, *args, decide=d)
+        diff = np.any(got != base, axis=0)
+        assert not (diff & ~und).any()
+        changed |= diff
+    assert changed.any()
+    # the sigma bounds: here the quant term is the real 20 / 0.5 = 40 on
+    # every block, so blocks whose sigma it sets are fixed without an
+    # alternative evaluation and ties with one just below 40; a relative
+    # slack on the range term leaves a block whose range term lies well
+    # inside an integer interval fixed
+    a, q = R.sigma_terms(R.block_ranges(R.guide_scaled(x, p), img['vmap']), img['acmul'],
+                         img['sharpness'], p)
+    by_q = q < a
+    assert by_q.any() and (~by_q).any()
+    _, _, lo, hi = R.epf_decision_bounds(x, *args, 0.0, 1e-9)
+    frac = a - np.floor(a)
+    assert not (lo != hi)[by_q].any()
+    assert not (lo != hi)[~by_q & (frac > 0.01) & (frac < 0.99)].any()
+    _, _, lo, hi = R.epf_decision_bounds(x, *args, 0.0, 0.0, quant_alt=q - 1e-9)
+    assert np.all((lo != hi)[by_q & (q < p.epf_sigma_max)])
+    assert not (lo != hi)[~by_q & (a < q - 1e-6)].any()
+
+
+def test_dc_smooth_margin():
+    """The margin is the distance of wa to the nearer window end: zero for a
+    sample whose neighbourhood puts wa exactly on an end, and a perturbation
+    of every sample smaller than margin / 3 (the weights sum to 1, and the
+    centre also moves the window) keeps every decision."""
+    p = R.Params(dc_smooth=True)
+    w0, w1, w2 = R.DC_SMOOTH_W
+    half = 0.5 * p.m_dc[1]
+    # centre 0, every neighbour t: wa = (1 - w0) t, on the upper end when
+    # (1 - w0) t = half
+    t = half / (1.0 - w0)
+    dc = np.zeros((3, 3, 3))
+    dc[1] = t
+    dc[1, 1, 1] = 0.0
+    assert R.dc_smooth_margin(dc, p)[1, 1, 1] == pytest.approx(0.0, abs=1e-18)
+    im = synth.make_image(160, 120, 63, mix='dct8', dc='smooth')
+    raw = R.dc_image(im['coeffs'], im['vmap'], p)
+    m = R.dc_smooth_margin(raw, p)
+    def decisions(d):
+        wa, s_, hf = R._dc_window(d, p)
+        return (s_ - hf <= wa) & (wa <= s_ + hf)
+
+    rng = np.random.default_rng(3)
+    eps = 1e-3 * np.asarray(p.m_dc)[:, None, None]
+    pert = raw + rng.uniform(-1, 1, raw.shape) * eps
+    moved = decisions(pert) != decisions(raw)
+    assert not (moved & (m[:, 1:-1, 1:-1] > 3 * eps)).any()
+    assert 0.2 < decisions(raw).mean() < 0.8
+    assert np.isinf(m[:, 0, :]).all() and np.isinf(m[:, :, -1]).all()
+
+
 def test_xyb_round_trip_through_opsin_inverse():
     """L.2 applies the inverse opsin matrix; inverting that matrix and the
     cube by hand from linear RGB and going back must return the RGB."""
