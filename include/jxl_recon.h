@@ -370,8 +370,9 @@ const char* jxl_recon_last_error(const jxl_recon_ctx* ctx);
  * path.)  Some callers may not call cudaMalloc: a framework or service that
  * must account for every device byte through its own allocator, or code
  * for which an allocation's implicit device synchronisation is not
- * allowed.  This call creates no context and allocates nothing, on the
- * host or the device: the scratch of the transform kernel (planar XYB and
+ * allowed.  This call creates no context and allocates no device memory
+ * (host memory only for the tables it builds on its first call per device
+ * and for error messages): the scratch of the transform kernel (planar XYB and
  * per-block EPF sigma, 12 B per padded pixel + 2 B per 8x8 block) is a
  * fixed array of JXL_RECON_NOALLOC_SCRATCH_BYTES inside the library, held
  * by every GPU that loads it until the process exits; a padded image that
@@ -380,7 +381,11 @@ const char* jxl_recon_last_error(const jxl_recon_ctx* ctx);
  * Inputs as for jxl_recon_submit() and all on the device (coeffs->on_device
  * = 1, out->on_device = 1); filter_params->dequant must be NULL (default
  * matrices).  The map is not validated: an ill-formed map gives unspecified
- * pixels but no out-of-bounds access.  The kernels are enqueued on
+ * pixels but no out-of-bounds access (a varblock whose code is above 14 or
+ * whose footprint is misaligned, leaves its 32x32 cell or the padded image
+ * is skipped; a block no varblock covers is left unfiltered).  With the
+ * EPF off and Gaborish on, the tiles are read with ordinary loads, so no
+ * device wait can expire unreported.  The kernels are enqueued on
  * cuda_stream (a cudaStream_t; NULL = the legacy default stream) of the
  * current device and the call returns without waiting.
  * The first call on a device copies the constant tables to it and looks up

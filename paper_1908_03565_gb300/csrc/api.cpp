@@ -559,9 +559,7 @@ extern "C" jxlr_status jxl_recon_submit(jxl_recon_ctx* ctx, const jxl_recon_coef
   ra.xs = xs; ra.ys = ys; ra.wp = wp; ra.hp = hp; ra.bw = bw; ra.bh = bh; ra.tw = tw;
   for (int c = 0; c < 3; ++c) {
     ra.m_dc[c] = fp->m_dc[c];
-    ra.one_minus_bias[c] = static_cast<float>(1.0 - (c == 0 ? 0.05465007330715401
-                                                      : c == 1 ? 0.07005449891748593
-                                                               : 0.049935103337343655));
+    ra.one_minus_bias[c] = one_minus_bias(c);
   }
   ra.kx_dc = cfl->kx_dc;
   ra.kb_dc = cfl->kb_dc;

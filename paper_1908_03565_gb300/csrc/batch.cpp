@@ -226,10 +226,9 @@ extern "C" jxlr_status jxl_recon_batch_create(jxl_recon_ctx* ctx, const jxl_reco
     a.sharp = fp->sharpness;
     a.dequant = ctx_default_dequant(ctx);
     a.xs = xs; a.ys = ys; a.wp = wp; a.hp = hp; a.bw = bw; a.bh = bh; a.tw = (wp + 63) / 64;
-    const double bias[3] = {0.05465007330715401, 0.07005449891748593, 0.049935103337343655};
     for (int c = 0; c < 3; ++c) {
       a.m_dc[c] = fp->m_dc[c];
-      a.one_minus_bias[c] = static_cast<float>(1.0 - bias[c]);
+      a.one_minus_bias[c] = one_minus_bias(c);
     }
     a.kx_dc = r.cfl_map->kx_dc;
     a.kb_dc = r.cfl_map->kb_dc;

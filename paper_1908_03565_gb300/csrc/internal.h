@@ -90,6 +90,7 @@ struct FilterArgs;
 ColorParams color_params(const jxl_recon_filter_params& p);
 SigmaParams sigma_params(const jxl_recon_filter_params& p);
 uint32_t weight_min_bits(float wmin);
+float one_minus_bias(int c);   // F.3, channel c
 FilterArgs filter_args(const jxl_recon_filter_params& p);
 
 // Context internals used by the batch path (api.cpp).

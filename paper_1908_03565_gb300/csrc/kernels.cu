@@ -2687,4 +2687,9 @@ void launch_filter(const FilterArgs& a, cudaStream_t s) {
   k_filter<<<grid, 256, 0, s>>>(a);
 }
 
+void launch_filter_plain(const FilterArgs& a, cudaStream_t s) {
+  dim3 grid((a.xs + kTW - 1) / kTW, (a.ys + kTH - 1) / kTH);
+  k_filter<<<grid, 256, 0, s>>>(a);
+}
+
 }  // namespace jxlr

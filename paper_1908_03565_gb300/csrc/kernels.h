@@ -124,6 +124,9 @@ constexpr int kTcBasisBytes = 6144;
 void launch_sigma(const SigmaArgs& a, cudaStream_t s);
 void launch_qco(const QcoArgs& a, cudaStream_t s);
 void launch_filter(const FilterArgs& a, cudaStream_t s);
+// Gaborish / noise / colour (a.epf == 0) with the tile loaded by all threads
+// (k_filter): no TMA and no bounded wait; same results bit for bit.
+void launch_filter_plain(const FilterArgs& a, cudaStream_t s);
 // J.2 on the blocks the sigma pass listed (EpfSink), into a.epf_out, where
 // that pass copied the other blocks; J.4 / L.2 then run as launch_filter()
 // on that output.  next: a zeroed counter the warps claim groups of 2 listed

@@ -4,7 +4,9 @@
 // (a framework's caching allocator, a memory-budgeted service) must account
 // for every device byte, or that runs where allocation is not allowed
 // because it would synchronise the device.  For them this entry point uses
-// device memory that exists for as long as the library is loaded: the
+// device memory that exists for as long as the library is loaded (it
+// allocates no device memory; host memory only for the tables it builds on
+// its first call per device and for error messages): the
 // scratch of the dequantise-and-transform kernel (planar XYB samples and the
 // per-block EPF sigma, read back by the filter kernel) lives in a file-scope
 // __device__ array of kNoAllocScratchBytes, and the dequantisation matrices
@@ -149,27 +151,15 @@ extern "C" jxlr_status jxl_recon_run_noalloc(const jxl_recon_coeffs* co, const u
   ra.sharp = fp->sharpness;
   ra.dequant = g_dequant_ptr[dev];
   ra.xs = xs; ra.ys = ys; ra.wp = wp; ra.hp = hp; ra.bw = bw; ra.bh = bh; ra.tw = tw;
-  const double bias[3] = {0.05465007330715401, 0.07005449891748593, 0.049935103337343655};
   for (int c = 0; c < 3; ++c) {
     ra.m_dc[c] = fp->m_dc[c];
-    ra.one_minus_bias[c] = static_cast<float>(1.0 - bias[c]);
+    ra.one_minus_bias[c] = one_minus_bias(c);
   }
   ra.kx_dc = cfl->kx_dc;
   ra.kb_dc = cfl->kb_dc;
-  // same parameter derivations as the context path
-  const double im3 = std::cbrt(fp->target_nits_div50 * 50.0 / 250.0);
-  for (int c = 0; c < 3; ++c) {
-    ra.sp.gmin[c] = static_cast<float>((c == 0 ? -0.03 : 0.0) * im3);
-    ra.sp.gscale[c] = fp->epf_scale[c];
-  }
-  ra.sp.range_max = fp->epf_range_max;
-  ra.sp.range_mul = fp->epf_range_mul;
-  ra.sp.quant_mul = fp->epf_quant_mul;
-  ra.sp.sigma_max = static_cast<float>(fp->epf_sigma_max);
-  for (int i = 0; i < 8; ++i) ra.sp.lut[i] = fp->epf_sharp_lut[i];
-  const double div = fp->target_nits_div50 * 50.0 / 250.0 * 255.0;
-  for (int i = 0; i < 9; ++i) ra.cp.m[i] = static_cast<float>(fp->inv_opsin[i] / div);
-  for (int i = 0; i < 3; ++i) ra.cp.bias[i] = fp->opsin_bias[i];
+  // the same parameter derivations as the context path
+  ra.sp = sigma_params(*fp);
+  ra.cp = color_params(*fp);
   OutParams op;
   op.data = out->data;
   op.stride = out->row_stride_bytes;
@@ -182,30 +172,19 @@ extern "C" jxlr_status jxl_recon_run_noalloc(const jxl_recon_coeffs* co, const u
     ra.xyb = xyb;
     ra.sigma = sig;
     launch_recon(ra, s);
-    FilterArgs fa;
-    std::memset(&fa, 0, sizeof(fa));
+    FilterArgs fa = filter_args(*fp);
     fa.xyb = xyb;
     fa.rstride = wp;
     fa.pstride = size_t(wp) * hp;
     fa.xs = xs; fa.ys = ys; fa.bw = bw;
     fa.sigma = sig;
-    fa.epf = fp->epf != 0;
-    fa.gab = fp->gab != 0;
-    for (int c = 0; c < 3; ++c) {
-      const double w1 = fp->gab_w1[c], w2 = fp->gab_w2[c];
-      const double n = 1.0 + 4.0 * w1 + 4.0 * w2;
-      fa.gw[c][0] = static_cast<float>(1.0 / n);
-      fa.gw[c][1] = static_cast<float>(w1 / n);
-      fa.gw[c][2] = static_cast<float>(w2 / n);
-    }
-    float wmin = fp->epf_weight_min;
-    uint32_t wb = 0;
-    if (wmin > 0) std::memcpy(&wb, &wmin, 4);
-    fa.wmin_bits = wb;
-    fa.sp = ra.sp;
-    fa.cp = ra.cp;
     fa.out = op;
-    launch_filter(fa, s);
+    // With the EPF: the single-launch J.2 + J.4 + L.2 kernel (no buffer for
+    // an intermediate image).  Gaborish alone: the form that loads its tiles
+    // with ordinary loads, which has no bounded wait whose expiry this call
+    // (which returns before the kernels run) could not report.
+    if (fp->epf) launch_filter(fa, s);
+    else launch_filter_plain(fa, s);
   } else {
     ra.write_xyb = 0;
     ra.out = op;

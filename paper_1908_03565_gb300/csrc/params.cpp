@@ -32,6 +32,13 @@ SigmaParams sigma_params(const jxl_recon_filter_params& p) {
   return sp;
 }
 
+float one_minus_bias(int c) {
+  // F.3: a quantised coefficient of magnitude <= 1 is scaled by 1 - kOneBias[c]
+  static const double kOneBias[3] = {0.05465007330715401, 0.07005449891748593,
+                                     0.049935103337343655};
+  return static_cast<float>(1.0 - kOneBias[c]);
+}
+
 uint32_t weight_min_bits(float wmin) {
   // smallest binary32 value >= wmin (weights below it are dropped, J.2.5)
   if (!(wmin > 0)) return 0;

@@ -7,6 +7,14 @@ uses a fixed scratch array inside the library instead of allocating.  This
 file is collected last so that, if it fails, a run that stops at the first
 failure has already run every other test.  It passes both alone in a fresh
 process (the first call does the per-device set-up) and after the others.
+
+Every filter combination runs the same arithmetic as the submit path: no
+filter (the transform kernel writes the pixels), Gaborish alone (the
+ordinary-load form of the Gaborish / colour kernel, bit-identical to the TMA
+form the submit path takes), and the EPF with or without Gaborish (the
+single-launch EPF, bit-identical to the block-list EPF).  So the outputs
+must equal the submit path's bit for bit, for every output type and on two
+calls in a row (the second reading scratch the first left behind).
 """
 import numpy as np
 import pytest
@@ -15,10 +23,19 @@ from paper_1908_03565_gb300 import synth
 
 pytestmark = pytest.mark.gpu
 
-TOL01 = 1e-4   # the linear-RGB tolerance of the parity tests
+# (epf, gab) combinations and output types
+FILTERS = [(0, 0), (0, 1), (1, 0), (1, 1)]
 
 
-def test_noalloc_matches_submit_on_two_calls_in_a_row():
+def _dtypes(B):
+    import torch
+    return [(B.OUT_F32_LINEAR, torch.float32, float("nan")),
+            (B.OUT_F16_LINEAR, torch.float16, float("nan")),
+            (B.OUT_U8_SRGB, torch.uint8, 7)]
+
+
+@pytest.mark.parametrize("epf,gab", FILTERS)
+def test_noalloc_matches_submit_on_two_calls_in_a_row(epf, gab):
     import torch
     assert torch.cuda.is_available()
     from paper_1908_03565_gb300 import binding as B
@@ -26,23 +43,23 @@ def test_noalloc_matches_submit_on_two_calls_in_a_row():
     stream = torch.cuda.Stream()
     cases = [((320, 200), 11), ((257, 129), 12)]   # the second reuses stale scratch
     with B.Context() as ctx:
-        got, want = [], []
-        for (xs, ys), seed in cases:
-            img = synth.make_image(xs, ys, seed, y_dc_offset_q=200)
-            dimg = B.to_device(img, torch)
-            params = B.filter_defaults(epf=1, gab=1)
-            ref = torch.empty((ys, xs, 3), dtype=torch.float32, device="cuda")
-            t = ctx.submit(dimg, params, ref, B.OUT_F32_LINEAR, on_device=True)
-            ctx.poll(t)
-            out = torch.full((ys, xs, 3), float("nan"), dtype=torch.float32, device="cuda")
-            B.run_noalloc(dimg, params, out, B.OUT_F32_LINEAR, stream=stream.cuda_stream)
-            stream.synchronize()
-            got.append(out.cpu().numpy())
-            want.append(ref.cpu().numpy())
-        for g, w in zip(got, want):
-            assert np.isfinite(g).all()
-            err = np.abs(np.clip(g, 0, 1) - np.clip(w, 0, 1)).max()
-            assert err <= TOL01, err
+        for dt, tdt, fill in _dtypes(B):
+            got, want = [], []
+            for (xs, ys), seed in cases:
+                img = synth.make_image(xs, ys, seed, y_dc_offset_q=200)
+                dimg = B.to_device(img, torch)
+                params = B.filter_defaults(epf=epf, gab=gab)
+                ref = torch.empty((ys, xs, 3), dtype=tdt, device="cuda")
+                ctx.poll(ctx.submit(dimg, params, ref, dt, on_device=True))
+                out = torch.full((ys, xs, 3), fill, dtype=tdt, device="cuda")
+                # the fill and the inputs were queued on the current stream
+                stream.wait_stream(torch.cuda.current_stream())
+                B.run_noalloc(dimg, params, out, dt, stream=stream.cuda_stream)
+                stream.synchronize()
+                got.append(out.cpu().numpy())
+                want.append(ref.cpu().numpy())
+            for g, w in zip(got, want):
+                np.testing.assert_array_equal(g, w)
 
 
 def test_noalloc_rejects_oversized_images():
