@@ -48,7 +48,8 @@ GUIDE_OPS_PER_PX = 17
 # blocks): 99,083,520 + 22,990,336; scaled to a launch by its pixels.  Set to
 # None whenever the kernel changes until it is captured again.
 EPF_WORK_DRAM_BYTES_4096x2048 = 99083520 + 22990336
-CPU_SAMPLE = 1024         # oracle sample: one 1024x1024 image, same statistics
+CPU_SAMPLE = 1024         # oracle sample on one core: one 1024x1024 image, same statistics
+CPU_SAMPLE_ALL = 2048     # oracle sample on every host core: one 2048x2048 image
 
 
 def env_int(k, d):
@@ -441,24 +442,97 @@ def jpeg1_leg(binding, torch, steps, peak_gbs):
     return res
 
 
-def cpu_baseline_run(steps=1, side=None):
-    """Times the FP64 oracle on a bounded sample of the workload: one
-    side x side image of the same statistics per step (median of steps)."""
+# ---------------------------------------------------------------------------
+# The FP64 oracle timed on the host cores (a reported baseline, not a target)
+# ---------------------------------------------------------------------------
+GROUP = 256               # the draft's group size (6.2), the unit of the parallel run
+_ORACLE_IMG = {}
+
+
+def _oracle_init(side, seed, pin):
+    """Worker start: one oracle thread, the sample image built once."""
     from oracle import recon as R
     from paper_1908_03565_gb300 import synth
-    side = side or CPU_SAMPLE
-    img = synth.make_image(side, side, SEED)
-    p = R.Params(epf=True, gab=True)
-    times = []
-    for _ in range(steps):
-        t0 = time.perf_counter()
-        R.reconstruct(img, p)
-        times.append(time.perf_counter() - t0)
-    t = statistics.median(times)
-    px = side * side
-    return {"value": px / t / 1e6, "unit": "Mpx/s", "cores": 1, "kind": "oracle",
-            "sample": f"one {side}x{side} image, mixed varblocks, EPF+Gaborish, "
-                      f"FP64 numpy oracle, single process ({px} px in {t:.1f} s)"}
+    if pin is not None and hasattr(os, "sched_setaffinity"):
+        os.sched_setaffinity(0, {pin})
+    R.THREADS = 1
+    _ORACLE_IMG["img"] = synth.make_image(side, side, seed)
+
+
+def _oracle_wait(t):
+    time.sleep(t)
+    return os.getpid()
+
+
+def _oracle_group(task):
+    """The oracle's whole path (F, G, I, J.2, J.4, L.2) for one group: the
+    64-aligned crop of the group with a margin of 64 samples (every
+    varblock, CfL tile and filter reach of the group's pixels inside it)."""
+    from oracle import recon as R
+    gx0, gy0 = task
+    img = _ORACLE_IMG["img"]
+    Wp, Hp = img['coeffs'].shape[2], img['coeffs'].shape[1]
+    x0, y0 = max(0, gx0 - 64), max(0, gy0 - 64)
+    x1, y1 = min(Wp, gx0 + GROUP + 64), min(Hp, gy0 + GROUP + 64)
+    sub = {'xsize': min(x1, img['xsize']) - x0, 'ysize': min(y1, img['ysize']) - y0,
+           'coeffs': img['coeffs'][:, y0:y1, x0:x1], 'vmap': img['vmap'][y0 // 8:y1 // 8, x0 // 8:x1 // 8],
+           'acmul': img['acmul'][y0 // 8:y1 // 8, x0 // 8:x1 // 8],
+           'sharpness': img['sharpness'][y0 // 8:y1 // 8, x0 // 8:x1 // 8],
+           'cfl': img['cfl'][y0 // 64:(y1 + 63) // 64, x0 // 64:(x1 + 63) // 64]}
+    out = R.reconstruct(sub, R.Params(epf=True, gab=True))['rgb01']
+    return float(out[gy0 - y0:gy0 - y0 + GROUP, gx0 - x0:gx0 + GROUP - x0].sum())
+
+
+def oracle_run(side, steps, warmup=0, procs=None):
+    """Times the FP64 oracle on a side x side image of the workload's
+    statistics, split into 256 x 256 groups processed by a pool of ``procs``
+    worker processes (spawned; each with one oracle thread and one BLAS
+    thread; a single worker is pinned to one core).  Returns (Mpx/s over the
+    timed steps, cores used, seconds)."""
+    import multiprocessing as mp
+    procs = procs or os.cpu_count() or 1
+    tasks = [(gx, gy) for gy in range(0, side, GROUP) for gx in range(0, side, GROUP)]
+    env_keys = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+    saved = {k: os.environ.get(k) for k in env_keys}
+    for k in env_keys:
+        os.environ[k] = "1"
+    try:
+        pin = None
+        if procs == 1 and hasattr(os, "sched_getaffinity"):
+            pin = sorted(os.sched_getaffinity(0))[0]
+        with mp.get_context("spawn").Pool(procs, initializer=_oracle_init,
+                                          initargs=(side, SEED, pin)) as pool:
+            pool.map(_oracle_wait, [0.5] * procs, chunksize=1)
+            for _ in range(warmup):
+                pool.map(_oracle_group, tasks, chunksize=1)
+            t0 = time.perf_counter()
+            for _ in range(steps):
+                pool.map(_oracle_group, tasks, chunksize=1)
+            total = time.perf_counter() - t0
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    return steps * side * side / total / 1e6, min(procs, len(tasks)), total
+
+
+def cpu_baseline_run():
+    """The oracle on a bounded sample of the workload: one core on a
+    CPU_SAMPLE^2 image, and every host core, group-parallel, on a
+    CPU_SAMPLE_ALL^2 image."""
+    v1, _, t1 = oracle_run(CPU_SAMPLE, 1, procs=1)
+    n = os.cpu_count() or 1
+    vn, cores, tn = oracle_run(CPU_SAMPLE_ALL, 1, procs=n)
+    return {"value": vn, "unit": "Mpx/s", "cores": cores, "kind": "oracle",
+            "sample": f"one {CPU_SAMPLE_ALL}x{CPU_SAMPLE_ALL} image of the workload's statistics, "
+                      f"EPF+Gaborish, FP64 numpy oracle, its {GROUP}x{GROUP} groups on {cores} "
+                      f"worker processes (each group from its crop with a 64-sample margin) "
+                      f"in {tn:.1f} s",
+            "single_core": {"value": v1, "unit": "Mpx/s", "cores": 1,
+                            "sample": f"one {CPU_SAMPLE}x{CPU_SAMPLE} image, the same groups "
+                                      f"on one worker pinned to one core, in {t1:.1f} s"}}
 
 
 def headline_meta(world):
@@ -478,42 +552,36 @@ def headline_meta(world):
 ORACLE_S_PER_PX = 14e-6
 
 
-def reference_side(k, w, budget_s=150.0):
+def reference_side(k, w, budget_s=150.0, cores=1):
     """Side of the reference arm's per-step sample: the largest of a fixed
-    list whose k + w steps take about budget_s of oracle time."""
-    for cand in (1024, 768, 512, 384, 256, 192, 128, 64):
-        if (k + w) * cand * cand * ORACLE_S_PER_PX <= budget_s:
+    list (multiples of the group size) whose k + w steps take about budget_s
+    of oracle time on ``cores`` cores (each group computed on its crop with
+    a 64-sample margin: about 2.3 times its own pixels)."""
+    for cand in (2048, 1536, 1024, 768, 512, 256):
+        work = (k + w) * cand * cand * 2.3 * ORACLE_S_PER_PX / max(1, min(cores, (cand // GROUP) ** 2))
+        if work <= budget_s:
             return cand
-    return 64
+    return 256
 
 
 def run_reference(args):
-    """The reference arm: the FP64 oracle as it stands, on one host core, W
-    untimed and K timed steps, each step one bounded sample of the workload
-    (a square image of the same statistics, its side the largest of a fixed
-    list whose W + K steps fit in about two and a half minutes)."""
+    """The reference arm: the FP64 oracle as it stands, on every host core
+    (its 256 x 256 groups on one worker process per core), W untimed and K
+    timed steps, each step one bounded sample of the workload (a square
+    image of the same statistics, its side the largest of a fixed list whose
+    W + K steps fit in about two and a half minutes)."""
     rank = env_int("RANK", 0)
     if rank != 0:
         return 0
-    from oracle import recon as R
-    from paper_1908_03565_gb300 import synth
     k, w = max(1, args.steps), max(0, args.warmup)
-    side = args.ref_side or reference_side(k, w)
-    img = synth.make_image(side, side, SEED)
-    p = R.Params(epf=True, gab=True)
-    for _ in range(w):
-        R.reconstruct(img, p)
-    t0 = time.perf_counter()
-    for _ in range(k):
-        R.reconstruct(img, p)
-    total = time.perf_counter() - t0
-    px = side * side
-    value = k * px / total / 1e6
+    n = os.cpu_count() or 1
+    side = args.ref_side or reference_side(k, w, cores=n)
+    value, cores, total = oracle_run(side, k, warmup=w, procs=n)
     metric, config = headline_meta(max(1, env_int("WORLD_SIZE", 1)))
-    cb = {"value": value, "unit": "Mpx/s", "cores": 1, "kind": "oracle",
+    cb = {"value": value, "unit": "Mpx/s", "cores": cores, "kind": "oracle",
           "sample": f"one {side}x{side} image of the same statistics per step, EPF+Gaborish, "
-                    f"FP64 numpy oracle, single process ({k} timed steps in {total:.1f} s "
-                    f"after {w} untimed)"}
+                    f"FP64 numpy oracle, its {GROUP}x{GROUP} groups on {cores} worker processes "
+                    f"({k} timed steps in {total:.1f} s after {w} untimed)"}
     line = {"impl": "reference", "metric": metric, "value": value,
             "unit": "Mpx/s", "n_gpus": args.gpus, "steps": k, "warmup": w,
             "ms_per_step": total / k * 1e3,

@@ -583,12 +583,13 @@ def epf_sigma(img, vmap, acmul, sharpness, params):
 # ---------------------------------------------------------------------------
 # Decisions of J.2 under uncertain input (for comparisons with binary32)
 # ---------------------------------------------------------------------------
-def epf_decision_bounds(img, vmap, acmul, sharpness, params, slack, rel=0.0, quant_alt=None):
+def epf_decision_bounds(img, vmap, acmul, sharpness, params, slack=0.0, guide_alt=None,
+                        sigma_alt=None):
     """The J.2 decisions for every input whose scaled guide samples lie
     within +-slack of those of ``img`` (slack: scalar or per sample, in
-    guide units), whose range term of sigma lies within a relative ``rel``
-    of the value those samples give, and whose quant term lies between the
-    real one and ``quant_alt`` (per block; another evaluation of it, or None).
+    guide units), joined with the decisions of another evaluation (for
+    instance binary32 arithmetic on another image of the same content):
+    ``guide_alt`` its guide bytes (3, h, w), ``sigma_alt`` its block sigmas.
     Returns (g_lo, g_hi, s_lo, s_hi): the smallest and largest guide bytes
     and block sigmas reachable.  A decision is fixed where the two agree;
     where they differ the input lies within the bound of a threshold and
@@ -596,18 +597,18 @@ def epf_decision_bounds(img, vmap, acmul, sharpness, params, slack, rel=0.0, qua
     s = guide_scaled(img, params)
     lo, hi = s - slack, s + slack
     r_lo, r_hi = block_ranges((lo, hi), vmap)
-    a_lo, q = sigma_terms(r_lo, acmul, sharpness, params)
-    a_hi, _ = sigma_terms(r_hi, acmul, sharpness, params)
-    q_lo = q if quant_alt is None else np.minimum(q, quant_alt)
-    q_hi = q if quant_alt is None else np.maximum(q, quant_alt)
-    smax = params.epf_sigma_max
-    s_lo = sigma_from_real(np.minimum(np.minimum(a_lo * (1.0 - rel), q_lo), smax))
-    s_hi = sigma_from_real(np.minimum(np.minimum(a_hi * (1.0 + rel), q_hi), smax))
-    return guide_from_scaled(lo), guide_from_scaled(hi), s_lo, s_hi
+    g_lo, g_hi = guide_from_scaled(lo), guide_from_scaled(hi)
+    s_lo = sigma_from_real(sigma_real(r_lo, acmul, sharpness, params))
+    s_hi = sigma_from_real(sigma_real(r_hi, acmul, sharpness, params))
+    if guide_alt is not None:
+        g_lo, g_hi = np.minimum(g_lo, guide_alt), np.maximum(g_hi, guide_alt)
+    if sigma_alt is not None:
+        s_lo, s_hi = np.minimum(s_lo, sigma_alt), np.maximum(s_hi, sigma_alt)
+    return g_lo, g_hi, s_lo, s_hi
 
 
-def epf_undetermined(img, vmap, acmul, sharpness, params, slack, rel=0.0, region=None,
-                     quant_alt=None):
+def epf_undetermined(img, vmap, acmul, sharpness, params, slack=0.0, region=None,
+                     guide_alt=None, sigma_alt=None):
     """Pixels of the J.2 output (over ``region``) that the input does not
     determine when its guide samples and sigmas are known only within the
     bounds of epf_decision_bounds: a pixel is undetermined if its block's
@@ -622,7 +623,7 @@ def epf_undetermined(img, vmap, acmul, sharpness, params, slack, rel=0.0, region
         region = (0, 0, xs, ys)
     x0, y0, x1, y1 = region
     g_lo, g_hi, s_lo, s_hi = epf_decision_bounds(img, vmap, acmul, sharpness, params,
-                                                 slack, rel, quant_alt)
+                                                 slack, guide_alt, sigma_alt)
     g = guide(img, params).astype(np.int32)
     loose = (g_lo != g_hi).astype(np.int32)
     mt4 = mul_table4()

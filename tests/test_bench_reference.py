@@ -34,6 +34,7 @@ def test_reference_line_matches_the_headline():
     # value is the timed steps' pixels over their time
     assert abs(line["value"] - 64 * 64 / (line["ms_per_step"] * 1e-3) / 1e6) < 1e-6 * line["value"] + 1e-9
     cb = line["cpu_baseline"]
+    # a 64x64 sample is one group: one worker
     assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] == line["value"]
     assert "64x64" in cb["sample"]
     e2e = line["e2e"]
@@ -43,11 +44,15 @@ def test_reference_line_matches_the_headline():
 
 def test_reference_sample_is_sized_to_the_run():
     """Without --ref-side the per-step sample shrinks as K + W grows, so the
-    whole run stays within a few minutes of oracle time."""
-    sides = [bench.reference_side(k, 10) for k in (1, 10, 50, 200, 1000)]
-    assert sides == sorted(sides, reverse=True)
-    assert bench.reference_side(3, 3) == 1024
-    for k, w in ((200, 10), (50, 3), (20, 5)):
-        s = bench.reference_side(k, w)
-        assert (k + w) * s * s * bench.ORACLE_S_PER_PX <= 150.0
-    assert bench.reference_side(10 ** 6, 0) == 64     # floor
+    whole run stays within a few minutes of oracle time on the cores it
+    uses (each group's crop is about 2.3 times the group)."""
+    for cores in (1, 16):
+        sides = [bench.reference_side(k, 10, cores=cores) for k in (1, 10, 50, 200, 1000)]
+        assert sides == sorted(sides, reverse=True)
+        for k, w in ((200, 10), (50, 3), (20, 5), (3, 3)):
+            s = bench.reference_side(k, w, cores=cores)
+            used = max(1, min(cores, (s // bench.GROUP) ** 2))
+            assert s % bench.GROUP == 0
+            assert s == 256 or (k + w) * s * s * 2.3 * bench.ORACLE_S_PER_PX / used <= 150.0
+        assert bench.reference_side(10 ** 6, 0, cores=cores) == 256     # floor
+    assert bench.reference_side(3, 3, cores=16) > bench.reference_side(3, 3, cores=1)

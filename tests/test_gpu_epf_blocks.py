@@ -13,8 +13,7 @@ import pytest
 from oracle import recon as R
 from paper_1908_03565_gb300 import synth
 from test_gpu_parity import (B, XYB, F32, U8, params_pair, run,  # noqa: F401
-                             _filters_on_gpu_xyb, assert_filter_stage, guide_slack, SIGMA_REL,
-                             quant_binary32)
+                             _filters_on_gpu_xyb, assert_filter_stage, decisions_binary32)
 
 pytestmark = pytest.mark.gpu
 
@@ -98,17 +97,18 @@ def _count_and_sigma(B, ctx, img, lp):
                                          (33, 17, 'active')])
 def test_block_count(B, tctx, xs, ys, stats):
     """The filtered blocks are those with sigma >= 16: on the GPU's own XYB
-    samples the count lies between those of the smallest and the largest
-    real-number sigmas that the binary32 rounding of J.2.2 and J.2.4 allows
-    (equal unless a block's sigma sits within that rounding of 16)."""
+    samples the count equals that of the binary32 evaluation of J.2.4 and
+    lies between those of the real-number and binary32 sigmas (equal unless
+    a block's sigma sits at 16 within binary32 rounding)."""
     kw = ACTIVE if stats == 'active' else {}
     img = synth.make_image(xs, ys, 7 * xs + ys, **kw)
     p, lp = params_pair(B, epf=True, gab=True)
-    xyb = run(B, tctx, img, params_pair(B)[1], XYB).transpose(2, 0, 1).astype(np.float64)
-    _, _, s_lo, s_hi = R.epf_decision_bounds(xyb, img['vmap'], img['acmul'], img['sharpness'],
-                                             p, guide_slack(xyb, xyb, p), SIGMA_REL,
-                                             quant_binary32(img, p))
+    xyb = run(B, tctx, img, params_pair(B)[1], XYB).transpose(2, 0, 1)
+    _, s32 = decisions_binary32(img, xyb, p)
+    _, _, s_lo, s_hi = R.epf_decision_bounds(xyb.astype(np.float64), img['vmap'], img['acmul'],
+                                             img['sharpness'], p, sigma_alt=s32)
     ms, n = _count_and_sigma(B, tctx, img, lp)
+    assert n == int(np.sum(s32 >= 16))
     assert int(np.sum(s_lo >= 16)) <= n <= int(np.sum(s_hi >= 16))
     assert int(np.sum(s_hi >= 16)) - int(np.sum(s_lo >= 16)) <= max(1, s_lo.size // 1000)
     assert 0 < n < s_lo.size

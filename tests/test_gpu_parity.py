@@ -12,13 +12,15 @@ Tolerances (written here; derived from binary32 arithmetic):
 The EPF decides integers (guide bytes, block sigmas) from real numbers.  The
 oracle takes them in real (FP64) arithmetic; the kernels take them in
 binary32 from their own XYB.  A comparison therefore excludes, and counts,
-the pixels whose output the decisions do not fix once the input is known
-only within the bound of the two sides' difference: the guide samples
-within |XYB difference| x epf_scale + the binary32 rounding of J.2.2 of a
-byte boundary, the block sigmas within the rounding of J.2.4 of an integer,
-and only where such a decision can change a weight above the cut-off
+the pixels whose output depends on a decision that the two take
+differently: the oracle's real-number guide byte or block sigma on its
+own samples against the kernels' binary32 evaluation on theirs (their XYB
+output, evaluated here in correctly rounded binary32 as the kernels do),
+and only where that decision can change a weight above the cut-off
 (oracle.recon.epf_undetermined), spread by one sample where Gaborish
-follows.  Every other pixel is held to the bounds above.
+follows.  Both differences come from rounding (binary32 against real
+arithmetic, and the transforms' binary32 error) at a threshold; every
+other pixel is held to the bounds above.
 """
 import numpy as np
 import pytest
@@ -244,7 +246,6 @@ def test_full_path_equals_staged_path(B, ctx):
     np.testing.assert_array_equal(full, staged)
 
 
-SIGMA_REL = 2.0 ** -21     # binary32 steps of the J.2.4 range term, relative
 AMBIG_MAX = 1e-3           # largest share of pixels a comparison may exclude
 # Largest share of RGB samples, at the workload's coefficient statistics, held
 # to the relaxed bound: there the draft's default 32x8 / 8x32 matrices give XYB
@@ -253,41 +254,44 @@ AMBIG_MAX = 1e-3           # largest share of pixels a comparison may exclude
 WORKLOAD_RELAXED = 0.03
 
 
-def guide_slack(x_gpu, x_ref, p):
-    """Per-sample bound, in guide units, on the difference between the
-    kernel's binary32 scaled guide value of its samples x_gpu and the real
-    scaled value of the oracle's samples x_ref: the sample difference times
-    epf_scale, plus the rounding of fl(fl(v - min32) * scale32) with min32
-    and scale32 the binary32 parameters, which is at most
-    2^-24 (3 |scaled| + |min| scale) (one rounding each of the difference,
-    the product and the scale, and that of min carried through the scale)."""
+def decisions_binary32(img, x_gpu, p):
+    """The guide bytes and block sigmas that the kernels take from their
+    samples x_gpu (3, h, w), evaluated here step by step in correctly
+    rounded binary32 arithmetic (numpy's float32 operations round as the
+    kernels' __fsub_rn / __fmul_rn / __frcp_rn do): scaled = fl(fl(v - min)
+    * scale) with binary32 parameters; guide = trunc(clamp(scaled, 0, 255));
+    per block and channel fl(max - min) of scaled over the in-image
+    samples, the largest over channels and over the varblock's blocks;
+    sigma = trunc(min(fl(fl(min(range, range_max) * range_mul) * lut),
+    fl(fl(1 / AcMul) * quant_mul), sigma_max)), at most 672.  This is the
+    error model of the comparison, not a reference: the oracle decides in
+    real arithmetic on its own samples."""
+    f32 = np.float32
     im3 = (p.target_nits_div50 * 50.0 / 250.0) ** (1.0 / 3.0)
-    s = R.guide_scaled(x_ref, p)
-    out = np.empty_like(s)
-    for c in range(3):
-        mn = (0.03 if c == 0 else 0.0) * im3
-        out[c] = (np.abs(np.asarray(x_gpu[c], np.float64) - x_ref[c]) * p.epf_scale[c]
-                  + 2.0 ** -24 * (3.0 * np.abs(s[c]) + mn * p.epf_scale[c]) + 1e-12)
-    return out
-
-
-def quant_binary32(img, p):
-    """The kernels' quant term of J.2.4 per block: the correctly rounded
-    binary32 reciprocal of AcMul times quant_mul, rounded (numpy's float32
-    division and product round correctly, as the kernels' do)."""
-    one = np.float32(1.0)
-    return (one / img['acmul'].astype(np.float32) * np.float32(p.epf_quant_mul)).astype(np.float64)
+    x = np.asarray(x_gpu, f32)
+    s = np.stack([(x[c] - f32((-0.03 if c == 0 else 0.0) * im3)) * f32(p.epf_scale[c])
+                  for c in range(3)])
+    g = np.trunc(np.clip(s, f32(0), f32(255))).astype(np.int64)
+    rng = R.block_ranges(s, img['vmap'])            # binary32 differences, exact maxima
+    bh, bw = rng.shape
+    lut = np.asarray(p.epf_sharp_lut, f32)[img['sharpness'][:bh, :bw].astype(np.int64)]
+    a = (np.minimum(rng.astype(f32), f32(p.epf_range_max)) * f32(p.epf_range_mul)) * lut
+    q = (f32(1.0) / img['acmul'][:bh, :bw].astype(f32)) * f32(p.epf_quant_mul)
+    sg = np.minimum(np.minimum(a, q), f32(p.epf_sigma_max))
+    return g, np.clip(np.trunc(sg).astype(np.int64), 0, 672)
 
 
 def undetermined(img, x_ref, x_gpu, p, gab, region=None):
-    """Pixels (over ``region``) whose J.2 output the decisions do not fix
-    for inputs within the bound of x_gpu - x_ref, grown by the Gaborish
-    reach when ``gab``."""
+    """Pixels (over ``region``) whose J.2 output depends on a decision that
+    the real-number definition on the oracle's samples x_ref and the
+    kernels' binary32 evaluation on their samples x_gpu take differently,
+    where that decision can change a weight above the cut-off; grown by the
+    Gaborish reach when ``gab``."""
     from scipy.ndimage import binary_dilation
     x_ref = np.asarray(x_ref, np.float64)
+    g32, s32 = decisions_binary32(img, x_gpu, p)
     u = R.epf_undetermined(x_ref, img['vmap'], img['acmul'], img['sharpness'], p,
-                           guide_slack(x_gpu, x_ref, p), SIGMA_REL, region=region,
-                           quant_alt=quant_binary32(img, p))
+                           region=region, guide_alt=g32, sigma_alt=s32)
     if gab:
         u = binary_dilation(u, structure=np.ones((3, 3), bool))
     return u

@@ -554,22 +554,19 @@ def test_undetermined_pixels_are_the_only_ones_a_perturbation_changes():
         assert not (diff & ~und).any()
         changed |= diff
     assert changed.any()
-    # the sigma bounds: here the quant term is the real 20 / 0.5 = 40 on
-    # every block, so blocks whose sigma it sets are fixed without an
-    # alternative evaluation and ties with one just below 40; a relative
-    # slack on the range term leaves a block whose range term lies well
-    # inside an integer interval fixed
-    a, q = R.sigma_terms(R.block_ranges(R.guide_scaled(x, p), img['vmap']), img['acmul'],
-                         img['sharpness'], p)
-    by_q = q < a
-    assert by_q.any() and (~by_q).any()
-    _, _, lo, hi = R.epf_decision_bounds(x, *args, 0.0, 1e-9)
-    frac = a - np.floor(a)
-    assert not (lo != hi)[by_q].any()
-    assert not (lo != hi)[~by_q & (frac > 0.01) & (frac < 0.99)].any()
-    _, _, lo, hi = R.epf_decision_bounds(x, *args, 0.0, 0.0, quant_alt=q - 1e-9)
-    assert np.all((lo != hi)[by_q & (q < p.epf_sigma_max)])
-    assert not (lo != hi)[~by_q & (a < q - 1e-6)].any()
+    # another evaluation's decisions widen exactly the decisions it takes
+    # differently (one below the real sigma on some blocks, one guide byte up)
+    s_real = R.epf_sigma(x, *args)
+    low = np.zeros_like(s_real, bool)
+    low[::2, ::3] = True
+    g = R.guide(x, p)
+    g_alt = g.copy()
+    g_alt[1, 5, 7] += 1
+    g_lo, g_hi, lo, hi = R.epf_decision_bounds(x, *args, 0.0, guide_alt=g_alt,
+                                               sigma_alt=np.where(low, s_real - 1, s_real))
+    assert np.array_equal(lo != hi, low) and np.array_equal(hi, s_real)
+    assert np.array_equal(lo[low], s_real[low] - 1)
+    assert (g_lo != g_hi).sum() == 1 and g_hi[1, 5, 7] == g[1, 5, 7] + 1
 
 
 def test_dc_smooth_margin():
