@@ -202,12 +202,12 @@ def assert_filter_stage(img, xyb, got, p, gab, name):
     pixels whose decisions lie within the binary32 rounding of a threshold
     (and that matter) are excluded; they are counted and must be rare."""
     want = _oracle_filters(img, xyb, p)
-    amb = (undetermined(img, xyb.astype(np.float64), xyb, p, gab) if p.epf
-           else np.zeros(xyb.shape[1:], bool))
-    assert amb.mean() <= AMBIG_MAX, (name, amb.mean())
+    amb, nd = (undetermined(img, xyb.astype(np.float64), xyb, p, gab) if p.epf
+               else (np.zeros(xyb.shape[1:], bool), 0))
+    assert_rare(amb, nd, name)
     g = np.where(amb[None], want, got.transpose(2, 0, 1))
     assert_xyb_close(g, want, abs_tol=5e-6, radius=8)
-    print(f"{name}: undetermined {amb.sum()} of {amb.size} pixels")
+    print(f"{name}: undetermined {amb.sum()} of {amb.size} pixels ({nd} decisions)")
     return amb
 
 
@@ -286,15 +286,25 @@ def undetermined(img, x_ref, x_gpu, p, gab, region=None):
     the real-number definition on the oracle's samples x_ref and the
     kernels' binary32 evaluation on their samples x_gpu take differently,
     where that decision can change a weight above the cut-off; grown by the
-    Gaborish reach when ``gab``."""
+    Gaborish reach when ``gab``.  Returns the mask and the number of
+    decisions (guide bytes and block sigmas) taken differently."""
     from scipy.ndimage import binary_dilation
     x_ref = np.asarray(x_ref, np.float64)
     g32, s32 = decisions_binary32(img, x_gpu, p)
+    ndiff = (int(np.sum(g32 != R.guide(x_ref, p)))
+             + int(np.sum(s32 != R.epf_sigma(x_ref, img['vmap'], img['acmul'], img['sharpness'], p))))
     u = R.epf_undetermined(x_ref, img['vmap'], img['acmul'], img['sharpness'], p,
                            region=region, guide_alt=g32, sigma_alt=s32)
     if gab:
         u = binary_dilation(u, structure=np.ones((3, 3), bool))
-    return u
+    return u, ndiff
+
+
+def assert_rare(amb, ndiff, name):
+    """Excluded pixels are rare: at most AMBIG_MAX of them, or, on images
+    too small for a share to mean anything (one decision reaches up to
+    ~150 pixels), at most 2 decisions taken differently."""
+    assert amb.mean() <= AMBIG_MAX or (amb.size < 10 ** 6 and ndiff <= 2), (name, amb.mean(), ndiff)
 
 
 def local_mag(*views, radius=8):
@@ -348,15 +358,17 @@ def assert_from_scratch(img, ref, gpu_xyb, f32, u8, p, name, region=None, relaxe
     1e-4 plus the XYB bound carried through L.2 (rgb_tolerance).  The RGB
     samples of the second kind whose oracle value is not clamped away from
     [0, 1] by more than that bound are counted and must be at most
-    ``relaxed_max`` of them; undetermined pixels at most AMBIG_MAX."""
+    ``relaxed_max`` of them (None: the caller checks the counts returned);
+    excluded pixels must be rare (assert_rare).  Returns (excluded pixels,
+    decisions taken differently, relaxed samples counted, samples)."""
     ys, xs = img['ysize'], img['xsize']
     if region is None:
         region = (0, 0, xs, ys)
     x0, y0, x1, y1 = region
     ref_xyb = ref['xyb_padded'][:, :ys, :xs]
     assert_xyb_close(gpu_xyb, ref_xyb)
-    amb = (undetermined(img, ref_xyb, gpu_xyb, p, p.gab, region) if p.epf
-           else np.zeros((y1 - y0, x1 - x0), bool))
+    amb, nd = (undetermined(img, ref_xyb, gpu_xyb, p, p.gab, region) if p.epf
+               else (np.zeros((y1 - y0, x1 - x0), bool), 0))
     ok = np.broadcast_to(~amb[..., None], (y1 - y0, x1 - x0, 3))
     rx = ref['xyb'][:, y0:y1, x0:x1]
     mag = local_mag(ref['xyb'], ref_xyb)[:, y0:y1, x0:x1]
@@ -373,15 +385,16 @@ def assert_from_scratch(img, ref, gpu_xyb, f32, u8, p, name, region=None, relaxe
                              f"plain); worst at {i}: err {err[i]:.3g} bound {bound[i]:.3g}")
     live = relaxed & (want01 >= -tol) & (want01 <= 1 + tol)
     d = np.abs(u8.astype(np.int64) - R.srgb_u8(want01).astype(np.int64))
-    print(f"{name}: undetermined {amb.mean():.2e} of pixels; RGB samples held to 1e-4: "
-          f"{plain.mean():.4f} (max err {err[plain].max():.2e}); to the relaxed bound and "
+    print(f"{name}: undetermined {amb.mean():.2e} of pixels ({nd} decisions); RGB samples held "
+          f"to 1e-4: {plain.mean():.4f} (max err {err[plain].max():.2e}); to the relaxed bound and "
           f"not clamped away: {live.mean():.4f} (max err "
           f"{err[live].max() if live.any() else 0:.2e}); u8 max diff {d[ok].max()} "
           f"(over all pixels {d.max()})")
     assert d[ok].max() <= 1, name
-    assert live.mean() <= relaxed_max, (name, live.mean())
-    assert amb.mean() <= AMBIG_MAX, (name, amb.mean())
-    return amb
+    if relaxed_max is not None:
+        assert live.mean() <= relaxed_max, (name, live.mean())
+        assert_rare(amb, nd, name)
+    return int(amb.sum()), nd, int(live.sum()), live.size
 
 
 def test_mixed_statistics_from_scratch(B, ctx):
@@ -391,9 +404,10 @@ def test_mixed_statistics_from_scratch(B, ctx):
     p, lp = params_pair(B, epf=True, gab=True)
     ref = R.reconstruct(img, p)
     gpu_xyb = run(B, ctx, img, params_pair(B)[1], XYB).transpose(2, 0, 1)
-    amb = assert_from_scratch(img, ref, gpu_xyb, run(B, ctx, img, lp, F32),
-                              run(B, ctx, img, lp, U8), p, "320x200", relaxed_max=WORKLOAD_RELAXED)
+    assert_from_scratch(img, ref, gpu_xyb, run(B, ctx, img, lp, F32),
+                        run(B, ctx, img, lp, U8), p, "320x200", relaxed_max=WORKLOAD_RELAXED)
     # the filtered XYB itself, everywhere the decisions fix
+    amb, _ = undetermined(img, ref['xyb_padded'][:, :200, :320], gpu_xyb, p, True)
     gx = run(B, ctx, img, lp, XYB).transpose(2, 0, 1)
     assert_xyb_close(np.where(amb[None], ref['xyb'], gx), ref['xyb'])
 
@@ -449,15 +463,21 @@ def test_4096_windows_from_scratch(B, ctx):
     wins = [(0, 0), (xs - 64, 0), (0, ys - 64), (xs - 64, ys - 64), (2048, 0), (0, 1344),
             (1984, 2048)] + [(int(64 * rng.integers(1, 62)), int(64 * rng.integers(1, 62)))
                              for _ in range(3)]
+    tot = np.zeros(4, np.int64)
     for wx, wy in wins:
         cx0, cy0 = max(0, wx - 64), max(0, wy - 64)
         sub = crop_input(img, cx0, cy0, wx + 128, wy + 128)
         ref = R.reconstruct(sub, p)
         region = (wx - cx0, wy - cy0, wx - cx0 + 64, wy - cy0 + 64)
         gx = outs[XYB][cy0:cy0 + sub['ysize'], cx0:cx0 + sub['xsize']].transpose(2, 0, 1)
-        assert_from_scratch(sub, ref, gx, outs[F32][wy:wy + 64, wx:wx + 64],
-                            outs[U8][wy:wy + 64, wx:wx + 64], p, f"4096^2 window ({wx}, {wy})",
-                            region=region, relaxed_max=WORKLOAD_RELAXED)
+        tot += assert_from_scratch(sub, ref, gx, outs[F32][wy:wy + 64, wx:wx + 64],
+                                   outs[U8][wy:wy + 64, wx:wx + 64], p,
+                                   f"4096^2 window ({wx}, {wy})", region=region, relaxed_max=None)
+    amb, nd, live, n = (int(v) for v in tot)
+    print(f"4096^2 windows: undetermined {amb} of {n // 3} pixels ({nd} decisions), relaxed "
+          f"samples not clamped away {live / n:.4f}")
+    assert live / n <= WORKLOAD_RELAXED
+    assert amb / (n // 3) <= AMBIG_MAX or nd <= 2
 
 
 # ---------------------------------------------------------------------------

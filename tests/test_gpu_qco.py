@@ -15,7 +15,7 @@ import pytest
 
 from oracle import recon as R
 from paper_1908_03565_gb300 import synth
-from test_gpu_parity import (B, ctx, XYB, F32, AMBIG_MAX, assert_xyb_close,  # noqa: F401
+from test_gpu_parity import (B, ctx, XYB, F32, assert_rare, assert_xyb_close,  # noqa: F401
                              params_pair, run, undetermined)
 
 pytestmark = pytest.mark.gpu
@@ -67,8 +67,8 @@ def _excluded(img, xyb, p, gab):
     """Samples of the varblocks holding an EPF pixel that the decisions do
     not fix on the samples xyb (grown by one sample with Gaborish)."""
     from scipy.ndimage import binary_dilation
-    amb = undetermined(img, xyb.astype(np.float64), xyb, p, False)
-    assert amb.mean() <= AMBIG_MAX
+    amb, nd = undetermined(img, xyb.astype(np.float64), xyb, p, False)
+    assert_rare(amb, nd, "J.3")
     m = np.zeros_like(amb)
     for code, bx, by in R.varblocks(img['vmap']):
         W, H = synth.SHAPE_WH[code]
@@ -77,7 +77,7 @@ def _excluded(img, xyb, p, gab):
             m[sl] = True
     if gab:
         m = binary_dilation(m, structure=np.ones((3, 3), bool))
-    assert m.mean() <= 0.02
+    assert m.mean() <= 0.02 or nd <= 2
     return m
 
 
