@@ -7,6 +7,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -90,6 +91,7 @@ struct jxl_recon_ctx {
   std::vector<Slot> slots;
   float* d_dequant = nullptr;        // prescaled default matrices
   int precision = JXLR_PREC_FP32;
+  int recon_variant = kReconPersistent;   // form of the FP32 transform kernel
   unsigned char* d_tcb = nullptr;    // tensor-core basis tables
   std::mutex mu;
   std::atomic<uint64_t> next_ticket{1};
@@ -201,6 +203,8 @@ jxlr_status jxl_recon_create(const jxl_recon_config* cfg, jxl_recon_ctx** out) {
   ctx->cap = cfg->hbm_cap_bytes;
   ctx->timing = cfg->timing != 0;
   ctx->precision = cfg->precision;
+  if (const char* v = std::getenv("JXLR_RECON_VARIANT"))
+    ctx->recon_variant = std::strcmp(v, "grid") == 0 ? kReconGrid : kReconPersistent;
   cudaError_t e = cudaMalloc(&ctx->d_dequant, sizeof(float) * kDequantFloats);
   if (e == cudaSuccess)
     e = cudaMemcpy(ctx->d_dequant, scaled.data(), sizeof(float) * kDequantFloats,
@@ -625,7 +629,7 @@ extern "C" jxlr_status jxl_recon_submit(jxl_recon_ctx* ctx, const jxl_recon_coef
     ra.sigma = sig;
     ra.epf = sink;
     if (tc) launch_recon_tc(ra, s);
-    else launch_recon(ra, s);
+    else launch_recon(ra, s, ctx->recon_variant);
     ctx->launches++;
     mark(slot, 3);
     FilterArgs fa = filter_args(*fp);
@@ -648,7 +652,7 @@ extern "C" jxlr_status jxl_recon_submit(jxl_recon_ctx* ctx, const jxl_recon_coef
     ra.write_xyb = 0;
     ra.out = op;
     if (tc) launch_recon_tc(ra, s);
-    else launch_recon(ra, s);
+    else launch_recon(ra, s, ctx->recon_variant);
     ctx->launches++;
     mark(slot, 3);
   }

@@ -845,20 +845,50 @@ __device__ void cell_sigma(float (*S)[kPR][kRS], CellState& cs, const SigmaParam
 // so that warps of the transform passes mostly share a shape.  Warp 0 does
 // it in parallel: lane b < 16 owns block b of the cell; its rank in the
 // sorted list and its item prefix sums come from shuffles.
+// The map entries of a cell's 16 blocks, loaded ahead of the cell (the
+// persistent transform kernel fetches the next cell's during the current
+// cell's stores).
+struct CellMap {
+  int code[16];
+  float am[16];
+  int sh[16];
+};
+
+// Block b's map entries (code, AcMul, sharpness), the defaults outside the map.
+__device__ __forceinline__ void cell_map_entry(const uint8_t* __restrict__ vmap,
+                                               const float* __restrict__ acmul,
+                                               const uint8_t* __restrict__ sharp, int gbx0,
+                                               int gby0, int bw, int bh, int b, int& code,
+                                               float& am, int& sh) {
+  const int gbx = gbx0 + (b & 3), gby = gby0 + (b >> 2);
+  code = kCovered;
+  am = 1.f;
+  sh = 0;
+  if (gbx < bw && gby < bh) {
+    code = vmap[gby * bw + gbx];
+    am = acmul[gby * bw + gbx];
+    if (sharp) sh = sharp[gby * bw + gbx];
+  }
+}
+
 __device__ void cell_setup(CellState& cs, const uint8_t* __restrict__ vmap,
                            const float* __restrict__ acmul, int gbx0, int gby0, int bw,
-                           int bh, bool tc = false, const uint8_t* __restrict__ sharp = nullptr) {
+                           int bh, bool tc = false, const uint8_t* __restrict__ sharp = nullptr,
+                           const CellMap* pre = nullptr) {
   const int tid = threadIdx.x;
   if (tid < 32) {
     const unsigned full = 0xffffffffu;
     const int b = tid & 15, bx = b & 3, by = b >> 2;
-    const int gbx = gbx0 + bx, gby = gby0 + by;
     int code = kCovered, sh = 0;
     float am = 1.f;
-    if (tid < 16 && gbx < bw && gby < bh) {
-      code = vmap[gby * bw + gbx];
-      am = acmul[gby * bw + gbx];
-      if (sharp) sh = sharp[gby * bw + gbx];
+    if (tid < 16) {
+      if (pre) {
+        code = pre->code[b];
+        am = pre->am[b];
+        sh = pre->sh[b];
+      } else {
+        cell_map_entry(vmap, acmul, sharp, gbx0, gby0, bw, bh, b, code, am, sh);
+      }
     }
     bool valid = false;
     int ri = 0, ci = 0, fi = 0, li = 0, w8 = 1, h8 = 1;
@@ -1078,14 +1108,51 @@ __device__ void tc_pass(TcShared& ts, uint32_t& phase, unsigned* err, int nrows,
 // One 32x32 cell (cell coordinates cxi, cyi) of image a; 128 threads.
 // kDc: whether the DC-domain inputs (dc1, lfp) may be set (single-image
 // launches only).
-template <bool kTC = false, bool kDc = true>
-__device__ __forceinline__ void recon_cell(const ReconArgs& a, int cxi, int cyi) {
+// Copies of cell (cxi, cyi)'s coefficients (3 x 32 rows x 64 bytes) into the
+// int16 buffer dst [3][32][32] with cp.async (zeros outside the padded
+// image), and its map entries to pm (threads 0..15, plain loads whose
+// results are stored at the end: the caller's work overlaps them).
+__device__ __forceinline__ void cell_coef_async(const ReconArgs& a, int cxi, int cyi,
+                                                int16_t* dst) {
+  const int tid = threadIdx.x;
+  const int y = tid >> 2, k = tid & 3;
+  const int gy = cyi * 32 + y, gx = cxi * 32 + 8 * k;
+  const bool inb = gy < a.hp && gx < a.wp;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const int16_t* src = inb ? a.coef[c] + static_cast<size_t>(gy) * a.cstride + gx : a.coef[c];
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::
+                 "r"(static_cast<uint32_t>(__cvta_generic_to_shared(dst + (c * 32 + y) * 32 + 8 * k))),
+                 "l"(src), "r"(inb ? 16 : 0) : "memory");
+  }
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+// kPf: the persistent form.  The cell's coefficients are in T (as int16
+// [3][32][32]) and its map entries in the CellMap, put there by the
+// previous cell's call (first: fetched here); with (ncxi, ncyi) >= 0 the
+// next cell's are fetched during this cell's output phase, when T is free.
+template <bool kTC = false, bool kDc = true, bool kPf = false>
+__device__ __forceinline__ void recon_cell(const ReconArgs& a, int cxi, int cyi, int ncxi = -1,
+                                           int ncyi = -1, bool first = false) {
   __shared__ __align__(16) float S[3][kPR][kRS];
   __shared__ __align__(16) float T[3][kPR][kRS];
   __shared__ CellState cs;
+  __shared__ CellMap cmap;
+  static_assert(sizeof(T) >= 3 * 32 * 32 * sizeof(int16_t), "coefficient prefetch buffer");
+  int16_t* const tq = reinterpret_cast<int16_t*>(&T[0][0][0]);
   const int tid = threadIdx.x;
   const int gbx0 = cxi * 4, gby0 = cyi * 4;
   const int px0 = gbx0 * 8, py0 = gby0 * 8;
+
+  if (kPf && first) {
+    cell_coef_async(a, cxi, cyi, tq);
+    if (tid < 16)
+      cell_map_entry(a.vmap, a.acmul, a.sigma ? a.sharp : nullptr, gbx0, gby0, a.bw, a.bh, tid,
+                     cmap.code[tid], cmap.am[tid], cmap.sh[tid]);
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    __syncthreads();
+  }
 
   // the coefficient loads do not depend on the map: issue them first
   const int y = tid >> 2, k = tid & 3;     // cell row, 8-column chunk
@@ -1093,9 +1160,13 @@ __device__ __forceinline__ void recon_cell(const ReconArgs& a, int cxi, int cyi)
   const bool inb = gy < a.hp && gx < a.wp;
   int4 raw[3];
 #pragma unroll
-  for (int c = 0; c < 3; ++c)
-    raw[c] = inb ? __ldg(reinterpret_cast<const int4*>(a.coef[c] + gy * a.cstride + gx))
-                 : make_int4(0, 0, 0, 0);
+  for (int c = 0; c < 3; ++c) {
+    if (kPf)
+      raw[c] = *reinterpret_cast<const int4*>(tq + (c * 32 + y) * 32 + 8 * k);
+    else
+      raw[c] = inb ? __ldg(reinterpret_cast<const int4*>(a.coef[c] + gy * a.cstride + gx))
+                   : make_int4(0, 0, 0, 0);
+  }
 
   extern __shared__ __align__(1024) unsigned char tc_dyn[];
   TcShared& ts = *reinterpret_cast<TcShared*>(tc_dyn);
@@ -1128,7 +1199,8 @@ __device__ __forceinline__ void recon_cell(const ReconArgs& a, int cxi, int cyi)
       v = *reinterpret_cast<const float2*>(a.lfp + 4 * c * bpl + static_cast<size_t>(y) * (2 * a.bw) + x);
     *reinterpret_cast<float2*>(&slp[c][r][2 * q]) = v;
   }
-  cell_setup(cs, a.vmap, a.acmul, gbx0, gby0, a.bw, a.bh, kTC, a.sigma ? a.sharp : nullptr);
+  cell_setup(cs, a.vmap, a.acmul, gbx0, gby0, a.bw, a.bh, kTC, a.sigma ? a.sharp : nullptr,
+             kPf ? &cmap : nullptr);
   if (kTC) tc_fence_after();
 
   // ---- F.2 / F.3 / G: one 8-sample row chunk of all three channels -------
@@ -1288,6 +1360,17 @@ __device__ __forceinline__ void recon_cell(const ReconArgs& a, int cxi, int cyi)
   __syncthreads();
 
   // ---- output ---------------------------------------------------------------
+  // (persistent form: T is free from here on; the next cell's coefficients
+  // and map entries arrive during the stores)
+  int pcode = kCovered, psh = 0;
+  float pam = 1.f;
+  const bool prefetch = kPf && ncxi >= 0;
+  if (prefetch) {
+    cell_coef_async(a, ncxi, ncyi, tq);
+    if (tid < 16)
+      cell_map_entry(a.vmap, a.acmul, a.sigma ? a.sharp : nullptr, ncxi * 4, ncyi * 4, a.bw,
+                     a.bh, tid, pcode, pam, psh);
+  }
   if (a.write_xyb && a.sigma) {
     // sigma, the EPF's block list, then the XYB store (and the copy of the
     // blocks the EPF leaves unchanged)
@@ -1319,10 +1402,35 @@ __device__ __forceinline__ void recon_cell(const ReconArgs& a, int cxi, int cyi)
     if (tid < 32)
       asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;" :: "r"(ts.tmem));
   }
+  if (prefetch) {
+    if (tid < 16) {
+      cmap.code[tid] = pcode;
+      cmap.am[tid] = pam;
+      cmap.sh[tid] = psh;
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    __syncthreads();   // the next cell's inputs are in place; S and cs are free
+  }
 }
 
 __global__ void __launch_bounds__(128, 7) k_recon(const __grid_constant__ ReconArgs a) {
   recon_cell(a, blockIdx.x, blockIdx.y);
+}
+
+// Persistent form: CTAs take cells cell, cell + gridDim.x, ... (raster
+// order, so the resident CTAs work on neighbouring cells), each cell's
+// coefficients and map fetched during the previous cell's output phase.
+__global__ void __launch_bounds__(128, 7) k_recon_pf(const __grid_constant__ ReconArgs a,
+                                                     int ncx, int ncells) {
+  int cell = blockIdx.x;
+  bool first = true;
+  while (cell < ncells) {
+    const int nxt = cell + static_cast<int>(gridDim.x);
+    recon_cell<false, true, true>(a, cell % ncx, cell / ncx, nxt < ncells ? nxt % ncx : -1,
+                                  nxt / ncx, first);
+    first = false;
+    cell = nxt;
+  }
 }
 
 // Multi-image form: work item w is cell item_cell[w].y (raster order) of
@@ -1356,9 +1464,28 @@ void launch_recon_tc(const ReconArgs& a, cudaStream_t s) {
   k_recon_tc<<<grid, 128, sizeof(TcShared) + 1024, s>>>(a);
 }
 
-void launch_recon(const ReconArgs& a, cudaStream_t s) {
-  dim3 grid((a.wp + 31) / 32, (a.hp + 31) / 32);
-  k_recon<<<grid, 128, 0, s>>>(a);
+int recon_pf_grid() {
+  static int grid_of[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  int& grid = grid_of[dev & 63];
+  if (grid == 0) {
+    int sms = 0, per = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_recon_pf, 128, 0);
+    grid = (sms > 0 ? sms : 1) * (per > 0 ? per : 1);
+  }
+  return grid;
+}
+
+void launch_recon(const ReconArgs& a, cudaStream_t s, int variant) {
+  const int ncx = (a.wp + 31) / 32, ncy = (a.hp + 31) / 32;
+  if (variant == kReconPersistent) {
+    const int ncells = ncx * ncy, grid = recon_pf_grid();
+    k_recon_pf<<<grid < ncells ? grid : ncells, 128, 0, s>>>(a, ncx, ncells);
+    return;
+  }
+  k_recon<<<dim3(ncx, ncy), 128, 0, s>>>(a);
 }
 
 void launch_recon_batch(const ReconArgs* args, const int* item_cell, int total, int grid,
@@ -2604,6 +2731,7 @@ void launch_epf_work_batch(const FilterArgs* args, const unsigned* counts, int n
 static void prefer_shared_carveout() {
   const int pct = cudaSharedmemCarveoutMaxShared;
   cudaFuncSetAttribute(k_recon, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+  cudaFuncSetAttribute(k_recon_pf, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
   cudaFuncSetAttribute(k_recon_tc, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
   cudaFuncSetAttribute(k_recon_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        static_cast<int>(sizeof(TcShared) + 1024));

@@ -116,7 +116,11 @@ struct QcoArgs {
 };
 
 void launch_validate(const uint8_t* vmap, int bw, int bh, unsigned* status, cudaStream_t s);
-void launch_recon(const ReconArgs& a, cudaStream_t s);
+// Forms of the transform kernel: one CTA per 32x32 cell (grid), or a
+// persistent grid of resident CTAs that fetch each next cell's
+// coefficients and map during the current cell's stores.
+enum { kReconGrid = 0, kReconPersistent = 1 };
+void launch_recon(const ReconArgs& a, cudaStream_t s, int variant = kReconGrid);
 // Variant whose separable passes of the varblocks larger than 8x8 run as
 // FP16 hi/lo split products on the tensor cores (tcgen05, FP32 accumulate).
 void launch_recon_tc(const ReconArgs& a, cudaStream_t s);
