@@ -288,18 +288,46 @@ typedef struct {
   uint64_t busy_refusals;  /* admissions refused (no slot / HBM) and retried     */
   uint64_t completed;      /* requests finished                                  */
   uint32_t max_in_flight;  /* most requests running at once                      */
+  uint64_t bypassed;       /* requests admitted ahead of an older refused one    */
 } jxl_recon_serve_stats;
 
-/* Request loop (the draft's data-parallel decoding of independent images,
- * 6.2 / 6.4, as a service).  Replays reqs[0..n) arriving at arrival_s[i]
- * seconds after the call (non-decreasing): each arrived request is admitted
- * in order as soon as the context has a free slot and room under its HBM cap
- * (a refused request waits at the head of the queue until one in flight
- * completes); admitted requests run concurrently on their slots' streams.
- * latency_ms[i] receives completion - arrival of request i (queueing
- * included).  Blocks until every request finished.  With max_slots = 1 the
- * loop is the plain one-image-at-a-time path.  Returns JXLR_OK, or the first
- * error a request produced (the others still complete). */
+/* Request server (the draft's data-parallel decoding of independent images,
+ * 6.2 / 6.4, as a service; no counterpart in the draft's text).  A
+ * long-lived thread admits enqueued requests into the context as slots and
+ * HBM under its cap free up (continuous batching): it scans the queue in
+ * arrival order and submits each request the context accepts; a request
+ * refused for want of HBM is passed by smaller ones behind it until it has
+ * waited longer than age_bound_ms, after which nothing behind it is
+ * admitted first.  Admitted requests run concurrently on their slots'
+ * streams; the context gives each a stream of lower priority than the
+ * requests in flight, so older requests keep the SMs they need.
+ * jxl_recon_server_enqueue() is safe from any thread and returns at once; the
+ * request's buffers (and, for host inputs, its host arrays) must stay valid
+ * until jxl_recon_server_wait() returned for it.  wait: timeout_us < 0
+ * blocks, 0 polls (JXLR_EAGAIN), > 0 waits at most that long
+ * (JXLR_ETIMEDOUT); latency_ms = completion - enqueue.  A request that
+ * submit rejects (JXLR_EINVAL, JXLR_ENOMEM, JXLR_ECUDA) reports that status
+ * from wait.  stop drains the queue, joins the thread, fills stats (may be
+ * NULL) and frees the server. */
+typedef struct jxl_recon_server jxl_recon_server;
+typedef struct {
+  double age_bound_ms;     /* longest wait a refused request lets others pass   */
+  int bypass;              /* 0: strict arrival order                           */
+} jxl_recon_server_config;
+jxlr_status jxl_recon_server_start(jxl_recon_ctx* ctx, const jxl_recon_server_config* cfg,
+                                   jxl_recon_server** out);
+jxlr_status jxl_recon_server_enqueue(jxl_recon_server* server, const jxl_recon_request* req,
+                                     uint64_t* id);
+jxlr_status jxl_recon_server_wait(jxl_recon_server* server, uint64_t id, int64_t timeout_us,
+                                  double* latency_ms);
+jxlr_status jxl_recon_server_stop(jxl_recon_server* server, jxl_recon_serve_stats* stats);
+
+/* Replay of an arrival schedule through a request server (age bound 5 ms):
+ * the calling thread enqueues reqs[0..n) at arrival_s[i] seconds after the
+ * call (non-decreasing) and waits for all.  latency_ms[i] receives
+ * completion - arrival of request i (queueing included).  With max_slots = 1
+ * the context runs one image at a time: the plain path.  Returns JXLR_OK, or
+ * the first error a request produced (the others still complete). */
 jxlr_status jxl_recon_serve(jxl_recon_ctx* ctx, const jxl_recon_request* reqs, size_t n,
                             const double* arrival_s, double* latency_ms,
                             jxl_recon_serve_stats* stats);

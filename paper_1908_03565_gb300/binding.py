@@ -7,6 +7,7 @@ There is no fallback: if the shared library is missing or fails to load,
 ``load()`` raises.
 """
 import ctypes
+import threading
 import os
 
 import numpy as np
@@ -26,7 +27,9 @@ EXPORTS = ("jxl_recon_filter_defaults", "jxl_recon_create", "jxl_recon_submit",
            "jxl_recon_last_error", "jxl_recon_run_noalloc", "jxl_recon_serve",
            "jxl_recon_batch_create", "jxl_recon_batch_launch", "jxl_recon_batch_query",
            "jxl_recon_batch_status",
-           "jxl_recon_batch_destroy", "jxl_recon_submit_jpeg", "jxl_recon_epf_stats")
+           "jxl_recon_batch_destroy", "jxl_recon_submit_jpeg", "jxl_recon_epf_stats",
+           "jxl_recon_server_start", "jxl_recon_server_enqueue", "jxl_recon_server_wait",
+           "jxl_recon_server_stop")
 
 
 class Config(ctypes.Structure):
@@ -89,7 +92,18 @@ class Request(ctypes.Structure):
 
 class ServeStats(ctypes.Structure):
     _fields_ = [("makespan_s", ctypes.c_double), ("busy_refusals", ctypes.c_uint64),
-                ("completed", ctypes.c_uint64), ("max_in_flight", ctypes.c_uint32)]
+                ("completed", ctypes.c_uint64), ("max_in_flight", ctypes.c_uint32),
+                ("bypassed", ctypes.c_uint64)]
+
+
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("age_bound_ms", ctypes.c_double), ("bypass", ctypes.c_int)]
+
+
+def _stats_dict(stats):
+    return {"makespan_s": stats.makespan_s, "busy_refusals": stats.busy_refusals,
+            "completed": stats.completed, "max_in_flight": stats.max_in_flight,
+            "bypassed": stats.bypassed}
 
 
 class BatchInfo(ctypes.Structure):
@@ -333,10 +347,12 @@ class Context:
         st = self.lib.jxl_recon_serve(self.h, reqs, n, arr, lat, ctypes.byref(stats))
         if st != JXLR_OK:
             raise JxlrError(st, self.last_error())
-        return np.array(lat[:]), {"makespan_s": stats.makespan_s,
-                                  "busy_refusals": stats.busy_refusals,
-                                  "completed": stats.completed,
-                                  "max_in_flight": stats.max_in_flight}
+        return np.array(lat[:]), _stats_dict(stats)
+
+    def server(self, age_bound_ms=5.0, bypass=True):
+        """A request server on this context (a native thread that admits
+        enqueued requests as slots and HBM free up)."""
+        return Server(self, age_bound_ms, bypass)
 
     def batch(self, jobs, autotune=True, plain_loads=False):
         """A multi-image batch (CUDA graph) over device-resident jobs;
@@ -386,6 +402,56 @@ def requests(jobs):
         reqs[i] = Request(ctypes.addressof(c), _ptr(img['vmap']), _ptr(img['acmul']),
                           ctypes.addressof(cfl), ctypes.addressof(p), ctypes.addressof(o))
     return reqs, keep
+
+
+class Server:
+    """jxl_recon_server_*: enqueue from any thread, wait per request."""
+
+    def __init__(self, ctx, age_bound_ms=5.0, bypass=True):
+        self.lib = ctx.lib
+        self.ctx = ctx
+        h = ctypes.c_void_p()
+        cfg = ServerConfig(age_bound_ms, int(bypass))
+        self.lib.jxl_recon_server_start.argtypes = [ctypes.c_void_p, ctypes.POINTER(ServerConfig),
+                                                    ctypes.POINTER(ctypes.c_void_p)]
+        self.lib.jxl_recon_server_enqueue.argtypes = [ctypes.c_void_p, ctypes.POINTER(Request),
+                                                      ctypes.POINTER(ctypes.c_uint64)]
+        self.lib.jxl_recon_server_wait.argtypes = [ctypes.c_void_p, ctypes.c_uint64,
+                                                   ctypes.c_int64, ctypes.POINTER(ctypes.c_double)]
+        self.lib.jxl_recon_server_stop.argtypes = [ctypes.c_void_p, ctypes.POINTER(ServeStats)]
+        st = self.lib.jxl_recon_server_start(ctx.h, ctypes.byref(cfg), ctypes.byref(h))
+        if st != JXLR_OK:
+            raise JxlrError(st, ctx.last_error())
+        self.h = h
+        self.keep = {}
+        self._lock = threading.Lock()
+
+    def enqueue(self, job):
+        """job: (img, params, out, out_dtype), device-resident; returns an id."""
+        reqs, keep = requests([job])
+        rid = ctypes.c_uint64()
+        st = self.lib.jxl_recon_server_enqueue(self.h, reqs, ctypes.byref(rid))
+        if st != JXLR_OK:
+            raise JxlrError(st, self.ctx.last_error())
+        with self._lock:
+            self.keep[rid.value] = (reqs, keep)
+        return rid.value
+
+    def wait(self, rid, timeout_us=-1):
+        """Latency in ms of request rid (completion - enqueue)."""
+        lat = ctypes.c_double()
+        st = self.lib.jxl_recon_server_wait(self.h, rid, timeout_us, ctypes.byref(lat))
+        with self._lock:
+            self.keep.pop(rid, None)
+        if st != JXLR_OK:
+            raise JxlrError(st, self.ctx.last_error())
+        return lat.value
+
+    def stop(self):
+        stats = ServeStats()
+        self.lib.jxl_recon_server_stop(self.h, ctypes.byref(stats))
+        self.h = None
+        return _stats_dict(stats)
 
 
 class Batch:

@@ -5,7 +5,9 @@
 #include <algorithm>
 #include <atomic>
 #include <chrono>
+#include <climits>
 #include <cmath>
+#include <cstdint>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -56,6 +58,7 @@ namespace {
 struct Slot {
   cudaStream_t stream = nullptr;
   bool own_stream = true;
+  int prio = 0;               // priority of the slot's stream (lower = served first)
   cudaEvent_t done = nullptr;
   // timing marks: start, staged, validated, recon, end, before J.2, after J.2
   cudaEvent_t ev[7] = {};
@@ -91,7 +94,7 @@ struct jxl_recon_ctx {
   std::vector<Slot> slots;
   float* d_dequant = nullptr;        // prescaled default matrices
   int precision = JXLR_PREC_FP32;
-  int recon_variant = kReconPersistent;   // form of the FP32 transform kernel
+  int recon_variant = kReconGrid;    // form of the FP32 transform kernel
   unsigned char* d_tcb = nullptr;    // tensor-core basis tables
   std::mutex mu;
   std::atomic<uint64_t> next_ticket{1};
@@ -102,6 +105,12 @@ struct jxl_recon_ctx {
 
 namespace jxlr {
 const float* ctx_default_dequant(const jxl_recon_ctx* c) { return c->d_dequant; }
+int ctx_idle_slots(jxl_recon_ctx* c) {
+  std::lock_guard<std::mutex> lock(c->mu);
+  int n = 0;
+  for (const auto& s : c->slots) n += !s.busy;
+  return n;
+}
 int ctx_device(const jxl_recon_ctx* c) { return c->device; }
 void ctx_count_launches(jxl_recon_ctx* c, int n) { c->launches += n; }
 }  // namespace jxlr
@@ -204,7 +213,7 @@ jxlr_status jxl_recon_create(const jxl_recon_config* cfg, jxl_recon_ctx** out) {
   ctx->timing = cfg->timing != 0;
   ctx->precision = cfg->precision;
   if (const char* v = std::getenv("JXLR_RECON_VARIANT"))
-    ctx->recon_variant = std::strcmp(v, "grid") == 0 ? kReconGrid : kReconPersistent;
+    ctx->recon_variant = std::strcmp(v, "persistent") == 0 ? kReconPersistent : kReconGrid;
   cudaError_t e = cudaMalloc(&ctx->d_dequant, sizeof(float) * kDequantFloats);
   if (e == cudaSuccess)
     e = cudaMemcpy(ctx->d_dequant, scaled.data(), sizeof(float) * kDequantFloats,
@@ -217,12 +226,21 @@ jxlr_status jxl_recon_create(const jxl_recon_config* cfg, jxl_recon_ctx** out) {
       e = cudaMemcpy(ctx->d_tcb, tcb.data(), kTcBasisBytes, cudaMemcpyHostToDevice);
   }
   ctx->slots.resize(cfg->max_slots);
-  for (auto& s : ctx->slots) {
+  // the slots' streams spread over the device's priority range, the first
+  // slots at the highest priorities
+  int least = 0, greatest = 0;
+  if (e == cudaSuccess && !cfg->cuda_stream)
+    e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
+  const int levels = least - greatest + 1;
+  for (size_t i = 0; i < ctx->slots.size(); ++i) {
+    Slot& s = ctx->slots[i];
     if (cfg->cuda_stream) {
       s.stream = static_cast<cudaStream_t>(cfg->cuda_stream);
       s.own_stream = false;
     } else if (e == cudaSuccess) {
-      e = cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking);
+      const int n = static_cast<int>(ctx->slots.size());
+      s.prio = greatest + static_cast<int>((static_cast<long>(i) * levels) / std::max(n, 1));
+      e = cudaStreamCreateWithPriority(&s.stream, cudaStreamNonBlocking, s.prio);
     }
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming);
     for (auto& ev : s.ev)
@@ -288,10 +306,29 @@ bool host_map_valid(const uint8_t* vmap, int bw, int bh, std::string* why) {
 // Finds a free slot and makes sure its arena holds `need` bytes within the
 // HBM cap.  Called with ctx->mu held.
 jxlr_status acquire_slot(jxl_recon_ctx* ctx, size_t need, Slot** out) {
+  // Priority: the request gets the highest stream priority below those of
+  // the requests in flight (the highest of all when none is), so that older
+  // requests are served first on the device; among the idle slots of that
+  // priority (else the nearest lower, else the nearest higher):
   Slot* fit = nullptr;   // smallest idle arena that already holds `need`
   Slot* any = nullptr;   // else the idle slot with the largest arena
+  bool busy_any = false;
+  int floor_prio = 0;    // numerically largest priority in flight
+  for (auto& s : ctx->slots)
+    if (s.busy) {
+      floor_prio = busy_any ? std::max(floor_prio, s.prio) : s.prio;
+      busy_any = true;
+    }
+  int want = INT32_MAX;  // the priority to use: the smallest idle one above floor_prio
+  int alt = INT32_MIN;   // else the largest idle one
   for (auto& s : ctx->slots) {
     if (s.busy) continue;
+    if ((!busy_any || s.prio > floor_prio) && s.prio < want) want = s.prio;
+    alt = std::max(alt, s.prio);
+  }
+  if (want == INT32_MAX) want = alt;
+  for (auto& s : ctx->slots) {
+    if (s.busy || s.prio != want) continue;
     if (s.arena_bytes >= need && (!fit || s.arena_bytes < fit->arena_bytes)) fit = &s;
     if (!any || s.arena_bytes > any->arena_bytes) any = &s;
   }

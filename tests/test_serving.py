@@ -67,3 +67,77 @@ def test_hbm_cap_bounds_concurrency():
         assert stats["max_in_flight"] <= 2
         assert stats["busy_refusals"] > 0
         assert ctx.device_bytes() <= 9 << 20
+
+
+def test_server_fed_from_several_threads():
+    """The request server on its own thread, fed by four producer threads at
+    once and waited on from them: every result equals its result alone."""
+    import threading
+    import torch
+    from paper_1908_03565_gb300 import binding as B
+    jobs = _jobs(B, torch)
+    alone = []
+    with B.Context(max_slots=1) as ctx:
+        for img, params, out, dtype in jobs:
+            ctx.poll(ctx.submit(img, params, out, dtype, on_device=True))
+            alone.append(out.cpu().numpy().copy())
+            out.zero_()
+    torch.cuda.synchronize()
+    with B.Context(max_slots=4) as ctx:
+        srv = ctx.server()
+        lat = [None] * len(jobs)
+        errors = []
+
+        def producer(k):
+            try:
+                for i in range(k, len(jobs), 4):
+                    rid = srv.enqueue(jobs[i])
+                    lat[i] = srv.wait(rid)
+            except Exception as e:       # reported below
+                errors.append(e)
+
+        threads = [threading.Thread(target=producer, args=(k,)) for k in range(4)]
+        for t in threads:
+            t.start()
+        for t in threads:
+            t.join()
+        stats = srv.stop()
+        torch.cuda.synchronize()
+        assert not errors, errors
+        assert stats["completed"] == len(jobs) and all(v > 0 for v in lat)
+        for (img, params, out, dtype), want in zip(jobs, alone):
+            np.testing.assert_array_equal(out.cpu().numpy(), want)
+
+
+def test_server_admits_past_a_request_that_does_not_fit():
+    """Under an HBM cap that holds one large request, a second large request
+    waits while small ones behind it are admitted (bypassed > 0); with a
+    zero age bound nothing passes it; every request completes correctly."""
+    import torch
+    from paper_1908_03565_gb300 import binding as B
+    big = [B.to_device(synth.make_image(1024, 1024, 950 + i), torch) for i in range(2)]
+    small = [B.to_device(synth.make_image(64, 64, 960 + i), torch) for i in range(6)]
+    p = B.filter_defaults(epf=1, gab=1)
+    jobs = [(img, p, torch.zeros((img['ysize'], img['xsize'], 3), dtype=torch.uint8,
+                                 device="cuda"), B.OUT_U8_SRGB) for img in big + small]
+    alone = []
+    with B.Context(max_slots=1) as ctx:
+        for img, params, out, dtype in jobs:
+            ctx.poll(ctx.submit(img, params, out, dtype, on_device=True))
+            alone.append(out.cpu().numpy().copy())
+            out.zero_()
+    # a 1024^2 request needs ~34 MB of scratch (XYB, J.2 output, lists); the
+    # cap holds one of them and the small ones
+    for age, want_bypass in ((1000.0, True), (0.0, False)):
+        with B.Context(max_slots=8, hbm_cap_bytes=48 << 20) as ctx:
+            srv = ctx.server(age_bound_ms=age)
+            ids = [srv.enqueue(j) for j in jobs]
+            for i in ids:
+                srv.wait(i)
+            stats = srv.stop()
+            torch.cuda.synchronize()
+        assert stats["completed"] == len(jobs)
+        assert (stats["bypassed"] > 0) == want_bypass, stats
+        for (img, params, out, dtype), want in zip(jobs, alone):
+            np.testing.assert_array_equal(out.cpu().numpy(), want)
+            out.zero_()
