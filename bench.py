@@ -141,7 +141,7 @@ def serve_leg(binding, torch, n_req, loads, pool_n=48, seed=4000, slots=8,
     resident on the device, requests drawn from it, Poisson arrivals at a
     fraction of the measured capacity, replayed through the native request
     server (a thread admitting requests as slots and HBM free up, passing a
-    request that does not fit for at most 5 ms, newer requests on lower
+    request that does not fit for at most 5 ms, larger images on higher
     stream priorities) with `slots` concurrent requests (continuous
     batching) against the plain path (one request at a time), both under a
     40 GB HBM cap.  Every request writes its own output buffer (while their
@@ -260,7 +260,17 @@ def batch_leg(binding, torch, n_img=512, pool_n=64, seed=3000, reps=10):
             "graph_kernels": info["kernels_per_launch"],
             "grids": [info["recon_grid"], info["epf_grid"], info["filter_grid"]],
             "work_items": [info["recon_items"], info["epf_items"], info["filter_items"]],
-            "autotuned": info["autotuned"], "outputs": "u8 sRGB / f16 linear alternating"}
+            "autotuned": info["autotuned"],
+            "chosen": {"class": {"images": info["images"], "cells": info["recon_items"],
+                                 "epf_images": info["epf_items"], "filter_tiles": info["filter_items"],
+                                 "u8_f16_f32": [info["mix"] & 255, (info["mix"] >> 8) & 255,
+                                                (info["mix"] >> 16) & 255]},
+                       "transform_grid": info["recon_grid"], "j2_grid": info["epf_grid"],
+                       "filter_form": "tma" if info["filter_tma"] else "ordinary loads",
+                       "filter_grid": info["filter_grid"],
+                       "kernel_ms": {"transform": info["kind_ms"][0], "j2": info["kind_ms"][1],
+                                     "gaborish_colour": info["kind_ms"][2]}},
+            "outputs": "u8 sRGB / f16 linear alternating"}
 
 
 PREC_WINDOWS = [(0, 0), (4032, 0), (0, 4032), (4032, 4032), (2048, 0), (0, 1344), (1984, 2048),

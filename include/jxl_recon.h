@@ -299,8 +299,10 @@ typedef struct {
  * refused for want of HBM is passed by smaller ones behind it until it has
  * waited longer than age_bound_ms, after which nothing behind it is
  * admitted first.  Admitted requests run concurrently on their slots'
- * streams; the context gives each a stream of lower priority than the
- * requests in flight, so older requests keep the SMs they need.
+ * streams; the context runs each on a stream whose priority rises with the
+ * image size (one level per factor of 4 in pixels from 256 Kpx), so large
+ * requests, which set the tail latency, take the SMs they need and small
+ * ones fill the rest.
  * jxl_recon_server_enqueue() is safe from any thread and returns at once; the
  * request's buffers (and, for host inputs, its host arrays) must stay valid
  * until jxl_recon_server_wait() returned for it.  wait: timeout_us < 0
@@ -339,11 +341,14 @@ jxlr_status jxl_recon_serve(jxl_recon_ctx* ctx, const jxl_recon_request* reqs, s
  * default dequantisation matrices; the batch owns the scratch of all its
  * images (XYB, sigma, and with the EPF its output and block list;
  * allocated at creation).  Maps are validated at creation (JXLR_EINVAL).
- * With JXLR_BATCH_AUTOTUNE the grids of the transform and filter kernels
- * are chosen by timing candidates on this batch (remembered per batch shape
- * in the process and in $JXLR_AUTOTUNE_CACHE if set); otherwise a
- * remembered choice is used, else one CTA per work item; the EPF kernel
- * runs on a persistent grid of its resident CTAs.  The inputs and outputs
+ * With JXLR_BATCH_AUTOTUNE the grids of the three kernel kinds (transform,
+ * J.2, Gaborish / colour) and the form of the last (TMA tiles or ordinary
+ * loads) are chosen by timing candidates on this batch, all of which give
+ * the same bits; the choice is remembered per batch class (images,
+ * transform cells, images with the EPF, filter tiles, output-type mix) in
+ * the process and in $JXLR_AUTOTUNE_CACHE if set.  Otherwise a remembered
+ * choice is used, else one CTA per transform cell and filter tile (the J.2
+ * kernel and the TMA form on their resident grids).  The inputs and outputs
  * of the requests must stay valid for the batch's lifetime. */
 typedef struct jxl_recon_batch jxl_recon_batch;
 #define JXLR_BATCH_AUTOTUNE 1
@@ -360,8 +365,11 @@ typedef struct {
   int kernels_per_launch;
   int autotuned;                                   /* 0 no, 1 tuned now, 2 cached */
   int filter_tma;                                  /* 1: the Gaborish / colour kernel loads
-                                                      its tiles by TMA (every filtered
-                                                      image's scratch allows it) */
+                                                      its tiles by TMA */
+  float kind_ms[3];                                /* tuned time of each kernel kind (0 if
+                                                      not timed), ms */
+  uint32_t mix;                                    /* output types: counts of u8, f16, f32
+                                                      images in bits 0-7, 8-15, 16-23 */
 } jxl_recon_batch_info;
 
 jxlr_status jxl_recon_batch_create(jxl_recon_ctx* ctx, const jxl_recon_request* reqs, size_t n,

@@ -112,7 +112,8 @@ class BatchInfo(ctypes.Structure):
                 ("filter_items", ctypes.c_uint32), ("recon_grid", ctypes.c_int),
                 ("epf_grid", ctypes.c_int), ("filter_grid", ctypes.c_int),
                 ("kernels_per_launch", ctypes.c_int), ("autotuned", ctypes.c_int),
-                ("filter_tma", ctypes.c_int)]
+                ("filter_tma", ctypes.c_int), ("kind_ms", ctypes.c_float * 3),
+                ("mix", ctypes.c_uint32)]
 
 
 BATCH_AUTOTUNE = 1
@@ -478,7 +479,9 @@ class Batch:
     def info(self):
         i = BatchInfo()
         self.lib.jxl_recon_batch_query(self.h, ctypes.byref(i))
-        return {k: getattr(i, k) for k, _ in BatchInfo._fields_}
+        d = {k: getattr(i, k) for k, _ in BatchInfo._fields_}
+        d["kind_ms"] = [round(float(v), 4) for v in i.kind_ms]
+        return d
 
     def status(self):
         """Error flags of the launches so far (bit 8: a filter tile-load wait

@@ -55,10 +55,15 @@ void jxlr::set_last_error(const std::string& msg) { g_err = msg; }
 
 namespace {
 
+constexpr int kMaxPrio = 8;   // stream priority levels a slot keeps a stream for
+
 struct Slot {
-  cudaStream_t stream = nullptr;
+  cudaStream_t stream = nullptr;   // the stream of the current request
   bool own_stream = true;
-  int prio = 0;               // priority of the slot's stream (lower = served first)
+  // the slot's streams, one per priority level from the lowest (0) up; a
+  // request runs on the one of its size class
+  cudaStream_t pstream[kMaxPrio] = {};
+  int nprio = 0;
   cudaEvent_t done = nullptr;
   // timing marks: start, staged, validated, recon, end, before J.2, after J.2
   cudaEvent_t ev[7] = {};
@@ -226,21 +231,22 @@ jxlr_status jxl_recon_create(const jxl_recon_config* cfg, jxl_recon_ctx** out) {
       e = cudaMemcpy(ctx->d_tcb, tcb.data(), kTcBasisBytes, cudaMemcpyHostToDevice);
   }
   ctx->slots.resize(cfg->max_slots);
-  // the slots' streams spread over the device's priority range, the first
-  // slots at the highest priorities
+  // each slot: one stream per priority level of the device (at most kMaxPrio)
   int least = 0, greatest = 0;
   if (e == cudaSuccess && !cfg->cuda_stream)
     e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
-  const int levels = least - greatest + 1;
-  for (size_t i = 0; i < ctx->slots.size(); ++i) {
-    Slot& s = ctx->slots[i];
+  const int levels = std::min(kMaxPrio, least - greatest + 1);
+  for (auto& s : ctx->slots) {
     if (cfg->cuda_stream) {
       s.stream = static_cast<cudaStream_t>(cfg->cuda_stream);
       s.own_stream = false;
-    } else if (e == cudaSuccess) {
-      const int n = static_cast<int>(ctx->slots.size());
-      s.prio = greatest + static_cast<int>((static_cast<long>(i) * levels) / std::max(n, 1));
-      e = cudaStreamCreateWithPriority(&s.stream, cudaStreamNonBlocking, s.prio);
+    } else {
+      for (int l = 0; l < levels && e == cudaSuccess; ++l)
+        e = cudaStreamCreateWithPriority(&s.pstream[l], cudaStreamNonBlocking, least - l);
+      if (e == cudaSuccess) {
+        s.nprio = levels;
+        s.stream = s.pstream[0];
+      }
     }
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming);
     for (auto& ev : s.ev)
@@ -265,7 +271,9 @@ jxlr_status jxl_recon_destroy(jxl_recon_ctx* ctx) {
     for (auto& ev : s.ev)
       if (ev) cudaEventDestroy(ev);
     if (s.done) cudaEventDestroy(s.done);
-    if (s.stream && s.own_stream) cudaStreamDestroy(s.stream);
+    if (s.own_stream)
+      for (int l = 0; l < s.nprio; ++l)
+        if (s.pstream[l]) cudaStreamDestroy(s.pstream[l]);
   }
   if (ctx->d_dequant) cudaFree(ctx->d_dequant);
   if (ctx->d_tcb) cudaFree(ctx->d_tcb);
@@ -303,32 +311,25 @@ bool host_map_valid(const uint8_t* vmap, int bw, int bh, std::string* why) {
   return true;
 }
 
+// The priority level of a request of `pixels` pixels: larger images get
+// higher levels (one level per factor of 4 from 256 Kpx up), so that on the
+// device the blocks of large requests, which set the tail latency, are
+// scheduled before those of small ones, and small ones fill the SMs that
+// large ones leave free.
+int size_level(uint64_t pixels, int nlevels) {
+  int lvl = 0;
+  for (uint64_t t = uint64_t(1) << 18; pixels >= t && lvl + 1 < nlevels; t <<= 2) ++lvl;
+  return lvl;
+}
+
 // Finds a free slot and makes sure its arena holds `need` bytes within the
-// HBM cap.  Called with ctx->mu held.
-jxlr_status acquire_slot(jxl_recon_ctx* ctx, size_t need, Slot** out) {
-  // Priority: the request gets the highest stream priority below those of
-  // the requests in flight (the highest of all when none is), so that older
-  // requests are served first on the device; among the idle slots of that
-  // priority (else the nearest lower, else the nearest higher):
+// HBM cap; its stream is the one of the request's size class.  Called with
+// ctx->mu held.
+jxlr_status acquire_slot(jxl_recon_ctx* ctx, size_t need, uint64_t pixels, Slot** out) {
   Slot* fit = nullptr;   // smallest idle arena that already holds `need`
   Slot* any = nullptr;   // else the idle slot with the largest arena
-  bool busy_any = false;
-  int floor_prio = 0;    // numerically largest priority in flight
-  for (auto& s : ctx->slots)
-    if (s.busy) {
-      floor_prio = busy_any ? std::max(floor_prio, s.prio) : s.prio;
-      busy_any = true;
-    }
-  int want = INT32_MAX;  // the priority to use: the smallest idle one above floor_prio
-  int alt = INT32_MIN;   // else the largest idle one
   for (auto& s : ctx->slots) {
     if (s.busy) continue;
-    if ((!busy_any || s.prio > floor_prio) && s.prio < want) want = s.prio;
-    alt = std::max(alt, s.prio);
-  }
-  if (want == INT32_MAX) want = alt;
-  for (auto& s : ctx->slots) {
-    if (s.busy || s.prio != want) continue;
     if (s.arena_bytes >= need && (!fit || s.arena_bytes < fit->arena_bytes)) fit = &s;
     if (!any || s.arena_bytes > any->arena_bytes) any = &s;
   }
@@ -365,6 +366,7 @@ jxlr_status acquire_slot(jxl_recon_ctx* ctx, size_t need, Slot** out) {
     best->arena_bytes = sz;
     ctx->bytes += sz;
   }
+  if (best->nprio) best->stream = best->pstream[size_level(pixels, best->nprio)];
   *out = best;
   return JXLR_OK;
 }
@@ -539,7 +541,7 @@ extern "C" jxlr_status jxl_recon_submit(jxl_recon_ctx* ctx, const jxl_recon_coef
   std::lock_guard<std::mutex> lock(ctx->mu);
   CK(cudaSetDevice(ctx->device));
   Slot* slot = nullptr;
-  jxlr_status st = acquire_slot(ctx, need, &slot);
+  jxlr_status st = acquire_slot(ctx, need, static_cast<uint64_t>(xs) * static_cast<uint64_t>(ys), &slot);
   if (st != JXLR_OK) return st;
   slot->timed = ctx->timing;
   slot->epf_marked = false;
@@ -728,7 +730,7 @@ extern "C" jxlr_status jxl_recon_submit_xyb(jxl_recon_ctx* ctx, const float* xyb
   std::lock_guard<std::mutex> lock(ctx->mu);
   CK(cudaSetDevice(ctx->device));
   Slot* slot = nullptr;
-  jxlr_status st = acquire_slot(ctx, need, &slot);
+  jxlr_status st = acquire_slot(ctx, need, static_cast<uint64_t>(xs) * static_cast<uint64_t>(ys), &slot);
   if (st != JXLR_OK) return st;
   slot->timed = ctx->timing;
   slot->epf_marked = false;
@@ -938,7 +940,7 @@ extern "C" jxlr_status jxl_recon_submit_jpeg(jxl_recon_ctx* ctx, const jxl_jpeg_
   std::lock_guard<std::mutex> lock(ctx->mu);
   CK(cudaSetDevice(ctx->device));
   Slot* slot = nullptr;
-  jxlr_status status = acquire_slot(ctx, need, &slot);
+  jxlr_status status = acquire_slot(ctx, need, static_cast<uint64_t>(xs) * static_cast<uint64_t>(ys), &slot);
   if (status != JXLR_OK) return status;
   slot->timed = ctx->timing;
   slot->epf_marked = false;

@@ -8,11 +8,12 @@
 // blocks with sigma >= 16 (and copies the others to its J.2 buffer), the
 // J.2 kernel's persistent warps take the images' listed blocks round robin,
 // and Gaborish + colour run on the J.2 buffers with the other images'
-// filter tiles.  The grids of the transform and filter kernels (one CTA per
-// item, or a persistent multiple of the resident CTAs) are chosen by timing
-// on the batch itself when JXLR_BATCH_AUTOTUNE is set, and remembered per
-// batch shape (in this process, and in the file named by
-// $JXLR_AUTOTUNE_CACHE if set); the J.2 kernel keeps its resident grid.
+// filter tiles.  With JXLR_BATCH_AUTOTUNE the grids of the three kernel kinds
+// and the form of the Gaborish / colour kernel (TMA tiles or ordinary
+// loads) are chosen by timing candidates on the batch itself, all of which
+// compute the same bits, and remembered per batch class (images, cells,
+// images with the EPF, filter tiles, output-type mix; in this process, and
+// in the file named by $JXLR_AUTOTUNE_CACHE if set).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -51,7 +52,10 @@ struct jxl_recon_batch {
   int nf = 0, ftotal = 0;
   void* d_maps = nullptr;          // their tensor maps (TMA form of the filter), or null
   unsigned* d_err = nullptr;       // bit 8: a bounded tile-load wait of the filter expired
+  bool use_tma = false;            // the filter runs in its TMA form (d_maps set)
   int grid[3] = {0, 0, 0};         // recon, epf, filter
+  float kind_ms[3] = {0, 0, 0};    // the tuned kernels' times (autotune), ms
+  uint32_t mix = 0;                // output types: 8 bits per count of f32 / f16 / u8 (capped)
   int autotuned = 0;
   cudaStream_t cap = nullptr;
   cudaGraph_t graph = nullptr;
@@ -73,7 +77,7 @@ void enqueue(const jxl_recon_batch* b, const int* grid, cudaStream_t s) {
   if (b->rtotal) launch_recon_batch(b->d_rargs, b->d_ritem, b->rtotal, grid[0], s);
   if (b->ne) launch_epf_work_batch(b->d_eargs, b->d_counts, b->ne, b->clamp, grid[1], s);
   if (b->ftotal) {
-    if (b->d_maps)
+    if (b->use_tma)
       launch_filter_batch_tma(b->d_fargs, b->d_fprefix, b->d_maps, b->nf, b->ftotal, grid[2],
                               b->d_err, s);
     else
@@ -81,82 +85,137 @@ void enqueue(const jxl_recon_batch* b, const int* grid, cudaStream_t s) {
   }
 }
 
-using Key = std::tuple<uint32_t, int, int, int>;
+// A batch class: images, transform cells, images with the EPF, filter
+// tiles, output-type mix.  The tuned choice: grids of the three kernel kinds
+// and the filter's form (1: TMA tiles, 0: ordinary loads).
+using Key = std::tuple<uint32_t, int, int, int, uint32_t>;
+struct Choice {
+  int grid[3];
+  int tma;
+  float ms[3];
+};
 std::mutex g_tune_mu;
-std::map<Key, std::vector<int>> g_tuned;
+std::map<Key, Choice> g_tuned;
 
-bool tuned_lookup(const Key& k, int* grid) {
+bool tuned_lookup(const Key& k, Choice* c) {
   std::lock_guard<std::mutex> lock(g_tune_mu);
   auto it = g_tuned.find(k);
   if (it == g_tuned.end()) {
     const char* path = std::getenv("JXLR_AUTOTUNE_CACHE");
     if (!path) return false;
     std::ifstream f(path);
-    uint32_t n;
-    int a, b, c, g0, g1, g2;
-    while (f >> n >> a >> b >> c >> g0 >> g1 >> g2)
-      g_tuned[Key(n, a, b, c)] = {g0, g1, g2};
+    std::string line;
+    while (std::getline(f, line)) {
+      std::istringstream in(line);
+      uint32_t n, mix;
+      int a, bb, cc;
+      Choice ch;
+      if (in >> n >> a >> bb >> cc >> mix >> ch.grid[0] >> ch.grid[1] >> ch.grid[2] >> ch.tma >>
+          ch.ms[0] >> ch.ms[1] >> ch.ms[2])
+        g_tuned[Key(n, a, bb, cc, mix)] = ch;
+    }
     it = g_tuned.find(k);
     if (it == g_tuned.end()) return false;
   }
-  for (int i = 0; i < 3; ++i) grid[i] = it->second[i];
+  *c = it->second;
   return true;
 }
 
-void tuned_store(const Key& k, const int* grid) {
+void tuned_store(const Key& k, const Choice& c) {
   std::lock_guard<std::mutex> lock(g_tune_mu);
-  g_tuned[k] = {grid[0], grid[1], grid[2]};
+  g_tuned[k] = c;
   if (const char* path = std::getenv("JXLR_AUTOTUNE_CACHE")) {
     std::ofstream f(path, std::ios::app);
     f << std::get<0>(k) << ' ' << std::get<1>(k) << ' ' << std::get<2>(k) << ' '
-      << std::get<3>(k) << ' ' << grid[0] << ' ' << grid[1] << ' ' << grid[2] << '\n';
+      << std::get<3>(k) << ' ' << std::get<4>(k) << ' ' << c.grid[0] << ' ' << c.grid[1] << ' '
+      << c.grid[2] << ' ' << c.tma << ' ' << c.ms[0] << ' ' << c.ms[1] << ' ' << c.ms[2] << '\n';
   }
 }
 
-// Times candidate grids for each kernel kind on the batch itself and keeps
-// the fastest (median of 3 after a warm-up).
-jxlr_status autotune(jxl_recon_batch* b) {
+// One kernel kind of the batch alone (k: 0 transform, 1 J.2, 2 Gaborish /
+// colour in the form tma) on grid g, on the batch's stream.  The transform
+// appends to the J.2 lists, so they restart empty; J.2 reads the lists the
+// last transform run left.
+void launch_kind(jxl_recon_batch* b, int k, int g, bool tma) {
+  if (k == 0) {
+    if (b->ne) cudaMemsetAsync(b->d_counts, 0, sizeof(unsigned) * b->ne, b->cap);
+    launch_recon_batch(b->d_rargs, b->d_ritem, b->rtotal, g, b->cap);
+  } else if (k == 1) {
+    launch_epf_work_batch(b->d_eargs, b->d_counts, b->ne, b->clamp, g, b->cap);
+  } else if (tma) {
+    launch_filter_batch_tma(b->d_fargs, b->d_fprefix, b->d_maps, b->nf, b->ftotal, g, b->d_err,
+                            b->cap);
+  } else {
+    launch_filter_batch(b->d_fargs, b->d_fprefix, b->nf, b->ftotal, g, b->cap);
+  }
+}
+
+// Times the candidate forms and grids of each kernel kind on the batch
+// itself and keeps the fastest (median of 3 after a warm-up).  Every
+// candidate computes the same bits: the grids only change which CTA takes
+// which work item, the two filter forms load the same tile with TMA or with
+// ordinary loads.  Candidates: transform one CTA per cell or 1, 2, 4 x the
+// resident CTAs; J.2 (persistent warps) 1/2, 3/4 or all of the resident
+// warps; Gaborish / colour in the TMA form on all or half of its resident
+// CTAs, or with ordinary loads on one CTA per tile or 1, 2 x the resident
+// CTAs.
+jxlr_status autotune(jxl_recon_batch* b, bool tma_allowed) {
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
-  const int kinds[3] = {0, 1, 2};
-  // the J.2 kernel and the TMA form of the filter keep their resident grids
-  const int totals[3] = {b->rtotal, 0, b->d_maps ? 0 : b->ftotal};
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
+  auto time_it = [&](int k, int g, bool tma) {
+    std::vector<float> t;
+    for (int rep = 0; rep < 4; ++rep) {
+      cudaEventRecord(e0, b->cap);
+      launch_kind(b, k, g, tma);
+      cudaEventRecord(e1, b->cap);
+      cudaEventSynchronize(e1);
+      float ms = 0;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (rep) t.push_back(ms);
+    }
+    std::sort(t.begin(), t.end());
+    return t[1];
+  };
   for (int k = 0; k < 3; ++k) {
-    if (!totals[k]) continue;
-    const int res = sms * batch_blocks_per_sm(kinds[k]);
-    std::vector<int> cand = {totals[k]};
-    for (int f : {1, 2, 4})
-      if (f * res < totals[k]) cand.push_back(f * res);
-    float best = 1e30f;
-    int bestg = totals[k];
-    for (int g : cand) {
-      int grid[3] = {b->grid[0], b->grid[1], b->grid[2]};
-      grid[k] = g;
-      std::vector<float> t;
-      for (int rep = 0; rep < 4; ++rep) {
-        cudaEventRecord(e0, b->cap);
-        if (k == 0) {
-          // the transform kernel appends to the J.2 lists: they restart empty
-          if (b->ne) cudaMemsetAsync(b->d_counts, 0, sizeof(unsigned) * b->ne, b->cap);
-          launch_recon_batch(b->d_rargs, b->d_ritem, b->rtotal, g, b->cap);
-        }
-        else launch_filter_batch(b->d_fargs, b->d_fprefix, b->nf, b->ftotal, g, b->cap);
-        cudaEventRecord(e1, b->cap);
-        cudaEventSynchronize(e1);
-        float ms = 0;
-        cudaEventElapsedTime(&ms, e0, e1);
-        if (rep) t.push_back(ms);
+    struct Cand {
+      int g;
+      bool tma;
+    };
+    std::vector<Cand> cand;
+    if (k == 0 && b->rtotal) {
+      const int res = sms * batch_blocks_per_sm(0);
+      cand.push_back({b->rtotal, false});
+      for (int f : {1, 2, 4})
+        if (f * res < b->rtotal) cand.push_back({f * res, false});
+    } else if (k == 1 && b->ne) {
+      const int res = sms * batch_blocks_per_sm(1);
+      for (int num : {2, 3, 4}) cand.push_back({std::max(1, res * num / 4), false});
+    } else if (k == 2 && b->ftotal) {
+      if (tma_allowed) {
+        const int res = sms * batch_blocks_per_sm(3);
+        cand.push_back({res, true});
+        cand.push_back({std::max(1, res / 2), true});
       }
-      std::sort(t.begin(), t.end());
-      if (t[1] < best) {
-        best = t[1];
-        bestg = g;
+      const int res = sms * batch_blocks_per_sm(2);
+      cand.push_back({b->ftotal, false});
+      for (int f : {1, 2})
+        if (f * res < b->ftotal) cand.push_back({f * res, false});
+    }
+    if (cand.empty()) continue;
+    if (k == 1) launch_kind(b, 0, b->grid[0], false);   // the lists J.2 reads
+    float best = 1e30f;
+    for (const Cand& c : cand) {
+      const float ms = time_it(k, c.g, c.tma);
+      if (ms < best) {
+        best = ms;
+        b->grid[k] = c.g;
+        if (k == 2) b->use_tma = c.tma;
       }
     }
-    b->grid[k] = bestg;
+    b->kind_ms[k] = best;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -346,6 +405,7 @@ extern "C" jxlr_status jxl_recon_batch_create(jxl_recon_ctx* ctx, const jxl_reco
   if (tma) {
     b->d_maps = base + o_tm;
     b->d_err = reinterpret_cast<unsigned*>(base + o_er);
+    b->use_tma = true;
   }
   b->d_rargs = reinterpret_cast<ReconArgs*>(base + o_r);
   b->d_ritem = reinterpret_cast<int*>(base + o_rp);
@@ -383,24 +443,38 @@ extern "C" jxlr_status jxl_recon_batch_create(jxl_recon_ctx* ctx, const jxl_reco
                                     " is ill-formed");
     }
   ctx_count_launches(ctx, static_cast<int>(n));
-  // grids: cached tuning, fresh tuning, or one CTA per work item
+  // grids and filter form: cached tuning, fresh tuning, or one CTA per work
+  // item (the J.2 kernel and the TMA form of the filter on their resident grids)
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   b->grid[0] = b->rtotal;
-  b->grid[1] = b->ne ? sms * batch_blocks_per_sm(1) : 0;   // persistent J.2 grid
-  b->grid[2] = b->d_maps ? sms * batch_blocks_per_sm(3) : b->ftotal;   // TMA form: persistent
-  const Key key(b->n, b->rtotal, b->etotal, b->ftotal);
-  const int grid_tma = b->grid[2];
-  if (tuned_lookup(key, b->grid)) {
-    if (b->d_maps) b->grid[2] = grid_tma;
+  b->grid[1] = b->ne ? sms * batch_blocks_per_sm(1) : 0;
+  b->grid[2] = b->use_tma ? sms * batch_blocks_per_sm(3) : b->ftotal;
+  for (size_t i = 0; i < n; ++i) {
+    const int dt = reqs[i].out->dtype == JXLR_OUT_U8_SRGB ? 0 : reqs[i].out->dtype == JXLR_OUT_F16_LINEAR ? 8 : 16;
+    if (((b->mix >> dt) & 0xFF) < 0xFF) b->mix += 1u << dt;
+  }
+  const Key key(b->n, b->rtotal, b->etotal, b->ftotal, b->mix);
+  Choice ch;
+  if (tuned_lookup(key, &ch) && (!ch.tma || b->d_maps)) {
+    for (int k = 0; k < 3; ++k) {
+      b->grid[k] = ch.grid[k];
+      b->kind_ms[k] = ch.ms[k];
+    }
+    b->use_tma = ch.tma != 0;
     b->autotuned = 2;
   } else if (flags & JXLR_BATCH_AUTOTUNE) {
-    jxlr_status ts = autotune(b);
+    jxlr_status ts = autotune(b, b->d_maps != nullptr);
     if (ts != JXLR_OK) {
       jxl_recon_batch_destroy(b);
       return ts;
     }
-    tuned_store(key, b->grid);
+    for (int k = 0; k < 3; ++k) {
+      ch.grid[k] = b->grid[k];
+      ch.ms[k] = b->kind_ms[k];
+    }
+    ch.tma = b->use_tma;
+    tuned_store(key, ch);
     b->autotuned = 1;
   }
   for (int k = 0; k < 3; ++k) b->grid[k] = std::max(1, b->grid[k]);
@@ -441,7 +515,9 @@ extern "C" jxlr_status jxl_recon_batch_query(const jxl_recon_batch* b, jxl_recon
   info->filter_grid = b->grid[2];
   info->kernels_per_launch = b->kernels;
   info->autotuned = b->autotuned;
-  info->filter_tma = b->d_maps != nullptr;
+  info->filter_tma = b->use_tma;
+  for (int k = 0; k < 3; ++k) info->kind_ms[k] = b->kind_ms[k];
+  info->mix = b->mix;
   return JXLR_OK;
 }
 

@@ -8,9 +8,9 @@
 // refused for want of HBM under the cap is passed over by smaller ones
 // behind it, until it has waited longer than the age bound: from then on
 // nothing behind it is admitted before it.  Admitted requests run on their
-// slots' streams and overlap on the device; the context gives a request a
-// stream of lower priority than those of the requests in flight, so the
-// older ones keep the SMs they need and the newer fill the rest.
+// slots' streams and overlap on the device; the context runs a request on a
+// stream whose priority rises with its image size, so large requests (the
+// tail of the latency) take the SMs they need and small ones fill the rest.
 // Latency = completion - enqueue (queueing included).
 #include <algorithm>
 #include <chrono>
