@@ -266,7 +266,10 @@ jxlr_status jxl_recon_destroy(jxl_recon_ctx* ctx) {
   cudaSetDevice(ctx->device);
   for (auto& s : ctx->slots) {
     if (s.stream) cudaStreamSynchronize(s.stream);
-    if (s.arena) cudaFree(s.arena);
+    if (s.arena) {
+      cudaFreeAsync(s.arena, s.stream);
+      cudaStreamSynchronize(s.stream);
+    }
     if (s.h_status) cudaFreeHost(s.h_status);
     for (auto& ev : s.ev)
       if (ev) cudaEventDestroy(ev);
@@ -336,13 +339,16 @@ jxlr_status acquire_slot(jxl_recon_ctx* ctx, size_t need, uint64_t pixels, Slot*
   Slot* best = fit ? fit : any;
   if (ctx->cap && need > ctx->cap) return fail(JXLR_ENOMEM, "request exceeds the HBM cap");
   if (!best) return fail(JXLR_EBUSY, "no free slot");
+  // the request's stream first: the arena below is freed and allocated in
+  // its order (the slot's earlier work, on whichever stream, has completed)
+  if (best->nprio) best->stream = best->pstream[size_level(pixels, best->nprio)];
   if (best->arena_bytes < need) {
     const size_t others = ctx->bytes - best->arena_bytes;
     if (ctx->cap && others + need > ctx->cap) {
       // free idle arenas before refusing
       for (auto& s : ctx->slots) {
         if (!s.busy && &s != best && s.arena) {
-          cudaFree(s.arena);
+          cudaFreeAsync(s.arena, s.stream);
           ctx->bytes -= s.arena_bytes;
           s.arena = nullptr;
           s.arena_bytes = 0;
@@ -351,14 +357,16 @@ jxlr_status acquire_slot(jxl_recon_ctx* ctx, size_t need, uint64_t pixels, Slot*
       if (ctx->bytes - best->arena_bytes + need > ctx->cap)
         return fail(JXLR_EBUSY, "not enough HBM under the cap now");
     }
+    // stream-ordered: growing an idle slot's arena does not synchronise the
+    // device (a plain cudaFree would wait for every request in flight)
     if (best->arena) {
-      cudaFree(best->arena);
+      cudaFreeAsync(best->arena, best->stream);
       ctx->bytes -= best->arena_bytes;
       best->arena = nullptr;
       best->arena_bytes = 0;
     }
     const size_t sz = align_up(need, size_t(1) << 20);
-    cudaError_t e = cudaMalloc(&best->arena, sz);
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&best->arena), sz, best->stream);
     if (e != cudaSuccess) {
       cudaGetLastError();
       return fail(JXLR_ENOMEM, std::string("device allocation failed: ") + cudaGetErrorString(e));
@@ -366,7 +374,6 @@ jxlr_status acquire_slot(jxl_recon_ctx* ctx, size_t need, uint64_t pixels, Slot*
     best->arena_bytes = sz;
     ctx->bytes += sz;
   }
-  if (best->nprio) best->stream = best->pstream[size_level(pixels, best->nprio)];
   *out = best;
   return JXLR_OK;
 }

@@ -253,15 +253,6 @@ __device__ __forceinline__ void emit4(const ColorParams& cp, const OutParams& o,
   store_px4(o, px, py, v, n);
 }
 
-// The horizontal offsets of J.2 in the order both J.2 kernels sum the 56
-// offsets (J.2.5 sums them all; a fixed order makes the kernels agree bit
-// for bit): 0, 1, -1, 2, -2, 3, -3, 4, each with the vertical offsets
-// -3 .. 3.  Pairs (ox, -ox) are adjacent so that the block-list kernel can
-// form the SADs of -ox from the sums of ox.
-__device__ __forceinline__ int j2_ox(int g) {
-  return g == 0 ? 0 : g == 7 ? 4 : (g & 1) ? (g + 1) >> 1 : -(g >> 1);
-}
-
 // J.2.2 scaled guide value in binary32, operation by operation.
 __device__ __forceinline__ float guide_scaled(const SigmaParams& sp, int c, float v) {
   return __fmul_rn(__fsub_rn(v, sp.gmin[c]), sp.gscale[c]);
@@ -1900,7 +1891,7 @@ __device__ __forceinline__ void epf_tile(const FilterArgs& a, int tbx, int tby) 
 
 #pragma unroll 1
   for (int g = 0; g < 8; ++g) {
-    const int ox = j2_ox(g);
+    const int ox = g - 3;
     // ---- step 1: horizontal 4-sums of D_o for the 7 offsets (ox, oy) ------
 #pragma unroll
     for (int oi = 0; oi < 7; ++oi) {
@@ -2401,24 +2392,17 @@ __global__ void __launch_bounds__(128, 4) k_epf(const __grid_constant__ FilterAr
 //   k_epf_work  persistent one-warp CTAs taking 2 listed blocks at a time
 //               (a group; the warps claim groups from a per-request counter):
 //               per block a window of mirrored samples and packed guide
-//               bytes (6.5, J.2.2), then the horizontal offsets in the order
-//               0, 1, -1, 2, -2, 3, -3, 4 (both J.2 kernels sum the 56
-//               offsets in this order):
-//               step 1  (for ox >= 0) the horizontal 4-sums H of the 7
+//               bytes (6.5, J.2.2), then per horizontal offset ox
+//               step 1  the horizontal 4-sums H_o of the 10 rows the block's
+//                       3x4 patches touch (block rows -1..8) for the 7
 //                       vertical offsets, as 16-bit values, one lane per
-//                       (block, window row) walking the offsets with its own
-//                       guide bytes in registers.  The patch SAD is
-//                       symmetric, SAD(p, o) = SAD(p + o, -o), so the sums
-//                       of (ox, oy) over rows and columns grown by oy and ox
-//                       also give the SADs of (-ox, -oy): the offsets with
-//                       ox < 0 (and ox = 0, oy < 0) need no sums of their
-//                       own (31 rows of sums per pixel instead of 56);
+//                       (block, row) walking the 7 offsets with its own
+//                       guide bytes in registers;
 //               step 2  one lane per half column (4 rows) of a block: the
 //                       sliding vertical 3-sums (the patch SADs) of the 7
-//                       vertical offsets, read directly or shifted, a warp
-//                       vote on which offsets give some pixel a weight above
-//                       the J.2.4 cut-off, and for those only the weights
-//                       and the J.2.5 sums.
+//                       vertical offsets, a warp vote on which offsets give
+//                       some pixel a weight above the J.2.4 cut-off, and for
+//                       those only the weights and the J.2.5 sums.
 //               Weights, cut-off and summation order are those of k_epf, so
 //               the two kernels give the same bits (an offset skipped by
 //               the vote would add exactly zero).  Warps synchronise only
@@ -2434,52 +2418,7 @@ constexpr int kLFB = 688;                         // floats per block (>= 3 kLFC
 // half-column lane groups of step 2) swap their 8-column halves, so that the
 // groups read different banks.
 __device__ __forceinline__ int lf_col(int fr, int fc) { return fc ^ (((fr >> 2) & 1) << 3); }
-constexpr int kLHR = 13;   // rows of horizontal sums per block and vertical offset (10 + |oy|)
-constexpr int kLHC = 12;   // their columns (8 + ox, padded)
-
-// Window rows (origin -4) of the horizontal sums of offset (ox, oy), ox >= 0:
-// the block's patch rows -1 .. 8 for the offset itself and, for ox in 1..3
-// and for ox = 0 (oy > 0), also rows -1 - oy .. 8 - oy, where the sums at
-// columns shifted by -ox are those of (-ox, -oy) at the block's pixels.
-__device__ __forceinline__ int hrow_lo(int ox, int oy) { return ox == 4 ? 3 : min(3, 3 - oy); }
-__device__ __forceinline__ int hrow_hi(int ox, int oy) { return ox == 4 ? 12 : max(12, 12 - oy); }
-
-// Step 1 for the horizontal offset OX >= 0 (OX = 0: vertical offsets 1..3
-// only): lane (block, window row j) forms, for each vertical offset whose
-// rows include j, the horizontal 4-sums of the channel SADs of its row at
-// block columns X0 .. 7 (X0 = -OX for OX in 1..3, else 0), stored at column
-// x - X0 of row j - hrow_lo.
-template <int OX>
-__device__ __forceinline__ void epf_hsums(const uint32_t (*G)[kLGS], uint16_t (*H)[kLHR][kLHC],
-                                          int j) {
-  constexpr int X0 = (OX >= 1 && OX <= 3) ? -OX : 0;
-  constexpr int NX = 8 - X0;       // output columns
-  constexpr int ND = NX + 3;       // channel SADs per row
-  uint32_t own[ND];
-#pragma unroll
-  for (int i = 0; i < ND; ++i) own[i] = G[j][X0 + 3 + i];    // block column X0 - 1 + i
-#pragma unroll
-  for (int oi = 0; oi < 7; ++oi) {
-    const int oy = oi - 3;
-    if (OX == 0 && oy <= 0) continue;
-    const int lo = hrow_lo(OX, oy), hi = hrow_hi(OX, oy);
-    if (j < lo || j > hi) continue;
-    const uint32_t* nb = &G[j + oy][X0 + 3 + OX];
-    uint32_t d[ND];   // sum over the 3 channel bytes of |own - neighbour|
-#pragma unroll
-    for (int i = 0; i < ND; ++i) d[i] = __vsadu4(own[i], nb[i]);
-    uint32_t h[kLHC];
-    h[0] = d[0] + d[1] + d[2] + d[3];
-#pragma unroll
-    for (int i = 1; i < NX; ++i) h[i] = h[i - 1] + d[i + 3] - d[i - 1];
-#pragma unroll
-    for (int i = NX; i < kLHC; ++i) h[i] = 0;
-    uint2* dst = reinterpret_cast<uint2*>(&H[oi][j - lo][0]);
-    dst[0] = make_uint2(h[0] | (h[1] << 16), h[2] | (h[3] << 16));
-    dst[1] = make_uint2(h[4] | (h[5] << 16), h[6] | (h[7] << 16));
-    if (NX > 8) dst[2] = make_uint2(h[8] | (h[9] << 16), h[10] | (h[11] << 16));
-  }
-}
+constexpr int kLHR = 10;                          // rows of horizontal sums per block
 
 // The groups of one image's list (total listed blocks) a warp takes: g0,
 // g0 + gs, ... or, with next (a zeroed counter), the ones it claims there one
@@ -2490,7 +2429,7 @@ __device__ __forceinline__ void epf_work_groups(const FilterArgs& a, const int* 
                                                 unsigned* next = nullptr) {
   __shared__ uint32_t G[kLG][kLGH][kLGS];
   __shared__ float F[kLG][kLFB];
-  __shared__ __align__(16) uint16_t Hb[kLG][7][kLHR][kLHC];
+  __shared__ __align__(16) uint16_t Hb[kLG][7][kLHR][8];
   const int lane = threadIdx.x;
   const int C = 0x3F800000;
   const int T16 = static_cast<int>((a.wmin_bits + 0xFFFFu) & 0xFFFF0000u);
@@ -2559,53 +2498,46 @@ __device__ __forceinline__ void epf_work_groups(const FilterArgs& a, const int* 
     float ax[4], ay[4], ab[4], ws[4];
 #pragma unroll
     for (int r = 0; r < 4; ++r) { ax[r] = ay[r] = ab[r] = ws[r] = 0.f; }
-    // step 1: lane = (block k1, window row j1)
-    const int k1 = lane >> 4, j1 = lane & 15;
-    const bool row1 = k1 < nb;
-    bool dense = false;     // step 2: every offset of the last horizontal offset was live
+    // step 1: lane = (block k1, row j1) for the first 10 nb lanes
+    const int k1 = lane >= kLHR ? 1 : 0, j1 = lane - kLHR * k1;
+    const bool row1 = lane < kLHR * nb;
+    bool dense = false;     // step 2: every offset of the last ox was live
     __syncwarp();
 
 #pragma unroll 1
     for (int g = 0; g < 8; ++g) {
-      const int ox = j2_ox(g);
-      // ---- step 1 (ox >= 0): the sums of (ox, oy), which also serve (-ox, -oy)
-      if (ox >= 0 && row1) {
-        switch (ox) {
-          case 0: epf_hsums<0>(G[k1], Hb[k1], j1); break;
-          case 1: epf_hsums<1>(G[k1], Hb[k1], j1); break;
-          case 2: epf_hsums<2>(G[k1], Hb[k1], j1); break;
-          case 3: epf_hsums<3>(G[k1], Hb[k1], j1); break;
-          default: epf_hsums<4>(G[k1], Hb[k1], j1); break;
+      const int ox = g - 3;
+      // ---- step 1: lane (block k1, row j1) walks the 7 offsets oy ----------
+      if (row1) {
+        uint32_t own[11];
+#pragma unroll
+        for (int i = 0; i < 11; ++i) own[i] = G[k1][j1 + 3][3 + i];
+#pragma unroll
+        for (int oi = 0; oi < 7; ++oi) {
+          const uint32_t* nbp = &G[k1][j1 + oi][3 + ox];
+          uint32_t d[11];   // sum over the 3 channel bytes of |own - neighbour|
+#pragma unroll
+          for (int i = 0; i < 11; ++i) d[i] = __vsadu4(own[i], nbp[i]);
+          uint32_t h[8];
+          h[0] = d[0] + d[1] + d[2] + d[3];
+#pragma unroll
+          for (int i = 1; i < 8; ++i) h[i] = h[i - 1] + d[i + 3] - d[i - 1];
+          *reinterpret_cast<uint4*>(&Hb[k1][oi][j1][0]) =
+              make_uint4(h[0] | (h[1] << 16), h[2] | (h[3] << 16), h[4] | (h[5] << 16),
+                         h[6] | (h[7] << 16));
         }
       }
       __syncwarp();
 
       // ---- step 2 ----------------------------------------------------------
-      // the patch SADs of the lane's 4 pixels for the 7 offsets (ox, oy):
-      // from the sums of (ox, oy) (ox > 0, or ox = 0 and oy > 0), or those of
-      // (-ox, -oy) at rows shifted by oy and columns by ox (zero for the
-      // centre); then which offsets give some pixel of the warp a weight
-      // above the cut-off
-      const int oxs = ox < 0 ? -ox : ox;                 // horizontal offset of the sums
-      const int x0s = (oxs >= 1 && oxs <= 3) ? -oxs : 0;
+      // the patch SADs of the lane's 4 pixels for the 7 offsets, and which
+      // offsets give some pixel of the warp a weight above the cut-off
       int sad[7][4];
 #pragma unroll
       for (int oi = 0; oi < 7; ++oi) {
-        const int oy = oi - 3;
-        const bool direct = ox > 0 || (ox == 0 && oy > 0);
-        const int oys = direct ? oy : -oy;               // vertical offset of the sums
-        const int si = oys + 3;
-        const int jb = direct ? r0 + 3 : r0 + 3 - oys;   // window row of pixel row r0 - 1
-        const int col = direct ? cx - x0s : cx;
-        const int lo = hrow_lo(oxs, oys);
         int hv[6];
-        if (ox == 0 && oy == 0) {
 #pragma unroll
-          for (int jj = 0; jj < 6; ++jj) hv[jj] = 0;
-        } else {
-#pragma unroll
-          for (int jj = 0; jj < 6; ++jj) hv[jj] = strip ? Hb[sk][si][jb + jj - lo][col] : 0;
-        }
+        for (int jj = 0; jj < 6; ++jj) hv[jj] = strip ? Hb[sk][oi][r0 + jj][cx] : 0;
         int v = hv[0] + hv[1] + hv[2];
 #pragma unroll
         for (int r = 0; r < 4; ++r) {

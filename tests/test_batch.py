@@ -38,7 +38,9 @@ def test_batch_equals_per_image(autotune):
         b = ctx.batch(jobs, autotune=autotune)
         info = b.info()
         assert info["images"] == len(jobs) and info["kernels_per_launch"] == 3
-        assert info["filter_tma"] == 1             # every scratch allows TMA tile loads
+        # every scratch allows TMA tile loads: the untuned batch takes them;
+        # the autotuner may choose either form (the same bits)
+        assert info["filter_tma"] == 1 or autotune
         stream = torch.cuda.Stream()
         for rep in range(2):                       # graph replayed twice
             b.launch(stream.cuda_stream)
