@@ -315,6 +315,9 @@ typedef struct jxl_recon_server jxl_recon_server;
 typedef struct {
   double age_bound_ms;     /* longest wait a refused request lets others pass   */
   int bypass;              /* 0: strict arrival order                           */
+  double exclusive_mpx;    /* requests of at least this many Mpx run alone: one
+                              is admitted only onto an idle device (the queue
+                              behind it waits too) and nothing joins it; 0: off */
 } jxl_recon_server_config;
 jxlr_status jxl_recon_server_start(jxl_recon_ctx* ctx, const jxl_recon_server_config* cfg,
                                    jxl_recon_server** out);
@@ -324,7 +327,8 @@ jxlr_status jxl_recon_server_wait(jxl_recon_server* server, uint64_t id, int64_t
                                   double* latency_ms);
 jxlr_status jxl_recon_server_stop(jxl_recon_server* server, jxl_recon_serve_stats* stats);
 
-/* Replay of an arrival schedule through a request server (age bound 5 ms):
+/* Replay of an arrival schedule through a request server (age bound 5 ms,
+ * images of 8 Mpx and more alone):
  * the calling thread enqueues reqs[0..n) at arrival_s[i] seconds after the
  * call (non-decreasing) and waits for all.  latency_ms[i] receives
  * completion - arrival of request i (queueing included).  With max_slots = 1

@@ -97,7 +97,8 @@ class ServeStats(ctypes.Structure):
 
 
 class ServerConfig(ctypes.Structure):
-    _fields_ = [("age_bound_ms", ctypes.c_double), ("bypass", ctypes.c_int)]
+    _fields_ = [("age_bound_ms", ctypes.c_double), ("bypass", ctypes.c_int),
+                ("exclusive_mpx", ctypes.c_double)]
 
 
 def _stats_dict(stats):
@@ -350,10 +351,10 @@ class Context:
             raise JxlrError(st, self.last_error())
         return np.array(lat[:]), _stats_dict(stats)
 
-    def server(self, age_bound_ms=5.0, bypass=True):
+    def server(self, age_bound_ms=5.0, bypass=True, exclusive_mpx=0.0):
         """A request server on this context (a native thread that admits
         enqueued requests as slots and HBM free up)."""
-        return Server(self, age_bound_ms, bypass)
+        return Server(self, age_bound_ms, bypass, exclusive_mpx)
 
     def batch(self, jobs, autotune=True, plain_loads=False):
         """A multi-image batch (CUDA graph) over device-resident jobs;
@@ -408,11 +409,11 @@ def requests(jobs):
 class Server:
     """jxl_recon_server_*: enqueue from any thread, wait per request."""
 
-    def __init__(self, ctx, age_bound_ms=5.0, bypass=True):
+    def __init__(self, ctx, age_bound_ms=5.0, bypass=True, exclusive_mpx=0.0):
         self.lib = ctx.lib
         self.ctx = ctx
         h = ctypes.c_void_p()
-        cfg = ServerConfig(age_bound_ms, int(bypass))
+        cfg = ServerConfig(age_bound_ms, int(bypass), exclusive_mpx)
         self.lib.jxl_recon_server_start.argtypes = [ctypes.c_void_p, ctypes.POINTER(ServerConfig),
                                                     ctypes.POINTER(ctypes.c_void_p)]
         self.lib.jxl_recon_server_enqueue.argtypes = [ctypes.c_void_p, ctypes.POINTER(Request),

@@ -141,3 +141,30 @@ def test_server_admits_past_a_request_that_does_not_fit():
         for (img, params, out, dtype), want in zip(jobs, alone):
             np.testing.assert_array_equal(out.cpu().numpy(), want)
             out.zero_()
+
+
+def test_server_runs_large_requests_alone():
+    """With exclusive_mpx, a request of that size is admitted only onto an
+    idle device and nothing joins it: with large requests enqueued among
+    small ones, at most one request is in flight whenever a large one is,
+    which shows as max_in_flight 1 when every request is large."""
+    import torch
+    from paper_1908_03565_gb300 import binding as B
+    big = [B.to_device(synth.make_image(1024, 1024, 970 + i), torch) for i in range(4)]
+    p = B.filter_defaults(epf=1, gab=1)
+    jobs = [(img, p, torch.zeros((1024, 1024, 3), dtype=torch.uint8, device="cuda"),
+             B.OUT_U8_SRGB) for img in big]
+    with B.Context(max_slots=4) as ctx:
+        srv = ctx.server(exclusive_mpx=1.0)
+        ids = [srv.enqueue(j) for j in jobs]
+        for i in ids:
+            srv.wait(i)
+        stats = srv.stop()
+    assert stats["completed"] == 4 and stats["max_in_flight"] == 1
+    with B.Context(max_slots=4) as ctx:
+        srv = ctx.server(exclusive_mpx=0.0)
+        ids = [srv.enqueue(j) for j in jobs]
+        for i in ids:
+            srv.wait(i)
+        stats = srv.stop()
+    assert stats["completed"] == 4 and stats["max_in_flight"] > 1
