@@ -179,12 +179,27 @@ __device__ __forceinline__ void pair4(const float* src, int sstride, float* dst,
 __device__ __forceinline__ void xyb_to_rgb01(const ColorParams& cp, float X, float Y, float B,
                                              float& r, float& g, float& b) {
   const float rg = Y + X, gg = Y - X, bg = B;
-  const float mr = rg * rg * rg + cp.bias[0];
-  const float mg = gg * gg * gg + cp.bias[1];
-  const float mb = bg * bg * bg + cp.bias[2];
+  const float mr = fmaf(rg * rg, rg, cp.bias[0]);
+  const float mg = fmaf(gg * gg, gg, cp.bias[1]);
+  const float mb = fmaf(bg * bg, bg, cp.bias[2]);
   r = fmaf(cp.m[0], mr, fmaf(cp.m[1], mg, cp.m[2] * mb));
   g = fmaf(cp.m[3], mr, fmaf(cp.m[4], mg, cp.m[5] * mb));
   b = fmaf(cp.m[6], mr, fmaf(cp.m[7], mg, cp.m[8] * mb));
+}
+
+// The same for two pixels at once (paired binary32 operations round each
+// lane as the scalar ones do; Y - X as fma(X, -1, Y), which is exact before
+// its one rounding).
+__device__ __forceinline__ float2 f2(float v) { return make_float2(v, v); }
+__device__ __forceinline__ void xyb_to_rgb01_x2(const ColorParams& cp, float2 X, float2 Y,
+                                                float2 B, float2& r, float2& g, float2& b) {
+  const float2 rg = __fadd2_rn(Y, X), gg = __ffma2_rn(X, f2(-1.f), Y), bg = B;
+  const float2 mr = __ffma2_rn(__fmul2_rn(rg, rg), rg, f2(cp.bias[0]));
+  const float2 mg = __ffma2_rn(__fmul2_rn(gg, gg), gg, f2(cp.bias[1]));
+  const float2 mb = __ffma2_rn(__fmul2_rn(bg, bg), bg, f2(cp.bias[2]));
+  r = __ffma2_rn(f2(cp.m[0]), mr, __ffma2_rn(f2(cp.m[1]), mg, __fmul2_rn(f2(cp.m[2]), mb)));
+  g = __ffma2_rn(f2(cp.m[3]), mr, __ffma2_rn(f2(cp.m[4]), mg, __fmul2_rn(f2(cp.m[5]), mb)));
+  b = __ffma2_rn(f2(cp.m[6]), mr, __ffma2_rn(f2(cp.m[7]), mg, __fmul2_rn(f2(cp.m[8]), mb)));
 }
 
 __device__ __forceinline__ uint32_t srgb8(float v) {
@@ -242,12 +257,19 @@ __device__ __forceinline__ void store_px4(const OutParams& o, int px, int py, co
 __device__ __forceinline__ void emit4(const ColorParams& cp, const OutParams& o, int px, int py,
                                       int n, const float* X, const float* Y, const float* B) {
   float v[12];
+  if (o.dtype == 3) {
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    if (o.dtype == 3) {
+    for (int i = 0; i < 4; ++i) {
       v[3 * i] = X[i]; v[3 * i + 1] = Y[i]; v[3 * i + 2] = B[i];
-    } else {
-      xyb_to_rgb01(cp, X[i], Y[i], B[i], v[3 * i], v[3 * i + 1], v[3 * i + 2]);
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < 4; i += 2) {
+      float2 r, g, b;
+      xyb_to_rgb01_x2(cp, make_float2(X[i], X[i + 1]), make_float2(Y[i], Y[i + 1]),
+                      make_float2(B[i], B[i + 1]), r, g, b);
+      v[3 * i] = r.x; v[3 * i + 1] = g.x; v[3 * i + 2] = b.x;
+      v[3 * i + 3] = r.y; v[3 * i + 4] = g.y; v[3 * i + 5] = b.y;
     }
   }
   store_px4(o, px, py, v, n);
@@ -2050,12 +2072,22 @@ __device__ __forceinline__ void gab4_finish(const FilterArgs& a, int gx, int gy,
   float o[3][4];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
+    // pixels p and p + 1 as pairs
 #pragma unroll
-    for (int p = 0; p < 4; ++p) {
-      const float edge = (w[c][0][p + 1] + w[c][2][p + 1]) + (w[c][1][p] + w[c][1][p + 2]);
-      const float corner = (w[c][0][p] + w[c][0][p + 2]) + (w[c][2][p] + w[c][2][p + 2]);
-      o[c][p] = a.gab ? fmaf(a.gw[c][0], w[c][1][p + 1], fmaf(a.gw[c][1], edge, a.gw[c][2] * corner))
-                      : w[c][1][p + 1];
+    for (int p = 0; p < 4; p += 2) {
+      auto at = [&](int r, int i) { return make_float2(w[c][r][i], w[c][r][i + 1]); };
+      const float2 centre = at(1, p + 1);
+      float2 v = centre;
+      if (a.gab) {
+        const float2 edge = __fadd2_rn(__fadd2_rn(at(0, p + 1), at(2, p + 1)),
+                                       __fadd2_rn(at(1, p), at(1, p + 2)));
+        const float2 corner = __fadd2_rn(__fadd2_rn(at(0, p), at(0, p + 2)),
+                                         __fadd2_rn(at(2, p), at(2, p + 2)));
+        v = __ffma2_rn(f2(a.gw[c][0]), centre,
+                       __ffma2_rn(f2(a.gw[c][1]), edge, __fmul2_rn(f2(a.gw[c][2]), corner)));
+      }
+      o[c][p] = v.x;
+      o[c][p + 1] = v.y;
     }
   }
   if (a.noise) {
@@ -2495,9 +2527,11 @@ __device__ __forceinline__ void epf_work_groups(const FilterArgs& a, const int* 
       Mneg = -M;
       vmax = (M < 0 && C >= T16) ? (C - T16) / (-M) : -1;
     }
-    float ax[4], ay[4], ab[4], ws[4];
+    // J.2.5 sums of the lane's pixels r = 2 q and 2 q + 1 as pairs: paired
+    // binary32 operations round each lane as the scalar ones do
+    float2 ax[2], ay[2], ab[2], ws[2];
 #pragma unroll
-    for (int r = 0; r < 4; ++r) { ax[r] = ay[r] = ab[r] = ws[r] = 0.f; }
+    for (int q = 0; q < 2; ++q) ax[q] = ay[q] = ab[q] = ws[q] = make_float2(0.f, 0.f);
     // step 1: lane = (block k1, row j1) for the first 10 nb lanes
     const int k1 = lane >= kLHR ? 1 : 0, j1 = lane - kLHR * k1;
     const bool row1 = lane < kLHR * nb;
@@ -2576,6 +2610,7 @@ __device__ __forceinline__ void epf_work_groups(const FilterArgs& a, const int* 
 #pragma unroll
         for (int oi = 0; oi < 7; ++oi) {
           if (!((live >> oi) & 1u)) continue;
+          float wr[4];
 #pragma unroll
           for (int r = 0; r < 4; ++r) {
             const int v = sad[oi][r];
@@ -2588,11 +2623,15 @@ __device__ __forceinline__ void epf_work_groups(const FilterArgs& a, const int* 
               bits = (0x3F800000u - static_cast<uint32_t>(v) * static_cast<uint32_t>(Mneg)) &
                      0xFFFF0000u & ~static_cast<uint32_t>((vmax - v) >> 31);
             }
-            const float w = __uint_as_float(bits);
-            ax[r] = fmaf(w, sx[r + oi], ax[r]);
-            ay[r] = fmaf(w, sy[r + oi], ay[r]);
-            ab[r] = fmaf(w, sb[r + oi], ab[r]);
-            ws[r] += w;
+            wr[r] = __uint_as_float(bits);
+          }
+#pragma unroll
+          for (int q = 0; q < 2; ++q) {
+            const float2 w = make_float2(wr[2 * q], wr[2 * q + 1]);
+            ax[q] = __ffma2_rn(w, make_float2(sx[2 * q + oi], sx[2 * q + 1 + oi]), ax[q]);
+            ay[q] = __ffma2_rn(w, make_float2(sy[2 * q + oi], sy[2 * q + 1 + oi]), ay[q]);
+            ab[q] = __ffma2_rn(w, make_float2(sb[2 * q + oi], sb[2 * q + 1 + oi]), ab[q]);
+            ws[q] = __fadd2_rn(ws[q], w);
           }
         }
       }
@@ -2606,11 +2645,12 @@ __device__ __forceinline__ void epf_work_groups(const FilterArgs& a, const int* 
         for (int r = 0; r < 4; ++r) {
           const int gy = 8 * sby + r0 + r;
           if (gy >= a.ys) break;
-          const float inv = 1.f / ws[r];
+          const float2 pw = ws[r >> 1], px = ax[r >> 1], py = ay[r >> 1], pb = ab[r >> 1];
+          const float inv = 1.f / ((r & 1) ? pw.y : pw.x);
           float* o = a.epf_out + static_cast<size_t>(gy) * a.ors + gx;
-          o[0] = ax[r] * inv;
-          o[a.ops] = ay[r] * inv;
-          o[2 * a.ops] = ab[r] * inv;
+          o[0] = ((r & 1) ? px.y : px.x) * inv;
+          o[a.ops] = ((r & 1) ? py.y : py.x) * inv;
+          o[2 * a.ops] = ((r & 1) ? pb.y : pb.x) * inv;
         }
       }
     }
