@@ -2532,33 +2532,46 @@ __device__ __forceinline__ void epf_work_groups(const FilterArgs& a, const int* 
     float2 ax[2], ay[2], ab[2], ws[2];
 #pragma unroll
     for (int q = 0; q < 2; ++q) ax[q] = ay[q] = ab[q] = ws[q] = make_float2(0.f, 0.f);
-    // step 1: lane = (block k1, row j1) for the first 10 nb lanes
-    const int k1 = lane >= kLHR ? 1 : 0, j1 = lane - kLHR * k1;
-    const bool row1 = lane < kLHR * nb;
+    // step 1: 140 units (block, row, vertical offset) over the 32 lanes in 5
+    // rounds.  Lanes 0..19 = (block, row) take the offsets oy = -3 .. 1 of
+    // their row (rounds 0..4, own guide bytes loaded once); lanes 20..31
+    // take the (block, row) pairs 0..11 and then 12..19 for oy = 2 and 3
+    // (rounds 0, 1 and 2, 3, own bytes loaded again at round 2).
+    const bool grpA = lane < 2 * kLHR;
+    const int pa = grpA ? lane : lane - 2 * kLHR;       // (block, row) pair of rounds 0, 1
+    const int pb = grpA ? lane : lane - 2 * kLHR + 12;  // ... of rounds 2, 3
     bool dense = false;     // step 2: every offset of the last ox was live
     __syncwarp();
 
 #pragma unroll 1
     for (int g = 0; g < 8; ++g) {
       const int ox = g - 3;
-      // ---- step 1: lane (block k1, row j1) walks the 7 offsets oy ----------
-      if (row1) {
+      // ---- step 1 --------------------------------------------------------------
+      {
         uint32_t own[11];
 #pragma unroll
-        for (int i = 0; i < 11; ++i) own[i] = G[k1][j1 + 3][3 + i];
+        for (int t = 0; t < 5; ++t) {
+          const int pr = t < 2 ? pa : pb;             // (block, row) of this lane and round
+          const int k1 = pr >= kLHR ? 1 : 0, j1 = pr - kLHR * k1;
+          const int oi = grpA ? t : 5 + (t & 1);
+          const bool on = k1 < nb && (grpA || (t < 4 && pr < 2 * kLHR));
+          if (t == 0 || t == 2) {
 #pragma unroll
-        for (int oi = 0; oi < 7; ++oi) {
-          const uint32_t* nbp = &G[k1][j1 + oi][3 + ox];
-          uint32_t d[11];   // sum over the 3 channel bytes of |own - neighbour|
+            for (int i = 0; i < 11; ++i) own[i] = on ? G[k1][j1 + 3][3 + i] : 0u;
+          }
+          if (on) {
+            const uint32_t* nbp = &G[k1][j1 + oi][3 + ox];
+            uint32_t d[11];   // sum over the 3 channel bytes of |own - neighbour|
 #pragma unroll
-          for (int i = 0; i < 11; ++i) d[i] = __vsadu4(own[i], nbp[i]);
-          uint32_t h[8];
-          h[0] = d[0] + d[1] + d[2] + d[3];
+            for (int i = 0; i < 11; ++i) d[i] = __vsadu4(own[i], nbp[i]);
+            uint32_t h[8];
+            h[0] = d[0] + d[1] + d[2] + d[3];
 #pragma unroll
-          for (int i = 1; i < 8; ++i) h[i] = h[i - 1] + d[i + 3] - d[i - 1];
-          *reinterpret_cast<uint4*>(&Hb[k1][oi][j1][0]) =
-              make_uint4(h[0] | (h[1] << 16), h[2] | (h[3] << 16), h[4] | (h[5] << 16),
-                         h[6] | (h[7] << 16));
+            for (int i = 1; i < 8; ++i) h[i] = h[i - 1] + d[i + 3] - d[i - 1];
+            *reinterpret_cast<uint4*>(&Hb[k1][oi][j1][0]) =
+                make_uint4(h[0] | (h[1] << 16), h[2] | (h[3] << 16), h[4] | (h[5] << 16),
+                           h[6] | (h[7] << 16));
+          }
         }
       }
       __syncwarp();
