@@ -330,23 +330,25 @@ def _through_l2(x, dx, p):
     return tol
 
 
-def rgb_tolerance(x, m, p):
+def rgb_tolerance(x, m, p, rel=LOCAL_REL):
     """Per-sample bound for linear RGB in [0, 1] at XYB samples x (3, h, w):
-    TOL01 plus the XYB bound XYB_TOL + LOCAL_REL * m (m from local_mag)
-    carried through L.2 by its Jacobian.  Where the XYB samples are O(1)
-    the added term is small; it grows where the synthetic coefficients meet
-    large default matrix entries and samples reach 1e2..1e4."""
-    return TOL01 + _through_l2(x, XYB_TOL + LOCAL_REL * m, p)
+    TOL01 plus the XYB bound XYB_TOL + rel * m (m from local_mag) carried
+    through L.2 by its Jacobian.  Where the XYB samples are O(1) the added
+    term is small; it grows where the synthetic coefficients meet large
+    default matrix entries and samples reach 1e2..1e4."""
+    return TOL01 + _through_l2(x, XYB_TOL + rel * m, p)
 
 
-def rgb_attainable(x, m, p):
-    """The RGB error that binary32 reconstruction can be held to at XYB
-    samples x: ERR_REL * m (+ 1e-7) carried through L.2.  Where it is within
-    TOL01 the flat 1e-4 bound applies."""
-    return _through_l2(x, ERR_REL * m + 1e-7, p)
+def rgb_attainable(x, m, p, err_rel=ERR_REL):
+    """The RGB error that the reconstruction can be held to at XYB samples x:
+    err_rel * m (+ 1e-7) carried through L.2 (err_rel: the path's XYB error
+    relative to the local magnitude).  Where it is within TOL01 the flat
+    1e-4 bound applies."""
+    return _through_l2(x, err_rel * m + 1e-7, p)
 
 
-def assert_from_scratch(img, ref, gpu_xyb, f32, u8, p, name, region=None, relaxed_max=0.01):
+def assert_from_scratch(img, ref, gpu_xyb, f32, u8, p, name, region=None, relaxed_max=0.01,
+                        xyb_rel=LOCAL_REL, err_rel=ERR_REL):
     """The library's output against the oracle's, both from the coefficients.
 
     ``ref``: oracle.recon.reconstruct of ``img``; ``gpu_xyb``: the library's
@@ -360,20 +362,22 @@ def assert_from_scratch(img, ref, gpu_xyb, f32, u8, p, name, region=None, relaxe
     [0, 1] by more than that bound are counted and must be at most
     ``relaxed_max`` of them (None: the caller checks the counts returned);
     excluded pixels must be rare (assert_rare).  Returns (excluded pixels,
-    decisions taken differently, relaxed samples counted, samples)."""
+    decisions taken differently, relaxed samples counted, samples).
+    ``xyb_rel`` / ``err_rel``: the path's XYB bound and error model relative
+    to the local magnitude (wider for the tensor-core path)."""
     ys, xs = img['ysize'], img['xsize']
     if region is None:
         region = (0, 0, xs, ys)
     x0, y0, x1, y1 = region
     ref_xyb = ref['xyb_padded'][:, :ys, :xs]
-    assert_xyb_close(gpu_xyb, ref_xyb)
+    assert_xyb_close(gpu_xyb, ref_xyb, rel=xyb_rel)
     amb, nd = (undetermined(img, ref_xyb, gpu_xyb, p, p.gab, region) if p.epf
                else (np.zeros((y1 - y0, x1 - x0), bool), 0))
     ok = np.broadcast_to(~amb[..., None], (y1 - y0, x1 - x0, 3))
     rx = ref['xyb'][:, y0:y1, x0:x1]
     mag = local_mag(ref['xyb'], ref_xyb)[:, y0:y1, x0:x1]
-    tol = rgb_tolerance(rx, mag, p)
-    plain = ok & (rgb_attainable(rx, mag, p) <= TOL01)
+    tol = rgb_tolerance(rx, mag, p, xyb_rel)
+    plain = ok & (rgb_attainable(rx, mag, p, err_rel) <= TOL01)
     relaxed = ok & ~plain
     want01 = ref['rgb01'][y0:y1, x0:x1]
     err = np.abs(np.clip(f32, 0, 1) - np.clip(want01, 0, 1))
