@@ -484,6 +484,77 @@ def test_4096_windows_from_scratch(B, ctx):
     assert amb / (n // 3) <= AMBIG_MAX or nd <= 2
 
 
+def _tiled_image(base, xs, ys):
+    """base (a square image whose side is a multiple of 64) repeated to cover
+    xs x ys: every varblock and CfL tile of base stays whole, so the result
+    is a well-formed image whose every 64-aligned crop is one base would give
+    at the same place modulo its side."""
+    s = base['xsize']
+    assert base['ysize'] == s and s % 64 == 0
+    wp, hp = (xs + 7) // 8 * 8, (ys + 7) // 8 * 8
+    assert hp % 32 == 0   # the last row of varblocks whole
+    nx, ny = -(-wp // s), -(-hp // s)
+    col = np.tile(base['coeffs'], (1, ny, 1))[:, :hp]
+    coeffs = np.empty((3, hp, wp), np.int16)
+    for j in range(nx):
+        w = min(s, wp - j * s)
+        coeffs[:, :, j * s:j * s + w] = col[:, :, :w]
+    del col
+
+    def per_block(a, k):
+        return np.ascontiguousarray(np.tile(a, (ny, nx) + (1,) * (a.ndim - 2))[:hp // k, :wp // k])
+    return {'xsize': xs, 'ysize': ys, 'coeffs': coeffs, 'vmap': per_block(base['vmap'], 8),
+            'acmul': per_block(base['acmul'], 8), 'sharpness': per_block(base['sharpness'], 8),
+            'cfl': per_block(base['cfl'], 64)}
+
+
+def test_widest_image_past_2e31_samples(B, ctx):
+    """The largest width the library takes (65536) at 10941 rows: 717 Mpx,
+    2.15 G samples per planar image, so sample offsets in the third plane
+    and in the interleaved outputs pass 2^31 (and byte offsets of the f32
+    output 2^32).  The input repeats a 2048x2048 image of the workload's
+    statistics (seed 2000) so that it is made in seconds; EPF + Gaborish,
+    XYB, f32 and u8 outputs.  The oracle from the coefficients on 64x64
+    windows at the corners, across the repeat seams and in the last rows
+    (ragged: 10941 is not a multiple of 8), as in the 4096^2 test."""
+    import torch
+    xs, ys = 65536, 10941
+    img = _tiled_image(synth.make_image(2048, 2048, 2000), xs, ys)
+    p, lp = params_pair(B, epf=True, gab=True)
+    wins = [(0, 0), (xs - 64, 0), (0, 10880), (xs - 64, 10880), (32768 - 64, 10880),
+            (2048 - 64, 2048 - 64), (xs - 2048, 8192), (40960, 6144)]
+    outs = {}
+    dimg = B.to_device(img, torch)
+    for dt, tdt in ((XYB, torch.float32), (F32, torch.float32), (U8, torch.uint8)):
+        o = torch.empty((ys, xs, 3), dtype=tdt, device="cuda")
+        ctx.poll(ctx.submit(dimg, params_pair(B)[1] if dt == XYB else lp, o, dt, on_device=True))
+        if dt == XYB:   # the windows' crops (margin 64)
+            outs[dt] = {w: o[max(0, w[1] - 64):w[1] + 128, max(0, w[0] - 64):w[0] + 128].cpu().numpy()
+                        for w in wins}
+        else:
+            outs[dt] = {w: o[w[1]:w[1] + 64, w[0]:w[0] + 64].cpu().numpy() for w in wins}
+        del o
+    del dimg
+    torch.cuda.empty_cache()
+    tot = np.zeros(4, np.int64)
+    for wx, wy in wins:
+        cx0, cy0 = max(0, wx - 64), max(0, wy - 64)
+        sub = crop_input(img, cx0, cy0, wx + 128, wy + 128)
+        ref = R.reconstruct(sub, p)
+        h, w = min(64, ys - wy), min(64, xs - wx)
+        region = (wx - cx0, wy - cy0, wx - cx0 + w, wy - cy0 + h)
+        gx = outs[XYB][(wx, wy)][:sub['ysize'], :sub['xsize']].transpose(2, 0, 1)
+        assert gx.shape[1:] == (sub['ysize'], sub['xsize'])
+        tot += assert_from_scratch(sub, ref, gx, outs[F32][(wx, wy)], outs[U8][(wx, wy)], p,
+                                   f"65536x10941 window ({wx}, {wy})", region=region,
+                                   relaxed_max=None)
+    amb, nd, live, n = (int(v) for v in tot)
+    print(f"65536x10941 windows: undetermined {amb} of {n // 3} pixels ({nd} decisions), "
+          f"relaxed samples not clamped away {live / n:.4f}")
+    assert live / n <= WORKLOAD_RELAXED
+    assert amb / (n // 3) <= AMBIG_MAX or nd <= 2
+
+
 # ---------------------------------------------------------------------------
 # boundary behaviour
 # ---------------------------------------------------------------------------
