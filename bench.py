@@ -210,22 +210,21 @@ def serve_leg(binding, torch, n_req, loads, pool_n=48, seed=4000, slots=8,
     return res
 
 
-def batch_leg(binding, torch, n_img=512, pool_n=64, seed=3000, reps=10):
-    """Multi-image batching: 512 images with sides log-uniform in
-    [64, 2048] (multiples of 8; drawn from a pool of 64 distinct images with
-    the main workload's statistics), EPF + Gaborish, half u8 sRGB and half
-    f16 linear outputs; one multi-image launch per kernel kind, autotuned grids, replayed
-    as a CUDA graph; against the plain path (one submit + poll per image)."""
+def batch_leg(binding, torch, n_img=512, seed=3000, reps=10):
+    """Multi-image batching: 512 distinct images with sides log-uniform in
+    [64, 2048] (multiples of 8) and the main workload's statistics (image i
+    from seed 3000 + i), EPF + Gaborish, half u8 sRGB and half f16 linear
+    outputs; one multi-image launch per kernel kind, autotuned grids,
+    replayed as a CUDA graph; against the plain path (one submit + poll per
+    image)."""
     import math
     from paper_1908_03565_gb300 import synth
     rng = np.random.default_rng(seed)
-    sides = (np.exp(rng.uniform(math.log(64), math.log(2048), size=(pool_n, 2))) // 8 * 8).astype(int)
-    pool = [binding.to_device(synth.make_image(int(x), int(y), seed + i), torch)
-            for i, (x, y) in enumerate(sides)]
+    sides = (np.exp(rng.uniform(math.log(64), math.log(2048), size=(n_img, 2))) // 8 * 8).astype(int)
     params = binding.filter_defaults(epf=1, gab=1)
     jobs = []
-    for i, k in enumerate(rng.integers(0, pool_n, n_img)):
-        img = pool[k]
+    for i, (x, y) in enumerate(sides):
+        img = binding.to_device(synth.make_image(int(x), int(y), seed + i), torch)
         if i % 2 == 0:
             dt, tdt = binding.OUT_U8_SRGB, torch.uint8
         else:

@@ -44,7 +44,8 @@ struct jxl_recon_batch {
   int* d_ritem = nullptr;          // per transform work item: (image, cell in it)
   int rtotal = 0;
   FilterArgs* d_eargs = nullptr;   // J.2 of the images with the EPF
-  unsigned* d_counts = nullptr;    // their listed-block counts (zeroed per launch)
+  unsigned* d_counts = nullptr;    // their listed-block counts, then the J.2 group counter
+                                   // (ne + 1 words, zeroed per launch)
   int ne = 0, etotal = 0;
   bool clamp = false;
   FilterArgs* d_fargs = nullptr;   // Gaborish / colour of every filtered image
@@ -73,9 +74,11 @@ jxlr_status bfail(jxlr_status s, const std::string& m) {
 }
 
 void enqueue(const jxl_recon_batch* b, const int* grid, cudaStream_t s) {
-  if (b->ne) cudaMemsetAsync(b->d_counts, 0, sizeof(unsigned) * b->ne, s);
+  if (b->ne) cudaMemsetAsync(b->d_counts, 0, sizeof(unsigned) * (b->ne + 1), s);
   if (b->rtotal) launch_recon_batch(b->d_rargs, b->d_ritem, b->rtotal, grid[0], s);
-  if (b->ne) launch_epf_work_batch(b->d_eargs, b->d_counts, b->ne, b->clamp, grid[1], s);
+  if (b->ne)
+    launch_epf_work_batch(b->d_eargs, b->d_counts, b->ne, b->clamp, grid[1], b->d_counts + b->ne,
+                          s);
   if (b->ftotal) {
     if (b->use_tma)
       launch_filter_batch_tma(b->d_fargs, b->d_fprefix, b->d_maps, b->nf, b->ftotal, grid[2],
@@ -138,10 +141,11 @@ void tuned_store(const Key& k, const Choice& c) {
 // last transform run left.
 void launch_kind(jxl_recon_batch* b, int k, int g, bool tma) {
   if (k == 0) {
-    if (b->ne) cudaMemsetAsync(b->d_counts, 0, sizeof(unsigned) * b->ne, b->cap);
+    if (b->ne) cudaMemsetAsync(b->d_counts, 0, sizeof(unsigned) * (b->ne + 1), b->cap);
     launch_recon_batch(b->d_rargs, b->d_ritem, b->rtotal, g, b->cap);
   } else if (k == 1) {
-    launch_epf_work_batch(b->d_eargs, b->d_counts, b->ne, b->clamp, g, b->cap);
+    cudaMemsetAsync(b->d_counts + b->ne, 0, sizeof(unsigned), b->cap);
+    launch_epf_work_batch(b->d_eargs, b->d_counts, b->ne, b->clamp, g, b->d_counts + b->ne, b->cap);
   } else if (tma) {
     launch_filter_batch_tma(b->d_fargs, b->d_fprefix, b->d_maps, b->nf, b->ftotal, g, b->d_err,
                             b->cap);
@@ -356,7 +360,7 @@ extern "C" jxlr_status jxl_recon_batch_create(jxl_recon_ctx* ctx, const jxl_reco
       ritem[2 * static_cast<size_t>(w) + 1] = w - rpre[i];
     }
   const size_t o_r = take(sizeof(ReconArgs) * n), o_rp = take(sizeof(int) * ritem.size());
-  const size_t o_e = take(sizeof(FilterArgs) * ea.size()), o_ec = take(sizeof(unsigned) * ea.size());
+  const size_t o_e = take(sizeof(FilterArgs) * ea.size()), o_ec = take(sizeof(unsigned) * (ea.size() + 1));
   const size_t o_f = take(sizeof(FilterArgs) * fa.size()), o_fp = take(sizeof(int) * fpre.size());
   const size_t o_st = take(sizeof(unsigned) * 4 * n);
   // one tensor map per filtered image when every one of them allows TMA

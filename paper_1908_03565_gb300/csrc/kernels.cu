@@ -2680,42 +2680,58 @@ __global__ void __launch_bounds__(32, 20) k_epf_work(const __grid_constant__ Fil
   epf_work_groups<kClamp>(a, list, static_cast<int>(*count), blockIdx.x, gridDim.x, next);
 }
 
-// Multi-image form: the warps take the images' groups round robin, the first
-// group of each image going to the warp after the one that took the previous
-// image's last group.  counts[j] is image j's number of listed blocks
-// (args[j].epf_count points there); they are read 128 images at a time in one
-// coalesced load, and a warp reads an image's parameter block only when it
-// has a group in that image.
-constexpr int kEpfCountChunk = 128;
-
+// Multi-image form: the groups of 2 listed blocks of all images, image after
+// image, form one sequence that the warps claim from the counter *next (the
+// next claim issued before the current group's work, as in k_epf_work).  A
+// warp finds the image of its group g with a cursor over 32 images at a
+// time: lane l holds the group count of image c0 + l and the inclusive
+// prefix of the chunk, so the image is the first lane whose prefix exceeds
+// g; the claims of a warp only increase, so the cursor only moves forward
+// (each warp reads every image's count once).  counts[j] is image j's number
+// of listed blocks (args[j].epf_count points there).  The image's parameter
+// block is read where it is (warp-uniform loads through L1), so that the
+// shared memory of a warp is that of k_epf_work and as many warps fit.
 template <bool kClamp>
-__global__ void __launch_bounds__(32, 18) k_epf_work_batch(const FilterArgs* __restrict__ args,
+__global__ void __launch_bounds__(32, 20) k_epf_work_batch(const FilterArgs* __restrict__ args,
                                                            const unsigned* __restrict__ counts,
-                                                           int nimg) {
-  __shared__ FilterArgs sa;
-  __shared__ unsigned scount[kEpfCountChunk];
-  static_assert(sizeof(FilterArgs) % 4 == 0, "word copy");
-  const int G = static_cast<int>(gridDim.x);
-  int rot = 0;
-  for (int c0 = 0; c0 < nimg; c0 += kEpfCountChunk) {
-    const int nc = min(kEpfCountChunk, nimg - c0);
-    __syncwarp();
-    for (int k = threadIdx.x; k < nc; k += 32) scount[k] = counts[c0 + k];
-    __syncwarp();
-    for (int jj = 0; jj < nc; ++jj) {
-      const int total = static_cast<int>(scount[jj]);
-      const int groups = (total + kLG - 1) / kLG;
-      int g0 = static_cast<int>(blockIdx.x) - rot;
-      if (g0 < 0) g0 += G;
-      rot = (rot + groups) % G;
-      if (g0 >= groups) continue;          // no group of this image for this warp
-      __syncwarp();
-      const int* src = reinterpret_cast<const int*>(&args[c0 + jj]);
-      for (int k = threadIdx.x; k < int(sizeof(FilterArgs) / 4); k += 32)
-        reinterpret_cast<int*>(&sa)[k] = src[k];
-      __syncwarp();
-      epf_work_groups<kClamp>(sa, sa.epf_list, total, g0, G);
+                                                           int nimg, unsigned* next) {
+  const unsigned full = 0xFFFFFFFFu;
+  const int lane = threadIdx.x;
+  int c0 = 0;                 // first image of the cursor's chunk
+  long long base = 0;         // groups of the images before c0
+  int cnt = 0, pre = 0;       // lane: listed blocks of image c0 + lane; inclusive group prefix
+  auto load_chunk = [&]() {
+    const int im = c0 + lane;
+    cnt = im < nimg ? static_cast<int>(__ldg(counts + im)) : 0;
+    pre = (cnt + kLG - 1) / kLG;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const int v = __shfl_up_sync(full, pre, off);
+      if (lane >= off) pre += v;
     }
+  };
+  load_chunk();
+  unsigned v = 0;
+  if (lane == 0) v = atomicAdd(next, 1u);
+  long long g = __shfl_sync(full, v, 0);
+  for (;;) {
+    long long end = base + __shfl_sync(full, pre, 31);
+    while (g >= end && c0 + 32 < nimg) {
+      base = end;
+      c0 += 32;
+      load_chunk();
+      end = base + __shfl_sync(full, pre, 31);
+    }
+    if (g >= end) break;      // past the last group of the last image
+    const int j = __ffs(__ballot_sync(full, g < base + pre)) - 1;
+    const int total = __shfl_sync(full, cnt, j);
+    const int first = static_cast<int>(base) + __shfl_sync(full, pre, j) - (total + kLG - 1) / kLG;
+    unsigned claim = 0;
+    if (lane == 0) claim = atomicAdd(next, 1u);   // used after this group
+    // exactly the group g - first of image c0 + j
+    const FilterArgs& a = args[c0 + j];
+    epf_work_groups<kClamp>(a, a.epf_list, total, static_cast<int>(g) - first, total);
+    g = __shfl_sync(full, claim, 0);
   }
 }
 
@@ -2774,9 +2790,9 @@ void launch_filter_batch_tma(const FilterArgs* args, const int* prefix, const vo
 }
 
 void launch_epf_work_batch(const FilterArgs* args, const unsigned* counts, int nimg, bool clamp,
-                           int grid, cudaStream_t s) {
-  if (clamp) k_epf_work_batch<true><<<grid, 32, 0, s>>>(args, counts, nimg);
-  else k_epf_work_batch<false><<<grid, 32, 0, s>>>(args, counts, nimg);
+                           int grid, unsigned* next, cudaStream_t s) {
+  if (clamp) k_epf_work_batch<true><<<grid, 32, 0, s>>>(args, counts, nimg, next);
+  else k_epf_work_batch<false><<<grid, 32, 0, s>>>(args, counts, nimg, next);
 }
 
 // The kernels use static shared memory; ask for the largest carveout so the

@@ -157,8 +157,9 @@ void launch_filter_batch_tma(const FilterArgs* args, const int* prefix, const vo
 // J.2 of many images (args[i].epf_list / epf_count / epf_out set; the sigma
 // pass copied the unchanged blocks), persistent grid of one-warp CTAs;
 // counts[i] is image i's listed-block count (args[i].epf_count == counts + i).
+// next: a zeroed counter the warps claim the groups of all images from.
 void launch_epf_work_batch(const FilterArgs* args, const unsigned* counts, int nimg, bool clamp,
-                           int grid, cudaStream_t s);
+                           int grid, unsigned* next, cudaStream_t s);
 // Work items (32x32 tiles) of k_filter for a, and whether the EPF needs its
 // exact-clamp variant for a's parameters.
 int filter_tiles(const FilterArgs& a);
