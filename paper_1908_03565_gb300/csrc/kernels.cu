@@ -1458,22 +1458,17 @@ __global__ void __launch_bounds__(128, 7) k_recon_pf(const __grid_constant__ Rec
 // Multi-image form: work item w is cell item_cell[w].y (raster order) of
 // image item_cell[w].x, a table made at batch creation (one load per item);
 // CTAs stride over the items.
-__global__ void __launch_bounds__(128, 6) k_recon_batch(const ReconArgs* __restrict__ args,
+__global__ void __launch_bounds__(128, 7) k_recon_batch(const ReconArgs* __restrict__ args,
                                                      const int2* __restrict__ item_cell,
                                                      int total) {
-  __shared__ ReconArgs sa;
-  __shared__ int2 s_ic;
   for (int w = blockIdx.x; w < total; w += gridDim.x) {
-    __syncthreads();
-    if (threadIdx.x == 0) s_ic = __ldg(item_cell + w);   // (image, its cell index)
-    __syncthreads();
-    const int img = s_ic.x, local = s_ic.y;
-    static_assert(sizeof(ReconArgs) % 4 == 0, "word copy");
-    for (int k = threadIdx.x; k < int(sizeof(ReconArgs) / 4); k += blockDim.x)
-      reinterpret_cast<int*>(&sa)[k] = reinterpret_cast<const int*>(&args[img])[k];
-    __syncthreads();
-    const int cells_x = (sa.wp + 31) / 32;
-    recon_cell<false, false>(sa, local % cells_x, local / cells_x);
+    const int2 ic = __ldg(item_cell + w);   // (image, its cell index), warp-uniform
+    // the image's parameter block is read where it is (warp-uniform loads
+    // through L1): no copy to shared memory and no barrier before the cell
+    const ReconArgs& a = args[ic.x];
+    const int cells_x = (a.wp + 31) / 32;
+    recon_cell<false, false>(a, ic.y % cells_x, ic.y / cells_x);
+    __syncthreads();   // the next item's cell reuses the shared buffers
   }
 }
 
