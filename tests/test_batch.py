@@ -120,3 +120,68 @@ def test_batch_rejects_bad_map():
         with pytest.raises(B.JxlrError) as e:
             ctx.batch(jobs, autotune=False)
         assert e.value.status == B.JXLR_EINVAL
+
+
+def test_config3_batch_sample_against_oracle():
+    """The 512-image batch of the throughput measurement as it is timed (512
+    distinct images, sides log-uniform in [64, 2048] in multiples of 8, the
+    workload's statistics, EPF + Gaborish, u8 sRGB and f16 linear outputs
+    alternating, autotuned, one graph replay), checked against the oracle
+    from the coefficients on a seeded 1% sample of its images: the whole
+    image up to 320x320, else a 64x64 window at a seeded 64-aligned place
+    (its oracle from a crop with a 64-sample margin).  The decisions are
+    modelled on the XYB of the same image (the batch equals the per-image
+    path bit for bit)."""
+    import math
+    import torch
+    from oracle import recon as R
+    from paper_1908_03565_gb300 import binding as B
+    from test_gpu_parity import XYB, assert_from_scratch, crop_input, params_pair, run
+    n_img, seed = 512, 3000
+    rng = np.random.default_rng(seed)
+    sides = (np.exp(rng.uniform(math.log(64), math.log(2048), size=(n_img, 2))) // 8 * 8).astype(int)
+    imgs = [synth.make_image(int(x), int(y), seed + i) for i, (x, y) in enumerate(sides)]
+    p, lp = params_pair(B, epf=True, gab=True)
+    jobs = []
+    for i, img in enumerate(imgs):
+        dt, tdt = ((B.OUT_U8_SRGB, torch.uint8) if i % 2 == 0 else
+                   (B.OUT_F16_LINEAR, torch.float16))
+        out = torch.zeros((img['ysize'], img['xsize'], 3), dtype=tdt, device="cuda")
+        jobs.append((B.to_device(img, torch), lp, out, dt))
+    stream = torch.cuda.Stream()
+    with B.Context(max_slots=1, stream=stream.cuda_stream) as ctx:
+        b = ctx.batch(jobs, autotune=True)
+        b.launch(stream.cuda_stream)
+        stream.synchronize()
+        assert b.status() == 0
+        b.close()
+    pick = np.random.default_rng(31).choice(n_img, n_img // 100, replace=False)
+    tot = np.zeros(4, np.int64)
+    with B.Context(max_slots=1) as ctx:
+        for i in (int(k) for k in pick):
+            img, out = imgs[i], jobs[i][2].cpu().numpy()
+            xs, ys = img['xsize'], img['ysize']
+            if xs * ys <= 320 * 320:
+                x0 = y0 = 0
+                sub, region = img, None
+                w, h = xs, ys
+            else:
+                r = np.random.default_rng(i)
+                x0 = 64 * int(r.integers(0, max(1, (xs - 1) // 64)))
+                y0 = 64 * int(r.integers(0, max(1, (ys - 1) // 64)))
+                cx0, cy0 = max(0, x0 - 64), max(0, y0 - 64)
+                sub = crop_input(img, cx0, cy0, x0 + 128, y0 + 128)
+                w, h = min(64, xs - x0), min(64, ys - y0)
+                region = (x0 - cx0, y0 - cy0, x0 - cx0 + w, y0 - cy0 + h)
+            ref = R.reconstruct(sub, p)
+            gx = run(B, ctx, sub, params_pair(B)[1], XYB).transpose(2, 0, 1)
+            o = out[y0:y0 + h, x0:x0 + w]
+            u8, f16 = (o, None) if jobs[i][3] == B.OUT_U8_SRGB else (None, o)
+            tot += assert_from_scratch(sub, ref, gx, None, u8, p,
+                                       f"batch image {i} ({xs}x{ys}) at ({x0}, {y0})",
+                                       region=region, relaxed_max=None, f16=f16)
+    amb, nd, live, n = (int(v) for v in tot)
+    print(f"batch sample: undetermined {amb} of {n // 3} pixels ({nd} decisions), relaxed "
+          f"samples not clamped away {live / n:.4f}")
+    assert live / n <= 0.03
+    assert amb / (n // 3) <= 1e-3 or nd <= 2

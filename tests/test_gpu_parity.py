@@ -348,7 +348,7 @@ def rgb_attainable(x, m, p, err_rel=ERR_REL):
 
 
 def assert_from_scratch(img, ref, gpu_xyb, f32, u8, p, name, region=None, relaxed_max=0.01,
-                        xyb_rel=LOCAL_REL, err_rel=ERR_REL):
+                        xyb_rel=LOCAL_REL, err_rel=ERR_REL, f16=None):
     """The library's output against the oracle's, both from the coefficients.
 
     ``ref``: oracle.recon.reconstruct of ``img``; ``gpu_xyb``: the library's
@@ -364,7 +364,10 @@ def assert_from_scratch(img, ref, gpu_xyb, f32, u8, p, name, region=None, relaxe
     excluded pixels must be rare (assert_rare).  Returns (excluded pixels,
     decisions taken differently, relaxed samples counted, samples).
     ``xyb_rel`` / ``err_rel``: the path's XYB bound and error model relative
-    to the local magnitude (wider for the tensor-core path)."""
+    to the local magnitude (wider for the tensor-core path).  ``f16``: a
+    float16 linear output checked instead of ``f32`` (the bound widened by
+    half an f16 ulp of the oracle's value); ``f32`` and ``f16`` None: no
+    linear output; ``u8`` None: no u8 output."""
     ys, xs = img['ysize'], img['xsize']
     if region is None:
         region = (0, 0, xs, ys)
@@ -380,15 +383,21 @@ def assert_from_scratch(img, ref, gpu_xyb, f32, u8, p, name, region=None, relaxe
     plain = ok & (rgb_attainable(rx, mag, p, err_rel) <= TOL01)
     relaxed = ok & ~plain
     want01 = ref['rgb01'][y0:y1, x0:x1]
-    err = np.abs(np.clip(f32, 0, 1) - np.clip(want01, 0, 1))
     bound = np.where(plain, TOL01, tol)
+    if f32 is None and f16 is not None:   # float16 output: its rounding on top (half an ulp)
+        f32 = f16.astype(np.float64)
+        w16 = np.abs(np.clip(want01, 0, 1)).astype(np.float16)
+        bound = bound + 0.5 * np.spacing(w16).astype(np.float64)
+    err = (np.zeros(want01.shape) if f32 is None else
+           np.abs(np.clip(f32, 0, 1) - np.clip(want01, 0, 1)))
     bad = (err > bound) & ok
     if bad.any():
         i = np.unravel_index(np.where(bad, err - bound, -1).argmax(), err.shape)
         raise AssertionError(f"{name}: {bad.sum()} RGB samples out of bound ({(bad & plain).sum()} "
                              f"plain); worst at {i}: err {err[i]:.3g} bound {bound[i]:.3g}")
     live = relaxed & (want01 >= -tol) & (want01 <= 1 + tol)
-    d = np.abs(u8.astype(np.int64) - R.srgb_u8(want01).astype(np.int64))
+    d = (np.zeros(want01.shape, np.int64) if u8 is None else
+         np.abs(u8.astype(np.int64) - R.srgb_u8(want01).astype(np.int64)))
     print(f"{name}: undetermined {amb.mean():.2e} of pixels ({nd} decisions); RGB samples held "
           f"to 1e-4: {plain.mean():.4f} (max err {err[plain].max():.2e}); to the relaxed bound and "
           f"not clamped away: {live.mean():.4f} (max err "
