@@ -1823,6 +1823,21 @@ constexpr int kET = 30;                  // output tile
 constexpr int kER = 32;                  // EPF region: tile plus a 1-sample ring
 constexpr int kHR = 34;                  // rows of horizontal sums
 constexpr int kWW = 42, kWH = 40;        // sample / guide window, origin (x0-5, y0-5)
+// The 8 horizontal 4-sums of 11 per-sample SADs d (each at most 3 x 255),
+// two per word: column 2 m in the low and 2 m + 1 in the high 16 bits.  e[i]
+// packs d[i] and d[i + 1]; the packed sum of 4 consecutive e is a pair of
+// 4-sums (each below 2^12, so no half carries into the other), with short
+// dependency chains instead of one sliding sum.
+__device__ __forceinline__ uint4 hsum4_packed(const uint32_t (&d)[11]) {
+  uint32_t e[10];
+#pragma unroll
+  for (int i = 0; i < 10; ++i) e[i] = d[i] + (d[i + 1] << 16);
+  uint32_t h[4];
+#pragma unroll
+  for (int m = 0; m < 4; ++m) h[m] = (e[2 * m] + e[2 * m + 1]) + (e[2 * m + 2] + e[2 * m + 3]);
+  return make_uint4(h[0], h[1], h[2], h[3]);
+}
+
 constexpr int kGS = 49;                  // guide row stride (words), = 17 mod 32: the
                                          // 8 rows x 4 runs a warp reads hit 32 banks
 
@@ -1915,14 +1930,8 @@ __device__ __forceinline__ void epf_tile(const FilterArgs& a, int tbx, int tby) 
       const uint32_t* nb = &G[hy + oi][k8 + 3 + ox];
       uint32_t d[11];
 #pragma unroll
-      for (int j = 0; j < 11; ++j) d[j] = __dp4a(__vabsdiffu4(own[j], nb[j]), 0x01010101u, 0u);
-      uint32_t h[8];
-      h[0] = d[0] + d[1] + d[2] + d[3];
-#pragma unroll
-      for (int i = 1; i < 8; ++i) h[i] = h[i - 1] + d[i + 3] - d[i - 1];
-      *reinterpret_cast<uint4*>(&Hb[oi][hy][k8]) =
-          make_uint4(h[0] | (h[1] << 16), h[2] | (h[3] << 16), h[4] | (h[5] << 16),
-                     h[6] | (h[7] << 16));
+      for (int j = 0; j < 11; ++j) d[j] = __vsadu4(own[j], nb[j]);
+      *reinterpret_cast<uint4*>(&Hb[oi][hy][k8]) = hsum4_packed(d);
     }
     // rows 32 and 33 of the sums: 8 runs x 7 offsets spread over threads 72..127
     if (tid >= 72) {
@@ -1932,14 +1941,8 @@ __device__ __forceinline__ void epf_tile(const FilterArgs& a, int tbx, int tby) 
       const uint32_t* nb = &G[hy2 + oi][kk + 3 + ox];
       uint32_t d[11];
 #pragma unroll
-      for (int j = 0; j < 11; ++j) d[j] = __dp4a(__vabsdiffu4(ow[j], nb[j]), 0x01010101u, 0u);
-      uint32_t h[8];
-      h[0] = d[0] + d[1] + d[2] + d[3];
-#pragma unroll
-      for (int i = 1; i < 8; ++i) h[i] = h[i - 1] + d[i + 3] - d[i - 1];
-      *reinterpret_cast<uint4*>(&Hb[oi][hy2][kk]) =
-          make_uint4(h[0] | (h[1] << 16), h[2] | (h[3] << 16), h[4] | (h[5] << 16),
-                     h[6] | (h[7] << 16));
+      for (int j = 0; j < 11; ++j) d[j] = __vsadu4(ow[j], nb[j]);
+      *reinterpret_cast<uint4*>(&Hb[oi][hy2][kk]) = hsum4_packed(d);
     }
     __syncthreads();
 
@@ -2559,13 +2562,7 @@ __device__ __forceinline__ void epf_work_groups(const FilterArgs& a, const int* 
             uint32_t d[11];   // sum over the 3 channel bytes of |own - neighbour|
 #pragma unroll
             for (int i = 0; i < 11; ++i) d[i] = __vsadu4(own[i], nbp[i]);
-            uint32_t h[8];
-            h[0] = d[0] + d[1] + d[2] + d[3];
-#pragma unroll
-            for (int i = 1; i < 8; ++i) h[i] = h[i - 1] + d[i + 3] - d[i - 1];
-            *reinterpret_cast<uint4*>(&Hb[k1][oi][j1][0]) =
-                make_uint4(h[0] | (h[1] << 16), h[2] | (h[3] << 16), h[4] | (h[5] << 16),
-                           h[6] | (h[7] << 16));
+            *reinterpret_cast<uint4*>(&Hb[k1][oi][j1][0]) = hsum4_packed(d);
           }
         }
       }
