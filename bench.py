@@ -135,7 +135,7 @@ def clocks_stop(p):
 
 
 def serve_leg(binding, torch, n_req, loads, pool_n=48, seed=4000, slots=8,
-              out_budget=48 << 30):
+              out_budget=48 << 30, reps=3):
     """Serving: a pool of images with sides log-uniform in [32, 8192] (the
     main workload's mixed-varblock statistics, EPF + Gaborish, u8 sRGB out)
     resident on the device, requests drawn from it, Poisson arrivals at a
@@ -146,7 +146,10 @@ def serve_leg(binding, torch, n_req, loads, pool_n=48, seed=4000, slots=8,
     batching) against the plain path (one request at a time), both under a
     40 GB HBM cap.  Every request writes its own output buffer (while their
     total fits in out_budget; beyond it a buffer is reused only by requests
-    at least that many apart in the schedule)."""
+    at least that many apart in the schedule).  Each load's schedule is
+    replayed `reps` times through each path, alternating continuous and
+    plain; p50 / p99 are the medians over the repetitions (each one's p99 is
+    reported too), so that slow drift of the device affects both alike."""
     import math
     from paper_1908_03565_gb300 import synth
     rng = np.random.default_rng(seed)
@@ -175,7 +178,8 @@ def serve_leg(binding, torch, n_req, loads, pool_n=48, seed=4000, slots=8,
                      binding.OUT_U8_SRGB))
     px = sum(pool[k]['xsize'] * pool[k]['ysize'] for k in idx)
     cap = 40 << 30
-    res = {"requests": n_req, "pool": pool_n, "mean_mpx": round(px / n_req / 1e6, 3),
+    res = {"requests": n_req, "reps_per_load": reps, "pool": pool_n,
+           "mean_mpx": round(px / n_req / 1e6, 3),
            "slots": slots, "hbm_cap_gb": 40, "output": "u8 sRGB",
            "distinct_outputs": distinct}
     with binding.Context(max_slots=slots, hbm_cap_bytes=cap) as cont, \
@@ -198,13 +202,20 @@ def serve_leg(binding, torch, n_req, loads, pool_n=48, seed=4000, slots=8,
             arr = np.cumsum(rng.exponential(1.0 / (load * cap_rps), n_req))
             arr -= arr[0]
             row = {"load": load}
-            for name, c in (("continuous", cont), ("plain", plain)):
-                lat, st = c.serve(jobs, arr)
-                row[name] = {"p50_ms": round(float(np.percentile(lat, 50)), 3),
-                             "p99_ms": round(float(np.percentile(lat, 99)), 3),
-                             "mpx_s": round(px / st["makespan_s"] / 1e6, 1),
-                             "max_in_flight": st["max_in_flight"],
-                             "bypassed": st["bypassed"]}
+            runs = {"continuous": [], "plain": []}
+            for _ in range(reps):
+                for name, c in (("continuous", cont), ("plain", plain)):
+                    lat, st = c.serve(jobs, arr)
+                    runs[name].append((float(np.percentile(lat, 50)), float(np.percentile(lat, 99)),
+                                       px / st["makespan_s"] / 1e6, st["max_in_flight"],
+                                       st["bypassed"]))
+            for name, rr in runs.items():
+                row[name] = {"p50_ms": round(float(np.median([r[0] for r in rr])), 3),
+                             "p99_ms": round(float(np.median([r[1] for r in rr])), 3),
+                             "p99_ms_reps": [round(r[1], 3) for r in rr],
+                             "mpx_s": round(float(np.median([r[2] for r in rr])), 1),
+                             "max_in_flight": max(r[3] for r in rr),
+                             "bypassed": int(np.median([r[4] for r in rr]))}
             row["p99_continuous_le_plain"] = row["continuous"]["p99_ms"] <= row["plain"]["p99_ms"]
             res["loads"].append(row)
     return res
@@ -675,6 +686,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=2000,
                     help="requests per serving run (0 = skip; 20000 = the full workload)")
+    ap.add_argument("--serve-reps", type=int, default=3,
+                    help="replays of each load's schedule per path, alternating (medians reported)")
     ap.add_argument("--precision-steps", type=int, default=20,
                     help="timed steps of the FP32 vs tensor-core comparison (0 = skip)")
     ap.add_argument("--batch-images", type=int, default=512,
@@ -861,7 +874,7 @@ def main():
     served = None
     if rank == 0 and args.serve_requests > 0:
         served = serve_leg(binding, torch, args.serve_requests,
-                           [float(v) for v in args.serve_loads.split(",")])
+                           [float(v) for v in args.serve_loads.split(",")], reps=args.serve_reps)
 
     if rank == 0:
         cb = None
