@@ -185,3 +185,47 @@ def test_config3_batch_sample_against_oracle():
           f"samples not clamped away {live / n:.4f}")
     assert live / n <= 0.03
     assert amb / (n // 3) <= 1e-3 or nd <= 2
+
+
+@pytest.mark.parametrize("all_flat", [False, True])
+def test_batch_j2_claims_span_images(all_flat):
+    """The J.2 kernel of a batch claims the groups of all images from one
+    counter and finds each group's image with a cursor over 32 images at a
+    time: 70 images with the EPF (three chunks of the cursor), among them
+    images with no block to filter (no AC coefficients, so every block's
+    range is 0 and sigma < 16: DCT8 blocks with only their DC) next to
+    images of the mixed workload; with all_flat, no image has any.  Every
+    image equals its per-image result."""
+    import torch
+    from paper_1908_03565_gb300 import binding as B
+    rng = np.random.default_rng(7400)
+    jobs = []
+    for i in range(70):
+        xs, ys = (int(v) for v in np.exp(rng.uniform(np.log(8), np.log(300), 2)))
+        flat = all_flat or i % 3 == 0
+        img = B.to_device(synth.make_image(xs, ys, 7400 + i, y_dc_offset_q=200, ac=not flat,
+                                           mix='dct8' if flat else 'mixed'), torch)
+        dtype = (B.OUT_U8_SRGB, B.OUT_F32_LINEAR)[i % 2]
+        params = B.filter_defaults(epf=1, gab=int(i % 4 != 1))
+        shape, npd = B.out_shape(img, dtype)
+        tdt = {np.float32: torch.float32, np.uint8: torch.uint8}[npd]
+        jobs.append((img, params, torch.zeros(shape, dtype=tdt, device="cuda"), dtype))
+    with B.Context(max_slots=1, timing=True) as ctx:
+        want, listed = [], 0
+        for img, params, out, dtype in jobs:
+            t = ctx.submit(img, params, out, dtype, on_device=True)
+            ctx.poll(t)
+            listed += ctx.epf_stats(t)[1]
+            want.append(out.cpu().numpy().copy())
+            out.zero_()
+        assert (listed == 0) == all_flat
+        b = ctx.batch(jobs, autotune=False)
+        stream = torch.cuda.Stream()
+        for _ in range(2):
+            b.launch(stream.cuda_stream)
+            stream.synchronize()
+            for (img, params, out, dtype), w in zip(jobs, want):
+                np.testing.assert_array_equal(out.cpu().numpy(), w)
+                out.zero_()
+        assert b.status() == 0
+        b.close()
