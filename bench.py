@@ -48,6 +48,9 @@ GUIDE_OPS_PER_PX = 17
 # blocks): 99,106,048 + 23,310,848; scaled to a launch by its pixels.  Set to
 # None whenever the kernel changes until it is captured again.
 EPF_WORK_DRAM_BYTES_4096x2048 = 99106048 + 23310848
+# The same for one k_recon launch (4096x2048, EPF + Gaborish: coefficients
+# in, XYB and the copy of the blocks J.2 leaves unchanged out).
+RECON_DRAM_BYTES_4096x2048 = 51271680 + 119876096
 CPU_SAMPLE = 1024         # oracle sample on one core: one 1024x1024 image, same statistics
 CPU_SAMPLE_ALL = 2048     # oracle sample on every host core: one 2048x2048 image
 
@@ -796,7 +799,9 @@ def main():
                 "filtered_frac": round(epf_blocks / nblk, 4)}
     roof_recon = {"kernel": "k_recon (dequantisation, CfL, LLF, transforms, sigma)",
                   "bound": "hbm", "achieved": round(recon_gbs, 1), "peak": hbm_peak,
-                  "unit": "GB/s", "frac": round(recon_gbs / hbm_peak, 4), "traffic": None,
+                  "unit": "GB/s", "frac": round(recon_gbs / hbm_peak, 4),
+                  "traffic": (None if RECON_DRAM_BYTES_4096x2048 is None else
+                              int(round(RECON_DRAM_BYTES_4096x2048 * px / (4096 * 2048)))),
                   "peak_source": f"{peak_kind} copy bandwidth",
                   "ms_per_launch": round(recon_ms, 4)}
     roof, roof_other = (roof_epf, roof_recon) if epf_ms >= recon_ms else (roof_recon, roof_epf)
