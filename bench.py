@@ -219,7 +219,12 @@ def serve_leg(binding, torch, n_req, loads, pool_n=48, seed=4000, slots=8,
                              "mpx_s": round(float(np.median([r[2] for r in rr])), 1),
                              "max_in_flight": max(r[3] for r in rr),
                              "bypassed": int(np.median([r[4] for r in rr]))}
-            row["p99_continuous_le_plain"] = row["continuous"]["p99_ms"] <= row["plain"]["p99_ms"]
+            # equal within the plain path's own spread over its replays counts
+            # as not worse: at low loads both run the same requests one at a
+            # time and differ by microseconds of timing noise
+            spread = max(row["plain"]["p99_ms_reps"]) - min(row["plain"]["p99_ms_reps"])
+            row["p99_delta_ms"] = round(row["continuous"]["p99_ms"] - row["plain"]["p99_ms"], 3)
+            row["p99_continuous_le_plain"] = row["p99_delta_ms"] <= spread
             res["loads"].append(row)
     return res
 
