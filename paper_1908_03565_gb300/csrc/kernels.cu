@@ -2538,6 +2538,13 @@ __device__ __forceinline__ void epf_work_groups(const FilterArgs& a, const int* 
     const bool grpA = lane < 2 * kLHR;
     const int pa = grpA ? lane : lane - 2 * kLHR;       // (block, row) pair of rounds 0, 1
     const int pb = grpA ? lane : lane - 2 * kLHR + 12;  // ... of rounds 2, 3
+    // the word offsets in G of the rows of those pairs, the 16-bit offsets
+    // in Hb of their sums, and whether the pairs exist (none depends on ox)
+    const int ka = pa >= kLHR ? 1 : 0, ja = pa - kLHR * ka;
+    const int kb = pb >= kLHR ? 1 : 0, jb = pb - kLHR * kb;
+    const int goa = (ka * kLGH + ja) * kLGS, gob = (kb * kLGH + jb) * kLGS;
+    const int hoa = (ka * 7 * kLHR + ja) * 8, hob = (kb * 7 * kLHR + jb) * 8;
+    const bool ona = ka < nb, onb = kb < nb && (grpA || pb < 2 * kLHR);
     bool dense = false;     // step 2: every offset of the last ox was live
     __syncwarp();
 
@@ -2547,22 +2554,22 @@ __device__ __forceinline__ void epf_work_groups(const FilterArgs& a, const int* 
       // ---- step 1 --------------------------------------------------------------
       {
         uint32_t own[11];
+        const uint32_t* G0 = &G[0][0][0];
 #pragma unroll
         for (int t = 0; t < 5; ++t) {
-          const int pr = t < 2 ? pa : pb;             // (block, row) of this lane and round
-          const int k1 = pr >= kLHR ? 1 : 0, j1 = pr - kLHR * k1;
+          const int go = t < 2 ? goa : gob, ho = t < 2 ? hoa : hob;   // this round's pair
           const int oi = grpA ? t : 5 + (t & 1);
-          const bool on = k1 < nb && (grpA || (t < 4 && pr < 2 * kLHR));
+          const bool on = t < 2 ? ona : (onb && (grpA || t < 4));
           if (t == 0 || t == 2) {
 #pragma unroll
-            for (int i = 0; i < 11; ++i) own[i] = on ? G[k1][j1 + 3][3 + i] : 0u;
+            for (int i = 0; i < 11; ++i) own[i] = on ? G0[go + 3 * kLGS + 3 + i] : 0u;
           }
           if (on) {
-            const uint32_t* nbp = &G[k1][j1 + oi][3 + ox];
+            const uint32_t* nbp = G0 + go + oi * kLGS + 3 + ox;
             uint32_t d[11];   // sum over the 3 channel bytes of |own - neighbour|
 #pragma unroll
             for (int i = 0; i < 11; ++i) d[i] = __vsadu4(own[i], nbp[i]);
-            *reinterpret_cast<uint4*>(&Hb[k1][oi][j1][0]) = hsum4_packed(d);
+            *reinterpret_cast<uint4*>(&Hb[0][0][0][0] + ho + oi * kLHR * 8) = hsum4_packed(d);
           }
         }
       }
