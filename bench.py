@@ -45,9 +45,9 @@ EPF_OPS_PER_FILTERED_PX = 56 * 8 + 4 + 4
 GUIDE_OPS_PER_PX = 17
 # DRAM bytes (read + write) of one k_epf_work launch, from an ncu capture of
 # the current kernel on the same statistics at 4096x2048 (50,730 listed
-# blocks): 99,106,048 + 23,310,848; scaled to a launch by its pixels.  Set to
+# blocks): 99,106,048 + 23,353,856; scaled to a launch by its pixels.  Set to
 # None whenever the kernel changes until it is captured again.
-EPF_WORK_DRAM_BYTES_4096x2048 = 99106048 + 23310848
+EPF_WORK_DRAM_BYTES_4096x2048 = 99106048 + 23353856
 # The same for one k_recon launch (4096x2048, EPF + Gaborish: coefficients
 # in, XYB and the copy of the blocks J.2 leaves unchanged out).
 RECON_DRAM_BYTES_4096x2048 = 51271680 + 119876096
