@@ -342,7 +342,8 @@ jxlr_status jxl_recon_serve(jxl_recon_ctx* ctx, const jxl_recon_request* reqs, s
  * images): many uneven images reconstructed by one launch per kernel kind,
  * captured once in a CUDA graph and replayed by jxl_recon_batch_launch().
  * Every request must be device-resident (inputs and output) with the
- * default dequantisation matrices; the batch owns the scratch of all its
+ * default dequantisation matrices, and the context must have been created
+ * with JXLR_PREC_FP32 (JXLR_EINVAL otherwise); the batch owns the scratch of all its
  * images (XYB, sigma, and with the EPF its output and block list;
  * allocated at creation).  Maps are validated at creation (JXLR_EINVAL).
  * With JXLR_BATCH_AUTOTUNE the grids of the three kernel kinds (transform,

@@ -117,6 +117,7 @@ int ctx_idle_slots(jxl_recon_ctx* c) {
   return n;
 }
 int ctx_device(const jxl_recon_ctx* c) { return c->device; }
+int ctx_precision(const jxl_recon_ctx* c) { return c->precision; }
 void ctx_count_launches(jxl_recon_ctx* c, int n) { c->launches += n; }
 }  // namespace jxlr
 

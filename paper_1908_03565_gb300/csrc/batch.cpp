@@ -245,6 +245,9 @@ extern "C" jxlr_status jxl_recon_batch_create(jxl_recon_ctx* ctx, const jxl_reco
                                               size_t n, int flags, jxl_recon_batch** out) {
   if (!ctx || !reqs || !out || n == 0 || n > (1u << 20))
     return bfail(JXLR_EINVAL, "batch_create: bad arguments");
+  if (ctx_precision(ctx) != JXLR_PREC_FP32)
+    return bfail(JXLR_EINVAL, "batch_create: batches run the FP32 path only (a context created "
+                              "with JXLR_PREC_FP32)");
   const int dev = ctx_device(ctx);
   if (cudaSetDevice(dev) != cudaSuccess) return bfail(JXLR_ECUDA, "batch_create: set device");
   std::vector<ReconArgs> ra(n);

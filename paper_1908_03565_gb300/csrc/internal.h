@@ -96,6 +96,7 @@ FilterArgs filter_args(const jxl_recon_filter_params& p);
 // Context internals used by the batch path (api.cpp).
 const float* ctx_default_dequant(const jxl_recon_ctx* c);
 int ctx_device(const jxl_recon_ctx* c);
+int ctx_precision(const jxl_recon_ctx* c);   // a jxlr_precision
 int ctx_idle_slots(jxl_recon_ctx* c);   // slots without a request in flight
 void ctx_count_launches(jxl_recon_ctx* c, int n);
 

@@ -229,3 +229,16 @@ def test_batch_j2_claims_span_images(all_flat):
                 out.zero_()
         assert b.status() == 0
         b.close()
+
+
+def test_batch_needs_an_fp32_context():
+    """Batches run the FP32 path: a context created for the tensor-core
+    precision mode refuses them (no silent change of precision)."""
+    import torch
+    from paper_1908_03565_gb300 import binding as B
+    jobs = _jobs(B, torch, n=2, seed=7500)
+    with B.Context(precision=B.PREC_TC_F16X3) as ctx:
+        with pytest.raises(B.JxlrError) as e:
+            ctx.batch(jobs, autotune=False)
+        assert e.value.status == B.JXLR_EINVAL
+        assert "FP32" in str(e.value)
