@@ -977,13 +977,13 @@ __device__ void cell_setup(CellState& cs, const uint8_t* __restrict__ vmap,
 // ---------------------------------------------------------------------------
 // Tensor-core separable pass (tcgen05, cta_group::1, kind::f16)
 //
-// One pass of one varblock is D[m][n] = sum_k A[m][k] B[n][k] with M = 128
-// rows (3 channels x H rows for the row pass, 3 x W columns for the column
-// pass; unused rows zero), K = N = the transform size (8 is padded to 16)
-// and B the unscaled cosine basis.  Each row of A is scaled by a power of two
-// so its largest entry lies in [2^13, 2^14), split into FP16 hi + lo, and
-// D = A_hi B_hi + A_hi B_lo + A_lo B_hi accumulates in FP32 in tensor memory
-// (128 lanes x 32 columns).  Operands use the canonical K-major layout
+// A pass is D[m][n] = sum_k A[m][k] B[n][k] over tiles of M = 128 rows (the
+// rows, or columns, of the three channels of the cell's varblocks of one
+// transform size; unused rows zero), K = N = the transform size (8 is padded
+// to 16) and B the unscaled cosine basis.  Each row of A is scaled by a power
+// of two so its largest entry lies in [2^13, 2^14), split into FP16 hi + lo,
+// and D = A_hi B_hi + A_hi B_lo + A_lo B_hi accumulates in FP32 in tensor
+// memory (128 lanes x 64 columns: up to two tiles, 32 columns apart).  Operands use the canonical K-major layout
 // without swizzle: element (r, k) at (r/8)*SBO + (k/8)*128 + (r%8)*16 +
 // (k%8)*2 bytes, SBO = (Kp/8)*128.
 // ---------------------------------------------------------------------------
@@ -1015,116 +1015,173 @@ __device__ __forceinline__ void tc_fence_after() {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
 
-// src / dst: element (row m = c*G + i, index k) at base + c*cstr + i*rstr + k*estr.
-__device__ void tc_pass(TcShared& ts, uint32_t& phase, unsigned* err, int nrows, int G, int K,
-                        const unsigned char* __restrict__ basis, const float* src, float* dst,
-                        int cstr, int rstr, int estr) {
+
+// The tensor-core passes of all the cell's varblocks larger than 8x8 at
+// once: their rows (kCol false: S -> T) or columns (kCol true: T -> S) of the
+// three channels, grouped by transform length K, fill 128-row tiles (row R
+// of a length's group: varblock by the running sum of 3 G over the
+// varblocks of that length in list order, then channel R' / G, index
+// R' % G).  Up to two tiles of length 8 or 16, one of length 32 (a cell has
+// at most 96 rows of 32), are staged together into the operand buffers
+// (tile s at byte offset s x 128 x Kp x 2), multiplied into TMEM columns
+// 32 s .. 32 s + Kp - 1, committed and waited for once, read back and
+// unscaled: one MMA round trip per length and pass for most cells instead of
+// one per varblock and pass.  Each row is scaled, split and multiplied on
+// its own, so its results do not depend on the rows beside it in a tile.
+template <bool kCol>
+__device__ void tc_cell_pass(TcShared& ts, uint32_t& phase, unsigned* err, const CellState& cs,
+                             const unsigned char* __restrict__ tcb, float (*src)[kPR][kRS],
+                             float (*dst)[kPR][kRS]) {
   const int m = threadIdx.x;
-  const int Kp = K < 16 ? 16 : K;
-  const int sbo = (Kp / 8) * 128;
-  // ---- stage A (hi, lo) row m ----
-  {
-    float v[32];
-    float amax = 0.f;
-    const int c = m / G, i = m - (m / G) * G;
-#pragma unroll
-    for (int k = 0; k < 32; ++k) {
-      float x = 0.f;
-      if (m < nrows && k < K) x = src[c * cstr + i * rstr + k * estr];
-      v[k] = x;
-      amax = fmaxf(amax, fabsf(x));
+  const int estr = kCol ? kRS : 1;
+  for (int lk = 3; lk <= 5; ++lk) {
+    int total = 0;   // rows of length 2^lk (the same in every thread: cs is shared)
+    for (int vi = 0; vi < cs.nvb; ++vi) {
+      const CellVB& v = cs.vb[vi];
+      if (tc_shape(v.code) && (kCol ? v.lh : v.lw) == lk) total += 3 << (kCol ? v.lw : v.lh);
     }
-    int e = 0;
-    frexpf(amax, &e);
-    const float sc = amax > 0.f ? ldexpf(1.f, 14 - e) : 1.f;
+    if (total == 0) continue;
+    const int K = 1 << lk, Kp = K < 16 ? 16 : K;
+    const int per = Kp == 32 ? 1 : 2;             // tiles per round trip
+    const int tbytes = 128 * Kp * 2;              // one tile's hi (or lo) operand
+    const int sbo = (Kp / 8) * 128;
+    for (int r0 = 0; r0 < total; r0 += 128 * per) {
+      const int nt = min(per, (total - r0 + 127) / 128);
+      float inv[2] = {1.f, 1.f};
+      float* drow[2] = {nullptr, nullptr};
 #pragma unroll
-    for (int g = 0; g < 4; ++g) {
-      if (g * 8 >= Kp) break;
-      uint32_t hw[4], lw[4];
+      for (int st = 0; st < 2; ++st) {
+        if (st >= nt) break;
+        const int R = r0 + 128 * st + m;
+        const float* srow = nullptr;
+        if (R < total) {
+          int base = 0;
+          for (int vi = 0; vi < cs.nvb; ++vi) {
+            const CellVB& v = cs.vb[vi];
+            if (!tc_shape(v.code) || (kCol ? v.lh : v.lw) != lk) continue;
+            const int lg = kCol ? v.lw : v.lh;      // G = 2^lg rows (or columns) per channel
+            const int n = 3 << lg;
+            if (R < base + n) {
+              const int loc = R - base, c = loc >> lg, i = loc & ((1 << lg) - 1);
+              const int x0 = 8 * v.bx, y0 = 8 * v.by;
+              srow = kCol ? &src[c][y0][x0 + i] : &src[c][y0 + i][x0];
+              drow[st] = kCol ? &dst[c][y0][x0 + i] : &dst[c][y0 + i][x0];
+              break;
+            }
+            base += n;
+          }
+        }
+        // stage the row (zeros past the group's end), scaled by a power of
+        // two so that its largest entry lies in [2^13, 2^14), as hi + lo
+        float vv[32];
+        float amax = 0.f;
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const float x0 = v[g * 8 + 2 * j] * sc, x1 = v[g * 8 + 2 * j + 1] * sc;
-        const __half h0 = __float2half_rn(x0), h1 = __float2half_rn(x1);
-        const __half l0 = __float2half_rn(x0 - __half2float(h0));
-        const __half l1 = __float2half_rn(x1 - __half2float(h1));
-        hw[j] = static_cast<uint32_t>(__half_as_ushort(h0)) |
-                (static_cast<uint32_t>(__half_as_ushort(h1)) << 16);
-        lw[j] = static_cast<uint32_t>(__half_as_ushort(l0)) |
-                (static_cast<uint32_t>(__half_as_ushort(l1)) << 16);
-      }
-      const int off = (m >> 3) * sbo + g * 128 + (m & 7) * 16;
-      *reinterpret_cast<uint4*>(ts.a_hi + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-      *reinterpret_cast<uint4*>(ts.a_lo + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
-    }
-    // ---- stage B (hi, lo), already canonical in global memory ----
-    const int bbytes = Kp * Kp * 2;
-    for (int o = m * 16; o < bbytes; o += 128 * 16) {
-      *reinterpret_cast<uint4*>(ts.b_hi + o) = *reinterpret_cast<const uint4*>(basis + o);
-      *reinterpret_cast<uint4*>(ts.b_lo + o) = *reinterpret_cast<const uint4*>(basis + bbytes + o);
-    }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    if (m == 0) {
-      const uint32_t idesc = (1u << 4) | (static_cast<uint32_t>(Kp >> 3) << 17) |
-                             (static_cast<uint32_t>(128 >> 4) << 24);
-      const uint32_t ah = smem_addr(ts.a_hi), al = smem_addr(ts.a_lo);
-      const uint32_t bh = smem_addr(ts.b_hi), bl = smem_addr(ts.b_lo);
-      uint32_t acc = 0;
-      for (int ks = 0; ks < Kp / 16; ++ks) {
-        const uint32_t o = ks * 256;
-        const unsigned long long da[3] = {umma_desc(ah + o, sbo), umma_desc(ah + o, sbo),
-                                          umma_desc(al + o, sbo)};
-        const unsigned long long db[3] = {umma_desc(bh + o, sbo), umma_desc(bl + o, sbo),
-                                          umma_desc(bh + o, sbo)};
+        for (int k = 0; k < 32; ++k) {
+          const float x = (srow && k < K) ? srow[k * estr] : 0.f;
+          vv[k] = x;
+          amax = fmaxf(amax, fabsf(x));
+        }
+        int e = 0;
+        frexpf(amax, &e);
+        const float sc = amax > 0.f ? ldexpf(1.f, 14 - e) : 1.f;
+        inv[st] = amax > 0.f ? ldexpf(1.f, e - 14) : 1.f;
 #pragma unroll
-        for (int t = 0; t < 3; ++t) {
-          asm volatile(
-              "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-              "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
-              :: "r"(ts.tmem), "l"(da[t]), "l"(db[t]), "r"(idesc), "r"(acc));
-          acc = 1;
+        for (int g = 0; g < 4; ++g) {
+          if (g * 8 >= Kp) break;
+          uint32_t hw[4], lw[4];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const float x0 = vv[g * 8 + 2 * j] * sc, x1 = vv[g * 8 + 2 * j + 1] * sc;
+            const __half h0 = __float2half_rn(x0), h1 = __float2half_rn(x1);
+            const __half l0 = __float2half_rn(x0 - __half2float(h0));
+            const __half l1 = __float2half_rn(x1 - __half2float(h1));
+            hw[j] = static_cast<uint32_t>(__half_as_ushort(h0)) |
+                    (static_cast<uint32_t>(__half_as_ushort(h1)) << 16);
+            lw[j] = static_cast<uint32_t>(__half_as_ushort(l0)) |
+                    (static_cast<uint32_t>(__half_as_ushort(l1)) << 16);
+          }
+          const int off = st * tbytes + (m >> 3) * sbo + g * 128 + (m & 7) * 16;
+          *reinterpret_cast<uint4*>(ts.a_hi + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+          *reinterpret_cast<uint4*>(ts.a_lo + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
         }
       }
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                   :: "r"(smem_addr(&ts.mbar)) : "memory");
-    }
-    // bounded wait for the products
-    uint32_t done = 0;
-    for (int it = 0; it < (1 << 24) && !done; ++it) {
-      asm volatile("{\n.reg .pred q;\nmbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\n"
-                   "selp.u32 %0, 1, 0, q;\n}\n"
-                   : "=r"(done) : "r"(smem_addr(&ts.mbar)), "r"(phase) : "memory");
-    }
-    phase ^= 1u;
-    tc_fence_after();
-    if (!done) {
-      if (m == 0) atomicOr(err, 4u);
-    } else {
-      uint32_t r[32];
-      const uint32_t taddr = ts.tmem + (static_cast<uint32_t>(m & ~31) << 16);
-      asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,"
-          "%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
-            "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]),
-            "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]),
-            "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-            "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]),
-            "=r"(r[30]), "=r"(r[31])
-          : "r"(taddr));
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      const float inv = amax > 0.f ? ldexpf(1.f, e - 14) : 1.f;
-      if (m < nrows) {
-#pragma unroll
-        for (int n = 0; n < 32; ++n)
-          if (n < K) dst[c * cstr + i * rstr + n * estr] = __uint_as_float(r[n]) * inv;
+      // the basis (hi, lo) of this length, already canonical in global memory
+      const unsigned char* basis = tcb + 1024 * (lk - 3);
+      const int bbytes = Kp * Kp * 2;
+      for (int o = m * 16; o < bbytes; o += 128 * 16) {
+        *reinterpret_cast<uint4*>(ts.b_hi + o) = *reinterpret_cast<const uint4*>(basis + o);
+        *reinterpret_cast<uint4*>(ts.b_lo + o) = *reinterpret_cast<const uint4*>(basis + bbytes + o);
       }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      tc_fence_before();
+      __syncthreads();
+      tc_fence_after();
+      if (m == 0) {
+        const uint32_t idesc = (1u << 4) | (static_cast<uint32_t>(Kp >> 3) << 17) |
+                               (static_cast<uint32_t>(128 >> 4) << 24);
+        const uint32_t bh = smem_addr(ts.b_hi), bl = smem_addr(ts.b_lo);
+        for (int st = 0; st < nt; ++st) {
+          const uint32_t ah = smem_addr(ts.a_hi) + st * tbytes, al = smem_addr(ts.a_lo) + st * tbytes;
+          const uint32_t dt = ts.tmem + 32u * st;
+          uint32_t acc = 0;
+          for (int ks = 0; ks < Kp / 16; ++ks) {
+            const uint32_t o = ks * 256;
+            const unsigned long long da[3] = {umma_desc(ah + o, sbo), umma_desc(ah + o, sbo),
+                                              umma_desc(al + o, sbo)};
+            const unsigned long long db[3] = {umma_desc(bh + o, sbo), umma_desc(bl + o, sbo),
+                                              umma_desc(bh + o, sbo)};
+#pragma unroll
+            for (int t = 0; t < 3; ++t) {
+              asm volatile(
+                  "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                  "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+                  :: "r"(dt), "l"(da[t]), "l"(db[t]), "r"(idesc), "r"(acc));
+              acc = 1;
+            }
+          }
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                     :: "r"(smem_addr(&ts.mbar)) : "memory");
+      }
+      // bounded wait for the products
+      uint32_t done = 0;
+      for (int it = 0; it < (1 << 24) && !done; ++it) {
+        asm volatile("{\n.reg .pred q;\nmbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\n"
+                     "selp.u32 %0, 1, 0, q;\n}\n"
+                     : "=r"(done) : "r"(smem_addr(&ts.mbar)), "r"(phase) : "memory");
+      }
+      phase ^= 1u;
+      tc_fence_after();
+      if (!done) {
+        if (m == 0) atomicOr(err, 4u);
+      } else {
+#pragma unroll
+        for (int st = 0; st < 2; ++st) {
+          if (st >= nt) break;
+          uint32_t r[32];
+          const uint32_t taddr = ts.tmem + (static_cast<uint32_t>(m & ~31) << 16) + 32u * st;
+          asm volatile(
+              "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,"
+              "%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+              : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+                "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]),
+                "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]),
+                "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+                "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]),
+                "=r"(r[30]), "=r"(r[31])
+              : "r"(taddr));
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+          if (drow[st]) {
+#pragma unroll
+            for (int n = 0; n < 32; ++n)
+              if (n < K) drow[st][n * estr] = __uint_as_float(r[n]) * inv[st];
+          }
+        }
+      }
+      tc_fence_before();
+      __syncthreads();
     }
   }
-  tc_fence_before();
-  __syncthreads();
 }
 
 // One 32x32 cell (cell coordinates cxi, cyi) of image a; 128 threads.
@@ -1196,7 +1253,7 @@ __device__ __forceinline__ void recon_cell(const ReconArgs& a, int cxi, int cyi,
   if (kTC) {
     if (tid == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_addr(&ts.mbar)));
     if (tid < 32) {
-      asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 32;"
+      asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 64;"
                    :: "r"(smem_addr(&ts.tmem)));
       asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
@@ -1345,19 +1402,11 @@ __device__ __forceinline__ void recon_cell(const ReconArgs& a, int cxi, int cyi,
 
   // ---- tensor-core passes of the varblocks larger than 8x8 ----------------
   if (kTC) {
-    for (int vi = 0; vi < cs.nvb; ++vi) {
-      const CellVB v = cs.vb[vi];
-      if (!tc_shape(v.code)) continue;
-      const int W = 1 << v.lw, H = 1 << v.lh;
-      const int x0 = 8 * v.bx, y0 = 8 * v.by;
-      // rows: S -> T
-      // basis tables at byte offsets 0, 1024, 2048 for N = 8, 16, 32
-      tc_pass(ts, phase, a.err, 3 * H, H, W, a.tcb + 1024 * (v.lw - 3), &S[0][y0][x0],
-              &T[0][y0][x0], kPR * kRS, kRS, 1);
-      // columns: T -> S
-      tc_pass(ts, phase, a.err, 3 * W, W, H, a.tcb + 1024 * (v.lh - 3), &T[0][y0][x0],
-              &S[0][y0][x0], kPR * kRS, 1, kRS);
-    }
+    // all of them at once, grouped by transform length: rows S -> T, then
+    // columns T -> S (basis tables at byte offsets 0, 1024, 2048 for N = 8,
+    // 16, 32)
+    tc_cell_pass<false>(ts, phase, a.err, cs, a.tcb, S, T);
+    tc_cell_pass<true>(ts, phase, a.err, cs, a.tcb, T, S);
   }
 
   // ---- I.2.4 row pass ------------------------------------------------------
@@ -1422,7 +1471,7 @@ __device__ __forceinline__ void recon_cell(const ReconArgs& a, int cxi, int cyi,
     tc_fence_before();
     __syncthreads();
     if (tid < 32)
-      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;" :: "r"(ts.tmem));
+      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;" :: "r"(ts.tmem));
   }
   if (prefetch) {
     if (tid < 16) {
