@@ -1075,12 +1075,19 @@ __device__ void tc_cell_pass(TcShared& ts, uint32_t& phase, unsigned* err, const
         // two so that its largest entry lies in [2^13, 2^14), as hi + lo
         float vv[32];
         float amax = 0.f;
+        if (!kCol) {   // a row: 16-byte aligned (x0 a multiple of 8, rows of kRS floats)
 #pragma unroll
-        for (int k = 0; k < 32; ++k) {
-          const float x = (srow && k < K) ? srow[k * estr] : 0.f;
-          vv[k] = x;
-          amax = fmaxf(amax, fabsf(x));
+          for (int k = 0; k < 32; k += 4) {
+            float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (srow && k < K) q = *reinterpret_cast<const float4*>(srow + k);
+            vv[k] = q.x; vv[k + 1] = q.y; vv[k + 2] = q.z; vv[k + 3] = q.w;
+          }
+        } else {
+#pragma unroll
+          for (int k = 0; k < 32; ++k) vv[k] = (srow && k < K) ? srow[k * estr] : 0.f;
         }
+#pragma unroll
+        for (int k = 0; k < 32; ++k) amax = fmaxf(amax, fabsf(vv[k]));
         int e = 0;
         frexpf(amax, &e);
         const float sc = amax > 0.f ? ldexpf(1.f, 14 - e) : 1.f;
@@ -1172,9 +1179,18 @@ __device__ void tc_cell_pass(TcShared& ts, uint32_t& phase, unsigned* err, const
               : "r"(taddr));
           asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
           if (drow[st]) {
+            if (!kCol) {
 #pragma unroll
-            for (int n = 0; n < 32; ++n)
-              if (n < K) drow[st][n * estr] = __uint_as_float(r[n]) * inv[st];
+              for (int n = 0; n < 32; n += 4)
+                if (n < K)
+                  *reinterpret_cast<float4*>(drow[st] + n) =
+                      make_float4(__uint_as_float(r[n]) * inv[st], __uint_as_float(r[n + 1]) * inv[st],
+                                  __uint_as_float(r[n + 2]) * inv[st], __uint_as_float(r[n + 3]) * inv[st]);
+            } else {
+#pragma unroll
+              for (int n = 0; n < 32; ++n)
+                if (n < K) drow[st][n * estr] = __uint_as_float(r[n]) * inv[st];
+            }
           }
         }
       }
