@@ -304,6 +304,7 @@ def _crop(img, x0, y0, x1, y1):
     of its own (whole varblocks and CfL tiles)."""
     Wp, Hp = img['coeffs'].shape[2], img['coeffs'].shape[1]
     x1, y1 = min(x1, Wp), min(y1, Hp)
+    assert 0 <= x0 < min(x1, img['xsize']) and 0 <= y0 < min(y1, img['ysize']), "crop outside the image"
     return {'xsize': min(x1, img['xsize']) - x0, 'ysize': min(y1, img['ysize']) - y0,
             'coeffs': img['coeffs'][:, y0:y1, x0:x1], 'vmap': img['vmap'][y0 // 8:y1 // 8, x0 // 8:x1 // 8],
             'acmul': img['acmul'][y0 // 8:y1 // 8, x0 // 8:x1 // 8],
@@ -333,7 +334,10 @@ def precision_leg(binding, torch, steps):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     pp = R.Params(epf=True, gab=True)
     refs = []
-    for wx, wy in PREC_WINDOWS:
+    # the windows (placed for 4096^2) moved inside a smaller image, 64-aligned
+    wins = sorted({(min(wx, (XS - 64) // 64 * 64), min(wy, (YS - 64) // 64 * 64))
+                   for wx, wy in PREC_WINDOWS}) if XS >= 64 and YS >= 64 else []
+    for wx, wy in wins:
         cx0, cy0 = max(0, wx - 64), max(0, wy - 64)
         sub = _crop(img, cx0, cy0, wx + 128, wy + 128)
         ref = R.reconstruct(sub, pp)
@@ -384,8 +388,8 @@ def precision_leg(binding, torch, steps):
                      "rgb01_max_abs_err": e_all,
                      "rgb01_max_abs_err_where_local_abs_xyb_lt_4": e_plain,
                      "u8_within_1": n_ok / n8}
-    res["error_sample"] = ("ten 64x64 windows of the 4096x4096 image, EPF + Gaborish, vs the "
-                           "FP64 oracle on 64-aligned crops of its coefficients")
+    res["error_sample"] = (f"{len(wins)} 64x64 windows of the {XS}x{YS} image, EPF + Gaborish, "
+                           "vs the FP64 oracle on 64-aligned crops of its coefficients")
     return res
 
 
