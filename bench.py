@@ -222,7 +222,7 @@ def serve_leg(binding, torch, n_req, loads, pool_n=48, seed=4000, slots=8,
             # equal within the plain path's own spread over its replays counts
             # as not worse: at low loads both run the same requests one at a
             # time and differ by microseconds of timing noise
-            spread = max(row["plain"]["p99_ms_reps"]) - min(row["plain"]["p99_ms_reps"])
+            spread = round(max(row["plain"]["p99_ms_reps"]) - min(row["plain"]["p99_ms_reps"]), 3)
             row["p99_delta_ms"] = round(row["continuous"]["p99_ms"] - row["plain"]["p99_ms"], 3)
             row["p99_continuous_le_plain"] = row["p99_delta_ms"] <= spread
             res["loads"].append(row)
